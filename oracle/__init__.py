@@ -1,0 +1,292 @@
+"""Plain FP64 CPU oracle for the fluctuating D3Q19 lattice-Boltzmann update and
+the frictional point-particle coupling of Duenweg & Ladd (arXiv 0803.2826).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py`` may import this package.  It
+shares no code with the CUDA library in ``paper_0803_2826_gb300`` and imports
+nothing from it.
+
+The arithmetic lives in ``lb_oracle.c`` (plain C, IEEE double, no fast-math);
+this module compiles it with gcc on first use and wraps it with ctypes and
+numpy.  Population arrays have shape ``(19, nz, ny, nx)`` and hold raw n_i.
+
+Function -> passage it follows:
+  tables()        Sec. 3.3 (D3Q19 weights), Sec. 3.4 Table 1 and Eq. (weights_unweighted)
+  philox()        Philox4x32-10 of Salmon et al., SC'11 (noise source for Sec. 3.5)
+  equilibrium()   Sec. 3.3, Eq. (original_equil_distrib)
+  step()          Eq. (LBE) streaming; Sec. 3.4-3.5 MRT collision with noise,
+                  Eqs. (lco_update), (stochupdaterule1), (detailedbalance1);
+                  Sec. 3.7 forcing; Sec. 4.1 Eq. (MBB) with u_b = 0 for walls
+  moments()       Sec. 3.4 Eqs. (hmodes_beg)-(hmodes_end); Sec. 3.7 for j
+  modes()         Sec. 3.4 Eq. (forward)
+  md_forces()     Sec. 2.1 Eqs. (ulennardjones), (ufene)
+  couple()        Sec. 4.5 Eqs. (fdrag), (ftotal), (langevin_momentum_update);
+                  Sec. 4.6 Eqs. (ufluid_discrete), (Delta), (2point)
+  interpolate()   Sec. 4.6 Eq. (ufluid_discrete)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lb_oracle.c")
+_LIB = os.path.join(_HERE, "liblboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+Q = 19
+
+
+def build(force: bool = False) -> str:
+    """Compile lb_oracle.c into liblboracle.so next to it (gcc, -O2, OpenMP)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+           "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("walls", C.c_int), ("noise_rho0", C.c_int), ("pad_", C.c_int),
+        ("rho0", C.c_double), ("kT", C.c_double),
+        ("gamma_shear", C.c_double), ("gamma_bulk", C.c_double),
+        ("gamma_odd", C.c_double), ("gamma_even", C.c_double),
+        ("body_force", C.c_double * 3),
+        ("seed", C.c_uint64), ("replica", C.c_uint32), ("pad2_", C.c_uint32),
+    ]
+
+
+class MD(C.Structure):
+    _fields_ = [
+        ("n_chains", C.c_int), ("chain_len", C.c_int), ("use_wca", C.c_int),
+        ("pad_", C.c_int),
+        ("eps", C.c_double), ("sigma", C.c_double),
+        ("k_fene", C.c_double), ("r0", C.c_double),
+    ]
+
+
+class CoupleParams(C.Structure):
+    _fields_ = [
+        ("n_substeps", C.c_int), ("noise_kind", C.c_int),
+        ("dt", C.c_double), ("seed", C.c_uint64),
+        ("md_step0", C.c_uint32), ("pad_", C.c_uint32),
+    ]
+
+
+_D = C.POINTER(C.c_double)
+_U32 = C.POINTER(C.c_uint32)
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            lib.ora_tables.argtypes = [C.POINTER(C.c_int), _D, _D, _D, C.POINTER(C.c_int)]
+            lib.ora_philox4x32_10.argtypes = [_U32, _U32, _U32]
+            lib.ora_uniform.argtypes = [C.c_uint32]
+            lib.ora_uniform.restype = C.c_double
+            lib.ora_raw16.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                      C.c_uint32, C.c_int, _U32]
+            lib.ora_gaussians.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                          C.c_uint32, C.c_int, _D]
+            P = C.POINTER(Params)
+            lib.ora_equilibrium.argtypes = [P, _D, _D, _D]
+            lib.ora_step.argtypes = [P, _D, _D, _D, C.c_uint32]
+            lib.ora_moments.argtypes = [P, _D, _D, _D, _D, _D]
+            lib.ora_modes.argtypes = [P, _D, _D]
+            lib.ora_md_forces.argtypes = [P, C.POINTER(MD), C.c_int, _D, _D]
+            lib.ora_md_forces.restype = C.c_int
+            lib.ora_couple.argtypes = [P, _D, _D, C.c_int, _D, _D, _D, _D,
+                                       C.POINTER(MD), C.POINTER(CoupleParams), _D]
+            lib.ora_couple.restype = C.c_int
+            lib.ora_interpolate.argtypes = [P, _D, _D, C.c_int, _D, _D]
+            lib.ora_stencil.argtypes = [P, _D, C.POINTER(C.c_longlong), _D]
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_D)
+
+
+def make_params(shape, *, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0,
+                gamma_odd=0.0, gamma_even=0.0, body_force=(0.0, 0.0, 0.0), seed=0,
+                replica=0, walls=False, noise_rho0=False) -> Params:
+    """shape = (nx, ny, nz)."""
+    p = Params()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    p.walls = int(bool(walls))
+    p.noise_rho0 = int(bool(noise_rho0))
+    p.rho0 = rho0
+    p.kT = kT
+    p.gamma_shear, p.gamma_bulk = gamma_shear, gamma_bulk
+    p.gamma_odd, p.gamma_even = gamma_odd, gamma_even
+    for d in range(3):
+        p.body_force[d] = float(body_force[d])
+    p.seed = int(seed)
+    p.replica = int(replica)
+    return p
+
+
+def tables():
+    """(c[19,3] int, a[19], e[19,19] (row k), w[19], opp[19]) built from the paper."""
+    lib = _load()
+    c = np.zeros((Q, 3), dtype=np.int32)
+    a = np.zeros(Q)
+    e = np.zeros((Q, Q))
+    w = np.zeros(Q)
+    opp = np.zeros(Q, dtype=np.int32)
+    lib.ora_tables(c.ctypes.data_as(C.POINTER(C.c_int)), _dp(a), _dp(e), _dp(w),
+                   opp.ctypes.data_as(C.POINTER(C.c_int)))
+    return c.astype(np.int64), a, e, w, opp.astype(np.int64)
+
+
+def philox(ctr, key):
+    lib = _load()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xffffffff for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xffffffff for v in key])
+    o = (C.c_uint32 * 4)()
+    lib.ora_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def uniform(x: int) -> float:
+    return _load().ora_uniform(int(x) & 0xffffffff)
+
+
+def raw_words(seed, node, step, domain=0, replica=0, nblocks=4):
+    lib = _load()
+    o = (C.c_uint32 * 16)()
+    lib.ora_raw16(int(seed), int(node), int(step), int(domain), int(replica), int(nblocks), o)
+    return np.array([int(v) for v in o[:4 * nblocks]], dtype=np.uint32)
+
+
+def gaussians(seed, node, step, domain=0, replica=0, nblocks=4):
+    lib = _load()
+    g = np.zeros(16)
+    lib.ora_gaussians(int(seed), int(node), int(step), int(domain), int(replica),
+                      int(nblocks), _dp(g))
+    return g[:4 * nblocks]
+
+
+def _nodes(p: Params):
+    return p.nx * p.ny * p.nz
+
+
+def equilibrium(p: Params, rho=None, u=None):
+    """n^eq(rho, u) per node; rho shape (nz,ny,nx) or None (rho0); u (3,nz,ny,nx) or None."""
+    lib = _load()
+    pops = np.zeros((Q, p.nz, p.ny, p.nx))
+    r = None if rho is None else np.ascontiguousarray(rho, dtype=np.float64)
+    uu = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+    lib.ora_equilibrium(C.byref(p), _dp(r), _dp(uu), _dp(pops))
+    return pops
+
+
+def step(p: Params, pops, force=None, step_index=0):
+    """One stream+collide step; returns the new post-collision populations.
+    force: optional (3, nz, ny, nx) field added to p.body_force."""
+    lib = _load()
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    dst = np.empty_like(src)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    lib.ora_step(C.byref(p), _dp(src), _dp(dst), _dp(f), int(step_index) & 0xffffffff)
+    return dst
+
+
+def run(p: Params, pops, nsteps, force=None, step0=0):
+    for t in range(nsteps):
+        pops = step(p, pops, force, step0 + t)
+    return pops
+
+
+def moments(p: Params, pops, force=None):
+    """(rho (nz,ny,nx), j (3,nz,ny,nx), pi (6,nz,ny,nx)) of the pre-collision state."""
+    lib = _load()
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    rho = np.empty((p.nz, p.ny, p.nx))
+    j = np.empty((3, p.nz, p.ny, p.nx))
+    pi = np.empty((6, p.nz, p.ny, p.nx))
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    lib.ora_moments(C.byref(p), _dp(src), _dp(f), _dp(rho), _dp(j), _dp(pi))
+    return rho, j, pi
+
+
+def modes(p: Params, pops):
+    """All 19 moments m_k of the pre-collision state, shape (19,nz,ny,nx)."""
+    lib = _load()
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    m = np.empty((Q, p.nz, p.ny, p.nx))
+    lib.ora_modes(C.byref(p), _dp(src), _dp(m))
+    return m
+
+
+def make_md(n_chains, chain_len, *, eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, use_wca=True) -> MD:
+    md = MD()
+    md.n_chains, md.chain_len, md.use_wca = int(n_chains), int(chain_len), int(bool(use_wca))
+    md.eps, md.sigma, md.k_fene, md.r0 = eps, sigma, k_fene, r0
+    return md
+
+
+def md_forces(p: Params, md: MD, pos):
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    F = np.zeros_like(pos)
+    broken = lib.ora_md_forces(C.byref(p), C.byref(md), pos.shape[0], _dp(pos), _dp(F))
+    return F, broken
+
+
+def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_step0=0,
+           md: MD | None = None, force=None, noise_kind=0):
+    """One LB step's worth of particle sub-steps.  Returns (pos, mom, facc, broken);
+    facc has shape (3, nz, ny, nx) and holds the spread impulses -J Delta."""
+    lib = _load()
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    mom = np.array(mom, dtype=np.float64, order="C", copy=True)
+    n = pos.shape[0]
+    mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)))
+    gamma = np.ascontiguousarray(np.broadcast_to(np.asarray(gamma, dtype=np.float64), (n,)))
+    facc = np.zeros((3, p.nz, p.ny, p.nx))
+    cp = CoupleParams()
+    cp.n_substeps, cp.noise_kind, cp.dt = int(n_substeps), int(noise_kind), float(dt)
+    cp.seed, cp.md_step0 = int(seed), int(md_step0)
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    broken = lib.ora_couple(C.byref(p), _dp(src), _dp(f), n, _dp(pos), _dp(mom), _dp(mass),
+                            _dp(gamma), None if md is None else C.byref(md), C.byref(cp),
+                            _dp(facc))
+    return pos, mom, facc, broken
+
+
+def interpolate(p: Params, pops, pos, force=None):
+    lib = _load()
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    up = np.empty_like(pos)
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    lib.ora_interpolate(C.byref(p), _dp(src), _dp(f), pos.shape[0], _dp(pos), _dp(up))
+    return up
+
+
+def stencil(p: Params, pos3):
+    lib = _load()
+    pp = np.ascontiguousarray(pos3, dtype=np.float64)
+    node = (C.c_longlong * 8)()
+    wt = np.zeros(8)
+    lib.ora_stencil(C.byref(p), _dp(pp), node, _dp(wt))
+    return np.array(list(node), dtype=np.int64), wt

@@ -1,0 +1,723 @@
+/*
+ * lb_oracle.c -- plain, slow FP64 CPU oracle for the fluctuating D3Q19
+ * lattice-Boltzmann update with frictional point-particle coupling
+ * (Duenweg & Ladd, "Lattice Boltzmann simulations of soft matter systems",
+ * arXiv 0803.2826).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file defines what the CUDA library must
+ * compute; it is used by the test-suite, by the smoke check and by the
+ * benchmark's CPU-baseline leg, and by nothing else.  It shares no source,
+ * header, table or constant with the CUDA library.  Every table here is built
+ * at start-up from the definitions printed in the paper (velocity set,
+ * weights, Table 1 polynomials); nothing is hand-factorised.
+ *
+ * Arithmetic is IEEE double throughout, no fast-math.  Loops follow the
+ * paper's steps in the paper's order.  The only parallelism is an OpenMP
+ * "parallel for" over independent lattice nodes / particles, which does not
+ * change any per-node result.
+ *
+ * Conventions that the paper leaves open (the project's readings):
+ *  - velocity order: i=0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = the twelve
+ *    (+-1,+-1,0), (0,+-1,+-1), (+-1,0,+-1) vectors in that group order, the
+ *    two signs (of the two non-zero components, x before y before z) in the
+ *    order (+,+),(+,-),(-,+),(-,-);
+ *  - lattice units b = h = 1, nodes at integer coordinates 0..L-1;
+ *  - population layout [19][nz][ny][nx] (x fastest), raw n_i in FP64;
+ *  - the stored state is the post-collision population n*_i(r); one step is
+ *    "stream (pull) then collide";
+ *  - conserved-mode eigenvalues gamma_0..3 = 1;
+ *  - noise: Philox4x32-10 keyed on (seed) with counter
+ *    (node, step, domain<<8 | block, replica), 23-bit odd uniforms,
+ *    Box-Muller pairs.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define Q 19
+#define CS2 (1.0 / 3.0)
+
+/* ------------------------------------------------------------------------ */
+/* Lattice algebra (Sec. 3.3, D3Q19 weights; Sec. 3.4, Table 1)             */
+/* ------------------------------------------------------------------------ */
+
+static int g_c[Q][3];      /* velocity vectors c_i                          */
+static double g_a[Q];      /* equilibrium weights a^{c_i}                   */
+static double g_e[Q][Q];   /* basis vectors e_{ki} (row k, column i)        */
+static double g_w[Q];      /* norms w_k = sum_i a_i e_ki^2                  */
+static int g_opp[Q];       /* index of -c_i                                 */
+static int g_ready = 0;
+
+static void build_tables(void)
+{
+    if (g_ready) return;
+    int i = 0;
+    g_c[i][0] = g_c[i][1] = g_c[i][2] = 0;
+    i++;
+    /* six nearest neighbours: +e_alpha then -e_alpha, alpha = x, y, z */
+    for (int al = 0; al < 3; al++) {
+        for (int s = 0; s < 2; s++) {
+            g_c[i][0] = g_c[i][1] = g_c[i][2] = 0;
+            g_c[i][al] = (s == 0) ? 1 : -1;
+            i++;
+        }
+    }
+    /* twelve next-nearest neighbours: (+-1,+-1,0), (0,+-1,+-1), (+-1,0,+-1);
+     * the two signs apply to the two non-zero components in x, y, z order */
+    const int plane[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    const int sg[4][2] = {{1, 1}, {1, -1}, {-1, 1}, {-1, -1}};
+    for (int p = 0; p < 3; p++) {
+        for (int s = 0; s < 4; s++) {
+            g_c[i][0] = g_c[i][1] = g_c[i][2] = 0;
+            g_c[i][plane[p][0]] = sg[s][0];
+            g_c[i][plane[p][1]] = sg[s][1];
+            i++;
+        }
+    }
+    /* weights by speed: a^0 = 1/3, a^1 = 1/18, a^sqrt2 = 1/36 (Sec. 3.3) */
+    for (i = 0; i < Q; i++) {
+        int c2 = g_c[i][0] * g_c[i][0] + g_c[i][1] * g_c[i][1] + g_c[i][2] * g_c[i][2];
+        g_a[i] = (c2 == 0) ? 1.0 / 3.0 : (c2 == 1) ? 1.0 / 18.0 : 1.0 / 36.0;
+    }
+    for (i = 0; i < Q; i++) {
+        for (int j = 0; j < Q; j++) {
+            if (g_c[j][0] == -g_c[i][0] && g_c[j][1] == -g_c[i][1] && g_c[j][2] == -g_c[i][2])
+                g_opp[i] = j;
+        }
+    }
+    /* Table 1: the nineteen polynomials in c_hat = c / (b/h) = c */
+    for (i = 0; i < Q; i++) {
+        double x = g_c[i][0], y = g_c[i][1], z = g_c[i][2];
+        double c2 = x * x + y * y + z * z;
+        g_e[0][i] = 1.0;
+        g_e[1][i] = x;
+        g_e[2][i] = y;
+        g_e[3][i] = z;
+        g_e[4][i] = c2 - 1.0;
+        g_e[5][i] = 3.0 * x * x - c2;
+        g_e[6][i] = y * y - z * z;
+        g_e[7][i] = x * y;
+        g_e[8][i] = y * z;
+        g_e[9][i] = z * x;
+        g_e[10][i] = (3.0 * c2 - 5.0) * x;
+        g_e[11][i] = (3.0 * c2 - 5.0) * y;
+        g_e[12][i] = (3.0 * c2 - 5.0) * z;
+        g_e[13][i] = (y * y - z * z) * x;
+        g_e[14][i] = (z * z - x * x) * y;
+        g_e[15][i] = (x * x - y * y) * z;
+        g_e[16][i] = 3.0 * c2 * c2 - 6.0 * c2 + 1.0;
+        g_e[17][i] = (2.0 * c2 - 3.0) * (3.0 * x * x - c2);
+        g_e[18][i] = (2.0 * c2 - 3.0) * (y * y - z * z);
+    }
+    /* normalising factors, Eq. (weights_unweighted) with q = a */
+    for (int k = 0; k < Q; k++) {
+        double s = 0.0;
+        for (i = 0; i < Q; i++) s += g_a[i] * g_e[k][i] * g_e[k][i];
+        g_w[k] = s;
+    }
+    g_ready = 1;
+}
+
+/* Export the tables so the tests can check them against the paper. */
+void ora_tables(int *c, double *a, double *e, double *w, int *opp)
+{
+    build_tables();
+    for (int i = 0; i < Q; i++) {
+        if (c) for (int d = 0; d < 3; d++) c[3 * i + d] = g_c[i][d];
+        if (a) a[i] = g_a[i];
+        if (opp) opp[i] = g_opp[i];
+    }
+    for (int k = 0; k < Q; k++) {
+        if (w) w[k] = g_w[k];
+        if (e) for (int i = 0; i < Q; i++) e[Q * k + i] = g_e[k][i];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,  */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11), written from the   */
+/* published round definition.                                              */
+/* ------------------------------------------------------------------------ */
+
+void ora_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;  /* Weyl increments: golden ratio, sqrt(3)-1 */
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform in (0,1): the top 23 bits of a word become the odd integer
+ * 2*(x>>9)+1 < 2^24, scaled by 2^-24 (exact in binary32 and binary64). */
+double ora_uniform(uint32_t x)
+{
+    return (2.0 * (double)(x >> 9) + 1.0) * (1.0 / 16777216.0);
+}
+
+/* 16 raw words for (seed, node, step, domain, replica): four Philox blocks. */
+void ora_raw16(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain,
+               uint32_t replica, int nblocks, uint32_t *out)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int b = 0; b < nblocks; b++) {
+        uint32_t ctr[4] = {node, step, (domain << 8) | (uint32_t)b, replica};
+        ora_philox4x32_10(ctr, key, out + 4 * b);
+    }
+}
+
+/* Gaussians by the Box-Muller transform on consecutive uniform pairs. */
+void ora_gaussians(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain,
+                   uint32_t replica, int nblocks, double *g)
+{
+    uint32_t raw[16];
+    ora_raw16(seed, node, step, domain, replica, nblocks, raw);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int p = 0; p < 2 * nblocks; p++) {
+        double v1 = ora_uniform(raw[2 * p]);
+        double v2 = ora_uniform(raw[2 * p + 1]);
+        double rad = sqrt(-2.0 * log(v1));
+        g[2 * p] = rad * cos(two_pi * v2);
+        g[2 * p + 1] = rad * sin(two_pi * v2);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Parameters                                                                */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int nx, ny, nz;
+    int walls;          /* 1: solid planes z = 0 and z = nz-1 (link bounce-back) */
+    int noise_rho0;     /* 1: noise amplitude uses rho0 instead of local rho      */
+    int pad_;
+    double rho0;
+    double kT;
+    double gamma_shear, gamma_bulk, gamma_odd, gamma_even;
+    double body_force[3];
+    uint64_t seed;
+    uint32_t replica;
+    uint32_t pad2_;
+} ora_params;
+
+static size_t nodes_of(const ora_params *P) { return (size_t)P->nx * P->ny * P->nz; }
+
+static size_t lin(const ora_params *P, int x, int y, int z)
+{
+    return ((size_t)z * P->ny + y) * P->nx + x;
+}
+
+static int is_solid(const ora_params *P, int z)
+{
+    return P->walls && (z == 0 || z == P->nz - 1);
+}
+
+static int wrap(int v, int L) { return ((v % L) + L) % L; }
+
+/* Eigenvalue gamma_k of mode k (Sec. 3.4): conserved modes 0..3 keep their
+ * non-equilibrium part (gamma = 1); bulk mode 4; shear modes 5..9; kinetic
+ * modes 10..15 (odd, gamma_3a = gamma_3b) and 16..18 (even, gamma_4a = gamma_4b). */
+static double gamma_of(const ora_params *P, int k)
+{
+    if (k <= 3) return 1.0;
+    if (k == 4) return P->gamma_bulk;
+    if (k <= 9) return P->gamma_shear;
+    if (k <= 15) return P->gamma_odd;
+    return P->gamma_even;
+}
+
+/* Eq. (original_equil_distrib): quadratic equilibrium. */
+static void equilibrium(double rho, const double u[3], double neq[Q])
+{
+    double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < Q; i++) {
+        double cu = u[0] * g_c[i][0] + u[1] * g_c[i][1] + u[2] * g_c[i][2];
+        neq[i] = g_a[i] * rho * (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2));
+    }
+}
+
+/* Equilibrium populations for given fields rho [N] and u [3][N] (NULL: rho0, 0). */
+void ora_equilibrium(const ora_params *P, const double *rho, const double *u, double *pops)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    for (size_t s = 0; s < N; s++) {
+        double r = rho ? rho[s] : P->rho0;
+        double uu[3] = {0.0, 0.0, 0.0};
+        if (u) { uu[0] = u[s]; uu[1] = u[N + s]; uu[2] = u[2 * N + s]; }
+        double ne[Q];
+        equilibrium(r, uu, ne);
+        for (int i = 0; i < Q; i++) pops[(size_t)i * N + s] = ne[i];
+    }
+}
+
+/* Pull streaming, Eq. (LBE): n_i(r) = n*_i(r - c_i).  With walls, a link
+ * whose source node is solid is bounced back (Sec. 4.1, Eq. (MBB) with
+ * u_b = 0): n_i(r) = n*_{opp(i)}(r). */
+static void gather(const ora_params *P, const double *src, int x, int y, int z, double n[Q])
+{
+    size_t N = nodes_of(P);
+    for (int i = 0; i < Q; i++) {
+        int sx = wrap(x - g_c[i][0], P->nx);
+        int sy = wrap(y - g_c[i][1], P->ny);
+        int sz = z - g_c[i][2];
+        if (P->walls) {
+            if (sz < 0 || sz >= P->nz || is_solid(P, sz)) {
+                n[i] = src[(size_t)g_opp[i] * N + lin(P, x, y, z)];
+                continue;
+            }
+        } else {
+            sz = wrap(sz, P->nz);
+        }
+        n[i] = src[(size_t)i * N + lin(P, sx, sy, sz)];
+    }
+}
+
+/* Total force density on node s: uniform body force plus the optional field
+ * (layout [3][N]). */
+static void node_force(const ora_params *P, const double *force, size_t s, double f[3])
+{
+    size_t N = nodes_of(P);
+    for (int d = 0; d < 3; d++) {
+        f[d] = P->body_force[d];
+        if (force) f[d] += force[(size_t)d * N + s];
+    }
+}
+
+/* One collision, Sec. 3.4, 3.5 and 3.7:
+ *   rho = sum n, j = sum n c + f/2, u = j / rho         (Eq. special_choice_momentum_density)
+ *   n^neq = n - n^eq(rho, u)                             (Eq. original_equil_distrib)
+ *   m^neq_k = sum_i e_ki n^neq_i                         (Eq. forward)
+ *   m*^neq_k = gamma_k m^neq_k + phi_k sqrt(w_k mu rho) r_k,  k >= 4
+ *                                                        (Eqs. lco_update, stochupdaterule1,
+ *                                                         detailedbalance1, normalized_mk)
+ *   n*_i = n^eq_i + a_i sum_k e_ki m*^neq_k / w_k + Delta''_i
+ *                                                        (Eq. back_transformation, q = a;
+ *                                                         Delta'' of Sec. 3.7)
+ * mu = k_B T / (b^3 c_s^2) (Sec. 3.5).  r: 15 Gaussians r_4..r_18 or NULL. */
+static void collide(const ora_params *P, const double n[Q], const double f[3],
+                    const double *r, double nstar[Q])
+{
+    double rho = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+    for (int i = 0; i < Q; i++) {
+        rho += n[i];
+        jx += n[i] * g_c[i][0];
+        jy += n[i] * g_c[i][1];
+        jz += n[i] * g_c[i][2];
+    }
+    double j[3] = {jx + 0.5 * f[0], jy + 0.5 * f[1], jz + 0.5 * f[2]};
+    double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+
+    double neq[Q], nneq[Q];
+    equilibrium(rho, u, neq);
+    for (int i = 0; i < Q; i++) nneq[i] = n[i] - neq[i];
+
+    double m[Q];
+    for (int k = 0; k < Q; k++) {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += g_e[k][i] * nneq[i];
+        m[k] = s;
+    }
+    double mu = P->kT / CS2;
+    double rho_noise = P->noise_rho0 ? P->rho0 : rho;
+    for (int k = 0; k < Q; k++) {
+        double gk = gamma_of(P, k);
+        double ms = gk * m[k];
+        if (k >= 4 && r && P->kT > 0.0) {
+            double phi = sqrt(1.0 - gk * gk);
+            ms += phi * sqrt(g_w[k] * mu * rho_noise) * r[k - 4];
+        }
+        m[k] = ms;
+    }
+    /* Sigma of Eq. (moment_two_external_force) */
+    double uf = u[0] * f[0] + u[1] * f[1] + u[2] * f[2];
+    double Sig[3][3];
+    for (int a = 0; a < 3; a++) {
+        for (int b = 0; b < 3; b++) {
+            double d = (a == b) ? 1.0 : 0.0;
+            Sig[a][b] = 0.5 * (1.0 + P->gamma_shear) * (u[a] * f[b] + u[b] * f[a] - (2.0 / 3.0) * uf * d)
+                      + (1.0 / 3.0) * (1.0 + P->gamma_bulk) * uf * d;
+        }
+    }
+    for (int i = 0; i < Q; i++) {
+        double s = 0.0;
+        for (int k = 0; k < Q; k++) s += g_e[k][i] * m[k] / g_w[k];
+        double fc = f[0] * g_c[i][0] + f[1] * g_c[i][1] + f[2] * g_c[i][2];
+        double sc = 0.0;
+        for (int a = 0; a < 3; a++)
+            for (int b = 0; b < 3; b++)
+                sc += Sig[a][b] * (g_c[i][a] * g_c[i][b] - CS2 * ((a == b) ? 1.0 : 0.0));
+        double dforce = g_a[i] * (fc / CS2 + sc / (2.0 * CS2 * CS2));
+        nstar[i] = neq[i] + g_a[i] * s + dforce;
+    }
+}
+
+/* One LB step over the whole box: dst(r) = C[ S src ](r).  Solid nodes are
+ * copied unchanged.  force: optional [3][N] field added to body_force. */
+void ora_step(const ora_params *P, const double *src, double *dst, const double *force, uint32_t step)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; z++) {
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                if (is_solid(P, z)) {
+                    for (int i = 0; i < Q; i++) dst[(size_t)i * N + s] = src[(size_t)i * N + s];
+                    continue;
+                }
+                double n[Q], ns[Q], f[3], g[16];
+                gather(P, src, x, y, z, n);
+                node_force(P, force, s, f);
+                const double *r = NULL;
+                if (P->kT > 0.0) {
+                    ora_gaussians(P->seed, (uint32_t)s, step, 0u, P->replica, 4, g);
+                    r = g;
+                }
+                collide(P, n, f, r, ns);
+                for (int i = 0; i < Q; i++) dst[(size_t)i * N + s] = ns[i];
+            }
+        }
+    }
+}
+
+/* Hydrodynamic moments of the pre-collision state (Eqs. hmodes_beg..hmodes_end
+ * written directly as sums over populations): rho = sum n, j = sum n c + f/2,
+ * pi_ab = sum n c_a c_b, components (xx, yy, zz, xy, yz, zx).  Layouts [N],
+ * [3][N], [6][N]; any output may be NULL.  Solid nodes get rho = rho0 and
+ * zero j, pi. */
+void ora_moments(const ora_params *P, const double *pops, const double *force,
+                 double *rho, double *j, double *pi)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    const int ab[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {1, 2}, {2, 0}};
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; z++) {
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                if (is_solid(P, z)) {
+                    if (rho) rho[s] = P->rho0;
+                    if (j) for (int d = 0; d < 3; d++) j[(size_t)d * N + s] = 0.0;
+                    if (pi) for (int c = 0; c < 6; c++) pi[(size_t)c * N + s] = 0.0;
+                    continue;
+                }
+                double n[Q], f[3];
+                gather(P, pops, x, y, z, n);
+                node_force(P, force, s, f);
+                double r = 0.0, jj[3] = {0, 0, 0}, pp[6] = {0, 0, 0, 0, 0, 0};
+                for (int i = 0; i < Q; i++) {
+                    r += n[i];
+                    for (int d = 0; d < 3; d++) jj[d] += n[i] * g_c[i][d];
+                    for (int c = 0; c < 6; c++) pp[c] += n[i] * g_c[i][ab[c][0]] * g_c[i][ab[c][1]];
+                }
+                if (rho) rho[s] = r;
+                if (j) for (int d = 0; d < 3; d++) j[(size_t)d * N + s] = jj[d] + 0.5 * f[d];
+                if (pi) for (int c = 0; c < 6; c++) pi[(size_t)c * N + s] = pp[c];
+            }
+        }
+    }
+}
+
+/* All nineteen moments m_k = sum_i e_ki n_i (Eq. forward) of the
+ * pre-collision populations, layout [19][N]; solid nodes give zeros. */
+void ora_modes(const ora_params *P, const double *pops, double *m)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; z++) {
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                double n[Q];
+                if (is_solid(P, z)) {
+                    for (int k = 0; k < Q; k++) m[(size_t)k * N + s] = 0.0;
+                    continue;
+                }
+                gather(P, pops, x, y, z, n);
+                for (int k = 0; k < Q; k++) {
+                    double acc = 0.0;
+                    for (int i = 0; i < Q; i++) acc += g_e[k][i] * n[i];
+                    m[(size_t)k * N + s] = acc;
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Point particles: Kremer-Grest forces (Sec. 2.1), force coupling           */
+/* (Sec. 4.5), linear interpolation (Sec. 4.6)                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int n_chains;      /* particles k*chain_len .. (k+1)*chain_len-1 form chain k */
+    int chain_len;     /* 0 or 1: no bonds                                        */
+    int use_wca;       /* purely repulsive LJ between all pairs                   */
+    int pad_;
+    double eps, sigma; /* WCA, Eq. (ulennardjones)                                */
+    double k_fene, r0; /* FENE, Eq. (ufene)                                       */
+} ora_md;
+
+/* Minimum-image separation d = a - b along each periodic axis. */
+static void min_image(const ora_params *P, const double *a, const double *b, double d[3])
+{
+    const int L[3] = {P->nx, P->ny, P->nz};
+    for (int c = 0; c < 3; c++) {
+        double v = a[c] - b[c];
+        int periodic = (c < 2) || !P->walls;
+        if (periodic) v -= L[c] * floor(v / L[c] + 0.5);
+        d[c] = v;
+    }
+}
+
+/* Conservative forces F^c = -dV/dr_i, brute force over all pairs.  Returns
+ * the number of FENE bonds stretched to r >= R0 (their force is left out). */
+int ora_md_forces(const ora_params *P, const ora_md *md, int np, const double *pos, double *F)
+{
+    int broken = 0;
+    double rc2 = pow(2.0, 1.0 / 3.0) * md->sigma * md->sigma;  /* (2^{1/6} sigma)^2 */
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : broken)
+    for (int i = 0; i < np; i++) {
+        double fi[3] = {0.0, 0.0, 0.0};
+        for (int j = 0; j < np; j++) {
+            if (j == i) continue;
+            double d[3];
+            min_image(P, pos + 3 * i, pos + 3 * j, d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (md->use_wca && r2 < rc2) {
+                /* V = 4 eps [(s/r)^12 - (s/r)^6 + 1/4];  F = -dV/dr * d/r */
+                double sr2 = md->sigma * md->sigma / r2;
+                double sr6 = sr2 * sr2 * sr2;
+                double mag = 24.0 * md->eps * (2.0 * sr6 * sr6 - sr6) / r2;
+                for (int c = 0; c < 3; c++) fi[c] += mag * d[c];
+            }
+            if (md->chain_len > 1) {
+                int ci = i / md->chain_len, cj = j / md->chain_len;
+                if (ci == cj && (j == i + 1 || j == i - 1)) {
+                    /* V = -(k/2) R0^2 ln(1 - r^2/R0^2);  F = -k d / (1 - r^2/R0^2) */
+                    double x = r2 / (md->r0 * md->r0);
+                    if (x >= 1.0) {
+                        broken++;
+                    } else {
+                        double mag = -md->k_fene / (1.0 - x);
+                        for (int c = 0; c < 3; c++) fi[c] += mag * d[c];
+                    }
+                }
+            }
+        }
+        for (int c = 0; c < 3; c++) F[3 * i + c] = fi[c];
+    }
+    return broken;
+}
+
+/* Fluid velocity at every node for the coupling: u = (sum n c + f_ext/2)/rho
+ * from the pre-collision populations (Sec. 4.5: the coupling interpolates u,
+ * not j; Sec. 3.7 for the half force).  Solid nodes: u = 0. */
+static void node_velocity(const ora_params *P, const double *pops, const double *force, double *u)
+{
+    size_t N = nodes_of(P);
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; z++) {
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                if (is_solid(P, z)) {
+                    u[3 * s] = u[3 * s + 1] = u[3 * s + 2] = 0.0;
+                    continue;
+                }
+                double n[Q], f[3];
+                gather(P, pops, x, y, z, n);
+                node_force(P, force, s, f);
+                double rho = 0.0, j[3] = {0, 0, 0};
+                for (int i = 0; i < Q; i++) {
+                    rho += n[i];
+                    for (int d = 0; d < 3; d++) j[d] += n[i] * g_c[i][d];
+                }
+                for (int d = 0; d < 3; d++) u[3 * s + d] = (j[d] + 0.5 * f[d]) / rho;
+            }
+        }
+    }
+}
+
+/* phi_2, Eq. (2point). */
+static double phi2(double v)
+{
+    double a = fabs(v);
+    return a <= 1.0 ? 1.0 - a : 0.0;
+}
+
+/* The eight nodes of the linear stencil around position p and their weights
+ * Delta(r - p) = phi2(x) phi2(y) phi2(z) (Eqs. Delta, 2point). */
+static void stencil(const ora_params *P, const double p[3], size_t node[8], double wt[8])
+{
+    int b[3];
+    for (int c = 0; c < 3; c++) b[c] = (int)floor(p[c]);
+    int q = 0;
+    for (int dz = 0; dz < 2; dz++)
+        for (int dy = 0; dy < 2; dy++)
+            for (int dx = 0; dx < 2; dx++) {
+                int nxv = b[0] + dx, nyv = b[1] + dy, nzv = b[2] + dz;
+                double w = phi2(nxv - p[0]) * phi2(nyv - p[1]) * phi2(nzv - p[2]);
+                nxv = wrap(nxv, P->nx);
+                nyv = wrap(nyv, P->ny);
+                nzv = P->walls ? nzv : wrap(nzv, P->nz);
+                if (nzv < 0 || nzv >= P->nz) { nzv = 0; w = 0.0; }
+                node[q] = lin(P, nxv, nyv, nzv);
+                wt[q] = w;
+                q++;
+            }
+}
+
+/* Put a position back into the box: periodic wrap in x, y (and z without
+ * walls); with walls, specular reflection keeps z in [1, nz-2] so that the
+ * stencil touches fluid nodes only (a project reading). */
+static void confine(const ora_params *P, double p[3], double m[3])
+{
+    const int L[3] = {P->nx, P->ny, P->nz};
+    for (int c = 0; c < 3; c++) {
+        if (c == 2 && P->walls) {
+            double lo = 1.0, hi = (double)(P->nz - 2);
+            if (p[2] < lo) { p[2] = 2.0 * lo - p[2]; m[2] = -m[2]; }
+            if (p[2] > hi) { p[2] = 2.0 * hi - p[2]; m[2] = -m[2]; }
+        } else {
+            p[c] -= L[c] * floor(p[c] / L[c]);
+            if (p[c] >= L[c]) p[c] -= L[c];
+        }
+    }
+}
+
+typedef struct {
+    int n_substeps;
+    int noise_kind;     /* 0: Gaussian theta; 1: three-point theta in {0, +-sqrt3} */
+    double dt;          /* particle time step in lattice units (h = 1 per LB step) */
+    uint64_t seed;      /* particle noise key                                      */
+    uint32_t md_step0;  /* global index of the first sub-step (noise counter)      */
+    uint32_t pad_;
+} ora_couple_params;
+
+/* Particle noise theta (3 components) for particle p at sub-step t:
+ * Philox domain 1, one block; Gaussian via Box-Muller, or the three-point
+ * distribution of Sec. 4.5 decided on the exact integer behind the uniform. */
+static void particle_theta(const ora_params *P, const ora_couple_params *C, uint32_t p,
+                           uint32_t t, double th[3])
+{
+    if (C->noise_kind == 1) {
+        uint32_t raw[4];
+        ora_raw16(C->seed, p, t, 1u, P->replica, 1, raw);
+        const double s3 = sqrt(3.0);
+        for (int c = 0; c < 3; c++) {
+            uint64_t k = 2ull * (raw[c] >> 9) + 1ull;  /* uniform = k / 2^24 */
+            if (6ull * k < (1ull << 24)) th[c] = -s3;          /* v < 1/6  */
+            else if (6ull * k > 5ull * (1ull << 24)) th[c] = s3; /* v > 5/6 */
+            else th[c] = 0.0;
+        }
+    } else {
+        double g[4];
+        ora_gaussians(C->seed, p, t, 1u, P->replica, 1, g);
+        th[0] = g[0]; th[1] = g[1]; th[2] = g[2];
+    }
+}
+
+/* Frictional coupling for one LB step (Sec. 4.5, "Langevin integrator"):
+ * the fluid velocity field is frozen for the n_substeps particle steps; per
+ * sub-step: half drift, conservative forces, exact Ornstein-Uhlenbeck
+ * momentum update (Eq. langevin_momentum_update), spreading of the
+ * non-conservative impulse J = p' - p - C2 F^c as -J Delta(r - r_half) into
+ * facc (layout [3][N]), second half drift.  mass/gamma: per-particle.
+ * Returns the number of broken FENE bonds met. */
+int ora_couple(const ora_params *P, const double *pops, const double *force, int np,
+               double *pos, double *mom, const double *mass, const double *gamma,
+               const ora_md *md, const ora_couple_params *C, double *facc)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    double *u = (double *)malloc(sizeof(double) * 3 * N);
+    double *fc = (double *)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
+    node_velocity(P, pops, force, u);
+    int broken = 0;
+    double h = C->dt;
+    for (int s = 0; s < C->n_substeps; s++) {
+        for (int p = 0; p < np; p++) {
+            for (int c = 0; c < 3; c++) pos[3 * p + c] += 0.5 * h * mom[3 * p + c] / mass[p];
+            confine(P, pos + 3 * p, mom + 3 * p);
+        }
+        if (md) broken += ora_md_forces(P, md, np, pos, fc);
+        for (int p = 0; p < np; p++) {
+            double m = mass[p], G = gamma[p];
+            double C1 = exp(-G * h / m);
+            double C2 = (m / G) * (1.0 - C1);
+            double C3 = sqrt(m * P->kT * (1.0 - exp(-2.0 * G * h / m)));
+            size_t node[8];
+            double wt[8];
+            stencil(P, pos + 3 * p, node, wt);
+            double up[3] = {0.0, 0.0, 0.0};
+            for (int q = 0; q < 8; q++)
+                for (int c = 0; c < 3; c++) up[c] += wt[q] * u[3 * node[q] + c];
+            double th[3] = {0.0, 0.0, 0.0};
+            if (P->kT > 0.0) particle_theta(P, C, (uint32_t)p, C->md_step0 + (uint32_t)s, th);
+            double pn[3], J[3];
+            for (int c = 0; c < 3; c++) {
+                double Fc = md ? fc[3 * p + c] : 0.0;
+                pn[c] = C1 * mom[3 * p + c] + C2 * (Fc + G * up[c]) + C3 * th[c];
+                J[c] = pn[c] - mom[3 * p + c] - C2 * Fc;
+            }
+            for (int q = 0; q < 8; q++)
+                for (int c = 0; c < 3; c++) facc[(size_t)c * N + node[q]] -= J[c] * wt[q];
+            for (int c = 0; c < 3; c++) mom[3 * p + c] = pn[c];
+        }
+        for (int p = 0; p < np; p++) {
+            for (int c = 0; c < 3; c++) pos[3 * p + c] += 0.5 * h * mom[3 * p + c] / mass[p];
+            confine(P, pos + 3 * p, mom + 3 * p);
+        }
+    }
+    free(u);
+    free(fc);
+    return broken;
+}
+
+/* Interpolated fluid velocity at arbitrary positions (Eq. ufluid_discrete). */
+void ora_interpolate(const ora_params *P, const double *pops, const double *force, int np,
+                     const double *pos, double *up)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    double *u = (double *)malloc(sizeof(double) * 3 * N);
+    node_velocity(P, pops, force, u);
+    for (int p = 0; p < np; p++) {
+        size_t node[8];
+        double wt[8], pp[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+        stencil(P, pp, node, wt);
+        for (int c = 0; c < 3; c++) {
+            double acc = 0.0;
+            for (int q = 0; q < 8; q++) acc += wt[q] * u[3 * node[q] + c];
+            up[3 * p + c] = acc;
+        }
+    }
+    free(u);
+}
+
+/* Stencil export for the interpolation-kernel tests. */
+void ora_stencil(const ora_params *P, const double *p, long long *node, double *wt)
+{
+    size_t nd[8];
+    stencil(P, p, nd, wt);
+    for (int q = 0; q < 8; q++) node[q] = (long long)nd[q];
+}

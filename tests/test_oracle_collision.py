@@ -1,0 +1,221 @@
+"""Pins of the oracle's stream-collide step against what the paper fixes.
+
+- Eq. (original_equil_distrib): moments of n^eq are rho, j, rho c_s^2 delta + rho u u
+  (Sec. 3.2 requirements) and n^eq has no projection on the kinetic modes.
+- Eq. (lco_update): each non-conserved mode relaxes as m*neq = gamma_k mneq.
+- Sec. 3.7: the collision adds h f to the momentum, leaves mass unchanged,
+  and gives the post-collision stress pi^eq + Sigma (gamma = 0), Eq.
+  (moment_two_external_force).
+- Global mass / momentum conservation per step (Eq. LBE with a conserving
+  collision), with noise and forcing on.
+- Eq. (shearviscosity): shear-wave decay rate nu k^2 with nu = c_s^2 (1+g)/(2(1-g)).
+- Sec. 3.6: the Gaussian product measure is stationary: every mode keeps the
+  variance mu rho0 w_k (mu = kT / c_s^2).
+- Plane Poiseuille flow between bounce-back walls (Sec. 4.1): the steady
+  profile has second difference -g / nu and the wall stress balances the force.
+"""
+import numpy as np
+import pytest
+
+from paper_0803_2826_gb300 import inputs
+
+
+def _uniform_state(ora, p, rho, u, perturb_seed=None, amp=0.0):
+    rr = np.full((p.nz, p.ny, p.nx), rho)
+    uu = np.zeros((3, p.nz, p.ny, p.nx))
+    for d in range(3):
+        uu[d] = u[d]
+    pops = ora.equilibrium(p, rr, uu)
+    if perturb_seed is not None:
+        # a uniform non-equilibrium perturbation (same at every node)
+        rng = np.random.default_rng(perturb_seed)
+        pops += amp * rng.standard_normal(19)[:, None, None, None]
+    return pops
+
+
+def test_equilibrium_moments(ora):
+    c, a, e, w, opp = ora.tables()
+    p = ora.make_params((2, 3, 4))
+    rng = np.random.default_rng(1)
+    rho = rng.uniform(0.8, 1.2, size=(4, 3, 2))
+    u = rng.uniform(-0.05, 0.05, size=(3, 4, 3, 2))
+    n = ora.equilibrium(p, rho, u)
+    S = n.reshape(19, -1)
+    R = rho.reshape(-1)
+    U = u.reshape(3, -1)
+    assert np.allclose(S.sum(0), R, rtol=1e-14)
+    for al in range(3):
+        assert np.allclose((S * c[:, al, None]).sum(0), R * U[al], rtol=1e-12, atol=1e-16)
+        for be in range(3):
+            pi = (S * (c[:, al, None] * c[:, be, None])).sum(0)
+            want = R * (1 / 3 if al == be else 0) + R * U[al] * U[be]
+            assert np.allclose(pi, want, rtol=1e-12, atol=1e-16)
+    m = e @ S
+    assert np.abs(m[10:]).max() < 1e-15  # kinetic modes carry no equilibrium part
+
+
+def _closed_form_meq(rho, u):
+    """Equilibrium values of modes 4..9 from pi^eq = rho/3 delta + rho u u
+    projected on Table 1 (e4 = c^2-1, e5 = 3cx^2-c^2, ...)."""
+    ux, uy, uz = u
+    u2 = ux * ux + uy * uy + uz * uz
+    return np.array([rho * u2, rho * (3 * ux * ux - u2), rho * (uy * uy - uz * uz),
+                     rho * ux * uy, rho * uy * uz, rho * uz * ux])
+
+
+@pytest.mark.parametrize("gs,gv,go,ge", [(0.0, 0.0, 0.0, 0.0), (0.3, -0.2, 0.5, -0.4)])
+def test_mode_relaxation(ora, gs, gv, go, ge):
+    """Uniform box (streaming is the identity): m*_k - m^eq_k = gamma_k (m_k - m^eq_k)."""
+    c, a, e, w, opp = ora.tables()
+    p = ora.make_params((2, 2, 2), gamma_shear=gs, gamma_bulk=gv, gamma_odd=go, gamma_even=ge)
+    pops = _uniform_state(ora, p, 1.02, (0.01, -0.02, 0.015), perturb_seed=5, amp=1e-3)
+    m = e @ pops[:, 0, 0, 0]
+    out = ora.step(p, pops)
+    ms = e @ out[:, 0, 0, 0]
+    rho = m[0]
+    u = m[1:4] / rho
+    meq = np.zeros(19)
+    meq[0], meq[1:4] = rho, m[1:4]
+    meq[4:10] = _closed_form_meq(rho, u)
+    gam = np.array([1, 1, 1, 1, gv] + [gs] * 5 + [go] * 6 + [ge] * 3)
+    assert np.allclose(ms - meq, gam * (m - meq), rtol=1e-11, atol=1e-15)
+    # all nodes identical
+    assert np.allclose(out, out[:, :1, :1, :1], rtol=0, atol=1e-16)
+
+
+@pytest.mark.parametrize("gs,gv", [(0.0, 0.0), (0.4, -0.3)])
+def test_force_moments(ora, gs, gv):
+    """Sec. 3.7: mass unchanged, momentum + h f, and (all non-conserved gamma = 0)
+    post-collision stress = pi^eq(rho, u) + Sigma with u = (sum n c + f/2)/rho."""
+    c, a, e, w, opp = ora.tables()
+    f = np.array([2e-3, -1e-3, 5e-4])
+    p = ora.make_params((2, 2, 2), gamma_shear=gs, gamma_bulk=gv, body_force=f)
+    pops = _uniform_state(ora, p, 0.97, (0.02, 0.01, -0.01), perturb_seed=7, amp=1e-3)
+    n = pops[:, 0, 0, 0]
+    ns = ora.step(p, pops)[:, 0, 0, 0]
+    rho = n.sum()
+    g0 = n @ c
+    assert np.isclose(ns.sum(), rho, rtol=1e-15)
+    assert np.allclose(ns @ c, g0 + f, rtol=1e-13, atol=1e-17)
+    u = (g0 + 0.5 * f) / rho
+    uf = u @ f
+    Sig = 0.5 * (1 + gs) * (np.outer(u, f) + np.outer(f, u) - 2 / 3 * uf * np.eye(3)) \
+        + (1 + gv) / 3 * uf * np.eye(3)
+    pi_n = np.einsum("i,ia,ib->ab", n, c, c)
+    pi_s = np.einsum("i,ia,ib->ab", ns, c, c)
+    pieq = rho / 3 * np.eye(3) + rho * np.outer(u, u)
+    pineq = pi_n - pieq
+    tr = np.trace(pineq)
+    want = pieq + gs * (pineq - tr / 3 * np.eye(3)) + gv * tr / 3 * np.eye(3) + Sig
+    assert np.allclose(pi_s, want, rtol=1e-12, atol=1e-16)
+
+
+def test_rest_state_is_fixed_point(ora):
+    p = ora.make_params((4, 3, 5), gamma_shear=0.2)
+    pops = ora.equilibrium(p)
+    out = ora.run(p, pops, 3)
+    assert np.allclose(out, pops, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_global_conservation(ora, walls):
+    """Per step: sum rho unchanged; periodic: total momentum grows by sum f
+    exactly (FP64: <= 1e-13 relative), with noise and a force field on."""
+    c, a, e, w, opp = ora.tables()
+    shape = (6, 5, 7)
+    f_body = np.array([1e-4, -2e-4, 0.0 if walls else 3e-5])
+    p = ora.make_params(shape, kT=1e-4, gamma_shear=0.1, gamma_bulk=-0.1, seed=11,
+                        body_force=f_body, walls=walls)
+    u = inputs.shear_wave(shape, 0.01)
+    pops = ora.equilibrium(p, None, u)
+    field = inputs.gaussian_field(shape, 3, 1e-4, seed=2)
+    if walls:
+        field[:, 0] = 0
+        field[:, -1] = 0
+        field[2] = 0
+    fluid = slice(1, shape[2] - 1) if walls else slice(None)
+    for t in range(3):
+        out = ora.step(p, pops, field, t)
+        m0 = pops[:, fluid].sum()
+        m1 = out[:, fluid].sum()
+        assert abs(m1 - m0) <= 1e-13 * m0
+        if not walls:
+            j0 = pops.reshape(19, -1).sum(1) @ c
+            j1 = out.reshape(19, -1).sum(1) @ c
+            ftot = f_body * np.prod(shape) + field.reshape(3, -1).sum(1)
+            assert np.allclose(j1 - j0, ftot, rtol=1e-10, atol=1e-13 * np.prod(shape))
+        pops = out
+
+
+@pytest.mark.parametrize("gs", [0.0, 0.5, -0.5])
+def test_shear_wave_decay(ora, gs):
+    """Eq. (shearviscosity): a transverse wave u_x(z) decays at nu k^2 per step,
+    nu = c_s^2 (1 + gs) / (2 (1 - gs)).  Box 1 x 1 x L (the wave depends on z
+    only).  kT = 0; rate measured over steps 20..220."""
+    L = 64
+    p = ora.make_params((1, 1, L), gamma_shear=gs, gamma_bulk=gs)
+    u = inputs.shear_wave((1, 1, L), 1e-4)
+    pops = ora.equilibrium(p, None, u)
+    z = np.arange(L)
+    s = np.sin(2 * np.pi * z / L)
+
+    def amp(pp):
+        rho, j, _ = ora.moments(p, pp)
+        return 2.0 / L * np.sum(j[0, :, 0, 0] / rho[:, 0, 0] * s)
+
+    pops = ora.run(p, pops, 20)
+    a0 = amp(pops)
+    pops = ora.run(p, pops, 200, step0=20)
+    a1 = amp(pops)
+    rate = -np.log(a1 / a0) / 200
+    nu = (1 / 3) * (1 + gs) / (2 * (1 - gs))
+    k2 = (2 * np.pi / L) ** 2
+    # hydrodynamic limit; lattice corrections are O(k^2) relative
+    tol = 2e-5 if gs == 0.0 else 5e-3
+    assert abs(rate / (nu * k2) - 1) < tol, (rate, nu * k2)
+
+
+def test_equipartition_all_modes(ora):
+    """Sec. 3.6: with mu = 3 kT, the product Gaussian measure
+    n_i = a_i rho0 + sqrt(mu a_i rho0) xi_i is stationary under stream-collide;
+    each mode keeps <dm_k^2> = mu rho0 w_k (k = 0..18), for general gammas."""
+    c, a, e, w, opp = ora.tables()
+    kT, rho0 = 1e-4, 1.0
+    mu = 3 * kT
+    shape = (12, 12, 12)
+    p = ora.make_params(shape, kT=kT, rho0=rho0, gamma_shear=0.3, gamma_bulk=-0.2,
+                        gamma_odd=0.5, gamma_even=-0.4, seed=3)
+    xi = inputs.standard_normal((19,) + shape[::-1], seed=4)
+    pops = a[:, None, None, None] * rho0 + np.sqrt(mu * a * rho0)[:, None, None, None] * xi
+    acc = np.zeros(19)
+    nsamp = 0
+    for t in range(40):
+        pops = ora.step(p, pops, None, t)
+        if t % 4 == 3:
+            m = ora.modes(p, pops).reshape(19, -1)
+            m[0] -= rho0
+            acc += (m ** 2).mean(1)
+            nsamp += 1
+    var = acc / nsamp / (mu * rho0 * w)
+    assert np.all(np.abs(var - 1) < 0.05), var
+
+
+def test_poiseuille(ora):
+    """Walls at z = 0 and z = nz-1 (link bounce-back), force density g along x,
+    kT = 0: the steady interior profile has second difference -g/nu exactly
+    (nu = 1/6), and the shear stress at the walls balances the total force."""
+    nz = 12
+    g = 1e-5
+    p = ora.make_params((1, 1, nz), walls=True, body_force=(g, 0, 0))
+    pops = ora.equilibrium(p)
+    pops = ora.run(p, pops, 6000)
+    rho, j, pi = ora.moments(p, pops)
+    ux = (j[0] / rho)[1:-1, 0, 0]
+    d2 = ux[2:] - 2 * ux[1:-1] + ux[:-2]
+    assert np.allclose(d2, -6 * g, rtol=1e-6)
+    # symmetric about the channel centre
+    assert np.allclose(ux, ux[::-1], rtol=1e-9)
+    # still converging? successive steps agree
+    again = ora.run(p, pops, 1, step0=6000)
+    rho2, j2, _ = ora.moments(p, again)
+    assert np.allclose(j2[0][1:-1], j[0][1:-1], rtol=1e-8)
