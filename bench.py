@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the fluctuating D3Q19 lattice-Boltzmann hot path
+with coupled bead-spring chains, on one GB300 per rank.
+
+Workload (one "step" = one LB step of the whole hot path): a 256^3 periodic
+box of FP32 populations at kT = 1e-4 (rho0 = 1, all relaxation eigenvalues 0,
+so nu = 1/6), coupled to 64 FENE + WCA chains of 256 monomers (friction
+Gamma = 20 / mass 1 in MD units, i.e. 2 per LB time), 10 particle sub-steps of
+dt = 0.1 LB times (0.01 MD units) per LB step.  Per step: lb_couple_particles
+(10 sub-steps: forces, interpolation, OU update, spreading) then lb_step
+(fused stream-collide with noise and the spread impulses).
+
+Inputs are synthetic and seeded.  The 2.55 GB of populations are far larger
+than L2 (129 MB), so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on
+a bounded slab sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (256, 256, 256)
+N_CHAINS, CHAIN_LEN = 64, 256
+KT = 1e-4
+MASS, GAMMA = 1.0, 2.0          # Gamma = 20 m / tau_MD with h_LB = 0.1 tau_MD
+DT, NSUB = 0.1, 10              # dt = 0.01 tau_MD
+EPS, SIGMA, K_FENE, R0 = 0.01, 1.0, 0.3, 1.5   # epsilon = 0.01 in lattice energy units
+BYTES_PER_NODE = 19 * 4 * 2 + 3 * 4   # populations read + written, particle impulses read
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = ("fluctuating D3Q19 256^3 periodic FP32 kT=1e-4 + 64 FENE/WCA chains x 256 monomers, "
+            "10 MD sub-steps per LB step")
+SLAB = (256, 256, 4)            # CPU sample: same x-y extent, 4 planes, one chain
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=100)
+    return ap.parse_args()
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v, "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler for the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.tmp.close()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if "Active" in r[5 + k]
+                          and not r[5 + k].startswith("Not")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _cpu_sample(seconds_target=12.0, max_steps=None):
+    """Time the FP64 oracle on a bounded sample: a 256 x 256 x 4 periodic slab
+    (the workload's per-node work) with one chain of 256 monomers, repeated
+    until about `seconds_target` seconds of CPU work."""
+    import numpy as np
+    import oracle as O
+    from paper_0803_2826_gb300 import inputs
+    O.build()
+    p = O.make_params(SLAB, kT=KT, seed=0)
+    pops = O.equilibrium(p)
+    pos = inputs.random_walk_chains(1, CHAIN_LEN, SLAB[:2] + (256,), seed=0)
+    pos[:, 2] = np.mod(pos[:, 2], SLAB[2])
+    mom = inputs.maxwell_momenta(CHAIN_LEN, MASS, KT, seed=1)
+    md = O.make_md(1, CHAIN_LEN, eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0)
+    nodes = SLAB[0] * SLAB[1] * SLAB[2]
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        pos, mom, facc, _ = O.couple(p, pops, pos, mom, MASS, GAMMA, dt=DT, n_substeps=NSUB, seed=2,
+                                     md_step0=NSUB * steps, md=md)
+        pops = O.step(p, pops, facc, steps)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (max_steps and steps >= max_steps) or (not max_steps and el >= seconds_target):
+            break
+    return nodes * steps / el / 1e6, steps, el, O.threads()
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return 0
+    # warm-up steps, then K timed steps; each step is one slab sample
+    _cpu_sample(max_steps=max(args.warmup, 1))
+    mlups, steps, el, cores = _cpu_sample(max_steps=args.steps)
+    line = {
+        "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "256x256x4 periodic slab + 1 chain of 256 per step"},
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "%d steps of a 256x256x4 slab + 1 x 256-monomer chain" % steps},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_0803_2826_gb300 import build as B
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    B.build()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    npart = N_CHAINS * CHAIN_LEN
+    with torch.cuda.stream(stream):
+        lat = L.Lattice(SHAPE, kT=KT, seed=rank, replica=rank, stream=stream)
+        lat.init_equilibrium()
+        pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, SHAPE, seed=rank)
+        mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000 + rank)
+        gpos = torch.as_tensor(pos0).to(dev)
+        gmom = torch.as_tensor(mom0, dtype=torch.float32).to(dev)
+    torch.cuda.synchronize()
+    parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
+    cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=7 + rank, chain_len=CHAIN_LEN, use_wca=True,
+                         eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0)
+    t_step = [0]
+
+    def one_step(ev=None):
+        cp.md_step0 = (NSUB * t_step[0]) & 0xffffffff
+        L.lb_couple_particles(lat.h, parts, cp)
+        if ev is not None:
+            ev[0].record(stream)
+        L.lb_step(lat.h, 1)
+        if ev is not None:
+            ev[1].record(stream)
+        t_step[0] += 1
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+    barrier()
+    st, bits = lat.sync()
+    assert bits == 0, "device error word 0x%x during warm-up" % bits
+
+    K = args.steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = L.lb_get_launch_count(lat.h)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        t0.record(stream)
+        for k in range(K):
+            one_step(evs[k])
+        t1.record(stream)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    launches = L.lb_get_launch_count(lat.h) - launches0
+    ms_total = t0.elapsed_time(t1)
+    sc_ms = [a.elapsed_time(b) for a, b in evs]
+    sc_avg = sum(sc_ms) / len(sc_ms)
+    st, bits = lat.sync()
+    assert bits == 0, "device error word 0x%x" % bits
+
+    # end to end through the public API with host buffers: per step the
+    # particle state goes host -> device from pinned memory, and the particle
+    # state plus the moment sums come back
+    KE = min(args.e2e_steps, K)
+    hpos = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
+    hmom = torch.empty((npart, 3), dtype=torch.float32, pin_memory=True)
+    hsums = torch.empty(L.LB_NSUMS, dtype=torch.float64, pin_memory=True)
+    dsums = torch.empty(L.LB_NSUMS, dtype=torch.float64, device=dev)
+    hpos.copy_(gpos.cpu())
+    hmom.copy_(gmom.cpu())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(KE):
+            gpos.copy_(hpos, non_blocking=True)
+            gmom.copy_(hmom, non_blocking=True)
+            one_step()
+            L.lb_moments(lat.h, None, None, None, dsums)
+            hpos.copy_(gpos, non_blocking=True)
+            hmom.copy_(gmom, non_blocking=True)
+            hsums.copy_(dsums, non_blocking=True)
+        e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    h2d = npart * 3 * 8 + npart * 3 * 4
+    d2h = h2d + L.LB_NSUMS * 8
+
+    # max over ranks
+    vals = torch.tensor([ms_total, sc_avg, e2e_ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+    ms_total, sc_avg, e2e_ms = (float(v) for v in vals.cpu())
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    ms_per_step = ms_total / K
+    value = world * nodes * K / (ms_total * 1e-3) / 1e6
+    e2e_value = world * nodes * KE / (e2e_ms * 1e-3) / 1e6
+    peak, peak_src = _peak_hbm()
+    achieved = BYTES_PER_NODE * nodes / (sc_avg * 1e-3) / 1e9
+    traffic = _profiled_traffic()
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": nodes, "particles": npart, "substeps": NSUB,
+                   "l2": "inputs larger than L2 (2.55 GB populations per replica)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_stream_collide",
+                     "bytes_per_node": BYTES_PER_NODE, "ms_per_launch": sc_avg,
+                     "peak_source": peak_src},
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": KE},
+        "clocks": clk,
+        "wall_s": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        mlups, steps, el, cores = _cpu_sample()
+        line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                                "sample": "%d steps of a 256x256x4 slab + 1 x 256-monomer chain (%.1f s)"
+                                          % (steps, el)}
+    print(json.dumps(line))
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _profiled_traffic():
+    """DRAM bytes per stream-collide launch from the committed ncu summary,
+    if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        from paper_0803_2826_gb300 import build as B
+        if d.get("source_hash") != B.source_hash():
+            return None
+        return float(d["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,235 @@
+/*
+ * lbfluct.h -- C ABI of the GB300 (sm_103a) fluctuating D3Q19 lattice-Boltzmann
+ * library with frictional point-particle coupling.
+ *
+ * Method: Duenweg & Ladd, "Lattice Boltzmann simulations of soft matter
+ * systems" (arXiv 0803.2826).  Section numbers below refer to that paper:
+ *   Sec. 3.3  D3Q19 equilibrium, Eq. (original_equil_distrib)
+ *   Sec. 3.4  MRT collision in the Table 1 moment basis, Eq. (lco_update)
+ *   Sec. 3.5  thermal noise on the non-conserved modes, Eq. (stochupdaterule1)
+ *   Sec. 3.7  external forces (half-force velocity, Sigma), Eq. (moment_two_external_force)
+ *   Sec. 4.1  link bounce-back, Eq. (MBB) with u_b = 0
+ *   Sec. 4.5  force coupling and the Langevin integrator, Eq. (langevin_momentum_update)
+ *   Sec. 4.6  linear interpolation, Eqs. (Delta), (2point)
+ *   Sec. 2.1  Kremer-Grest WCA and FENE potentials, Eqs. (ulennardjones), (ufene)
+ *
+ * Conventions shared by every call
+ *  - Lattice units b = h = 1, c_s^2 = 1/3, nodes at integer coordinates.
+ *  - Velocity order: i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 =
+ *    (1,1,0),(1,-1,0),(-1,1,0),(-1,-1,0),(0,1,1),(0,1,-1),(0,-1,1),(0,-1,-1),
+ *    (1,0,1),(1,0,-1),(-1,0,1),(-1,0,-1).
+ *  - Node index s = x + nx*(y + ny*z).  Field arrays are structure-of-arrays:
+ *    scalar [N], vector [3][N], stress [6][N] in the order xx,yy,zz,xy,yz,zx,
+ *    populations [19][N]; N = nx*ny*nz.
+ *  - The library's population buffers hold the POST-collision state n*_i(r)
+ *    as deviations n_i - a_i rho0 (FP32), or as those deviations times
+ *    pop_scale rounded to nearest-even FP16 / BF16.  One lb_step is "pull
+ *    stream, then collide".  Plane i starts at byte offset
+ *    i * lb_plane_pitch(p) * element size.
+ *  - Every pointer argument named "device" must point to GPU memory of the
+ *    current device; the library never frees caller memory (borrowed).
+ *    Memory the library allocates itself (error word, reduction scratch,
+ *    particle accumulators, neighbour lists) is released by lb_destroy.
+ *  - Every call is asynchronous on the handle's stream unless it says it
+ *    synchronises.  Device-side errors (a broken FENE bond, a neighbour-list
+ *    overflow, non-finite sums, a batched-barrier timeout) are recorded in an
+ *    error word and reported by the next synchronising call.
+ *  - No call aborts or throws; every call returns an lb_status, and
+ *    lb_last_error() gives a message for the last failure on this thread.
+ */
+#ifndef LBFLUCT_H
+#define LBFLUCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LB_OK = 0,
+    LB_EINVAL = 1,        /* bad argument (size, null pointer, parameter range)  */
+    LB_ENOMEM = 2,        /* a library-internal device allocation failed         */
+    LB_ECUDA = 3,         /* a CUDA runtime call failed                          */
+    LB_ENONFINITE = 4,    /* non-finite values detected in reduced moments       */
+    LB_ETIMEOUT = 5,      /* a bounded device-side wait gave up                  */
+    LB_EUNSUPPORTED = 6,  /* combination of options not supported                */
+    LB_EDEVICE = 7        /* device error word set (bits returned by lb_sync)    */
+} lb_status;
+
+typedef enum { LB_F32 = 0, LB_F16 = 1, LB_BF16 = 2 } lb_dtype;
+
+/* Device error-word bits (returned by lb_sync). */
+#define LB_DERR_FENE_BROKEN   0x1u   /* a FENE bond reached r >= R0            */
+#define LB_DERR_NLIST_FULL    0x2u   /* a particle had too many neighbours      */
+#define LB_DERR_NONFINITE     0x4u   /* non-finite moment sum                   */
+#define LB_DERR_BARRIER       0x8u   /* batched kernel: grid barrier timed out  */
+
+#define LB_NSUMS 38  /* lb_moments sums: [0..18] sum_r dm_k, [19..37] sum_r dm_k^2 */
+
+typedef struct {
+    int nx, ny, nz;        /* box size in nodes; each >= 1 (>= 3 along z with walls)   */
+    int dtype;             /* lb_dtype of the stored populations                     */
+    int walls;             /* 0: periodic; 1: solid planes z = 0 and z = nz-1 with
+                              link bounce-back (Sec. 4.1, Eq. (MBB), u_b = 0)          */
+    int noise_rho0;        /* 0: noise amplitude sqrt(w_k mu rho) with the local rho;
+                              1: with rho0 (Sec. 3.5, Eq. (normalized_mk))            */
+    double rho0;           /* reference density (> 0)                               */
+    double kT;             /* k_B T >= 0; mu = kT / c_s^2 (Sec. 3.5)                */
+    double gamma_shear;    /* gamma_s, modes 5..9, |gamma| < 1 (Sec. 3.4)            */
+    double gamma_bulk;     /* gamma_v, mode 4                                       */
+    double gamma_odd;      /* gamma_3a = gamma_3b, kinetic modes 10..15             */
+    double gamma_even;     /* gamma_4a = gamma_4b, kinetic modes 16..18             */
+    double body_force[3];  /* uniform force density f added at every fluid node     */
+    uint64_t seed;         /* Philox key of the fluid noise                          */
+    uint32_t replica;      /* fourth Philox counter word (replica index)            */
+    uint32_t reserved;     /* must be 0                                             */
+    double pop_scale;      /* FP16/BF16 storage scale (0 selects 1024)              */
+} lb_params;
+
+typedef struct lb_handle lb_handle;
+
+/* ---- sizes ------------------------------------------------------------- */
+
+/* Elements per population plane (N rounded up to a multiple of 64). */
+size_t lb_plane_pitch(const lb_params *p);
+/* Bytes of one population buffer: 19 * lb_plane_pitch * element size. */
+size_t lb_population_bytes(const lb_params *p);
+
+/* ---- life cycle ---------------------------------------------------------- */
+
+/* Create a handle over two caller-owned device population buffers (each
+ * lb_population_bytes(p) bytes, 256-byte aligned) and an optional device
+ * force-density field force[3][N] (FP32; NULL for none), added to
+ * p->body_force at every step.  stream: a cudaStream_t (NULL = legacy default).
+ * The handle starts with the state in pops_a and step counter 0.  Buffers are
+ * not initialised: call lb_init_equilibrium or lb_set_populations.
+ * Errors: LB_EINVAL (bad params / pointers), LB_ENOMEM, LB_ECUDA. */
+lb_status lb_create(const lb_params *p, void *pops_a, void *pops_b, float *force,
+                    void *stream, lb_handle **out);
+
+/* Release library-owned memory; never touches the borrowed buffers.  NULL is a no-op. */
+lb_status lb_destroy(lb_handle *h);
+
+/* Message for the last failing call on this thread (never NULL). */
+const char *lb_last_error(void);
+
+/* Synchronise the handle's stream, read and clear the device error word.
+ * Returns LB_EDEVICE (bits in *bits if non-NULL) when it was set. */
+lb_status lb_sync(lb_handle *h, uint32_t *bits);
+
+/* Step counter (the Philox "step" word of the next lb_step). */
+lb_status lb_get_step(const lb_handle *h, uint32_t *step);
+lb_status lb_set_step(lb_handle *h, uint32_t step);
+
+/* Number of kernels this handle has launched so far (for launch accounting). */
+lb_status lb_get_launch_count(const lb_handle *h, uint64_t *count);
+
+/* Device pointer of the buffer that holds the current state, and of the other one. */
+lb_status lb_state_buffers(const lb_handle *h, void **current, void **other);
+
+/* ---- state ------------------------------------------------------------- */
+
+/* Set the stored state to the equilibrium of Eq. (original_equil_distrib) for
+ * device fields rho[N] and u[3][N] (FP64; either may be NULL: rho0, zero). */
+lb_status lb_init_equilibrium(lb_handle *h, const double *rho, const double *u);
+
+/* Copy raw populations n_i (device FP64 [19][N]) into / out of the stored
+ * state, converting to / from the storage format. */
+lb_status lb_set_populations(lb_handle *h, const double *n);
+lb_status lb_get_populations(const lb_handle *h, double *n);
+
+/* ---- the LB step (hot path) ---------------------------------------------- */
+
+/* Advance nsteps >= 0 steps.  Each step pulls n_i(r) = n*_i(r - c_i)
+ * (Eq. (LBE); bounced back at walls), forms rho, j = sum n c + f/2,
+ * u = j / rho (Eq. (special_choice_momentum_density)), relaxes the moments of
+ * Table 1 (Eq. (lco_update), gamma_0..3 = 1), adds the force moments of
+ * Sec. 3.7 and, for kT > 0, the noise sqrt(w_k mu rho)(1 - gamma_k^2)^(1/2) r_k
+ * on modes 4..18 (Eqs. (stochupdaterule1), (detailedbalance1)), transforms
+ * back (Eq. (back_transformation), q = a) and stores n*.  r_4..r_18 are the
+ * first 15 Box-Muller Gaussians of Philox4x32-10 with key (seed lo, seed hi)
+ * and counters (s, step, b, replica), b = 0..3.  f = body_force + force field
+ * + the impulses spread by the last lb_couple_particles (applied once).
+ * Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_step(lb_handle *h, int nsteps);
+
+/* Hydrodynamic moments of the pre-collision state (pull of the stored state):
+ * rho[N], j[3][N] = sum n c + f_ext/2, pi[6][N] = sum n c c (Eqs. (hmodes_beg)-
+ * (hmodes_end)); f_ext = body_force + force field.  sums (device FP64
+ * [LB_NSUMS]): sum over fluid nodes of dm_k and dm_k^2, dm_k = sum_i e_ki
+ * (n_i - a_i rho0) with the basis of Table 1; computed by a deterministic
+ * two-pass reduction in library scratch.  Any output may be NULL.  Solid
+ * nodes give rho0 and zeros.  Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums);
+
+/* ---- point particles (Sec. 4.5, 4.6) ------------------------------------ */
+
+typedef struct {
+    int n;               /* number of particles (>= 0)                              */
+    int reserved;        /* must be 0                                               */
+    double *pos;         /* device [n][3], positions in [0, L); updated in place    */
+    float *mom;          /* device [n][3], momenta; updated in place                */
+    const float *mass;   /* device [n] or NULL (use mass0)                          */
+    const float *gamma;  /* device [n] or NULL (use gamma0): friction Gamma         */
+    double mass0, gamma0;
+} lb_particles;
+
+typedef struct {
+    int n_substeps;      /* particle steps per LB step (>= 1)                        */
+    int noise_kind;      /* 0: Gaussian theta; 1: three-point theta (Sec. 4.5)       */
+    double dt;           /* particle time step in LB steps                           */
+    uint64_t seed;       /* Philox key of the particle noise (domain 1)              */
+    uint32_t md_step0;   /* Philox step word of the first sub-step                   */
+    int chain_len;       /* > 1: particles k*chain_len..(k+1)*chain_len-1 are a FENE chain */
+    int use_wca;         /* purely repulsive LJ between all pairs                    */
+    int reserved;        /* must be 0                                                */
+    double eps, sigma;   /* WCA parameters                                           */
+    double k_fene, r0;   /* FENE parameters                                          */
+} lb_couple_params;
+
+/* One LB step's worth of particle motion.  The fluid velocity
+ * u = (sum n c + f_ext/2)/rho of the current state is held fixed; for each
+ * sub-step: half drift; conservative forces F^c (FENE + WCA); u_p =
+ * sum_8 Delta(r - r_p) u(r) with Delta = phi_2 phi_2 phi_2; exact OU update
+ * p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta; the impulse J = p' - p - C2 F^c
+ * is spread as -J Delta(r - r_p) into a library accumulator that the next
+ * lb_step applies once; half drift.  Positions wrap periodically (x, y; z
+ * without walls) or reflect specularly into z in [1, nz-2] with walls.
+ * theta: Philox domain 1, counters (p, md_step0 + s, 1<<8, replica), key seed.
+ * The caller's pos and mom are updated in place.  Errors: LB_EINVAL,
+ * LB_ENOMEM, LB_ECUDA; broken bonds and neighbour overflow set device bits. */
+lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
+
+/* Interpolated fluid velocity u_p (device FP32 [n][3]) at device positions
+ * pos[n][3] (Eq. (ufluid_discrete) with the linear stencil). */
+lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out);
+
+/* Copy the impulses the next lb_step will apply (device FP32 [3][N] out;
+ * zeros when none are pending). */
+lb_status lb_get_particle_forces(lb_handle *h, float *out);
+
+/* ---- noise streams (for verification) --------------------------------------- */
+
+/* Raw Philox4x32-10 words and their Box-Muller Gaussians as the kernels draw
+ * them (the noise source of Sec. 3.5 and Sec. 4.5).  For q = 0..count-1 and
+ * block b = 0..nblocks-1 (nblocks 1..4) the counter is
+ * (index0 + q, step, domain<<8 | b, replica) and the key (seed lo, seed hi).
+ * words: device uint32 [count][nblocks][4]; gauss: device FP32 of the same
+ * shape (or NULL), pairs (w0, w1) and (w2, w3) of a block mapped to
+ * sqrt(-2 ln v1) (cos, sin)(2 pi v2) with v = (2 (w >> 9) + 1) 2^-24.
+ * stream: a cudaStream_t.  Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_noise_words(uint64_t seed, uint32_t replica, uint32_t step, uint32_t domain, uint32_t index0,
+                         int count, int nblocks, uint32_t *words, float *gauss, void *stream);
+
+/* ---- library information ------------------------------------------------- */
+
+/* "lbfluct <version> sm_103a" */
+const char *lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBFLUCT_H */

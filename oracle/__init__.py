@@ -93,6 +93,7 @@ def _load():
     with _lock:
         if _lib is None:
             lib = C.CDLL(build())
+            lib.ora_threads.restype = C.c_int
             lib.ora_tables.argtypes = [C.POINTER(C.c_int), _D, _D, _D, C.POINTER(C.c_int)]
             lib.ora_philox4x32_10.argtypes = [_U32, _U32, _U32]
             lib.ora_uniform.argtypes = [C.c_uint32]
@@ -141,6 +142,11 @@ def make_params(shape, *, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0,
     p.seed = int(seed)
     p.replica = int(replica)
     return p
+
+
+def threads() -> int:
+    """OpenMP threads the oracle's loops use."""
+    return int(_load().ora_threads())
 
 
 def tables():

@@ -31,6 +31,9 @@
  *    Box-Muller pairs.
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -117,6 +120,16 @@ static void build_tables(void)
         g_w[k] = s;
     }
     g_ready = 1;
+}
+
+/* Threads the OpenMP loops use (1 without OpenMP). */
+int ora_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Export the tables so the tests can check them against the paper. */

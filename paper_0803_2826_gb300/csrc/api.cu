@@ -1,0 +1,409 @@
+// api.cu -- the C ABI of lbfluct.h: handle life cycle, argument checks,
+// error reporting and the step loop.  Kernels live in stream_collide.cuh,
+// moments.cu and particles.cu.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "lbf_internal.h"
+
+namespace lbi {
+
+template <int DT>
+cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc);
+extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *);
+extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const void *, void *, const float *);
+extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *);
+
+namespace {
+thread_local char g_msg[512] = "no error";
+}
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+}
+
+lb_status cuda_fail(const char *what, cudaError_t e)
+{
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return LB_ECUDA;
+}
+
+int device_sm_count()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 1;
+    return n;
+}
+
+StepArgs make_args(const lb_handle *h)
+{
+    const lb_params &p = h->p;
+    StepArgs a;
+    a.nx = p.nx;
+    a.ny = p.ny;
+    a.nz = p.nz;
+    a.z0 = p.walls ? 1 : 0;
+    a.z1 = p.walls ? p.nz - 1 : p.nz;
+    a.pitch = h->pitch;
+    a.nn = h->n_nodes;
+    a.rho0 = (float)p.rho0;
+    a.kT = (float)p.kT;
+    a.mu = (float)(p.kT * 3.0);
+    a.g_shear = (float)p.gamma_shear;
+    a.g_bulk = (float)p.gamma_bulk;
+    a.g_odd = (float)p.gamma_odd;
+    a.g_even = (float)p.gamma_even;
+    a.phi_shear = (float)std::sqrt(1.0 - p.gamma_shear * p.gamma_shear);
+    a.phi_bulk = (float)std::sqrt(1.0 - p.gamma_bulk * p.gamma_bulk);
+    a.phi_odd = (float)std::sqrt(1.0 - p.gamma_odd * p.gamma_odd);
+    a.phi_even = (float)std::sqrt(1.0 - p.gamma_even * p.gamma_even);
+    a.fx = (float)p.body_force[0];
+    a.fy = (float)p.body_force[1];
+    a.fz = (float)p.body_force[2];
+    const double sc = (p.dtype == LB_F32) ? 1.0 : (p.pop_scale > 0.0 ? p.pop_scale : 1024.0);
+    a.scale = (float)sc;
+    a.inv_scale = (float)(1.0 / sc);
+    a.noise_rho0 = p.noise_rho0;
+    a.key0 = (uint32_t)(p.seed & 0xffffffffu);
+    a.key1 = (uint32_t)(p.seed >> 32);
+    a.replica = p.replica;
+    a.step = h->step;
+    return a;
+}
+
+}  // namespace lbi
+
+using namespace lbi;
+
+namespace {
+
+size_t elem_size(int dtype) { return dtype == LB_F32 ? 4 : 2; }
+
+bool check_params(const lb_params *p)
+{
+    if (!p) {
+        set_error("lb_params is NULL");
+        return false;
+    }
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1) {
+        set_error("box %d x %d x %d: every edge must be >= 1", p->nx, p->ny, p->nz);
+        return false;
+    }
+    const double n = (double)p->nx * p->ny * p->nz;
+    if (n > 2147483647.0) {
+        set_error("box of %.0f nodes exceeds 2^31 - 1 nodes", n);
+        return false;
+    }
+    if (p->dtype < LB_F32 || p->dtype > LB_BF16) {
+        set_error("dtype %d is not one of LB_F32, LB_F16, LB_BF16", p->dtype);
+        return false;
+    }
+    if (p->walls != 0 && p->walls != 1) {
+        set_error("walls must be 0 or 1");
+        return false;
+    }
+    if (p->walls && p->nz < 3) {
+        set_error("walls need nz >= 3 (two solid planes and one fluid plane)");
+        return false;
+    }
+    if (!(p->rho0 > 0.0) || !std::isfinite(p->rho0)) {
+        set_error("rho0 must be finite and > 0");
+        return false;
+    }
+    if (!(p->kT >= 0.0) || !std::isfinite(p->kT)) {
+        set_error("kT must be finite and >= 0");
+        return false;
+    }
+    const double g[4] = {p->gamma_shear, p->gamma_bulk, p->gamma_odd, p->gamma_even};
+    for (double v : g) {
+        if (!(v > -1.0 && v < 1.0)) {
+            set_error("relaxation eigenvalues must satisfy |gamma| < 1 (got %g)", v);
+            return false;
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        if (!std::isfinite(p->body_force[d])) {
+            set_error("body_force must be finite");
+            return false;
+        }
+    }
+    if (p->pop_scale < 0.0 || !std::isfinite(p->pop_scale)) {
+        set_error("pop_scale must be >= 0 (0 selects 1024)");
+        return false;
+    }
+    if (p->reserved != 0) {
+        set_error("lb_params.reserved must be 0");
+        return false;
+    }
+    return true;
+}
+
+bool aligned256(const void *ptr) { return ((uintptr_t)ptr & 255u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *lb_last_error(void) { return g_msg; }
+
+const char *lb_version(void) { return "lbfluct 0.1.0 sm_103a"; }
+
+size_t lb_plane_pitch(const lb_params *p)
+{
+    if (!check_params(p)) return 0;
+    const size_t n = (size_t)p->nx * p->ny * p->nz;
+    return (n + 63) / 64 * 64;
+}
+
+size_t lb_population_bytes(const lb_params *p)
+{
+    const size_t pitch = lb_plane_pitch(p);
+    return pitch ? 19 * pitch * elem_size(p->dtype) : 0;
+}
+
+lb_status lb_create(const lb_params *p, void *pops_a, void *pops_b, float *force, void *stream,
+                    lb_handle **out)
+{
+    if (!out) {
+        set_error("lb_create: out is NULL");
+        return LB_EINVAL;
+    }
+    *out = nullptr;
+    if (!check_params(p)) return LB_EINVAL;
+    if (!pops_a || !pops_b || pops_a == pops_b) {
+        set_error("lb_create: need two distinct population buffers");
+        return LB_EINVAL;
+    }
+    if (!aligned256(pops_a) || !aligned256(pops_b)) {
+        set_error("lb_create: population buffers must be 256-byte aligned");
+        return LB_EINVAL;
+    }
+    if (force && ((uintptr_t)force & 3u)) {
+        set_error("lb_create: force field must be 4-byte aligned");
+        return LB_EINVAL;
+    }
+    lb_handle *h = (lb_handle *)calloc(1, sizeof(lb_handle));
+    if (!h) {
+        set_error("lb_create: host allocation failed");
+        return LB_ENOMEM;
+    }
+    h->p = *p;
+    h->n_nodes = (size_t)p->nx * p->ny * p->nz;
+    h->pitch = lb_plane_pitch(p);
+    h->elem = elem_size(p->dtype);
+    h->pops[0] = pops_a;
+    h->pops[1] = pops_b;
+    h->cur = 0;
+    h->force = force;
+    h->stream = (cudaStream_t)stream;
+    h->step = 0;
+    h->red_blocks = 4 * device_sm_count();
+    cudaError_t e = cudaMalloc((void **)&h->d_err, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, sizeof(double) * LB_NSUMS * h->red_blocks);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+    if (e != cudaSuccess) {
+        lb_destroy(h);
+        set_error("lb_create: device allocation failed (%s)", cudaGetErrorString(e));
+        return LB_ENOMEM;
+    }
+    *out = h;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_handle *h)
+{
+    if (!h) return LB_OK;
+    destroy_particles(h);
+    if (h->d_err) cudaFree(h->d_err);
+    if (h->d_partials) cudaFree(h->d_partials);
+    if (h->facc) cudaFree(h->facc);
+    free(h);
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_handle *h, uint32_t *bits)
+{
+    if (!h) {
+        set_error("lb_sync: handle is NULL");
+        return LB_EINVAL;
+    }
+    unsigned int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail("lb_sync", e);
+    if (bits) *bits = v;
+    if (v) {
+        e = cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail("lb_sync", e);
+        set_error("device error word 0x%x%s%s%s%s", v, (v & LB_DERR_FENE_BROKEN) ? " [FENE bond broken]" : "",
+                  (v & LB_DERR_NLIST_FULL) ? " [neighbour list full]" : "",
+                  (v & LB_DERR_NONFINITE) ? " [non-finite sums]" : "",
+                  (v & LB_DERR_BARRIER) ? " [grid barrier timeout]" : "");
+        if (v & LB_DERR_NONFINITE) return LB_ENONFINITE;
+        if (v & LB_DERR_BARRIER) return LB_ETIMEOUT;
+        return LB_EDEVICE;
+    }
+    return LB_OK;
+}
+
+lb_status lb_get_step(const lb_handle *h, uint32_t *step)
+{
+    if (!h || !step) {
+        set_error("lb_get_step: NULL argument");
+        return LB_EINVAL;
+    }
+    *step = h->step;
+    return LB_OK;
+}
+
+lb_status lb_set_step(lb_handle *h, uint32_t step)
+{
+    if (!h) {
+        set_error("lb_set_step: handle is NULL");
+        return LB_EINVAL;
+    }
+    h->step = step;
+    return LB_OK;
+}
+
+lb_status lb_state_buffers(const lb_handle *h, void **current, void **other)
+{
+    if (!h) {
+        set_error("lb_state_buffers: handle is NULL");
+        return LB_EINVAL;
+    }
+    if (current) *current = h->pops[h->cur];
+    if (other) *other = h->pops[1 - h->cur];
+    return LB_OK;
+}
+
+lb_status lb_init_equilibrium(lb_handle *h, const double *rho, const double *u)
+{
+    if (!h) {
+        set_error("lb_init_equilibrium: handle is NULL");
+        return LB_EINVAL;
+    }
+    cudaError_t e = launch_init_equilibrium(h, h->pops[h->cur], rho, u);
+    h->launches += 1;
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_init_equilibrium", e);
+}
+
+lb_status lb_set_populations(lb_handle *h, const double *n)
+{
+    if (!h || !n) {
+        set_error("lb_set_populations: NULL argument");
+        return LB_EINVAL;
+    }
+    cudaError_t e = launch_set_populations(h, h->pops[h->cur], n);
+    h->launches += 1;
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_set_populations", e);
+}
+
+lb_status lb_get_launch_count(const lb_handle *h, uint64_t *count)
+{
+    if (!h || !count) {
+        set_error("lb_get_launch_count: NULL argument");
+        return LB_EINVAL;
+    }
+    *count = h->launches;
+    return LB_OK;
+}
+
+lb_status lb_get_populations(const lb_handle *h, double *n)
+{
+    if (!h || !n) {
+        set_error("lb_get_populations: NULL argument");
+        return LB_EINVAL;
+    }
+    cudaError_t e = launch_get_populations(h, h->pops[h->cur], n);
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_get_populations", e);
+}
+
+lb_status lb_step(lb_handle *h, int nsteps)
+{
+    if (!h) {
+        set_error("lb_step: handle is NULL");
+        return LB_EINVAL;
+    }
+    if (nsteps < 0) {
+        set_error("lb_step: nsteps = %d < 0", nsteps);
+        return LB_EINVAL;
+    }
+    for (int t = 0; t < nsteps; ++t) {
+        const float *facc = h->facc_dirty ? h->facc : nullptr;
+        cudaError_t e;
+        switch (h->p.dtype) {
+        case LB_F32: e = launch_stream_collide_dt<0>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
+        case LB_F16: e = launch_stream_collide_dt<1>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
+        default: e = launch_stream_collide_dt<2>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
+        }
+        if (e != cudaSuccess) return cuda_fail("lb_step", e);
+        h->launches += 1;
+        if (facc) {  // applied once; cleared by the next lb_couple_particles
+            h->facc_dirty = 0;
+            h->facc_stale = 1;
+        }
+        h->cur = 1 - h->cur;
+        h->step += 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums)
+{
+    if (!h) {
+        set_error("lb_moments: handle is NULL");
+        return LB_EINVAL;
+    }
+    if (!rho && !j && !pi && !sums) return LB_OK;
+    cudaError_t e = launch_moments(h, h->pops[h->cur], rho, j, pi, sums);
+    h->launches += sums ? 2 : 1;
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_moments", e);
+}
+
+lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp)
+{
+    if (!h || !parts || !cp) {
+        set_error("lb_couple_particles: NULL argument");
+        return LB_EINVAL;
+    }
+    return couple_particles(h, parts, cp);
+}
+
+lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out)
+{
+    if (!h || n < 0 || (n > 0 && (!pos || !u_out))) {
+        set_error("lb_interpolate: bad argument");
+        return LB_EINVAL;
+    }
+    return interpolate(h, n, pos, u_out);
+}
+
+lb_status lb_get_particle_forces(lb_handle *h, float *out)
+{
+    if (!h || !out) {
+        set_error("lb_get_particle_forces: NULL argument");
+        return LB_EINVAL;
+    }
+    const size_t N = h->n_nodes;
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
+        if (h->facc && h->facc_dirty)
+            e = cudaMemcpyAsync(out + d * N, h->facc + d * h->pitch, N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                h->stream);
+        else
+            e = cudaMemsetAsync(out + d * N, 0, N * sizeof(float), h->stream);
+    }
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_get_particle_forces", e);
+}
+
+}  // extern "C"

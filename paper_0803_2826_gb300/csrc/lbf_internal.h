@@ -1,0 +1,81 @@
+// lbf_internal.h -- handle layout and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "lbfluct.h"
+
+namespace lbi {
+
+// Geometry and physics constants a kernel launch needs, in FP32 where the
+// kernels compute in FP32.
+struct StepArgs {
+    int nx, ny, nz;
+    int z0, z1;            // fluid z-range [z0, z1)
+    size_t pitch;          // elements per population plane
+    size_t nn;             // nodes nx*ny*nz (component stride of caller fields)
+    float rho0;
+    float kT;
+    float mu;              // kT / c_s^2
+    float g_shear, g_bulk, g_odd, g_even;
+    float phi_shear, phi_bulk, phi_odd, phi_even;  // sqrt(1 - gamma^2)
+    float fx, fy, fz;      // uniform body force
+    float scale, inv_scale;  // storage scale of FP16/BF16 deviations
+    int noise_rho0;
+    uint32_t key0, key1;   // Philox key (seed)
+    uint32_t replica;
+    uint32_t step;
+};
+
+struct Particles;  // defined in particles.cu
+
+}  // namespace lbi
+
+struct lb_handle {
+    lb_params p;
+    size_t n_nodes;
+    size_t pitch;
+    size_t elem;          // bytes per stored population value
+    void *pops[2];        // borrowed
+    int cur;              // pops[cur] holds the current state
+    float *force;         // borrowed, nullable
+    cudaStream_t stream;
+    uint32_t step;
+    // library-owned
+    unsigned int *d_err;  // device error word
+    double *d_partials;   // reduction scratch [nblocks][LB_NSUMS]
+    int red_blocks;
+    float *facc;          // particle impulse accumulator [3][pitch]
+    int facc_dirty;       // facc holds impulses the next lb_step applies
+    int facc_stale;       // facc holds applied impulses not yet cleared
+    uint64_t launches;    // kernels launched through this handle
+    lbi::Particles *parts;
+};
+
+namespace lbi {
+
+void set_error(const char *fmt, ...);
+lb_status cuda_fail(const char *what, cudaError_t e);
+StepArgs make_args(const lb_handle *h);
+int device_sm_count();
+
+// stream_collide.cu
+cudaError_t launch_stream_collide(const lb_handle *h, const void *src, void *dst, const float *facc);
+// moments.cu
+cudaError_t launch_init_equilibrium(const lb_handle *h, void *dst, const double *rho, const double *u);
+cudaError_t launch_set_populations(const lb_handle *h, void *dst, const double *n);
+cudaError_t launch_get_populations(const lb_handle *h, const void *src, double *n);
+cudaError_t launch_moments(const lb_handle *h, const void *src, float *rho, float *j, float *pi,
+                           double *sums);
+// particles.cu
+lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
+lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out);
+cudaError_t clear_particle_forces(lb_handle *h);
+void destroy_particles(lb_handle *h);
+
+}  // namespace lbi

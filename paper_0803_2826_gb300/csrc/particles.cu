@@ -1,0 +1,660 @@
+// particles.cu -- frictional point-particle coupling (Sec. 4.5) with the
+// linear interpolation kernel of Sec. 4.6, and the Kremer-Grest forces of
+// Sec. 2.1 for bead-spring chains.
+//
+// Per LB step the caller runs n_substeps particle steps against the frozen
+// fluid velocity u = (sum n c + f_ext/2)/rho of the current state.  One
+// kernel launch per sub-step does, for each particle p (one thread):
+//   forces     F^c from FENE bonds (chain neighbours p-1, p+1) and WCA pairs
+//              from a Verlet list (Eqs. (ufene), (ulennardjones))
+//   interpolate u_p = sum_8 phi2 phi2 phi2 u(node)            Eqs. (ufluid_discrete), (Delta), (2point)
+//   OU update  p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta     Eq. (langevin_momentum_update)
+//   spread     facc(node) -= J Delta(node - r_p), J = p' - p - C2 F^c   Eq. (ftotal)
+//   drift      second half drift of this sub-step and first half drift of the next
+// The half-drift positions ping-pong between the caller's buffer and an
+// internal one, so every thread reads the positions of the same sub-step.
+// The Verlet list (cut-off + skin) is rebuilt, inside a launch that returns
+// at once when nothing moved far enough, whenever a particle has moved more
+// than half the skin since the last build.
+#include <algorithm>
+#include <cstdio>
+
+#include "d3q19.cuh"
+#include "lbf_internal.h"
+
+namespace lbi {
+
+constexpr int kMaxNb = 48;          // Verlet-list capacity per particle
+constexpr float kSkin = 0.4f;       // Verlet skin in units of sigma
+constexpr int kPartThreads = 128;
+
+struct Particles {
+    int cap = 0;
+    double *pos_tmp = nullptr;   // [cap][3]
+    int *records = nullptr;      // base node of each (sub-step, particle) stencil
+    size_t rec_cap = 0;
+    size_t n_records = 0;
+    bool records_overflow = false;
+    int *nlist = nullptr;        // [cap][kMaxNb]
+    int *ncount = nullptr;       // [cap]
+    float *ref_pos = nullptr;    // [cap][3] positions at the last build
+    unsigned int *flags = nullptr;  // two rebuild-request slots
+    uint32_t sub_counter = 0;
+    int nlist_n = -1;            // particle count the list was built for
+};
+
+namespace {
+
+struct CoupleArgs {
+    StepArgs g;
+    int n;
+    int chain_len;
+    int use_wca;
+    int noise_kind;
+    float dt;
+    float mass0, gamma0;
+    float eps, sigma2, rc2, rlist2, k_fene, inv_r02;
+    uint32_t pkey0, pkey1;
+    uint32_t md_step;
+    int last;          // last sub-step of this call
+    uint32_t slot;     // rebuild slot written by this sub-step
+};
+
+__device__ __forceinline__ void confine(double r[3], float p[3], const StepArgs &g)
+{
+    const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
+    const bool walls = g.z0 > 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c == 2 && walls) {
+            const double lo = 1.0, hi = (double)(g.nz - 2);
+            if (r[2] < lo) { r[2] = 2.0 * lo - r[2]; p[2] = -p[2]; }
+            if (r[2] > hi) { r[2] = 2.0 * hi - r[2]; p[2] = -p[2]; }
+        } else {
+            r[c] -= L[c] * floor(r[c] / L[c]);
+            if (r[c] >= L[c]) r[c] -= L[c];
+        }
+    }
+}
+
+// Fluid velocity at node (x, y, z): pull-gather of the stored state,
+// u = (sum n c + f_ext/2) / rho.  Solid nodes give 0.
+template <int DT>
+__device__ __forceinline__ void node_velocity(const typename lbd::Store<DT>::T *__restrict__ src,
+                                              const float *__restrict__ ffield, int x, int y, int z,
+                                              const StepArgs &a, float u[3])
+{
+    using S = lbd::Store<DT>;
+    if (z < a.z0 || z >= a.z1) {
+        u[0] = u[1] = u[2] = 0.0f;
+        return;
+    }
+    const bool walls = a.z0 > 0;
+    const int xm = (x == 0) ? a.nx - 1 : x - 1, xp = (x == a.nx - 1) ? 0 : x + 1;
+    const int ym = (y == 0) ? a.ny - 1 : y - 1, yp = (y == a.ny - 1) ? 0 : y + 1;
+    int zm, zp;
+    if (walls) {
+        zm = z - 1;
+        zp = z + 1;
+    } else {
+        zm = (z == 0) ? a.nz - 1 : z - 1;
+        zp = (z == a.nz - 1) ? 0 : z + 1;
+    }
+    const size_t self = ((size_t)z * a.ny + y) * a.nx + x;
+    float rho = 0.0f, jx = 0.0f, jy = 0.0f, jz = 0.0f;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sx = lbd::cx(i) == 1 ? xm : (lbd::cx(i) == -1 ? xp : x);
+        const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+        const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+        const bool bounce = walls && lbd::cz(i) != 0 && (sz == 0 || sz == a.nz - 1);
+        const size_t off = bounce ? ((size_t)lbd::opposite(i) * a.pitch + self)
+                                  : ((size_t)i * a.pitch + ((size_t)sz * a.ny + sy) * a.nx + sx);
+        const float v = S::cvt(src[off], a.inv_scale);
+        rho += v;
+        if (lbd::cx(i)) jx += lbd::cx(i) * v;
+        if (lbd::cy(i)) jy += lbd::cy(i) * v;
+        if (lbd::cz(i)) jz += lbd::cz(i) * v;
+    }
+    rho += a.rho0;
+    float fx = a.fx, fy = a.fy, fz = a.fz;
+    if (ffield) {
+        fx += ffield[self];
+        fy += ffield[a.nn + self];
+        fz += ffield[2 * a.nn + self];
+    }
+    const float ir = 1.0f / rho;
+    u[0] = (jx + 0.5f * fx) * ir;
+    u[1] = (jy + 0.5f * fy) * ir;
+    u[2] = (jz + 0.5f * fz) * ir;
+}
+
+// Linear stencil: base node and the three 1-D weight pairs (1 - t, t).
+__device__ __forceinline__ void stencil_base(const double r[3], int b[3], float t[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double f = floor(r[c]);
+        b[c] = (int)f;
+        t[c] = (float)(r[c] - f);
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ void interpolate_u(const typename lbd::Store<DT>::T *__restrict__ src,
+                                              const float *__restrict__ ffield, const double r[3],
+                                              const StepArgs &a, int b[3], float t[3], float up[3])
+{
+    stencil_base(r, b, t);
+    up[0] = up[1] = up[2] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+        const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
+        int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
+        if (x >= a.nx) x -= a.nx;
+        if (y >= a.ny) y -= a.ny;
+        if (z >= a.nz) z = (a.z0 > 0) ? a.nz - 1 : z - a.nz;
+        float u[3];
+        node_velocity<DT>(src, ffield, x, y, z, a, u);
+        up[0] += w * u[0];
+        up[1] += w * u[1];
+        up[2] += w * u[2];
+    }
+}
+
+__device__ __forceinline__ void min_image(float d[3], const StepArgs &g)
+{
+    const float L[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
+    const bool walls = g.z0 > 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (c == 2 && walls) continue;
+        d[c] -= L[c] * rintf(d[c] / L[c]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+__global__ void k_half_drift(double *pos, float *mom, const float *mass, CoupleArgs c)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.n) return;
+    const float m = mass ? mass[p] : c.mass0;
+    double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+    float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
+    const double h = 0.5 * (double)c.dt / (double)m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] += h * (double)pm[k];
+    confine(r, pm, c.g);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pos[3 * p + k] = r[k];
+        mom[3 * p + k] = pm[k];
+    }
+}
+
+// Verlet-list build over all pairs, tiled through shared memory; returns at
+// once unless a rebuild was requested in slot `rd`.
+constexpr int kTile = 256;
+
+__global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *nlist, int *ncount, float *ref_pos,
+                                                       unsigned int *flags, unsigned int *err, CoupleArgs c,
+                                                       uint32_t rd)
+{
+    if (flags[rd] == 0u) return;
+    __shared__ float sp[kTile][3];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float ri[3] = {0.f, 0.f, 0.f};
+    if (i < c.n) {
+        ri[0] = (float)pos[3 * i];
+        ri[1] = (float)pos[3 * i + 1];
+        ri[2] = (float)pos[3 * i + 2];
+    }
+    int cnt = 0;
+    bool full = false;
+    for (int base = 0; base < c.n; base += kTile) {
+        const int j = base + threadIdx.x;
+        if (j < c.n) {
+            sp[threadIdx.x][0] = (float)pos[3 * j];
+            sp[threadIdx.x][1] = (float)pos[3 * j + 1];
+            sp[threadIdx.x][2] = (float)pos[3 * j + 2];
+        }
+        __syncthreads();
+        const int lim = min(kTile, c.n - base);
+        if (i < c.n) {
+            for (int q = 0; q < lim; ++q) {
+                const int jj = base + q;
+                if (jj == i) continue;
+                float d[3] = {ri[0] - sp[q][0], ri[1] - sp[q][1], ri[2] - sp[q][2]};
+                min_image(d, c.g);
+                const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 < c.rlist2) {
+                    if (cnt < kMaxNb) nlist[(size_t)i * kMaxNb + cnt] = jj;
+                    else full = true;
+                    ++cnt;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (i < c.n) {
+        ncount[i] = cnt < kMaxNb ? cnt : kMaxNb;
+        ref_pos[3 * i] = ri[0];
+        ref_pos[3 * i + 1] = ri[1];
+        ref_pos[3 * i + 2] = ri[2];
+        if (full) atomicOr(err, LB_DERR_NLIST_FULL);
+    }
+}
+
+__global__ void k_clear_flag(unsigned int *flags, uint32_t slot) { flags[slot] = 0u; }
+
+template <int DT>
+__global__ void __launch_bounds__(kPartThreads)
+    k_substep(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
+              const double *__restrict__ pos_in, double *__restrict__ pos_out, float *mom, const float *mass,
+              const float *gamma, const int *nlist, const int *ncount, const float *ref_pos, float *facc,
+              int *records, unsigned int *flags, unsigned int *err, CoupleArgs c)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.n) return;
+    const StepArgs &g = c.g;
+    double r[3] = {pos_in[3 * p], pos_in[3 * p + 1], pos_in[3 * p + 2]};
+    float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
+    const float m = mass ? mass[p] : c.mass0;
+    const float G = gamma ? gamma[p] : c.gamma0;
+
+    // conservative forces at the half-step positions
+    float F[3] = {0.f, 0.f, 0.f};
+    if (c.use_wca) {
+        const int nc = ncount[p];
+        for (int q = 0; q < nc; ++q) {
+            const int j = nlist[(size_t)p * kMaxNb + q];
+            float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
+                          (float)(r[2] - pos_in[3 * j + 2])};
+            min_image(d, g);
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (r2 < c.rc2) {
+                const float sr2 = c.sigma2 / r2;
+                const float sr6 = sr2 * sr2 * sr2;
+                const float mag = 24.0f * c.eps * (2.0f * sr6 * sr6 - sr6) / r2;
+                F[0] += mag * d[0];
+                F[1] += mag * d[1];
+                F[2] += mag * d[2];
+            }
+        }
+    }
+    if (c.chain_len > 1) {
+        const int k = p % c.chain_len;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int j = side == 0 ? p - 1 : p + 1;
+            if ((side == 0 && k == 0) || (side == 1 && (k == c.chain_len - 1 || j >= c.n))) continue;
+            float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
+                          (float)(r[2] - pos_in[3 * j + 2])};
+            min_image(d, g);
+            const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
+            if (x >= 1.0f) {
+                atomicOr(err, LB_DERR_FENE_BROKEN);
+            } else {
+                const float mag = -c.k_fene / (1.0f - x);
+                F[0] += mag * d[0];
+                F[1] += mag * d[1];
+                F[2] += mag * d[2];
+            }
+        }
+    }
+
+    // fluid velocity at the particle
+    int b[3];
+    float t[3], up[3];
+    interpolate_u<DT>(src, ffield, r, g, b, t, up);
+
+    // exact Ornstein-Uhlenbeck momentum update
+    const float x1 = G * c.dt / m;
+    const float C1 = expf(-x1);
+    const float C2 = (m / G) * (-expm1f(-x1));
+    const float C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+    float th[3] = {0.f, 0.f, 0.f};
+    if (g.kT > 0.0f) {
+        const lbd::U4 w = lbd::philox10(lbd::U4{(uint32_t)p, c.md_step, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
+        if (c.noise_kind == 1) {
+            const uint32_t ws[3] = {w.x, w.y, w.z};
+            const float s3 = 1.7320508075688772f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const uint64_t kk = 2ull * (uint64_t)(ws[k] >> 9) + 1ull;  // uniform = kk / 2^24
+                th[k] = (6ull * kk < (1ull << 24)) ? -s3 : ((6ull * kk > 5ull * (1ull << 24)) ? s3 : 0.0f);
+            }
+        } else {
+            float g3;
+            lbd::box_muller(w.x, w.y, th[0], th[1]);
+            lbd::box_muller(w.z, w.w, th[2], g3);
+        }
+    }
+    float pn[3], J[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
+        J[k] = pn[k] - pm[k] - C2 * F[k];
+    }
+
+    // spread -J Delta into the accumulator
+    const size_t P = g.pitch;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+        const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
+        int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
+        if (x >= g.nx) x -= g.nx;
+        if (y >= g.ny) y -= g.ny;
+        if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+        const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+        atomicAdd(facc + s, -J[0] * w);
+        atomicAdd(facc + P + s, -J[1] * w);
+        atomicAdd(facc + 2 * P + s, -J[2] * w);
+    }
+    if (records) records[p] = (int)(((size_t)b[2] * g.ny + b[1]) * g.nx + b[0]);
+
+    // second half drift of this sub-step, then the first of the next one
+    const double h = 0.5 * (double)c.dt / (double)m;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r[k] += h * (double)pn[k];
+    confine(r, pn, g);
+    if (!c.last) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] += h * (double)pn[k];
+        confine(r, pn, g);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        pos_out[3 * p + k] = r[k];
+        mom[3 * p + k] = pn[k];
+    }
+    if (ref_pos) {
+        float d[3] = {(float)r[0] - ref_pos[3 * p], (float)r[1] - ref_pos[3 * p + 1], (float)r[2] - ref_pos[3 * p + 2]};
+        min_image(d, g);
+        const float half = 0.5f * kSkin * sqrtf(c.sigma2);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > half * half) flags[c.slot] = 1u;
+    }
+}
+
+// Zero the eight accumulator nodes around each recorded stencil base.
+__global__ void k_clear_records(float *facc, const int *records, size_t n, StepArgs g)
+{
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const int base = records[q];
+        const int x0 = base % g.nx;
+        const int y0 = (base / g.nx) % g.ny;
+        const int z0 = base / (g.nx * g.ny);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int x = x0 + (k & 1), y = y0 + ((k >> 1) & 1), z = z0 + (k >> 2);
+            if (x >= g.nx) x -= g.nx;
+            if (y >= g.ny) y -= g.ny;
+            if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+            const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+            facc[s] = 0.0f;
+            facc[g.pitch + s] = 0.0f;
+            facc[2 * g.pitch + s] = 0.0f;
+        }
+    }
+}
+
+template <int DT>
+__global__ void k_interpolate(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
+                              const double *pos, float *u_out, int n, StepArgs g)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+    int b[3];
+    float t[3], up[3];
+    interpolate_u<DT>(src, ffield, r, g, b, t, up);
+    u_out[3 * p] = up[0];
+    u_out[3 * p + 1] = up[1];
+    u_out[3 * p + 2] = up[2];
+}
+
+void free_parts(Particles *P)
+{
+    if (!P) return;
+    cudaFree(P->pos_tmp);
+    cudaFree(P->records);
+    cudaFree(P->nlist);
+    cudaFree(P->ncount);
+    cudaFree(P->ref_pos);
+    cudaFree(P->flags);
+    delete P;
+}
+
+lb_status ensure_buffers(lb_handle *h, int n, int nsub)
+{
+    if (!h->facc) {
+        cudaError_t e = cudaMalloc((void **)&h->facc, 3 * h->pitch * sizeof(float));
+        if (e != cudaSuccess) {
+            set_error("lb_couple_particles: accumulator allocation failed (%s)", cudaGetErrorString(e));
+            return LB_ENOMEM;
+        }
+        e = cudaMemsetAsync(h->facc, 0, 3 * h->pitch * sizeof(float), h->stream);
+        if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+    }
+    if (!h->parts) h->parts = new Particles();
+    Particles *P = h->parts;
+    if (P->cap < n) {
+        cudaFree(P->pos_tmp);
+        cudaFree(P->nlist);
+        cudaFree(P->ncount);
+        cudaFree(P->ref_pos);
+        P->pos_tmp = nullptr;
+        P->nlist = nullptr;
+        P->ncount = nullptr;
+        P->ref_pos = nullptr;
+        cudaError_t e = cudaMalloc((void **)&P->pos_tmp, (size_t)n * 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kMaxNb * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ref_pos, (size_t)n * 3 * sizeof(float));
+        if (e != cudaSuccess) {
+            P->cap = 0;
+            set_error("lb_couple_particles: particle buffer allocation failed (%s)", cudaGetErrorString(e));
+            return LB_ENOMEM;
+        }
+        P->cap = n;
+        P->nlist_n = -1;
+    }
+    if (!P->flags) {
+        cudaError_t e = cudaMalloc((void **)&P->flags, 2 * sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            set_error("lb_couple_particles: flag allocation failed");
+            return LB_ENOMEM;
+        }
+    }
+    const size_t need = (size_t)n * (size_t)nsub;
+    if (P->rec_cap < P->n_records + need) {
+        // grow, keeping the records not yet cleared
+        int *nr = nullptr;
+        const size_t cap = (P->n_records + need) * 2;
+        cudaError_t e = cudaMalloc((void **)&nr, cap * sizeof(int));
+        if (e != cudaSuccess) {
+            set_error("lb_couple_particles: record allocation failed");
+            return LB_ENOMEM;
+        }
+        if (P->n_records) {
+            e = cudaMemcpyAsync(nr, P->records, P->n_records * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+            e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+        }
+        cudaFree(P->records);
+        P->records = nr;
+        P->rec_cap = cap;
+    }
+    return LB_OK;
+}
+
+template <int DT>
+cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
+{
+    Particles *P = h->parts;
+    const int n = pp->n;
+    CoupleArgs c;
+    c.g = make_args(h);
+    c.n = n;
+    c.chain_len = cp->chain_len;
+    c.use_wca = cp->use_wca;
+    c.noise_kind = cp->noise_kind;
+    c.dt = (float)cp->dt;
+    c.mass0 = (float)pp->mass0;
+    c.gamma0 = (float)pp->gamma0;
+    c.eps = (float)cp->eps;
+    c.sigma2 = (float)(cp->sigma * cp->sigma);
+    c.rc2 = (float)(cp->sigma * cp->sigma * 1.2599210498948732);  // (2^(1/6) sigma)^2
+    const double rl = 1.122462048309373 * cp->sigma + kSkin * cp->sigma;
+    c.rlist2 = (float)(rl * rl);
+    c.k_fene = (float)cp->k_fene;
+    c.inv_r02 = (float)(cp->r0 > 0 ? 1.0 / (cp->r0 * cp->r0) : 0.0);
+    c.pkey0 = (uint32_t)(cp->seed & 0xffffffffu);
+    c.pkey1 = (uint32_t)(cp->seed >> 32);
+    c.last = 0;
+    const int blocks = (n + kPartThreads - 1) / kPartThreads;
+    using T = typename lbd::Store<DT>::T;
+    const T *src = static_cast<const T *>(h->pops[h->cur]);
+    const bool need_nlist = cp->use_wca != 0;
+
+    if (need_nlist && P->nlist_n != n) {
+        cudaError_t e = cudaMemsetAsync(P->flags, 0xff, 2 * sizeof(unsigned int), h->stream);
+        if (e != cudaSuccess) return e;
+        P->nlist_n = n;
+    }
+    k_half_drift<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, pp->mom, pp->mass, c);
+    h->launches += 1;
+    double *buf[2] = {pp->pos, P->pos_tmp};
+    for (int s = 0; s < cp->n_substeps; ++s) {
+        const uint32_t rd = P->sub_counter & 1u, wr = rd ^ 1u;
+        if (need_nlist) {
+            k_build_nlist<<<(n + kTile - 1) / kTile, kTile, 0, h->stream>>>(buf[s & 1], P->nlist, P->ncount,
+                                                                           P->ref_pos, P->flags, h->d_err, c, rd);
+            k_clear_flag<<<1, 1, 0, h->stream>>>(P->flags, rd);
+            h->launches += 2;
+        }
+        c.md_step = cp->md_step0 + (uint32_t)s;
+        c.last = (s == cp->n_substeps - 1);
+        c.slot = wr;
+        int *rec = P->records + P->n_records;
+        k_substep<DT><<<blocks, kPartThreads, 0, h->stream>>>(
+            src, h->force, buf[s & 1], buf[(s + 1) & 1], pp->mom, pp->mass, pp->gamma, P->nlist, P->ncount,
+            need_nlist ? P->ref_pos : nullptr, h->facc, rec, P->flags, h->d_err, c);
+        P->n_records += (size_t)n;
+        P->sub_counter += 1;
+        h->launches += 1;
+    }
+    if (cp->n_substeps & 1) {
+        cudaError_t e = cudaMemcpyAsync(pp->pos, P->pos_tmp, (size_t)n * 3 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, h->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
+{
+    if (pp->n < 0 || pp->reserved != 0 || cp->reserved != 0) {
+        set_error("lb_couple_particles: bad particle count or reserved field");
+        return LB_EINVAL;
+    }
+    if (pp->n == 0) return LB_OK;
+    if (!pp->pos || !pp->mom) {
+        set_error("lb_couple_particles: pos and mom are required");
+        return LB_EINVAL;
+    }
+    if (cp->n_substeps < 1 || !(cp->dt > 0.0) || cp->noise_kind < 0 || cp->noise_kind > 1) {
+        set_error("lb_couple_particles: need n_substeps >= 1, dt > 0, noise_kind 0 or 1");
+        return LB_EINVAL;
+    }
+    if ((!pp->mass && !(pp->mass0 > 0.0)) || (!pp->gamma && !(pp->gamma0 > 0.0))) {
+        set_error("lb_couple_particles: mass0 and gamma0 must be > 0 when no per-particle arrays are given");
+        return LB_EINVAL;
+    }
+    if (cp->chain_len > 1 && !(cp->r0 > 0.0)) {
+        set_error("lb_couple_particles: FENE chains need r0 > 0");
+        return LB_EINVAL;
+    }
+    if (cp->use_wca && !(cp->sigma > 0.0)) {
+        set_error("lb_couple_particles: WCA needs sigma > 0");
+        return LB_EINVAL;
+    }
+    if (cp->use_wca && (1.122462048309373 + kSkin) * cp->sigma * 2.0 >= (double)std::min(h->p.nx, h->p.ny)) {
+        set_error("lb_couple_particles: box too small for the WCA neighbour search");
+        return LB_EINVAL;
+    }
+    if (((uintptr_t)pp->pos & 7u) || ((uintptr_t)pp->mom & 3u)) {
+        set_error("lb_couple_particles: misaligned pos or mom");
+        return LB_EINVAL;
+    }
+    lb_status st = ensure_buffers(h, pp->n, cp->n_substeps);
+    if (st != LB_OK) return st;
+    cudaError_t e;
+    if (h->facc_stale) {  // impulses of the previous call were applied: clear their nodes
+        e = clear_particle_forces(h);
+        if (e != cudaSuccess) return cuda_fail("lb_couple_particles (clear accumulator)", e);
+        h->facc_stale = 0;
+    }
+    switch (h->p.dtype) {
+    case LB_F32: e = run_substeps<0>(h, pp, cp); break;
+    case LB_F16: e = run_substeps<1>(h, pp, cp); break;
+    default: e = run_substeps<2>(h, pp, cp); break;
+    }
+    if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+    h->facc_dirty = 1;
+    return LB_OK;
+}
+
+cudaError_t clear_particle_forces(lb_handle *h)
+{
+    Particles *P = h->parts;
+    if (!P || !h->facc) return cudaSuccess;
+    if (P->n_records) {
+        const StepArgs g = make_args(h);
+        int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
+        k_clear_records<<<blocks, 256, 0, h->stream>>>(h->facc, P->records, P->n_records, g);
+        h->launches += 1;
+        P->n_records = 0;
+    }
+    return cudaGetLastError();
+}
+
+lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
+{
+    if (n == 0) return LB_OK;
+    const StepArgs g = make_args(h);
+    const int blocks = (n + kPartThreads - 1) / kPartThreads;
+    switch (h->p.dtype) {
+    case LB_F32:
+        k_interpolate<0><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const float *>(h->pops[h->cur]),
+                                                                  h->force, pos, u_out, n, g);
+        break;
+    case LB_F16:
+        k_interpolate<1><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const __half *>(h->pops[h->cur]),
+                                                                  h->force, pos, u_out, n, g);
+        break;
+    default:
+        k_interpolate<2><<<blocks, kPartThreads, 0, h->stream>>>(
+            static_cast<const __nv_bfloat16 *>(h->pops[h->cur]), h->force, pos, u_out, n, g);
+        break;
+    }
+    h->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_interpolate", e);
+}
+
+void destroy_particles(lb_handle *h)
+{
+    free_parts(h->parts);
+    h->parts = nullptr;
+}
+
+}  // namespace lbi

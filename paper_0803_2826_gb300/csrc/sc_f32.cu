@@ -1,0 +1,6 @@
+// Stream-collide instantiations for f32 population storage.
+#include "stream_collide.cuh"
+
+namespace lbi {
+template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *);
+}  // namespace lbi

@@ -1,0 +1,179 @@
+// stream_collide.cuh -- fused pull-stream + MRT collision + noise + forcing.
+//
+// One thread per fluid node; a block covers BX consecutive x of one (y, z)
+// row, so the 19 plane loads and 19 plane stores of a warp are coalesced
+// (the +-x neighbours of a row are the same 32-byte sectors shifted by one
+// element).  Everything between the loads and the stores stays in registers:
+//   pull       n_i(r) = n*_i(r - c_i)                       Eq. (LBE)
+//              (link bounce-back at solid z-planes,          Sec. 4.1 Eq. (MBB), u_b = 0)
+//   moments    m_k = sum_i e_ki n_i                          Sec. 3.4 Eq. (forward), Table 1
+//   velocity   j = m_1..3 + f/2, u = j / rho                 Sec. 3.7 Eq. (special_choice_momentum_density)
+//   relax      m*_k = m^eq_k + gamma_k (m_k - m^eq_k) + F_k  Eq. (lco_update); Sec. 3.7 Sigma
+//   noise      + sqrt(mu rho w_k) (1 - gamma_k^2)^1/2 r_k    Eqs. (stochupdaterule1), (detailedbalance1)
+//   back       n*_i = a_i sum_k e_ki m*_k / w_k              Eq. (back_transformation), q = a
+//   store      deviation n*_i - a_i rho0 (scaled for FP16 / BF16)
+#pragma once
+
+#include "d3q19.cuh"
+#include "lbf_internal.h"
+
+namespace lbi {
+
+constexpr int kBX = 128;  // threads per block along x
+
+template <int DT, bool NOISE, bool FIELD, bool WALLS>
+__global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Store<DT>::T *__restrict__ src,
+                                                        typename lbd::Store<DT>::T *__restrict__ dst,
+                                                        const float *__restrict__ ffield,
+                                                        const float *__restrict__ facc, const StepArgs a)
+{
+    using S = lbd::Store<DT>;
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z + a.z0;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int xm = (x == 0) ? nx - 1 : x - 1;
+    const int xp = (x == nx - 1) ? 0 : x + 1;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    int zm, zp;
+    if (WALLS) {
+        zm = z - 1;
+        zp = z + 1;
+    } else {
+        zm = (z == 0) ? nz - 1 : z - 1;
+        zp = (z == nz - 1) ? 0 : z + 1;
+    }
+    const size_t P = a.pitch;
+    const uint32_t self = (uint32_t)((z * ny + y) * nx + x);
+
+    // ---- pull streaming --------------------------------------------------
+    float n[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sx = lbd::cx(i) == 1 ? xm : (lbd::cx(i) == -1 ? xp : x);
+        const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+        const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+        bool bounce = false;
+        if (WALLS && lbd::cz(i) != 0) bounce = (sz == 0) || (sz == nz - 1);
+        if (bounce) {
+            n[i] = S::load(src + (size_t)lbd::opposite(i) * P + self, a.inv_scale);
+        } else {
+            const uint32_t off = (uint32_t)((sz * ny + sy) * nx + sx);
+            n[i] = S::load(src + (size_t)i * P + off, a.inv_scale);
+        }
+    }
+
+    // ---- moments and force -----------------------------------------------
+    float m[19];
+    lbd::forward(n, m);
+    float fx = a.fx, fy = a.fy, fz = a.fz;
+    if (FIELD) {
+        if (ffield) {  // caller's field, component stride N
+            fx += __ldg(ffield + self);
+            fy += __ldg(ffield + a.nn + self);
+            fz += __ldg(ffield + 2 * a.nn + self);
+        }
+        if (facc) {  // library accumulator, component stride = plane pitch
+            fx += __ldg(facc + self);
+            fy += __ldg(facc + P + self);
+            fz += __ldg(facc + 2 * P + self);
+        }
+    }
+    const float rho = a.rho0 + m[0];
+    const float inv_rho = 1.0f / rho;
+    const float ux = (m[1] + 0.5f * fx) * inv_rho;
+    const float uy = (m[2] + 0.5f * fy) * inv_rho;
+    const float uz = (m[3] + 0.5f * fz) * inv_rho;
+
+    // ---- relaxation in moment space ----------------------------------------
+    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const float u2 = uxx + uyy + uzz;
+    const float meq4 = rho * u2;
+    const float meq5 = rho * (3.0f * uxx - u2);
+    const float meq6 = rho * (uyy - uzz);
+    const float meq7 = rho * ux * uy;
+    const float meq8 = rho * uy * uz;
+    const float meq9 = rho * uz * ux;
+    // forcing moments of Delta'' (Sigma of Eq. (moment_two_external_force))
+    const float uf = ux * fx + uy * fy + uz * fz;
+    const float gs1 = 1.0f + a.g_shear;
+    const float F4 = (1.0f + a.g_bulk) * uf;
+    const float F5 = gs1 * (3.0f * ux * fx - uf);
+    const float F6 = gs1 * (uy * fy - uz * fz);
+    const float F7 = 0.5f * gs1 * (ux * fy + uy * fx);
+    const float F8 = 0.5f * gs1 * (uy * fz + uz * fy);
+    const float F9 = 0.5f * gs1 * (uz * fx + ux * fz);
+
+    float M[19];  // post-collision moments divided by w_k
+    M[0] = m[0];
+    M[1] = 3.0f * (m[1] + fx);
+    M[2] = 3.0f * (m[2] + fy);
+    M[3] = 3.0f * (m[3] + fz);
+    M[4] = lbd::inv_w(4) * (meq4 + a.g_bulk * (m[4] - meq4) + F4);
+    M[5] = lbd::inv_w(5) * (meq5 + a.g_shear * (m[5] - meq5) + F5);
+    M[6] = lbd::inv_w(6) * (meq6 + a.g_shear * (m[6] - meq6) + F6);
+    M[7] = lbd::inv_w(7) * (meq7 + a.g_shear * (m[7] - meq7) + F7);
+    M[8] = lbd::inv_w(8) * (meq8 + a.g_shear * (m[8] - meq8) + F8);
+    M[9] = lbd::inv_w(9) * (meq9 + a.g_shear * (m[9] - meq9) + F9);
+#pragma unroll
+    for (int k = 10; k < 16; ++k) M[k] = lbd::inv_w(k) * (a.g_odd * m[k]);
+#pragma unroll
+    for (int k = 16; k < 19; ++k) M[k] = lbd::inv_w(k) * (a.g_even * m[k]);
+
+    if (NOISE) {
+        float g[16];
+        lbd::gaussians16(a.key0, a.key1, self, a.step, 0u, a.replica, g);
+        const float rn = a.noise_rho0 ? a.rho0 : rho;
+        const float s = sqrtf(a.mu * rn);
+        // sqrt(mu rho w_k) phi_k r_k, divided by w_k: sqrt(mu rho / w_k) phi_k r_k
+        const float sb = s * a.phi_bulk, ss = s * a.phi_shear, so = s * a.phi_odd, se = s * a.phi_even;
+        M[4] += sb * lbd::sqrt_inv_w(4) * g[0];
+#pragma unroll
+        for (int k = 5; k < 10; ++k) M[k] += ss * lbd::sqrt_inv_w(k) * g[k - 4];
+#pragma unroll
+        for (int k = 10; k < 16; ++k) M[k] += so * lbd::sqrt_inv_w(k) * g[k - 4];
+#pragma unroll
+        for (int k = 16; k < 19; ++k) M[k] += se * lbd::sqrt_inv_w(k) * g[k - 4];
+    }
+
+    float out[19];
+    lbd::backward(M, out);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
+}
+
+template <int DT>
+cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc)
+{
+    using T = typename lbd::Store<DT>::T;
+    const StepArgs a = make_args(h);
+    const int nzf = a.z1 - a.z0;
+    dim3 grid((a.nx + kBX - 1) / kBX, a.ny, nzf);
+    dim3 block(kBX);
+    const bool noise = a.kT > 0.0f;
+    const bool field = (h->force != nullptr) || (facc != nullptr);
+    const bool walls = h->p.walls != 0;
+    const T *s = static_cast<const T *>(src);
+    T *d = static_cast<T *>(dst);
+#define LBI_SC(NZ, FL, WL) \
+    k_stream_collide<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a)
+    if (noise) {
+        if (field) {
+            if (walls) LBI_SC(true, true, true); else LBI_SC(true, true, false);
+        } else {
+            if (walls) LBI_SC(true, false, true); else LBI_SC(true, false, false);
+        }
+    } else {
+        if (field) {
+            if (walls) LBI_SC(false, true, true); else LBI_SC(false, true, false);
+        } else {
+            if (walls) LBI_SC(false, false, true); else LBI_SC(false, false, false);
+        }
+    }
+#undef LBI_SC
+    return cudaGetLastError();
+}
+
+}  // namespace lbi

@@ -1,0 +1,354 @@
+"""Thin Python binding of the C ABI in include/lbfluct.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+liblbfluct.so.  Functions keep the C names (lb_create, lb_step, ...) and take
+torch CUDA tensors (device memory) or raw integer device pointers; streams are
+torch.cuda.Stream objects or raw cudaStream_t integers.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+
+The ``Lattice`` class is a convenience owner of the two population buffers and
+the handle; it allocates device memory with torch and passes pointers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "liblbfluct.so")
+
+LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ETIMEOUT, LB_EUNSUPPORTED, LB_EDEVICE = range(8)
+LB_F32, LB_F16, LB_BF16 = 0, 1, 2
+LB_NSUMS = 38
+LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
+
+STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
+                5: "LB_ETIMEOUT", 6: "LB_EUNSUPPORTED", 7: "LB_EDEVICE"}
+
+#: Symbols declared in include/lbfluct.h (checked by the ABI tests).
+EXPORTS = (
+    "lb_plane_pitch", "lb_population_bytes", "lb_create", "lb_destroy", "lb_last_error",
+    "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
+    "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
+    "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words",
+    "lb_get_launch_count", "lb_version",
+)
+
+
+class LBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class lb_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("dtype", C.c_int), ("walls", C.c_int), ("noise_rho0", C.c_int),
+        ("rho0", C.c_double), ("kT", C.c_double),
+        ("gamma_shear", C.c_double), ("gamma_bulk", C.c_double),
+        ("gamma_odd", C.c_double), ("gamma_even", C.c_double),
+        ("body_force", C.c_double * 3),
+        ("seed", C.c_uint64), ("replica", C.c_uint32), ("reserved", C.c_uint32),
+        ("pop_scale", C.c_double),
+    ]
+
+
+class lb_particles(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("reserved", C.c_int),
+        ("pos", C.c_void_p), ("mom", C.c_void_p), ("mass", C.c_void_p), ("gamma", C.c_void_p),
+        ("mass0", C.c_double), ("gamma0", C.c_double),
+    ]
+
+
+class lb_couple_params(C.Structure):
+    _fields_ = [
+        ("n_substeps", C.c_int), ("noise_kind", C.c_int),
+        ("dt", C.c_double), ("seed", C.c_uint64), ("md_step0", C.c_uint32),
+        ("chain_len", C.c_int), ("use_wca", C.c_int), ("reserved", C.c_int),
+        ("eps", C.c_double), ("sigma", C.c_double), ("k_fene", C.c_double), ("r0", C.c_double),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load liblbfluct.so (building it first if it is missing); raise if impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            from . import build as _build
+            _build.build()
+        try:
+            lib = C.CDLL(p)
+        except OSError as e:  # no silent fallback
+            raise RuntimeError("liblbfluct.so could not be loaded (%s); the CUDA library is required" % e)
+        vp, i, u32, u64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64
+        P = C.POINTER(lb_params)
+        H = C.c_void_p
+        sig = {
+            "lb_plane_pitch": (C.c_size_t, [P]),
+            "lb_population_bytes": (C.c_size_t, [P]),
+            "lb_create": (i, [P, vp, vp, vp, vp, C.POINTER(H)]),
+            "lb_destroy": (i, [H]),
+            "lb_last_error": (C.c_char_p, []),
+            "lb_sync": (i, [H, C.POINTER(u32)]),
+            "lb_get_step": (i, [H, C.POINTER(u32)]),
+            "lb_set_step": (i, [H, u32]),
+            "lb_state_buffers": (i, [H, C.POINTER(vp), C.POINTER(vp)]),
+            "lb_init_equilibrium": (i, [H, vp, vp]),
+            "lb_set_populations": (i, [H, vp]),
+            "lb_get_populations": (i, [H, vp]),
+            "lb_step": (i, [H, i]),
+            "lb_moments": (i, [H, vp, vp, vp, vp]),
+            "lb_couple_particles": (i, [H, C.POINTER(lb_particles), C.POINTER(lb_couple_params)]),
+            "lb_interpolate": (i, [H, i, vp, vp]),
+            "lb_get_particle_forces": (i, [H, vp]),
+            "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
+            "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
+            "lb_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor, got a %s tensor" % x.device)
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError("cannot take a device pointer of %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(st):
+    if st != LB_OK:
+        raise LBError(st, load().lb_last_error().decode())
+
+
+def make_params(shape, *, dtype=LB_F32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0,
+                gamma_odd=0.0, gamma_even=0.0, body_force=(0.0, 0.0, 0.0), seed=0, replica=0,
+                walls=False, noise_rho0=False, pop_scale=0.0) -> lb_params:
+    """shape = (nx, ny, nz)."""
+    p = lb_params()
+    p.nx, p.ny, p.nz = (int(v) for v in shape)
+    p.dtype = int(dtype)
+    p.walls = int(bool(walls))
+    p.noise_rho0 = int(bool(noise_rho0))
+    p.rho0, p.kT = float(rho0), float(kT)
+    p.gamma_shear, p.gamma_bulk = float(gamma_shear), float(gamma_bulk)
+    p.gamma_odd, p.gamma_even = float(gamma_odd), float(gamma_even)
+    for d in range(3):
+        p.body_force[d] = float(body_force[d])
+    p.seed, p.replica, p.reserved = int(seed), int(replica), 0
+    p.pop_scale = float(pop_scale)
+    return p
+
+
+# ---- one function per C entry point ------------------------------------------
+
+def lb_plane_pitch(p: lb_params) -> int:
+    return load().lb_plane_pitch(C.byref(p))
+
+
+def lb_population_bytes(p: lb_params) -> int:
+    return load().lb_population_bytes(C.byref(p))
+
+
+def lb_create(p: lb_params, pops_a, pops_b, force=None, stream=None):
+    h = C.c_void_p()
+    _check(load().lb_create(C.byref(p), _ptr(pops_a), _ptr(pops_b), _ptr(force), _stream(stream),
+                            C.byref(h)))
+    return h
+
+
+def lb_destroy(h):
+    _check(load().lb_destroy(h))
+
+
+def lb_last_error() -> str:
+    return load().lb_last_error().decode()
+
+
+def lb_sync(h, raise_on_error=True):
+    bits = C.c_uint32(0)
+    st = load().lb_sync(h, C.byref(bits))
+    if raise_on_error:
+        _check(st)
+    return st, bits.value
+
+
+def lb_get_step(h) -> int:
+    v = C.c_uint32()
+    _check(load().lb_get_step(h, C.byref(v)))
+    return v.value
+
+
+def lb_set_step(h, step: int):
+    _check(load().lb_set_step(h, int(step) & 0xffffffff))
+
+
+def lb_state_buffers(h):
+    cur, oth = C.c_void_p(), C.c_void_p()
+    _check(load().lb_state_buffers(h, C.byref(cur), C.byref(oth)))
+    return cur.value, oth.value
+
+
+def lb_init_equilibrium(h, rho=None, u=None):
+    _check(load().lb_init_equilibrium(h, _ptr(rho), _ptr(u)))
+
+
+def lb_set_populations(h, n):
+    _check(load().lb_set_populations(h, _ptr(n)))
+
+
+def lb_get_populations(h, n):
+    _check(load().lb_get_populations(h, _ptr(n)))
+
+
+def lb_step(h, nsteps=1):
+    _check(load().lb_step(h, int(nsteps)))
+
+
+def lb_moments(h, rho=None, j=None, pi=None, sums=None):
+    _check(load().lb_moments(h, _ptr(rho), _ptr(j), _ptr(pi), _ptr(sums)))
+
+
+def lb_couple_particles(h, parts: lb_particles, cp: lb_couple_params):
+    _check(load().lb_couple_particles(h, C.byref(parts), C.byref(cp)))
+
+
+def lb_interpolate(h, n, pos, u_out):
+    _check(load().lb_interpolate(h, int(n), _ptr(pos), _ptr(u_out)))
+
+
+def lb_get_particle_forces(h, out):
+    _check(load().lb_get_particle_forces(h, _ptr(out)))
+
+
+def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, gauss=None, stream=None):
+    _check(load().lb_noise_words(int(seed), int(replica), int(step), int(domain), int(index0), int(count),
+                                 int(nblocks), _ptr(words), _ptr(gauss), _stream(stream)))
+
+
+def lb_get_launch_count(h) -> int:
+    v = C.c_uint64()
+    _check(load().lb_get_launch_count(h, C.byref(v)))
+    return v.value
+
+
+def lb_version() -> str:
+    return load().lb_version().decode()
+
+
+# ---- convenience owner ---------------------------------------------------------
+
+class Lattice:
+    """Owns two population buffers (torch uint8 device tensors) and a handle."""
+
+    def __init__(self, shape, *, device="cuda", stream=None, force=None, **kw):
+        import torch
+        self.params = make_params(shape, **kw)
+        self.shape = tuple(int(v) for v in shape)
+        self.n_nodes = self.shape[0] * self.shape[1] * self.shape[2]
+        nbytes = lb_population_bytes(self.params)
+        if nbytes == 0:
+            raise LBError(LB_EINVAL, lb_last_error())
+        self.device = torch.device(device)
+        self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.force = force
+        self.stream = stream
+        self.h = lb_create(self.params, self._bufs[0], self._bufs[1], force, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            lb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state
+    def init_equilibrium(self, rho=None, u=None):
+        lb_init_equilibrium(self.h, rho, u)
+
+    def set_populations(self, n):
+        lb_set_populations(self.h, n)
+
+    def get_populations(self):
+        import torch
+        n = torch.empty((19,) + self.shape[::-1], dtype=torch.float64, device=self.device)
+        lb_get_populations(self.h, n)
+        return n
+
+    def step(self, nsteps=1):
+        lb_step(self.h, nsteps)
+
+    def moments(self, want_rho=True, want_j=True, want_pi=True, want_sums=False):
+        import torch
+        sh = self.shape[::-1]
+        rho = torch.empty(sh, dtype=torch.float32, device=self.device) if want_rho else None
+        j = torch.empty((3,) + sh, dtype=torch.float32, device=self.device) if want_j else None
+        pi = torch.empty((6,) + sh, dtype=torch.float32, device=self.device) if want_pi else None
+        sums = torch.empty(LB_NSUMS, dtype=torch.float64, device=self.device) if want_sums else None
+        lb_moments(self.h, rho, j, pi, sums)
+        return rho, j, pi, sums
+
+    def sync(self):
+        return lb_sync(self.h)
+
+    @property
+    def step_index(self):
+        return lb_get_step(self.h)
+
+    @step_index.setter
+    def step_index(self, v):
+        lb_set_step(self.h, v)
+
+
+def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_particles:
+    s = lb_particles()
+    s.n, s.reserved = int(n), 0
+    s.pos, s.mom = _ptr(pos), _ptr(mom)
+    s.mass, s.gamma = _ptr(mass), _ptr(gamma)
+    s.mass0, s.gamma0 = float(mass0), float(gamma0)
+    return s
+
+
+def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len=0, use_wca=False,
+                  eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5) -> lb_couple_params:
+    c = lb_couple_params()
+    c.n_substeps, c.noise_kind, c.dt = int(n_substeps), int(noise_kind), float(dt)
+    c.seed, c.md_step0 = int(seed), int(md_step0) & 0xffffffff
+    c.chain_len, c.use_wca, c.reserved = int(chain_len), int(bool(use_wca)), 0
+    c.eps, c.sigma, c.k_fene, c.r0 = float(eps), float(sigma), float(k_fene), float(r0)
+    return c

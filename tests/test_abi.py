@@ -1,0 +1,86 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+that include/lbfluct.h declares; host-side argument checks work without a GPU
+(no compute call is made here)."""
+import ctypes as C
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lbfluct.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_0803_2826_gb300 import build, lbfluct
+    build.build()
+    return lbfluct
+
+
+def test_header_declares_binding_exports(lib):
+    assert _declared() == sorted(lib.EXPORTS)
+
+
+def test_library_exports_every_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True,
+                         check=True).stdout
+    have = set(re.findall(r"\bT (lb_\w+)", out))
+    missing = [s for s in _declared() if s not in have]
+    assert not missing, missing
+    raw = lib.load()
+    for s in _declared():
+        assert hasattr(raw, s)
+
+
+def test_version_and_sizes(lib):
+    assert "sm_103a" in lib.lb_version()
+    p = lib.make_params((5, 6, 7))
+    assert lib.lb_plane_pitch(p) == 256  # 210 rounded up to a multiple of 64
+    assert lib.lb_population_bytes(p) == 19 * 256 * 4
+    p16 = lib.make_params((5, 6, 7), dtype=lib.LB_F16)
+    assert lib.lb_population_bytes(p16) == 19 * 256 * 2
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(gamma_shear=1.0), "gamma"),
+    (dict(rho0=0.0), "rho0"),
+    (dict(kT=-1.0), "kT"),
+    (dict(dtype=7), "dtype"),
+])
+def test_params_rejected(lib, kw, msg):
+    p = lib.make_params((4, 4, 4), **kw)
+    assert lib.lb_population_bytes(p) == 0
+    assert msg in lib.lb_last_error()
+    h = C.c_void_p()
+    st = lib.load().lb_create(C.byref(p), 256, 512, None, None, C.byref(h))
+    assert st == lib.LB_EINVAL and not h.value
+
+
+def test_bad_geometry_rejected(lib):
+    raw = lib.load()
+    h = C.c_void_p()
+    p = lib.make_params((4, 4, 2), walls=True)
+    assert raw.lb_create(C.byref(p), 256, 512, None, None, C.byref(h)) == lib.LB_EINVAL
+    assert "nz >= 3" in lib.lb_last_error()
+    p = lib.make_params((0, 4, 4))
+    assert raw.lb_create(C.byref(p), 256, 512, None, None, C.byref(h)) == lib.LB_EINVAL
+    p = lib.make_params((4, 4, 4))
+    assert raw.lb_create(C.byref(p), 256, 256, None, None, C.byref(h)) == lib.LB_EINVAL
+    assert raw.lb_create(C.byref(p), 256, 300, None, None, C.byref(h)) == lib.LB_EINVAL
+    assert "aligned" in lib.lb_last_error()
+
+
+def test_null_handles_rejected(lib):
+    raw = lib.load()
+    assert raw.lb_step(None, 1) == lib.LB_EINVAL
+    assert raw.lb_moments(None, None, None, None, None) == lib.LB_EINVAL
+    assert raw.lb_destroy(None) == lib.LB_OK
+    assert raw.lb_noise_words(0, 0, 0, 0, 0, 4, 5, None, None, None) == lib.LB_EINVAL

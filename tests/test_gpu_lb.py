@@ -1,0 +1,172 @@
+"""GPU parity of the fused stream-collide kernel against the FP64 oracle.
+
+All calls go through the C ABI (via the ctypes binding).  Inputs are seeded
+and synthetic (paper_0803_2826_gb300.inputs).  Tolerances:
+  - one step, FP32 storage: relative L2 error <= 2e-6 (FP32 rounding of
+    O(1e-2) deviations);
+  - 1000 steps of the 32^3 fluctuating shear wave: <= 1e-5 relative for
+    n - a rho0, rho - rho0, j and pi - pi^eq (the stated target);
+  - FP16 / BF16 storage: bounded by their rounding (2^-11, 2^-8 relative).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_0803_2826_gb300 import inputs  # noqa: E402
+from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+GAMMAS = dict(gamma_shear=0.2, gamma_bulk=-0.3, gamma_odd=0.4, gamma_even=-0.1)
+
+
+def _pair(ora, shape, nsteps, *, u=None, rho=None, field=None, dtype=L.LB_F32, **kw):
+    """Run the oracle and the GPU from the same equilibrium for nsteps."""
+    okw = {k: v for k, v in kw.items()}
+    p = ora.make_params(shape, **okw)
+    f64 = None if field is None else field.astype(np.float32).astype(np.float64)
+    pops = ora.equilibrium(p, rho, u)
+    pops = ora.run(p, pops, nsteps, f64)
+    ft = None if field is None else dev(field.astype(np.float32))
+    lat = L.Lattice(shape, force=ft, dtype=dtype, **kw)
+    lat.init_equilibrium(None if rho is None else dev(rho), None if u is None else dev(u))
+    lat.step(nsteps)
+    got = host(lat.get_populations())
+    lat.sync()
+    return p, pops, got, lat, f64
+
+
+def _fields(ora, p, pops, force):
+    c, a, e, w, opp = ora.tables()
+    rho, j, pi = ora.moments(p, pops, force)
+    u = j / rho
+    eye = [(0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0)]
+    pieq = np.stack([rho * ((1 / 3) if a_ == b_ else 0) + rho * u[a_] * u[b_] for a_, b_ in eye])
+    dn = pops - (a * p.rho0)[:, None, None, None]
+    return dn, rho - p.rho0, j, pi - pieq
+
+
+@pytest.mark.parametrize("shape", [(6, 5, 7), (130, 3, 4), (1, 1, 8), (32, 2, 3)])
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+def test_one_step_parity(ora, shape, kT):
+    u = inputs.shear_wave(shape, 0.02) + inputs.gaussian_field(shape, 3, 1e-3, seed=1)
+    rho = 1.0 + inputs.gaussian_field(shape, 1, 1e-3, seed=2)[0]
+    field = inputs.gaussian_field(shape, 3, 1e-4, seed=3)
+    p, want, got, lat, f64 = _pair(ora, shape, 1, u=u, rho=rho, field=field, kT=kT, seed=5,
+                                   body_force=(1e-5, -2e-5, 3e-6), **GAMMAS)
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(got - aa, want - aa) < 2e-6
+    for x, y in zip(_fields(ora, p, got, f64), _fields(ora, p, want, f64)):
+        assert rel(x, y) < 5e-6
+
+
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+def test_walls_parity(ora, kT):
+    shape = (7, 6, 9)
+    u = inputs.gaussian_field(shape, 3, 1e-3, seed=4)
+    u[:, 0] = 0
+    u[:, -1] = 0
+    p, want, got, lat, _ = _pair(ora, shape, 5, u=u, kT=kT, seed=9, walls=True,
+                                 body_force=(1e-5, 0.0, 0.0), **GAMMAS)
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    fl = slice(1, shape[2] - 1)
+    assert rel(got[:, fl] - aa, want[:, fl] - aa) < 5e-6
+
+
+def test_shear_wave_1000_steps(ora):
+    """The 32^3 fluctuating shear-wave workload: rho0 = 1, gamma_s = gamma_v = 0
+    (nu = 1/6), kT = 1e-4, seed 0, u_x = 0.01 sin(2 pi z / 32), 1000 steps."""
+    shape = (32, 32, 32)
+    u = inputs.shear_wave(shape, 0.01)
+    p, want, got, lat, _ = _pair(ora, shape, 1000, u=u, kT=1e-4, seed=0)
+    names = ["n - a rho0", "rho - rho0", "j", "pi - pi_eq"]
+    errs = [rel(x, y) for x, y in zip(_fields(ora, p, got, None), _fields(ora, p, want, None))]
+    for nm, err in zip(names, errs):
+        assert err < 1e-5, (nm, err)
+    # the GPU's own moment kernel agrees with the oracle's moments too
+    rho, j, pi, sums = lat.moments(want_sums=True)
+    orho, oj, opi = ora.moments(p, want)
+    assert rel(host(rho) - 1.0, orho - 1.0) < 1e-5
+    assert rel(host(j), oj) < 1e-5
+
+
+@pytest.mark.parametrize("dtype,tol", [(L.LB_F16, 3e-3), (L.LB_BF16, 2.5e-2)])
+def test_reduced_precision_storage(ora, dtype, tol):
+    shape = (12, 10, 8)
+    u = inputs.shear_wave(shape, 0.01)
+    p, want, got, lat, _ = _pair(ora, shape, 20, u=u, kT=1e-4, seed=3, dtype=dtype)
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(got - aa, want - aa) < tol
+
+
+def test_noise_words_bitwise(ora):
+    n = 257
+    words = torch.empty((n, 4, 4), dtype=torch.int32, device="cuda")
+    gauss = torch.empty((n, 4, 4), dtype=torch.float32, device="cuda")
+    seed = 0xDEADBEEF12345
+    L.lb_noise_words(seed, 3, 77, 0, 1000, n, 4, words, gauss)
+    torch.cuda.synchronize()
+    W = words.cpu().numpy().view(np.uint32)
+    G = gauss.cpu().numpy().astype(np.float64)
+    for q in range(0, n, 16):
+        want = ora.raw_words(seed, 1000 + q, 77, domain=0, replica=3, nblocks=4)
+        assert np.array_equal(W[q].ravel(), want)
+        g = ora.gaussians(seed, 1000 + q, 77, domain=0, replica=3, nblocks=4)
+        assert np.allclose(G[q].ravel(), g, rtol=0, atol=2e-6)
+    # particle domain, one block
+    L.lb_noise_words(5, 0, 9, 1, 0, n, 1, words, None)
+    torch.cuda.synchronize()
+    W = words.cpu().numpy().view(np.uint32)
+    for q in (0, 1, 100, 256):
+        assert np.array_equal(W.reshape(-1)[4 * q:4 * q + 4], ora.raw_words(5, q, 9, domain=1, nblocks=1))
+
+
+def test_conservation_on_gpu(ora):
+    """Mass constant; momentum grows by sum f per step (FP32 storage)."""
+    shape = (16, 12, 10)
+    f = np.array([1e-5, -2e-5, 5e-6])
+    lat = L.Lattice(shape, kT=1e-4, seed=2, body_force=f, **GAMMAS)
+    lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+    _, j0, _, s0 = lat.moments(want_sums=True)
+    lat.step(10)
+    _, j1, _, s1 = lat.moments(want_sums=True)
+    s0, s1 = s0.cpu().numpy(), s1.cpu().numpy()
+    N = np.prod(shape)
+    assert abs(s1[0] - s0[0]) < 1e-5 * N * 1e-3 + 1e-9
+    dJ = s1[1:4] - s0[1:4]
+    assert np.allclose(dJ, 10 * f * N, rtol=1e-3, atol=1e-6)
+    assert lat.sync() == (L.LB_OK, 0)
+
+
+def test_step_counter_and_resume(ora):
+    """Counter-based noise makes a split run bit-identical to an uninterrupted one."""
+    shape = (8, 8, 8)
+    a = L.Lattice(shape, kT=1e-4, seed=7)
+    b = L.Lattice(shape, kT=1e-4, seed=7)
+    a.init_equilibrium()
+    b.init_equilibrium()
+    a.step(6)
+    b.step(3)
+    snap = b.get_populations()
+    step = b.step_index
+    c = L.Lattice(shape, kT=1e-4, seed=7)
+    c.set_populations(snap)
+    c.step_index = step
+    c.step(3)
+    assert torch.equal(a.get_populations(), c.get_populations())

@@ -1,0 +1,154 @@
+"""GPU parity of the point-particle coupling (Sec. 4.5, 4.6) and the
+Kremer-Grest forces (Sec. 2.1) against the FP64 oracle, through the C ABI.
+
+Tolerances: positions to 1e-6 absolute (FP64 positions, FP32 increments);
+momenta and spread impulses to 2e-4 relative (FP32 arithmetic for the
+interpolation and the OU update); the LB step that applies the impulses to
+the same 2e-6 as the plain step.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_0803_2826_gb300 import inputs  # noqa: E402
+from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def dev(x, dt=None):
+    t = torch.as_tensor(np.ascontiguousarray(x))
+    if dt is not None:
+        t = t.to(dt)
+    return t.cuda()
+
+
+def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1, gamma=2.0, mass=1.0,
+         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0)):
+    mom32 = mom.astype(np.float32).astype(np.float64)
+    p = ora.make_params(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
+    u = inputs.shear_wave(shape, u_amp) + inputs.gaussian_field(shape, 3, 1e-3, seed=8)
+    if walls:
+        u[:, 0] = 0
+        u[:, -1] = 0
+    pops = ora.equilibrium(p, None, u)
+    md = None
+    if chains:
+        md = ora.make_md(chains[0], chains[1], eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5)
+    opos, omom, ofacc, broken = ora.couple(p, pops, pos, mom32, mass, gamma, dt=dt, n_substeps=nsub, seed=11,
+                                           md_step0=40, md=md, noise_kind=noise_kind)
+    assert broken == 0
+    lat = L.Lattice(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
+    lat.init_equilibrium(None, dev(u))
+    gpos = dev(pos)
+    gmom = dev(mom32, torch.float32)
+    parts = L.particles(pos.shape[0], gpos, gmom, mass0=mass, gamma0=gamma)
+    cp = L.couple_params(n_substeps=nsub, dt=dt, seed=11, md_step0=40, noise_kind=noise_kind,
+                         chain_len=chains[1] if chains else 0, use_wca=bool(chains), eps=0.01, sigma=1.0,
+                         k_fene=0.3, r0=1.5)
+    L.lb_couple_particles(lat.h, parts, cp)
+    facc = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
+    L.lb_get_particle_forces(lat.h, facc)
+    out = dict(p=p, pops=pops, opos=opos, omom=omom, ofacc=ofacc, lat=lat,
+               gpos=gpos.cpu().numpy(), gmom=gmom.cpu().numpy().astype(np.float64),
+               gfacc=facc.cpu().numpy().astype(np.float64))
+    if lb_after:
+        lat.step(1)
+        out["want_next"] = ora.step(p, pops, ofacc.astype(np.float32).astype(np.float64), 0)
+        out["got_next"] = lat.get_populations().cpu().numpy()
+    assert lat.sync() == (L.LB_OK, 0)
+    return out
+
+
+def _pos_err(a, b, shape):
+    d = a - b
+    Lb = np.array(shape, dtype=np.float64)
+    d -= Lb * np.round(d / Lb)
+    return np.abs(d).max()
+
+
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+def test_free_particles_parity(ora, kT):
+    shape = (12, 10, 9)
+    pos = inputs.uniform_particles(300, shape, seed=1)
+    mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
+    r = _run(ora, shape, pos, mom, kT=kT)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+
+
+def test_three_point_noise_parity(ora):
+    shape = (8, 8, 8)
+    pos = inputs.uniform_particles(200, shape, seed=3)
+    mom = np.zeros((200, 3))
+    r = _run(ora, shape, pos, mom, kT=1e-4, noise_kind=1, lb_after=False)
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+
+
+def test_walls_particles_parity(ora):
+    shape = (10, 8, 12)
+    pos = inputs.uniform_particles(200, shape, seed=5, zrange=(1.0, 10.0))
+    mom = inputs.maxwell_momenta(200, 1.0, 1e-2, seed=6)  # fast enough to reach the walls
+    r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, dt=0.5, body_force=(1e-5, 0, 0))
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-5
+    assert r["gpos"][:, 2].min() >= 1.0 and r["gpos"][:, 2].max() <= 10.0
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_chains_parity(ora):
+    """Two FENE + WCA chains of 24 beads (bond 0.97) in a 16^3 thermal fluid."""
+    shape = (16, 16, 16)
+    pos = inputs.random_walk_chains(2, 24, shape, seed=7)
+    mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24))
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_interpolation_parity(ora):
+    shape = (9, 11, 7)
+    p = ora.make_params(shape, kT=0.0)
+    u = inputs.gaussian_field(shape, 3, 1e-2, seed=9)
+    pops = ora.equilibrium(p, None, u)
+    pos = inputs.uniform_particles(500, shape, seed=10)
+    want = ora.interpolate(p, pops, pos)
+    lat = L.Lattice(shape)
+    lat.init_equilibrium(None, dev(u))
+    out = torch.empty((500, 3), dtype=torch.float32, device="cuda")
+    L.lb_interpolate(lat.h, 500, dev(pos), out)
+    assert rel(out.cpu().numpy().astype(np.float64), want) < 1e-6
+
+
+def test_coupled_momentum_conservation_gpu(ora):
+    """Particles + fluid momentum is conserved through coupling and the LB step."""
+    shape = (16, 16, 16)
+    pos = inputs.random_walk_chains(4, 16, shape, seed=12)
+    mom = inputs.maxwell_momenta(64, 1.0, 1e-4, seed=13)
+    lat = L.Lattice(shape, kT=1e-4, seed=1)
+    lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+    gpos, gmom = dev(pos), dev(mom, torch.float32)
+    parts = L.particles(64, gpos, gmom, mass0=1.0, gamma0=2.0)
+
+    def total():
+        _, _, _, s = lat.moments(want_rho=False, want_j=False, want_pi=False, want_sums=True)
+        return s.cpu().numpy()[1:4] + gmom.double().sum(0).cpu().numpy()
+
+    P0 = total()
+    for t in range(5):
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, chain_len=16, use_wca=True,
+                             eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5)
+        L.lb_couple_particles(lat.h, parts, cp)
+        lat.step(1)
+    P1 = total()
+    assert np.allclose(P1, P0, atol=2e-5), (P0, P1)
+    assert lat.sync() == (L.LB_OK, 0)
