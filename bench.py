@@ -51,7 +51,51 @@ def _args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="time lb_step alone (no particles) on --shape for each --kT and --dtype")
+    ap.add_argument("--shape", default="256,256,256")
+    ap.add_argument("--kT", default="0,1e-4")
+    ap.add_argument("--dtype", default="f32")
     return ap.parse_args()
+
+
+def run_kernel_only(args):
+    """lb_step alone: one JSON line per (dtype, kT) with ms per launch and the
+    algorithmic bandwidth 2 * 19 * element size bytes per node."""
+    import torch
+    from paper_0803_2826_gb300 import build as B
+    from paper_0803_2826_gb300 import lbfluct as L
+    B.build()
+    torch.cuda.set_device(0)
+    shape = tuple(int(v) for v in args.shape.split(","))
+    nodes = shape[0] * shape[1] * shape[2]
+    peak, src = _peak_hbm()
+    dts = {"f32": (L.LB_F32, 4), "f16": (L.LB_F16, 2), "bf16": (L.LB_BF16, 2)}
+    stream = torch.cuda.Stream()
+    for dname in args.dtype.split(","):
+        code, esz = dts[dname]
+        for kT in (float(v) for v in args.kT.split(",")):
+            with torch.cuda.stream(stream):
+                lat = L.Lattice(shape, kT=kT, seed=1, dtype=code, stream=stream)
+                lat.init_equilibrium()
+                lat.step(args.warmup)
+            torch.cuda.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                   for _ in range(args.steps)]
+            with torch.cuda.stream(stream):
+                for a, b in evs:
+                    a.record(stream)
+                    lat.step(1)
+                    b.record(stream)
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in evs)
+            med = ms[len(ms) // 2]
+            gbs = 2 * 19 * esz * nodes / (med * 1e-3) / 1e9
+            print(json.dumps({"kernel": "k_stream_collide", "dtype": dname, "kT": kT, "shape": shape,
+                              "ms_median": med, "ms_min": ms[0], "mlups": nodes / (med * 1e-3) / 1e6,
+                              "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": src}))
+            lat.close()
+    return 0
 
 
 def _peak_hbm():
@@ -337,6 +381,8 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_only:
+        return run_kernel_only(args)
     return run_ours(args)
 
 

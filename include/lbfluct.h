@@ -65,6 +65,8 @@ typedef enum { LB_F32 = 0, LB_F16 = 1, LB_BF16 = 2 } lb_dtype;
 #define LB_DERR_NLIST_FULL    0x2u   /* a particle had too many neighbours      */
 #define LB_DERR_NONFINITE     0x4u   /* non-finite moment sum                   */
 #define LB_DERR_BARRIER       0x8u   /* batched kernel: grid barrier timed out  */
+#define LB_DERR_PARTICLE_RANGE 0x10u /* a particle position outside the box or not
+                                        finite (its stencil was clamped)         */
 
 #define LB_NSUMS 38  /* lb_moments sums: [0..18] sum_r dm_k, [19..37] sum_r dm_k^2 */
 

@@ -88,9 +88,11 @@ __global__ void __launch_bounds__(kRedThreads)
     using S = lbd::Store<DT>;
     const size_t N = a.nn;
     const bool walls = a.z0 > 0;
-    double acc[2 * 19];
+    // per-thread partial sums in FP32 (a thread sees ~N / grid nodes); the
+    // block and grid levels add in FP64
+    float acc[2 * 19];
 #pragma unroll
-    for (int k = 0; k < 38; ++k) acc[k] = 0.0;
+    for (int k = 0; k < 38; ++k) acc[k] = 0.0f;
 
     for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N;
          s += (size_t)gridDim.x * blockDim.x) {
@@ -149,8 +151,8 @@ __global__ void __launch_bounds__(kRedThreads)
         if (partials) {
 #pragma unroll
             for (int k = 0; k < 19; ++k) {
-                acc[k] += (double)m[k];
-                acc[19 + k] += (double)m[k] * (double)m[k];
+                acc[k] += m[k];
+                acc[19 + k] = fmaf(m[k], m[k], acc[19 + k]);
             }
         }
     }
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kRedThreads)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < 38; ++k) {
-        double v = acc[k];
+        double v = (double)acc[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) red[warp][k] = v;

@@ -130,22 +130,34 @@ __device__ __forceinline__ void node_velocity(const typename lbd::Store<DT>::T *
 }
 
 // Linear stencil: base node and the three 1-D weight pairs (1 - t, t).
-__device__ __forceinline__ void stencil_base(const double r[3], int b[3], float t[3])
+// Positions outside the box (or not finite) never index memory: the base is
+// clamped into the box and false is returned so the caller can flag it.
+__device__ __forceinline__ bool stencil_base(const double r[3], const StepArgs &a, int b[3], float t[3])
 {
+    const int L[3] = {a.nx, a.ny, a.nz};
+    bool ok = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double f = floor(r[c]);
-        b[c] = (int)f;
-        t[c] = (float)(r[c] - f);
+        double v = r[c];
+        if (!(v >= 0.0 && v < (double)L[c])) {
+            ok = false;
+            v = 0.0;
+        }
+        const double f = floor(v);
+        int bi = (int)f;
+        bi = bi < 0 ? 0 : (bi > L[c] - 1 ? L[c] - 1 : bi);
+        b[c] = bi;
+        t[c] = (float)(v - (double)bi);
     }
+    return ok;
 }
 
 template <int DT>
-__device__ __forceinline__ void interpolate_u(const typename lbd::Store<DT>::T *__restrict__ src,
+__device__ __forceinline__ bool interpolate_u(const typename lbd::Store<DT>::T *__restrict__ src,
                                               const float *__restrict__ ffield, const double r[3],
                                               const StepArgs &a, int b[3], float t[3], float up[3])
 {
-    stencil_base(r, b, t);
+    const bool ok = stencil_base(r, a, b, t);
     up[0] = up[1] = up[2] = 0.0f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -161,6 +173,7 @@ __device__ __forceinline__ void interpolate_u(const typename lbd::Store<DT>::T *
         up[1] += w * u[1];
         up[2] += w * u[2];
     }
+    return ok;
 }
 
 __device__ __forceinline__ void min_image(float d[3], const StepArgs &g)
@@ -310,7 +323,7 @@ __global__ void __launch_bounds__(kPartThreads)
     // fluid velocity at the particle
     int b[3];
     float t[3], up[3];
-    interpolate_u<DT>(src, ffield, r, g, b, t, up);
+    if (!interpolate_u<DT>(src, ffield, r, g, b, t, up)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
 
     // exact Ornstein-Uhlenbeck momentum update
     const float x1 = G * c.dt / m;
@@ -405,14 +418,14 @@ __global__ void k_clear_records(float *facc, const int *records, size_t n, StepA
 
 template <int DT>
 __global__ void k_interpolate(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
-                              const double *pos, float *u_out, int n, StepArgs g)
+                              const double *pos, float *u_out, int n, unsigned int *err, StepArgs g)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
     int b[3];
     float t[3], up[3];
-    interpolate_u<DT>(src, ffield, r, g, b, t, up);
+    if (!interpolate_u<DT>(src, ffield, r, g, b, t, up)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
     u_out[3 * p] = up[0];
     u_out[3 * p + 1] = up[1];
     u_out[3 * p + 2] = up[2];
@@ -635,15 +648,15 @@ lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
     switch (h->p.dtype) {
     case LB_F32:
         k_interpolate<0><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const float *>(h->pops[h->cur]),
-                                                                  h->force, pos, u_out, n, g);
+                                                                  h->force, pos, u_out, n, h->d_err, g);
         break;
     case LB_F16:
         k_interpolate<1><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const __half *>(h->pops[h->cur]),
-                                                                  h->force, pos, u_out, n, g);
+                                                                  h->force, pos, u_out, n, h->d_err, g);
         break;
     default:
         k_interpolate<2><<<blocks, kPartThreads, 0, h->stream>>>(
-            static_cast<const __nv_bfloat16 *>(h->pops[h->cur]), h->force, pos, u_out, n, g);
+            static_cast<const __nv_bfloat16 *>(h->pops[h->cur]), h->force, pos, u_out, n, h->d_err, g);
         break;
     }
     h->launches += 1;

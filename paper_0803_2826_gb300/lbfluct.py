@@ -22,6 +22,7 @@ LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ETIMEOUT, LB_EUNSUPPORT
 LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
+LB_DERR_PARTICLE_RANGE = 16
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
                 5: "LB_ETIMEOUT", 6: "LB_EUNSUPPORTED", 7: "LB_EDEVICE"}
