@@ -76,6 +76,7 @@ StepArgs make_args(const lb_handle *h)
     a.key1 = (uint32_t)(p.seed >> 32);
     a.replica = p.replica;
     a.step = h->step;
+    a.rk = lbd::make_round_keys(p.seed);
     return a;
 }
 

@@ -206,62 +206,121 @@ __device__ __forceinline__ void backward(const float M[19], float n[19])
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): multipliers 0xD2511F53, 0xCD9E8D57,
-// key increments 0x9E3779B9, 0xBB67AE85, ten rounds.
+// key increments 0x9E3779B9, 0xBB67AE85, ten rounds.  The 64-bit product
+// gives both halves of each multiply in one instruction.
 // ---------------------------------------------------------------------------
 struct U4 {
     uint32_t x, y, z, w;
 };
 
-__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u, kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u, kPhiloxW1 = 0xBB67AE85u;
+
+__host__ __device__ __forceinline__ void philox_round(U4 &c, uint32_t k0, uint32_t k1)
 {
-#ifdef __CUDA_ARCH__
-    return __umulhi(a, b);
-#else
-    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
-#endif
+    const uint64_t p0 = (uint64_t)kPhiloxM0 * (uint64_t)c.x;
+    const uint64_t p1 = (uint64_t)kPhiloxM1 * (uint64_t)c.z;
+    c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0};
 }
 
+// Key schedule computed in the loop (particle kernels: one call per thread).
 __host__ __device__ __forceinline__ U4 philox10(U4 c, uint32_t k0, uint32_t k1)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = mulhi32(0xD2511F53u, c.x);
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = mulhi32(0xCD9E8D57u, c.z);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        philox_round(c, k0, k1);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
     }
     return c;
 }
 
-// Uniform in (0,1): odd 24-bit integer times 2^-24, exact in FP32.
-__device__ __forceinline__ float uniform01(uint32_t x)
+// Round keys precomputed on the host (kernel parameters, so every XOR with a
+// key reads the constant bank).
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__host__ __device__ __forceinline__ U4 philox10(U4 c, const RoundKeys &rk)
 {
-    return __uint2float_rn((x >> 9) * 2u + 1u) * 5.9604644775390625e-8f;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) philox_round(c, rk.k0[r], rk.k1[r]);
+    return c;
 }
 
-// Box-Muller pair from two raw words.
+inline RoundKeys make_round_keys(uint64_t seed)
+{
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k0[r] = k0;
+        rk.k1[r] = k1;
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return rk;
+}
+
+// Uniform in (0,1): (2 (x >> 9) + 1) 2^-24.  The top 23 bits become the
+// mantissa of a float in [1, 2); subtracting 1 - 2^-24 is exact (Sterbenz)
+// and yields the odd multiple of 2^-24, so no integer-to-float conversion.
+__device__ __forceinline__ float uniform01(uint32_t x)
+{
+    return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
+}
+
+// sin and cos of 2 pi v for a dyadic v in (0, 1): v = q/4 + f exactly with
+// q = rint(4 v) and |f| <= 1/8, so the polynomial argument needs no rounded
+// multiple of pi.  Taylor series of sin(2 pi f) to f^9 and cos(2 pi f) to
+// f^10 (truncation below 2e-9 for |2 pi f| <= pi/4), then the quadrant q.
+__device__ __forceinline__ void sincos_2pi(float v, float &sn, float &cs)
+{
+    constexpr double T = 6.283185307179586476925286766559;
+    constexpr float S1 = (float)T;
+    constexpr float S3 = (float)(-T * T * T / 6.0);
+    constexpr float S5 = (float)(T * T * T * T * T / 120.0);
+    constexpr float S7 = (float)(-T * T * T * T * T * T * T / 5040.0);
+    constexpr float S9 = (float)(T * T * T * T * T * T * T * T * T / 362880.0);
+    constexpr float C2 = (float)(-T * T / 2.0);
+    constexpr float C4 = (float)(T * T * T * T / 24.0);
+    constexpr float C6 = (float)(-T * T * T * T * T * T / 720.0);
+    constexpr float C8 = (float)(T * T * T * T * T * T * T * T / 40320.0);
+    constexpr float C10 = (float)(-T * T * T * T * T * T * T * T * T * T / 3628800.0);
+    const float q = rintf(4.0f * v);
+    const float f = fmaf(q, -0.25f, v);
+    const float f2 = f * f;
+    const float s = f * fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, S9, S7), S5), S3), S1);
+    const float c = fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, C10, C8), C6), C4), C2), 1.0f);
+    const int qi = (int)q;
+    float cq = (qi & 1) ? s : c;
+    float sq = (qi & 1) ? c : s;
+    if ((qi + 1) & 2) cq = -cq;  // quadrants 1, 2
+    if (qi & 2) sq = -sq;        // quadrants 2, 3
+    sn = sq;
+    cs = cq;
+}
+
+// Box-Muller pair from two raw words: sqrt(-2 ln v1) (cos, sin)(2 pi v2).
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
     const float v1 = uniform01(a);
     const float v2 = uniform01(b);
-    const float r = sqrtf(-2.0f * logf(v1));
+    const float L = -2.0f * logf(v1);  // > 0 since v1 <= 1 - 2^-24
+    const float r = L * rsqrtf(L);
     float s, c;
-    sincospif(2.0f * v2, &s, &c);
+    sincos_2pi(v2, s, c);
     g0 = r * c;
     g1 = r * s;
 }
 
-// Sixteen Gaussians for (seed, counter word 0, step, domain, replica):
-// Philox blocks b = 0..3 with counter (w0, step, domain<<8 | b, replica).
-__device__ __forceinline__ void gaussians16(uint32_t k0, uint32_t k1, uint32_t w0, uint32_t step,
-                                            uint32_t domain, uint32_t replica, float g[16])
+// Sixteen Gaussians for counter word 0, step, domain, replica: Philox blocks
+// b = 0..3 with counter (w0, step, domain<<8 | b, replica).
+__device__ __forceinline__ void gaussians16(const RoundKeys &rk, uint32_t w0, uint32_t step, uint32_t domain,
+                                            uint32_t replica, float g[16])
 {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
-        const U4 r = philox10(U4{w0, step, (domain << 8) | (uint32_t)b, replica}, k0, k1);
+        const U4 r = philox10(U4{w0, step, (domain << 8) | (uint32_t)b, replica}, rk);
         box_muller(r.x, r.y, g[4 * b + 0], g[4 * b + 1]);
         box_muller(r.z, r.w, g[4 * b + 2], g[4 * b + 3]);
     }

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <string>
 
+#include "d3q19.cuh"
 #include "lbfluct.h"
 
 namespace lbi {
@@ -30,6 +31,7 @@ struct StepArgs {
     uint32_t key0, key1;   // Philox key (seed)
     uint32_t replica;
     uint32_t step;
+    lbd::RoundKeys rk;     // Philox round keys of (key0, key1)
 };
 
 struct Particles;  // defined in particles.cu

@@ -24,7 +24,8 @@
 
 namespace lbi {
 
-constexpr int kMaxNb = 48;          // Verlet-list capacity per particle
+constexpr int kMaxNb = 48;          // Verlet-list capacity per particle and chunk
+constexpr int kChunks = 8;          // neighbour-list chunks = lanes per particle
 constexpr float kSkin = 0.4f;       // Verlet skin in units of sigma
 constexpr int kPartThreads = 128;
 
@@ -35,8 +36,8 @@ struct Particles {
     size_t rec_cap = 0;
     size_t n_records = 0;
     bool records_overflow = false;
-    int *nlist = nullptr;        // [cap][kMaxNb]
-    int *ncount = nullptr;       // [cap]
+    int *nlist = nullptr;        // [cap][kChunks][kMaxNb]
+    int *ncount = nullptr;       // [cap][kChunks]
     float *ref_pos = nullptr;    // [cap][3] positions at the last build
     unsigned int *flags = nullptr;  // two rebuild-request slots
     uint32_t sub_counter = 0;
@@ -209,17 +210,23 @@ __global__ void k_half_drift(double *pos, float *mom, const float *mass, CoupleA
     }
 }
 
-// Verlet-list build over all pairs, tiled through shared memory; returns at
-// once unless a rebuild was requested in slot `rd`.
-constexpr int kTile = 256;
+// Verlet-list build over all pairs.  Particles j are split into kChunks
+// contiguous chunks; block (bi, c) tests 128 particles i against chunk c
+// (tiled through shared memory) and writes the partial list of (i, c), so no
+// atomics or clearing are needed and the sub-step kernel's lane c reads
+// chunk c.  Returns at once unless a rebuild was requested in slot `rd`.
+constexpr int kTile = 128;
 
 __global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *nlist, int *ncount, float *ref_pos,
-                                                       unsigned int *flags, unsigned int *err, CoupleArgs c,
+                                                       const unsigned int *flags, unsigned int *err, CoupleArgs c,
                                                        uint32_t rd)
 {
     if (flags[rd] == 0u) return;
     __shared__ float sp[kTile][3];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int per = (c.n + kChunks - 1) / kChunks;
+    const int j0 = chunk * per, j1 = min(c.n, j0 + per);
     float ri[3] = {0.f, 0.f, 0.f};
     if (i < c.n) {
         ri[0] = (float)pos[3 * i];
@@ -228,15 +235,16 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *n
     }
     int cnt = 0;
     bool full = false;
-    for (int base = 0; base < c.n; base += kTile) {
+    int *mine = nlist + ((size_t)i * kChunks + chunk) * kMaxNb;
+    for (int base = j0; base < j1; base += kTile) {
         const int j = base + threadIdx.x;
-        if (j < c.n) {
+        if (j < j1) {
             sp[threadIdx.x][0] = (float)pos[3 * j];
             sp[threadIdx.x][1] = (float)pos[3 * j + 1];
             sp[threadIdx.x][2] = (float)pos[3 * j + 2];
         }
         __syncthreads();
-        const int lim = min(kTile, c.n - base);
+        const int lim = min(kTile, j1 - base);
         if (i < c.n) {
             for (int q = 0; q < lim; ++q) {
                 const int jj = base + q;
@@ -245,7 +253,7 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *n
                 min_image(d, c.g);
                 const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 if (r2 < c.rlist2) {
-                    if (cnt < kMaxNb) nlist[(size_t)i * kMaxNb + cnt] = jj;
+                    if (cnt < kMaxNb) mine[cnt] = jj;
                     else full = true;
                     ++cnt;
                 }
@@ -254,37 +262,48 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *n
         __syncthreads();
     }
     if (i < c.n) {
-        ncount[i] = cnt < kMaxNb ? cnt : kMaxNb;
-        ref_pos[3 * i] = ri[0];
-        ref_pos[3 * i + 1] = ri[1];
-        ref_pos[3 * i + 2] = ri[2];
+        ncount[(size_t)i * kChunks + chunk] = cnt < kMaxNb ? cnt : kMaxNb;
+        if (chunk == 0) {
+            ref_pos[3 * i] = ri[0];
+            ref_pos[3 * i + 1] = ri[1];
+            ref_pos[3 * i + 2] = ri[2];
+        }
         if (full) atomicOr(err, LB_DERR_NLIST_FULL);
     }
 }
 
-__global__ void k_clear_flag(unsigned int *flags, uint32_t slot) { flags[slot] = 0u; }
-
+// One particle sub-step; eight lanes per particle.  Lane q gathers the fluid
+// velocity of stencil node q (19 loads) and spreads the impulse there; the
+// lanes split the neighbour list (lane q reads chunk q) and the FENE bonds,
+// and shuffle-reduce u_p and F^c.  Every lane then has the same u_p, F^c and
+// theta and does the (cheap) momentum update; lane 0 writes the particle.
 template <int DT>
 __global__ void __launch_bounds__(kPartThreads)
     k_substep(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
               const double *__restrict__ pos_in, double *__restrict__ pos_out, float *mom, const float *mass,
               const float *gamma, const int *nlist, const int *ncount, const float *ref_pos, float *facc,
-              int *records, unsigned int *flags, unsigned int *err, CoupleArgs c)
+              int *records, unsigned int *flags, unsigned int *err, CoupleArgs c, uint32_t clear_slot)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= c.n) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && c.use_wca) flags[clear_slot] = 0u;  // the list build has run
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid >> 3;
+    const int q = tid & 7;
+    if (p >= c.n) return;  // whole groups of eight leave together
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     const StepArgs &g = c.g;
     double r[3] = {pos_in[3 * p], pos_in[3 * p + 1], pos_in[3 * p + 2]};
     float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
     const float m = mass ? mass[p] : c.mass0;
     const float G = gamma ? gamma[p] : c.gamma0;
 
-    // conservative forces at the half-step positions
+    // conservative forces at the half-step positions, split over the lanes
     float F[3] = {0.f, 0.f, 0.f};
     if (c.use_wca) {
-        const int nc = ncount[p];
-        for (int q = 0; q < nc; ++q) {
-            const int j = nlist[(size_t)p * kMaxNb + q];
+        const size_t li = (size_t)p * kChunks + q;
+        const int nc = ncount[li];
+        const int *lst = nlist + li * kMaxNb;
+        for (int k = 0; k < nc; ++k) {
+            const int j = lst[k];
             float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
                           (float)(r[2] - pos_in[3 * j + 2])};
             min_image(d, g);
@@ -299,12 +318,11 @@ __global__ void __launch_bounds__(kPartThreads)
             }
         }
     }
-    if (c.chain_len > 1) {
+    if (c.chain_len > 1 && q < 2) {
         const int k = p % c.chain_len;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            const int j = side == 0 ? p - 1 : p + 1;
-            if ((side == 0 && k == 0) || (side == 1 && (k == c.chain_len - 1 || j >= c.n))) continue;
+        const int j = q == 0 ? p - 1 : p + 1;
+        const bool bonded = (q == 0) ? (k > 0) : (k < c.chain_len - 1 && j < c.n);
+        if (bonded) {
             float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
                           (float)(r[2] - pos_in[3 * j + 2])};
             min_image(d, g);
@@ -320,21 +338,38 @@ __global__ void __launch_bounds__(kPartThreads)
         }
     }
 
-    // fluid velocity at the particle
+    // fluid velocity at the particle: lane q takes stencil node q
     int b[3];
-    float t[3], up[3];
-    if (!interpolate_u<DT>(src, ffield, r, g, b, t, up)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    float t[3];
+    if (!stencil_base(r, g, b, t) && q == 0) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+    const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
+    int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
+    if (x >= g.nx) x -= g.nx;
+    if (y >= g.ny) y -= g.ny;
+    if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+    float un[3];
+    node_velocity<DT>(src, ffield, x, y, z, g, un);
+    float up[3] = {w * un[0], w * un[1], w * un[2]};
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            up[k] += __shfl_xor_sync(gmask, up[k], o);
+            F[k] += __shfl_xor_sync(gmask, F[k], o);
+        }
+    }
 
-    // exact Ornstein-Uhlenbeck momentum update
+    // exact Ornstein-Uhlenbeck momentum update (same in every lane)
     const float x1 = G * c.dt / m;
     const float C1 = expf(-x1);
     const float C2 = (m / G) * (-expm1f(-x1));
     const float C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
     float th[3] = {0.f, 0.f, 0.f};
     if (g.kT > 0.0f) {
-        const lbd::U4 w = lbd::philox10(lbd::U4{(uint32_t)p, c.md_step, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
+        const lbd::U4 wv = lbd::philox10(lbd::U4{(uint32_t)p, c.md_step, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
         if (c.noise_kind == 1) {
-            const uint32_t ws[3] = {w.x, w.y, w.z};
+            const uint32_t ws[3] = {wv.x, wv.y, wv.z};
             const float s3 = 1.7320508075688772f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -343,8 +378,8 @@ __global__ void __launch_bounds__(kPartThreads)
             }
         } else {
             float g3;
-            lbd::box_muller(w.x, w.y, th[0], th[1]);
-            lbd::box_muller(w.z, w.w, th[2], g3);
+            lbd::box_muller(wv.x, wv.y, th[0], th[1]);
+            lbd::box_muller(wv.z, wv.w, th[2], g3);
         }
     }
     float pn[3], J[3];
@@ -354,21 +389,15 @@ __global__ void __launch_bounds__(kPartThreads)
         J[k] = pn[k] - pm[k] - C2 * F[k];
     }
 
-    // spread -J Delta into the accumulator
-    const size_t P = g.pitch;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
-        const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
-        int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
-        if (x >= g.nx) x -= g.nx;
-        if (y >= g.ny) y -= g.ny;
-        if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+    // spread -J Delta: lane q into its own node
+    {
+        const size_t P = g.pitch;
         const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
         atomicAdd(facc + s, -J[0] * w);
         atomicAdd(facc + P + s, -J[1] * w);
         atomicAdd(facc + 2 * P + s, -J[2] * w);
     }
+    if (q != 0) return;
     if (records) records[p] = (int)(((size_t)b[2] * g.ny + b[1]) * g.nx + b[0]);
 
     // second half drift of this sub-step, then the first of the next one
@@ -466,8 +495,8 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
         P->ncount = nullptr;
         P->ref_pos = nullptr;
         cudaError_t e = cudaMalloc((void **)&P->pos_tmp, (size_t)n * 3 * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kMaxNb * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kChunks * kMaxNb * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * kChunks * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->ref_pos, (size_t)n * 3 * sizeof(float));
         if (e != cudaSuccess) {
             P->cap = 0;
@@ -547,18 +576,19 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     for (int s = 0; s < cp->n_substeps; ++s) {
         const uint32_t rd = P->sub_counter & 1u, wr = rd ^ 1u;
         if (need_nlist) {
-            k_build_nlist<<<(n + kTile - 1) / kTile, kTile, 0, h->stream>>>(buf[s & 1], P->nlist, P->ncount,
-                                                                           P->ref_pos, P->flags, h->d_err, c, rd);
-            k_clear_flag<<<1, 1, 0, h->stream>>>(P->flags, rd);
-            h->launches += 2;
+            dim3 bgrid((n + kTile - 1) / kTile, kChunks);
+            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(buf[s & 1], P->nlist, P->ncount, P->ref_pos, P->flags,
+                                                          h->d_err, c, rd);
+            h->launches += 1;
         }
         c.md_step = cp->md_step0 + (uint32_t)s;
         c.last = (s == cp->n_substeps - 1);
         c.slot = wr;
         int *rec = P->records + P->n_records;
-        k_substep<DT><<<blocks, kPartThreads, 0, h->stream>>>(
+        const int sblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
+        k_substep<DT><<<sblocks, kPartThreads, 0, h->stream>>>(
             src, h->force, buf[s & 1], buf[(s + 1) & 1], pp->mom, pp->mass, pp->gamma, P->nlist, P->ncount,
-            need_nlist ? P->ref_pos : nullptr, h->facc, rec, P->flags, h->d_err, c);
+            need_nlist ? P->ref_pos : nullptr, h->facc, rec, P->flags, h->d_err, c, rd);
         P->n_records += (size_t)n;
         P->sub_counter += 1;
         h->launches += 1;

@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
 
     if (NOISE) {
         float g[16];
-        lbd::gaussians16(a.key0, a.key1, self, a.step, 0u, a.replica, g);
+        lbd::gaussians16(a.rk, self, a.step, 0u, a.replica, g);
         const float rn = a.noise_rho0 ? a.rho0 : rho;
         const float s = sqrtf(a.mu * rn);
         // sqrt(mu rho w_k) phi_k r_k, divided by w_k: sqrt(mu rho / w_k) phi_k r_k
