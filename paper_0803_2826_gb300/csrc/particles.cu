@@ -4,18 +4,20 @@
 //
 // Per LB step the caller runs n_substeps particle steps against the frozen
 // fluid velocity u = (sum n c + f_ext/2)/rho of the current state.  One
-// kernel launch per sub-step does, for each particle p (one thread):
-//   forces     F^c from FENE bonds (chain neighbours p-1, p+1) and WCA pairs
-//              from a Verlet list (Eqs. (ufene), (ulennardjones))
-//   interpolate u_p = sum_8 phi2 phi2 phi2 u(node)            Eqs. (ufluid_discrete), (Delta), (2point)
-//   OU update  p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta     Eq. (langevin_momentum_update)
-//   spread     facc(node) -= J Delta(node - r_p), J = p' - p - C2 F^c   Eq. (ftotal)
-//   drift      second half drift of this sub-step and first half drift of the next
-// The half-drift positions ping-pong between the caller's buffer and an
-// internal one, so every thread reads the positions of the same sub-step.
-// The Verlet list (cut-off + skin) is rebuilt, inside a launch that returns
-// at once when nothing moved far enough, whenever a particle has moved more
-// than half the skin since the last build.
+// kernel launch per sub-step does, for each particle (a group of 8 lanes):
+//   forces      F^c from FENE bonds (chain neighbours p-1, p+1) and WCA pairs
+//               from a Verlet list                          Eqs. (ufene), (ulennardjones)
+//   interpolate u_p = sum_8 phi2 phi2 phi2 u(node)          Eqs. (ufluid_discrete), (Delta), (2point)
+//   OU update   p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta  Eq. (langevin_momentum_update)
+//   spread      facc(node) -= J Delta(node - r_p), J = p' - p - C2 F^c   Eq. (ftotal)
+//   drift       second half drift of this sub-step and first half drift of the next
+//
+// Positions are double in the caller's buffer, but inside a coupling call a
+// position is an integer cell plus an FP32 offset in [0, 1) (a "shadow"
+// float4, the cell packed in 10-bit fields), so the kernels do no FP64
+// arithmetic except one conversion in and one out per call (GB300 runs FP64
+// at a small fraction of its FP32 rate).  Shadows ping-pong between two
+// buffers so every thread reads the positions of the same sub-step.
 #include <algorithm>
 #include <cstdio>
 
@@ -28,17 +30,17 @@ constexpr int kMaxNb = 48;          // Verlet-list capacity per particle and chu
 constexpr int kChunks = 8;          // neighbour-list chunks = lanes per particle
 constexpr float kSkin = 0.4f;       // Verlet skin in units of sigma
 constexpr int kPartThreads = 128;
+constexpr int kMaxCellDim = 1024;   // cells are packed in 10-bit fields
 
 struct Particles {
     int cap = 0;
-    double *pos_tmp = nullptr;   // [cap][3]
+    float4 *shadow[2] = {nullptr, nullptr};  // [cap] cell + offset
     int *records = nullptr;      // base node of each (sub-step, particle) stencil
     size_t rec_cap = 0;
     size_t n_records = 0;
-    bool records_overflow = false;
     int *nlist = nullptr;        // [cap][kChunks][kMaxNb]
     int *ncount = nullptr;       // [cap][kChunks]
-    float *ref_pos = nullptr;    // [cap][3] positions at the last build
+    float4 *ref = nullptr;       // [cap] shadow positions at the last build
     unsigned int *flags = nullptr;  // two rebuild-request slots
     uint32_t sub_counter = 0;
     int nlist_n = -1;            // particle count the list was built for
@@ -54,18 +56,50 @@ struct CoupleArgs {
     int noise_kind;
     float dt;
     float mass0, gamma0;
-    float eps, sigma2, rc2, rlist2, k_fene, inv_r02;
+    int uniform_coef;      // no per-particle mass / gamma: C1..C3 below are valid
+    float C1, C2, C3;
+    float eps, sigma2, rc2, rlist2, k_fene, inv_r02, half_skin2;
     uint32_t pkey0, pkey1;
     uint32_t md_step;
-    int last;          // last sub-step of this call
-    uint32_t slot;     // rebuild slot written by this sub-step
+    int last;              // last sub-step of this call
+    uint32_t slot;         // rebuild slot written by this sub-step
 };
 
-__device__ __forceinline__ void confine(double r[3], float p[3], const StepArgs &g)
+// ---- cell + offset positions -----------------------------------------------
+
+struct CPos {
+    int c[3];
+    float f[3];
+};
+
+__device__ __forceinline__ float4 pack(const CPos &q)
+{
+    const uint32_t w = (uint32_t)q.c[0] | ((uint32_t)q.c[1] << 10) | ((uint32_t)q.c[2] << 20);
+    return make_float4(q.f[0], q.f[1], q.f[2], __uint_as_float(w));
+}
+
+__device__ __forceinline__ CPos unpack(float4 v)
+{
+    const uint32_t w = __float_as_uint(v.w);
+    CPos q;
+    q.c[0] = (int)(w & 1023u);
+    q.c[1] = (int)((w >> 10) & 1023u);
+    q.c[2] = (int)((w >> 20) & 1023u);
+    q.f[0] = v.x;
+    q.f[1] = v.y;
+    q.f[2] = v.z;
+    return q;
+}
+
+__device__ __forceinline__ double join1(int c, float f) { return (double)c + (double)f; }
+
+// Put a double position into the box (periodic wrap; specular reflection
+// into z in [1, nz-2] with walls, flipping p_z) -- the definition the
+// FP32 path below follows.
+__device__ void confine_d(double r[3], float p[3], const StepArgs &g)
 {
     const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
     const bool walls = g.z0 > 0;
-#pragma unroll
     for (int c = 0; c < 3; ++c) {
         if (c == 2 && walls) {
             const double lo = 1.0, hi = (double)(g.nz - 2);
@@ -75,6 +109,79 @@ __device__ __forceinline__ void confine(double r[3], float p[3], const StepArgs 
             r[c] -= L[c] * floor(r[c] / L[c]);
             if (r[c] >= L[c]) r[c] -= L[c];
         }
+    }
+}
+
+// Split a double position (already in the box) into cell + offset.  Returns
+// false (and a clamped position) for positions outside the box or not finite.
+__device__ __forceinline__ bool split(const double r[3], const StepArgs &g, CPos &q)
+{
+    const int L[3] = {g.nx, g.ny, g.nz};
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double v = r[k];
+        if (!(v >= 0.0 && v < (double)L[k])) {
+            ok = false;
+            v = 0.0;
+        }
+        int c = (int)floor(v);
+        c = c < 0 ? 0 : (c > L[k] - 1 ? L[k] - 1 : c);
+        q.c[k] = c;
+        float f = (float)(v - (double)c);
+        q.f[k] = f < 1.0f ? f : 0.99999994f;
+    }
+    return ok;
+}
+
+// r += h p (FP32 offset), then wrap / reflect as confine_d does.  A step of
+// more than a few cells, or a non-finite one, is not a valid particle move:
+// the position is clamped into the box and false is returned.
+__device__ __forceinline__ bool drift(CPos &q, float p[3], float h, const StepArgs &g)
+{
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const bool walls = g.z0 > 0;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float f = fmaf(h, p[k], q.f[k]);
+        if (!(f > -4.0f && f < 5.0f)) {  // also catches NaN
+            ok = false;
+            f = q.f[k];
+        }
+        const float fl = floorf(f);
+        q.c[k] += (int)fl;
+        q.f[k] = f - fl;
+        if (q.f[k] >= 1.0f) {  // rounding of f - fl up to 1
+            q.f[k] = 0.0f;
+            q.c[k] += 1;
+        }
+        if (!(k == 2 && walls)) q.c[k] = ((q.c[k] % L[k]) + L[k]) % L[k];
+    }
+    if (walls) {
+        const int hi = g.nz - 2;
+        if (q.c[2] < 1 || q.c[2] > hi || (q.c[2] == hi && q.f[2] > 0.0f)) {
+            double r[3] = {join1(q.c[0], q.f[0]), join1(q.c[1], q.f[1]), join1(q.c[2], q.f[2])};
+            confine_d(r, p, g);
+            if (!split(r, g, q)) ok = false;  // split clamps into the box
+        }
+    }
+    return ok;
+}
+
+// Minimum-image separation a - b in FP32 from cell + offset positions.
+__device__ __forceinline__ void separation(const CPos &a, const CPos &b, const StepArgs &g, float d[3])
+{
+    const int L[3] = {g.nx, g.ny, g.nz};
+    const bool walls = g.z0 > 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int dc = a.c[k] - b.c[k];
+        if (!(k == 2 && walls)) {
+            if (2 * dc > L[k]) dc -= L[k];
+            else if (2 * dc < -L[k]) dc += L[k];
+        }
+        d[k] = (float)dc + (a.f[k] - b.f[k]);
     }
 }
 
@@ -130,69 +237,29 @@ __device__ __forceinline__ void node_velocity(const typename lbd::Store<DT>::T *
     u[2] = (jz + 0.5f * fz) * ir;
 }
 
-// Linear stencil: base node and the three 1-D weight pairs (1 - t, t).
-// Positions outside the box (or not finite) never index memory: the base is
-// clamped into the box and false is returned so the caller can flag it.
-__device__ __forceinline__ bool stencil_base(const double r[3], const StepArgs &a, int b[3], float t[3])
+// Stencil node q (0..7) of the cell containing position pos: coordinates and
+// linear weight phi2(x) phi2(y) phi2(z).
+__device__ __forceinline__ float stencil_node(const CPos &pos, int q, const StepArgs &g, int &x, int &y, int &z)
 {
-    const int L[3] = {a.nx, a.ny, a.nz};
-    bool ok = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        double v = r[c];
-        if (!(v >= 0.0 && v < (double)L[c])) {
-            ok = false;
-            v = 0.0;
-        }
-        const double f = floor(v);
-        int bi = (int)f;
-        bi = bi < 0 ? 0 : (bi > L[c] - 1 ? L[c] - 1 : bi);
-        b[c] = bi;
-        t[c] = (float)(v - (double)bi);
-    }
-    return ok;
-}
-
-template <int DT>
-__device__ __forceinline__ bool interpolate_u(const typename lbd::Store<DT>::T *__restrict__ src,
-                                              const float *__restrict__ ffield, const double r[3],
-                                              const StepArgs &a, int b[3], float t[3], float up[3])
-{
-    const bool ok = stencil_base(r, a, b, t);
-    up[0] = up[1] = up[2] = 0.0f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
-        const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
-        int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
-        if (x >= a.nx) x -= a.nx;
-        if (y >= a.ny) y -= a.ny;
-        if (z >= a.nz) z = (a.z0 > 0) ? a.nz - 1 : z - a.nz;
-        float u[3];
-        node_velocity<DT>(src, ffield, x, y, z, a, u);
-        up[0] += w * u[0];
-        up[1] += w * u[1];
-        up[2] += w * u[2];
-    }
-    return ok;
-}
-
-__device__ __forceinline__ void min_image(float d[3], const StepArgs &g)
-{
-    const float L[3] = {(float)g.nx, (float)g.ny, (float)g.nz};
-    const bool walls = g.z0 > 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        if (c == 2 && walls) continue;
-        d[c] -= L[c] * rintf(d[c] / L[c]);
-    }
+    const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
+    const float w = (dx ? pos.f[0] : 1.0f - pos.f[0]) * (dy ? pos.f[1] : 1.0f - pos.f[1]) *
+                    (dz ? pos.f[2] : 1.0f - pos.f[2]);
+    x = pos.c[0] + dx;
+    y = pos.c[1] + dy;
+    z = pos.c[2] + dz;
+    if (x >= g.nx) x -= g.nx;
+    if (y >= g.ny) y -= g.ny;
+    if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+    return w;
 }
 
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
 
-__global__ void k_half_drift(double *pos, float *mom, const float *mass, CoupleArgs c)
+// First half drift of a call: double positions in, shadow out.
+__global__ void k_half_drift(const double *pos, float *mom, const float *mass, float4 *shadow, unsigned int *err,
+                             CoupleArgs c)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= c.n) return;
@@ -202,12 +269,13 @@ __global__ void k_half_drift(double *pos, float *mom, const float *mass, CoupleA
     const double h = 0.5 * (double)c.dt / (double)m;
 #pragma unroll
     for (int k = 0; k < 3; ++k) r[k] += h * (double)pm[k];
-    confine(r, pm, c.g);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        pos[3 * p + k] = r[k];
-        mom[3 * p + k] = pm[k];
-    }
+    confine_d(r, pm, c.g);
+    CPos q;
+    if (!split(r, c.g, q)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    shadow[p] = pack(q);
+    mom[3 * p] = pm[0];
+    mom[3 * p + 1] = pm[1];
+    mom[3 * p + 2] = pm[2];
 }
 
 // Verlet-list build over all pairs.  Particles j are split into kChunks
@@ -217,40 +285,36 @@ __global__ void k_half_drift(double *pos, float *mom, const float *mass, CoupleA
 // chunk c.  Returns at once unless a rebuild was requested in slot `rd`.
 constexpr int kTile = 128;
 
-__global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *nlist, int *ncount, float *ref_pos,
+__global__ void __launch_bounds__(kTile) k_build_nlist(const float4 *shadow, int *nlist, int *ncount, float4 *ref,
                                                        const unsigned int *flags, unsigned int *err, CoupleArgs c,
                                                        uint32_t rd)
 {
     if (flags[rd] == 0u) return;
-    __shared__ float sp[kTile][3];
+    __shared__ float4 sp[kTile];
     const int i = blockIdx.x * kTile + threadIdx.x;
     const int chunk = blockIdx.y;
     const int per = (c.n + kChunks - 1) / kChunks;
     const int j0 = chunk * per, j1 = min(c.n, j0 + per);
-    float ri[3] = {0.f, 0.f, 0.f};
+    CPos pi{};
+    float4 raw = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < c.n) {
-        ri[0] = (float)pos[3 * i];
-        ri[1] = (float)pos[3 * i + 1];
-        ri[2] = (float)pos[3 * i + 2];
+        raw = shadow[i];
+        pi = unpack(raw);
     }
     int cnt = 0;
     bool full = false;
     int *mine = nlist + ((size_t)i * kChunks + chunk) * kMaxNb;
     for (int base = j0; base < j1; base += kTile) {
         const int j = base + threadIdx.x;
-        if (j < j1) {
-            sp[threadIdx.x][0] = (float)pos[3 * j];
-            sp[threadIdx.x][1] = (float)pos[3 * j + 1];
-            sp[threadIdx.x][2] = (float)pos[3 * j + 2];
-        }
+        if (j < j1) sp[threadIdx.x] = shadow[j];
         __syncthreads();
         const int lim = min(kTile, j1 - base);
         if (i < c.n) {
             for (int q = 0; q < lim; ++q) {
                 const int jj = base + q;
                 if (jj == i) continue;
-                float d[3] = {ri[0] - sp[q][0], ri[1] - sp[q][1], ri[2] - sp[q][2]};
-                min_image(d, c.g);
+                float d[3];
+                separation(pi, unpack(sp[q]), c.g, d);
                 const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
                 if (r2 < c.rlist2) {
                     if (cnt < kMaxNb) mine[cnt] = jj;
@@ -263,26 +327,23 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const double *pos, int *n
     }
     if (i < c.n) {
         ncount[(size_t)i * kChunks + chunk] = cnt < kMaxNb ? cnt : kMaxNb;
-        if (chunk == 0) {
-            ref_pos[3 * i] = ri[0];
-            ref_pos[3 * i + 1] = ri[1];
-            ref_pos[3 * i + 2] = ri[2];
-        }
+        if (chunk == 0) ref[i] = raw;
         if (full) atomicOr(err, LB_DERR_NLIST_FULL);
     }
 }
 
 // One particle sub-step; eight lanes per particle.  Lane q gathers the fluid
 // velocity of stencil node q (19 loads) and spreads the impulse there; the
-// lanes split the neighbour list (lane q reads chunk q) and the FENE bonds,
-// and shuffle-reduce u_p and F^c.  Every lane then has the same u_p, F^c and
-// theta and does the (cheap) momentum update; lane 0 writes the particle.
+// lanes split the neighbour list (lane q reads chunk q) and the two FENE
+// bonds, and shuffle-reduce u_p and F^c.  Every lane then holds the same
+// u_p, F^c and theta and does the (cheap) momentum update; lane 0 writes.
 template <int DT>
 __global__ void __launch_bounds__(kPartThreads)
     k_substep(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
-              const double *__restrict__ pos_in, double *__restrict__ pos_out, float *mom, const float *mass,
-              const float *gamma, const int *nlist, const int *ncount, const float *ref_pos, float *facc,
-              int *records, unsigned int *flags, unsigned int *err, CoupleArgs c, uint32_t clear_slot)
+              const float4 *__restrict__ sh_in, float4 *__restrict__ sh_out, double *pos_out, float *mom,
+              const float *mass, const float *gamma, const int *nlist, const int *ncount, const float4 *ref,
+              float *facc, int *records, unsigned int *flags, unsigned int *err, CoupleArgs c,
+              uint32_t clear_slot)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && c.use_wca) flags[clear_slot] = 0u;  // the list build has run
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -291,10 +352,8 @@ __global__ void __launch_bounds__(kPartThreads)
     if (p >= c.n) return;  // whole groups of eight leave together
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     const StepArgs &g = c.g;
-    double r[3] = {pos_in[3 * p], pos_in[3 * p + 1], pos_in[3 * p + 2]};
+    const CPos me = unpack(sh_in[p]);
     float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
-    const float m = mass ? mass[p] : c.mass0;
-    const float G = gamma ? gamma[p] : c.gamma0;
 
     // conservative forces at the half-step positions, split over the lanes
     float F[3] = {0.f, 0.f, 0.f};
@@ -303,10 +362,8 @@ __global__ void __launch_bounds__(kPartThreads)
         const int nc = ncount[li];
         const int *lst = nlist + li * kMaxNb;
         for (int k = 0; k < nc; ++k) {
-            const int j = lst[k];
-            float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
-                          (float)(r[2] - pos_in[3 * j + 2])};
-            min_image(d, g);
+            float d[3];
+            separation(me, unpack(sh_in[lst[k]]), g, d);
             const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             if (r2 < c.rc2) {
                 const float sr2 = c.sigma2 / r2;
@@ -323,9 +380,8 @@ __global__ void __launch_bounds__(kPartThreads)
         const int j = q == 0 ? p - 1 : p + 1;
         const bool bonded = (q == 0) ? (k > 0) : (k < c.chain_len - 1 && j < c.n);
         if (bonded) {
-            float d[3] = {(float)(r[0] - pos_in[3 * j]), (float)(r[1] - pos_in[3 * j + 1]),
-                          (float)(r[2] - pos_in[3 * j + 2])};
-            min_image(d, g);
+            float d[3];
+            separation(me, unpack(sh_in[j]), g, d);
             const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
             if (x >= 1.0f) {
                 atomicOr(err, LB_DERR_FENE_BROKEN);
@@ -339,15 +395,8 @@ __global__ void __launch_bounds__(kPartThreads)
     }
 
     // fluid velocity at the particle: lane q takes stencil node q
-    int b[3];
-    float t[3];
-    if (!stencil_base(r, g, b, t) && q == 0) atomicOr(err, LB_DERR_PARTICLE_RANGE);
-    const int dx = q & 1, dy = (q >> 1) & 1, dz = q >> 2;
-    const float w = (dx ? t[0] : 1.0f - t[0]) * (dy ? t[1] : 1.0f - t[1]) * (dz ? t[2] : 1.0f - t[2]);
-    int x = b[0] + dx, y = b[1] + dy, z = b[2] + dz;
-    if (x >= g.nx) x -= g.nx;
-    if (y >= g.ny) y -= g.ny;
-    if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+    int x, y, z;
+    const float w = stencil_node(me, q, g, x, y, z);
     float un[3];
     node_velocity<DT>(src, ffield, x, y, z, g, un);
     float up[3] = {w * un[0], w * un[1], w * un[2]};
@@ -361,10 +410,15 @@ __global__ void __launch_bounds__(kPartThreads)
     }
 
     // exact Ornstein-Uhlenbeck momentum update (same in every lane)
-    const float x1 = G * c.dt / m;
-    const float C1 = expf(-x1);
-    const float C2 = (m / G) * (-expm1f(-x1));
-    const float C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+    const float m = mass ? mass[p] : c.mass0;
+    const float G = gamma ? gamma[p] : c.gamma0;
+    float C1 = c.C1, C2 = c.C2, C3 = c.C3;
+    if (!c.uniform_coef) {
+        const float x1 = G * c.dt / m;
+        C1 = expf(-x1);
+        C2 = (m / G) * (-expm1f(-x1));
+        C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+    }
     float th[3] = {0.f, 0.f, 0.f};
     if (g.kT > 0.0f) {
         const lbd::U4 wv = lbd::philox10(lbd::U4{(uint32_t)p, c.md_step, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
@@ -398,28 +452,28 @@ __global__ void __launch_bounds__(kPartThreads)
         atomicAdd(facc + 2 * P + s, -J[2] * w);
     }
     if (q != 0) return;
-    if (records) records[p] = (int)(((size_t)b[2] * g.ny + b[1]) * g.nx + b[0]);
+    if (records) records[p] = (int)(((size_t)me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0]);
 
     // second half drift of this sub-step, then the first of the next one
-    const double h = 0.5 * (double)c.dt / (double)m;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) r[k] += h * (double)pn[k];
-    confine(r, pn, g);
-    if (!c.last) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) r[k] += h * (double)pn[k];
-        confine(r, pn, g);
+    const float h = 0.5f * c.dt / m;
+    CPos nx = me;
+    bool ok = drift(nx, pn, h, g);
+    if (c.last) {
+        pos_out[3 * p] = join1(nx.c[0], nx.f[0]);
+        pos_out[3 * p + 1] = join1(nx.c[1], nx.f[1]);
+        pos_out[3 * p + 2] = join1(nx.c[2], nx.f[2]);
+    } else {
+        ok = drift(nx, pn, h, g) && ok;
     }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        pos_out[3 * p + k] = r[k];
-        mom[3 * p + k] = pn[k];
-    }
-    if (ref_pos) {
-        float d[3] = {(float)r[0] - ref_pos[3 * p], (float)r[1] - ref_pos[3 * p + 1], (float)r[2] - ref_pos[3 * p + 2]};
-        min_image(d, g);
-        const float half = 0.5f * kSkin * sqrtf(c.sigma2);
-        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > half * half) flags[c.slot] = 1u;
+    if (!ok) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    sh_out[p] = pack(nx);
+    mom[3 * p] = pn[0];
+    mom[3 * p + 1] = pn[1];
+    mom[3 * p + 2] = pn[2];
+    if (ref) {
+        float d[3];
+        separation(nx, unpack(ref[p]), g, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] > c.half_skin2) flags[c.slot] = 1u;
     }
 }
 
@@ -445,29 +499,43 @@ __global__ void k_clear_records(float *facc, const int *records, size_t n, StepA
     }
 }
 
+// Interpolated velocity at caller positions; eight lanes per position.
 template <int DT>
 __global__ void k_interpolate(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
                               const double *pos, float *u_out, int n, unsigned int *err, StepArgs g)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid >> 3, q = tid & 7;
     if (p >= n) return;
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
-    int b[3];
-    float t[3], up[3];
-    if (!interpolate_u<DT>(src, ffield, r, g, b, t, up)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
-    u_out[3 * p] = up[0];
-    u_out[3 * p + 1] = up[1];
-    u_out[3 * p + 2] = up[2];
+    CPos me;
+    if (!split(r, g, me) && q == 0) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    int x, y, z;
+    const float w = stencil_node(me, q, g, x, y, z);
+    float un[3];
+    node_velocity<DT>(src, ffield, x, y, z, g, un);
+    float up[3] = {w * un[0], w * un[1], w * un[2]};
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) up[k] += __shfl_xor_sync(gmask, up[k], o);
+    if (q == 0) {
+        u_out[3 * p] = up[0];
+        u_out[3 * p + 1] = up[1];
+        u_out[3 * p + 2] = up[2];
+    }
 }
 
 void free_parts(Particles *P)
 {
     if (!P) return;
-    cudaFree(P->pos_tmp);
+    cudaFree(P->shadow[0]);
+    cudaFree(P->shadow[1]);
     cudaFree(P->records);
     cudaFree(P->nlist);
     cudaFree(P->ncount);
-    cudaFree(P->ref_pos);
+    cudaFree(P->ref);
     cudaFree(P->flags);
     delete P;
 }
@@ -486,18 +554,20 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
     if (!h->parts) h->parts = new Particles();
     Particles *P = h->parts;
     if (P->cap < n) {
-        cudaFree(P->pos_tmp);
+        cudaFree(P->shadow[0]);
+        cudaFree(P->shadow[1]);
         cudaFree(P->nlist);
         cudaFree(P->ncount);
-        cudaFree(P->ref_pos);
-        P->pos_tmp = nullptr;
+        cudaFree(P->ref);
+        P->shadow[0] = P->shadow[1] = nullptr;
         P->nlist = nullptr;
         P->ncount = nullptr;
-        P->ref_pos = nullptr;
-        cudaError_t e = cudaMalloc((void **)&P->pos_tmp, (size_t)n * 3 * sizeof(double));
+        P->ref = nullptr;
+        cudaError_t e = cudaMalloc((void **)&P->shadow[0], (size_t)n * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->shadow[1], (size_t)n * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kChunks * kMaxNb * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * kChunks * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ref_pos, (size_t)n * 3 * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ref, (size_t)n * sizeof(float4));
         if (e != cudaSuccess) {
             P->cap = 0;
             set_error("lb_couple_particles: particle buffer allocation failed (%s)", cudaGetErrorString(e));
@@ -550,16 +620,26 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     c.dt = (float)cp->dt;
     c.mass0 = (float)pp->mass0;
     c.gamma0 = (float)pp->gamma0;
+    c.uniform_coef = (pp->mass == nullptr && pp->gamma == nullptr);
+    {
+        const double x1 = pp->gamma0 * cp->dt / pp->mass0;
+        c.C1 = (float)std::exp(-x1);
+        c.C2 = (float)(pp->mass0 / pp->gamma0 * (-std::expm1(-x1)));
+        c.C3 = (float)std::sqrt(pp->mass0 * h->p.kT * (-std::expm1(-2.0 * x1)));
+    }
     c.eps = (float)cp->eps;
     c.sigma2 = (float)(cp->sigma * cp->sigma);
     c.rc2 = (float)(cp->sigma * cp->sigma * 1.2599210498948732);  // (2^(1/6) sigma)^2
     const double rl = 1.122462048309373 * cp->sigma + kSkin * cp->sigma;
     c.rlist2 = (float)(rl * rl);
+    c.half_skin2 = (float)(0.25 * kSkin * kSkin * cp->sigma * cp->sigma);
     c.k_fene = (float)cp->k_fene;
     c.inv_r02 = (float)(cp->r0 > 0 ? 1.0 / (cp->r0 * cp->r0) : 0.0);
     c.pkey0 = (uint32_t)(cp->seed & 0xffffffffu);
     c.pkey1 = (uint32_t)(cp->seed >> 32);
     c.last = 0;
+    c.md_step = cp->md_step0;
+    c.slot = 0;
     const int blocks = (n + kPartThreads - 1) / kPartThreads;
     using T = typename lbd::Store<DT>::T;
     const T *src = static_cast<const T *>(h->pops[h->cur]);
@@ -570,14 +650,13 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         if (e != cudaSuccess) return e;
         P->nlist_n = n;
     }
-    k_half_drift<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, pp->mom, pp->mass, c);
+    k_half_drift<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, pp->mom, pp->mass, P->shadow[0], h->d_err, c);
     h->launches += 1;
-    double *buf[2] = {pp->pos, P->pos_tmp};
     for (int s = 0; s < cp->n_substeps; ++s) {
         const uint32_t rd = P->sub_counter & 1u, wr = rd ^ 1u;
         if (need_nlist) {
             dim3 bgrid((n + kTile - 1) / kTile, kChunks);
-            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(buf[s & 1], P->nlist, P->ncount, P->ref_pos, P->flags,
+            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(P->shadow[s & 1], P->nlist, P->ncount, P->ref, P->flags,
                                                           h->d_err, c, rd);
             h->launches += 1;
         }
@@ -587,16 +666,11 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         int *rec = P->records + P->n_records;
         const int sblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
         k_substep<DT><<<sblocks, kPartThreads, 0, h->stream>>>(
-            src, h->force, buf[s & 1], buf[(s + 1) & 1], pp->mom, pp->mass, pp->gamma, P->nlist, P->ncount,
-            need_nlist ? P->ref_pos : nullptr, h->facc, rec, P->flags, h->d_err, c, rd);
+            src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma,
+            P->nlist, P->ncount, need_nlist ? P->ref : nullptr, h->facc, rec, P->flags, h->d_err, c, rd);
         P->n_records += (size_t)n;
         P->sub_counter += 1;
         h->launches += 1;
-    }
-    if (cp->n_substeps & 1) {
-        cudaError_t e = cudaMemcpyAsync(pp->pos, P->pos_tmp, (size_t)n * 3 * sizeof(double),
-                                        cudaMemcpyDeviceToDevice, h->stream);
-        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -612,6 +686,10 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
     if (pp->n == 0) return LB_OK;
     if (!pp->pos || !pp->mom) {
         set_error("lb_couple_particles: pos and mom are required");
+        return LB_EINVAL;
+    }
+    if (h->p.nx > kMaxCellDim || h->p.ny > kMaxCellDim || h->p.nz > kMaxCellDim) {
+        set_error("lb_couple_particles: particles need box edges <= %d", kMaxCellDim);
         return LB_EINVAL;
     }
     if (cp->n_substeps < 1 || !(cp->dt > 0.0) || cp->noise_kind < 0 || cp->noise_kind > 1) {
@@ -674,7 +752,7 @@ lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
 {
     if (n == 0) return LB_OK;
     const StepArgs g = make_args(h);
-    const int blocks = (n + kPartThreads - 1) / kPartThreads;
+    const int blocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
     switch (h->p.dtype) {
     case LB_F32:
         k_interpolate<0><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const float *>(h->pops[h->cur]),
