@@ -166,6 +166,23 @@ lb_status lb_step(lb_handle *h, int nsteps);
  * nodes give rho0 and zeros.  Errors: LB_EINVAL, LB_ECUDA. */
 lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums);
 
+/* The sums of lb_moments (LB_NSUMS doubles into device `sums`) for the
+ * state in the device population buffer `pops` (storage format and layout of
+ * p), without a handle and without allocating anything.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * (a host application whose device memory another framework reserved up
+ * front, or a monitoring loop that must not block on or fail in an allocation
+ * mid-run), which also rules out lb_create.  Its reduction scratch is a
+ * static 1.2 MiB device array that every GPU loading the library keeps until
+ * exit.  Boxes of more than 2^28 nodes are rejected with LB_EINVAL.  The first
+ * call on a device looks up that array's device address, so make that first
+ * call before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU (different streams or threads) race and must be
+ * serialised by the caller.  stream: a cudaStream_t.  No force field is
+ * involved (the sums use sum n c without f/2).  Errors: LB_EINVAL, LB_ECUDA,
+ * LB_EUNSUPPORTED (device index >= 64). */
+lb_status lb_moment_sums_static(const lb_params *p, const void *pops, double *sums, void *stream);
+
 /* ---- point particles (Sec. 4.5, 4.6) ------------------------------------ */
 
 typedef struct {

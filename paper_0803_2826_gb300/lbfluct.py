@@ -33,7 +33,7 @@ EXPORTS = (
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words",
-    "lb_get_launch_count", "lb_version",
+    "lb_get_launch_count", "lb_moment_sums_static", "lb_version",
 )
 
 
@@ -114,6 +114,7 @@ def load(path: str | None = None):
             "lb_get_particle_forces": (i, [H, vp]),
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
+            "lb_moment_sums_static": (i, [P, vp, vp, vp]),
             "lb_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -262,6 +263,12 @@ def lb_get_launch_count(h) -> int:
     v = C.c_uint64()
     _check(load().lb_get_launch_count(h, C.byref(v)))
     return v.value
+
+
+def lb_moment_sums_static(p: lb_params, pops, sums, stream=None):
+    """Moment sums of a population buffer without a handle and without any
+    device allocation (see the header for who needs this)."""
+    _check(load().lb_moment_sums_static(C.byref(p), _ptr(pops), _ptr(sums), _stream(stream)))
 
 
 def lb_version() -> str:
