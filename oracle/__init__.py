@@ -23,6 +23,11 @@ Function -> passage it follows:
   couple()        Sec. 4.5 Eqs. (fdrag), (ftotal), (langevin_momentum_update);
                   Sec. 4.6 Eqs. (ufluid_discrete), (Delta), (2point)
   interpolate()   Sec. 4.6 Eq. (ufluid_discrete)
+  adjoint_step()  reverse mode of step() at kT = 0, derived by hand in
+                  population space (chain rule through Eq. (original_equil_distrib),
+                  the MRT relaxation and Delta'' of Sec. 3.7, then the pull)
+  kinetic_seed()  L = 1/2 sum |j|^2 / rho over a sub-box and dL/dstate
+  kinetic_energy_and_grad()  forward + reverse pass of a whole run
 """
 from __future__ import annotations
 
@@ -114,6 +119,9 @@ def _load():
             lib.ora_couple.restype = C.c_int
             lib.ora_interpolate.argtypes = [P, _D, _D, C.c_int, _D, _D]
             lib.ora_stencil.argtypes = [P, _D, C.POINTER(C.c_longlong), _D]
+            lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
+            lib.ora_kinetic_seed.argtypes = [P, _D, _D, C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _D]
+            lib.ora_kinetic_seed.restype = C.c_double
             _lib = lib
     return _lib
 
@@ -296,3 +304,47 @@ def stencil(p: Params, pos3):
     wt = np.zeros(8)
     lib.ora_stencil(C.byref(p), _dp(pp), node, _dp(wt))
     return np.array(list(node), dtype=np.int64), wt
+
+
+def adjoint_step(p: Params, state, lam_in, force=None, grad_f=None):
+    """dL/dn*(t) from dL/dn*(t+1) for the step leaving `state`; adds dL/df to grad_f."""
+    lib = _load()
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    li = np.ascontiguousarray(lam_in, dtype=np.float64)
+    lo = np.empty_like(st)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    if grad_f is None:
+        grad_f = np.zeros((3, p.nz, p.ny, p.nx))
+    lib.ora_adjoint_step(C.byref(p), _dp(st), _dp(f), _dp(li), _dp(lo), _dp(grad_f))
+    return lo, grad_f
+
+
+def kinetic_seed(p: Params, state, lo, hi, force=None, grad_f=None):
+    lib = _load()
+    st = np.ascontiguousarray(state, dtype=np.float64)
+    lam = np.empty_like(st)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    if grad_f is None:
+        grad_f = np.zeros((3, p.nz, p.ny, p.nx))
+    L = lib.ora_kinetic_seed(C.byref(p), _dp(st), _dp(f), (C.c_int * 3)(*lo), (C.c_int * 3)(*hi), _dp(lam),
+                             _dp(grad_f))
+    return L, lam, grad_f
+
+
+def kinetic_energy(p: Params, pops0, force, nsteps, lo, hi):
+    """L after nsteps from pops0 with the force field (forward only)."""
+    pops = run(p, pops0, nsteps, force)
+    rho, j, _ = moments(p, pops, force)
+    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    return float(0.5 * np.sum((j[(slice(None),) + sl] ** 2).sum(0) / rho[sl]))
+
+
+def kinetic_energy_and_grad(p: Params, pops0, force, nsteps, lo, hi):
+    """(L, dL/dforce) by storing every state and running the reverse pass."""
+    states = [np.ascontiguousarray(pops0, dtype=np.float64)]
+    for t in range(nsteps):
+        states.append(step(p, states[-1], force, t))
+    L, lam, g = kinetic_seed(p, states[-1], lo, hi, force)
+    for t in range(nsteps - 1, -1, -1):
+        lam, g = adjoint_step(p, states[t], lam, force, g)
+    return L, g

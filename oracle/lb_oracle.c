@@ -734,3 +734,172 @@ void ora_stencil(const ora_params *P, const double *p, long long *node, double *
     stencil(P, p, nd, wt);
     for (int q = 0; q < 8; q++) node[q] = (long long)nd[q];
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode (kT = 0): a hand-derived adjoint of one stream-collide step  */
+/* in population space, following the oracle's own formulation above:       */
+/*   n* = n^eq(rho, u) + a_i sum_k e_ki gamma_k m^neq_k / w_k + Delta''(u, f) */
+/* with m^neq = E (n - n^eq), rho = sum n, u = (sum n c + f/2)/rho.          */
+/* ------------------------------------------------------------------------ */
+
+/* d n^eq_i / d u_alpha at fixed rho, from Eq. (original_equil_distrib). */
+static double dneq_du(int i, double rho, const double u[3], int al)
+{
+    double cu = u[0] * g_c[i][0] + u[1] * g_c[i][1] + u[2] * g_c[i][2];
+    return g_a[i] * rho * (g_c[i][al] / CS2 + cu * g_c[i][al] / (CS2 * CS2) - u[al] / CS2);
+}
+
+/* d Sigma_bg / d u_al and d Sigma_bg / d f_al of Eq. (moment_two_external_force). */
+static double dsig_du(const ora_params *P, const double f[3], int al, int b, int g)
+{
+    double d_ab = (al == b), d_ag = (al == g), d_bg = (b == g);
+    return 0.5 * (1.0 + P->gamma_shear) * (d_ab * f[g] + d_ag * f[b] - (2.0 / 3.0) * f[al] * d_bg)
+         + (1.0 / 3.0) * (1.0 + P->gamma_bulk) * f[al] * d_bg;
+}
+
+static double dsig_df(const ora_params *P, const double u[3], int al, int b, int g)
+{
+    double d_ab = (al == b), d_ag = (al == g), d_bg = (b == g);
+    return 0.5 * (1.0 + P->gamma_shear) * (u[b] * d_ag + u[g] * d_ab - (2.0 / 3.0) * u[al] * d_bg)
+         + (1.0 / 3.0) * (1.0 + P->gamma_bulk) * u[al] * d_bg;
+}
+
+/* Adjoint of collide() at one node: given lam = dL/dn*, returns dn = dL/dn
+ * and adds dL/df to df. */
+static void collide_adjoint(const ora_params *P, const double n[Q], const double f[3], const double lam[Q],
+                            double dn[Q], double df[3])
+{
+    double rho = 0.0, J[3] = {0, 0, 0};
+    for (int i = 0; i < Q; i++) {
+        rho += n[i];
+        for (int d = 0; d < 3; d++) J[d] += n[i] * g_c[i][d];
+    }
+    double u[3] = {(J[0] + 0.5 * f[0]) / rho, (J[1] + 0.5 * f[1]) / rho, (J[2] + 0.5 * f[2]) / rho};
+    double neq[Q];
+    equilibrium(rho, u, neq);
+    /* through the back transform and the relaxation: mu_k = gamma_k sum_i lam_i a_i e_ki / w_k */
+    double mu[Q];
+    for (int k = 0; k < Q; k++) {
+        double s = 0.0;
+        for (int i = 0; i < Q; i++) s += lam[i] * g_a[i] * g_e[k][i];
+        mu[k] = gamma_of(P, k) * s / g_w[k];
+    }
+    /* m^neq = E (n - n^eq): direct part g_i = sum_k e_ki mu_k, and dL/dn^eq = lam - g */
+    double gvec[Q], leq[Q];
+    for (int i = 0; i < Q; i++) {
+        double s = 0.0;
+        for (int k = 0; k < Q; k++) s += g_e[k][i] * mu[k];
+        gvec[i] = s;
+        leq[i] = lam[i] - s;
+    }
+    /* n^eq(rho, u) and Delta''(u, f) */
+    double rbar = 0.0, ubar[3] = {0, 0, 0}, fbar[3] = {0, 0, 0};
+    for (int i = 0; i < Q; i++) {
+        rbar += leq[i] * neq[i] / rho;
+        for (int al = 0; al < 3; al++) ubar[al] += leq[i] * dneq_du(i, rho, u, al);
+    }
+    for (int i = 0; i < Q; i++) {
+        for (int al = 0; al < 3; al++) {
+            double su = 0.0, sf = 0.0;
+            for (int b = 0; b < 3; b++)
+                for (int g = 0; g < 3; g++) {
+                    double proj = g_c[i][b] * g_c[i][g] - CS2 * (b == g);
+                    su += dsig_du(P, f, al, b, g) * proj;
+                    sf += dsig_df(P, u, al, b, g) * proj;
+                }
+            ubar[al] += lam[i] * g_a[i] * su / (2.0 * CS2 * CS2);
+            fbar[al] += lam[i] * g_a[i] * (g_c[i][al] / CS2 + sf / (2.0 * CS2 * CS2));
+        }
+    }
+    /* rho = sum n, u = (sum n c + f/2) / rho */
+    for (int i = 0; i < Q; i++) {
+        double s = gvec[i] + rbar;
+        for (int al = 0; al < 3; al++) s += ubar[al] * (g_c[i][al] - u[al]) / rho;
+        dn[i] = s;
+    }
+    for (int al = 0; al < 3; al++) df[al] += fbar[al] + ubar[al] / (2.0 * rho);
+}
+
+/* Reverse of the pull: n_i(r) came from n*_i(r - c_i), or from n*_opp(i)(r)
+ * when the source is solid; the adjoint of n_i(r) goes back to that entry. */
+static void push_adjoint(const ora_params *P, double *lam_out, int x, int y, int z, const double dn[Q])
+{
+    size_t N = nodes_of(P);
+    for (int i = 0; i < Q; i++) {
+        int sx = wrap(x - g_c[i][0], P->nx);
+        int sy = wrap(y - g_c[i][1], P->ny);
+        int sz = z - g_c[i][2];
+        if (P->walls) {
+            if (sz < 0 || sz >= P->nz || is_solid(P, sz)) {
+                lam_out[(size_t)g_opp[i] * N + lin(P, x, y, z)] += dn[i];
+                continue;
+            }
+        } else {
+            sz = wrap(sz, P->nz);
+        }
+        lam_out[(size_t)i * N + lin(P, sx, sy, sz)] += dn[i];
+    }
+}
+
+/* lam_out = dL/dn*(t) from lam_in = dL/dn*(t+1) for the step that maps the
+ * stored state `state` (at t) to t+1; adds dL/df into grad_f ([3][N]).
+ * Requires kT = 0.  lam_out is overwritten. */
+void ora_adjoint_step(const ora_params *P, const double *state, const double *force, const double *lam_in,
+                      double *lam_out, double *grad_f)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    memset(lam_out, 0, sizeof(double) * Q * N);
+    for (int z = 0; z < P->nz; z++) {
+        if (is_solid(P, z)) continue;
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                double n[Q], f[3], lam[Q], dn[Q], df[3] = {0, 0, 0};
+                gather(P, state, x, y, z, n);
+                node_force(P, force, s, f);
+                for (int i = 0; i < Q; i++) lam[i] = lam_in[(size_t)i * N + s];
+                collide_adjoint(P, n, f, lam, dn, df);
+                push_adjoint(P, lam_out, x, y, z, dn);
+                if (grad_f) for (int d = 0; d < 3; d++) grad_f[(size_t)d * N + s] += df[d];
+            }
+        }
+    }
+}
+
+/* L = 1/2 sum over fluid nodes in [lo, hi) of |j|^2 / rho with j = sum n c + f/2
+ * of the pre-collision state pulled from `state`; writes lam_out = dL/dstate,
+ * adds dL/df into grad_f, returns L. */
+double ora_kinetic_seed(const ora_params *P, const double *state, const double *force, const int lo[3],
+                        const int hi[3], double *lam_out, double *grad_f)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    memset(lam_out, 0, sizeof(double) * Q * N);
+    double L = 0.0;
+    for (int z = lo[2]; z < hi[2]; z++) {
+        if (is_solid(P, z)) continue;
+        for (int y = lo[1]; y < hi[1]; y++) {
+            for (int x = lo[0]; x < hi[0]; x++) {
+                size_t s = lin(P, x, y, z);
+                double n[Q], f[3], dn[Q];
+                gather(P, state, x, y, z, n);
+                node_force(P, force, s, f);
+                double rho = 0.0, j[3] = {0, 0, 0};
+                for (int i = 0; i < Q; i++) {
+                    rho += n[i];
+                    for (int d = 0; d < 3; d++) j[d] += n[i] * g_c[i][d];
+                }
+                for (int d = 0; d < 3; d++) j[d] += 0.5 * f[d];
+                double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+                double u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                L += 0.5 * (j[0] * j[0] + j[1] * j[1] + j[2] * j[2]) / rho;
+                for (int i = 0; i < Q; i++)
+                    dn[i] = u[0] * g_c[i][0] + u[1] * g_c[i][1] + u[2] * g_c[i][2] - 0.5 * u2;
+                push_adjoint(P, lam_out, x, y, z, dn);
+                if (grad_f) for (int d = 0; d < 3; d++) grad_f[(size_t)d * N + s] += 0.5 * u[d];
+            }
+        }
+    }
+    return L;
+}
