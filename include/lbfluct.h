@@ -229,6 +229,43 @@ lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out);
  * zeros when none are pending). */
 lb_status lb_get_particle_forces(lb_handle *h, float *out);
 
+/* ---- reverse mode (deterministic runs, kT = 0) ------------------------------- */
+
+/* One forward step from the state in `src` into `dst` (device buffers in the
+ * storage format, lb_population_bytes each) with Philox step word `step`;
+ * the handle's own state and step counter are not touched.  Used to
+ * recompute states inside a checkpoint segment.  Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_step_from(lb_handle *h, const void *src, void *dst, uint32_t step);
+
+/* Adjoint of one step (the transposed Jacobian of pull + collide, Sec. 3.4 and
+ * 3.7, evaluated at the state `state` the step starts from): lambda_out =
+ * dL/dstate_t from lambda_in = dL/dstate_{t+1} (device FP32, [19][pitch], the
+ * population layout; entries of solid nodes must be zero and stay zero), and
+ * dL/df of this step added into grad_force (device FP32 [3][N], may be NULL).
+ * f = body_force + force field; particle impulses are not differentiated.
+ * Requires kT = 0 (LB_EUNSUPPORTED otherwise).  Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_adjoint_step(lb_handle *h, const void *state, const float *lambda_in, float *lambda_out,
+                          float *grad_force);
+
+/* Seed of the reverse pass for L = 1/2 sum over nodes in [lo, hi) (host int[3]
+ * each) of |j|^2 / rho, with j = sum n c + f/2 of the state pulled from
+ * `state`: writes lambda_out = dL/dstate (FP32 [19][pitch]), adds dL/df into
+ * grad_force (may be NULL) and stores L in *loss (device double). */
+lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[3], const int hi[3],
+                                  float *lambda_out, float *grad_force, double *loss);
+
+/* The whole reverse pass of "advance nsteps, then L of the sub-box": runs the
+ * forward steps from the current state (which advances by nsteps, as lb_step
+ * would), storing a checkpoint every `checkpoint_every` steps, then walks the
+ * segments backwards, recomputing each segment's states from its checkpoint
+ * and applying lb_adjoint_step.  Writes dL/d(force field) into grad_force
+ * (device FP32 [3][N]; the field is the one the handle was created with) and
+ * L into *loss (device double).  Checkpoint and segment buffers are allocated
+ * for the call and freed before it returns (it synchronises the stream).
+ * Requires kT = 0.  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
+                             float *grad_force, double *loss);
+
 /* ---- noise streams (for verification) --------------------------------------- */
 
 /* Raw Philox4x32-10 words and their Box-Muller Gaussians as the kernels draw

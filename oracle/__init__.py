@@ -339,12 +339,23 @@ def kinetic_energy(p: Params, pops0, force, nsteps, lo, hi):
     return float(0.5 * np.sum((j[(slice(None),) + sl] ** 2).sum(0) / rho[sl]))
 
 
-def kinetic_energy_and_grad(p: Params, pops0, force, nsteps, lo, hi):
-    """(L, dL/dforce) by storing every state and running the reverse pass."""
-    states = [np.ascontiguousarray(pops0, dtype=np.float64)]
+def kinetic_energy_and_grad(p: Params, pops0, force, nsteps, lo, hi, checkpoint_every=None):
+    """(L, dL/dforce) by the reverse pass.  Every state is kept, or with
+    checkpoint_every = K only every K-th one, the others being recomputed
+    segment by segment (same results, less host memory)."""
+    K = nsteps if checkpoint_every is None else int(checkpoint_every)
+    ckpt = {}
+    s = np.ascontiguousarray(pops0, dtype=np.float64)
     for t in range(nsteps):
-        states.append(step(p, states[-1], force, t))
-    L, lam, g = kinetic_seed(p, states[-1], lo, hi, force)
-    for t in range(nsteps - 1, -1, -1):
-        lam, g = adjoint_step(p, states[t], lam, force, g)
+        if t % K == 0:
+            ckpt[t] = s
+        s = step(p, s, force, t)
+    L, lam, g = kinetic_seed(p, s, lo, hi, force)
+    for t0 in sorted(ckpt, reverse=True):
+        t1 = min(nsteps, t0 + K)
+        states = [ckpt[t0]]
+        for t in range(t0, t1 - 1):
+            states.append(step(p, states[-1], force, t))
+        for t in range(t1 - 1, t0 - 1, -1):
+            lam, g = adjoint_step(p, states[t - t0], lam, force, g)
     return L, g

@@ -33,7 +33,8 @@ EXPORTS = (
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words",
-    "lb_get_launch_count", "lb_moment_sums_static", "lb_version",
+    "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
+    "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic", "lb_version",
 )
 
 
@@ -115,6 +116,10 @@ def load(path: str | None = None):
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
             "lb_moment_sums_static": (i, [P, vp, vp, vp]),
+            "lb_step_from": (i, [H, vp, vp, u32]),
+            "lb_adjoint_step": (i, [H, vp, vp, vp, vp]),
+            "lb_adjoint_seed_kinetic": (i, [H, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, vp]),
+            "lb_adjoint_kinetic": (i, [H, i, i, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp]),
             "lb_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -269,6 +274,28 @@ def lb_moment_sums_static(p: lb_params, pops, sums, stream=None):
     """Moment sums of a population buffer without a handle and without any
     device allocation (see the header for who needs this)."""
     _check(load().lb_moment_sums_static(C.byref(p), _ptr(pops), _ptr(sums), _stream(stream)))
+
+
+def lb_step_from(h, src, dst, step):
+    _check(load().lb_step_from(h, _ptr(src), _ptr(dst), int(step) & 0xffffffff))
+
+
+def lb_adjoint_step(h, state, lambda_in, lambda_out, grad_force=None):
+    _check(load().lb_adjoint_step(h, _ptr(state), _ptr(lambda_in), _ptr(lambda_out), _ptr(grad_force)))
+
+
+def _int3(v):
+    return (C.c_int * 3)(*[int(x) for x in v])
+
+
+def lb_adjoint_seed_kinetic(h, state, lo, hi, lambda_out, grad_force, loss):
+    _check(load().lb_adjoint_seed_kinetic(h, _ptr(state), _int3(lo), _int3(hi), _ptr(lambda_out),
+                                          _ptr(grad_force), _ptr(loss)))
+
+
+def lb_adjoint_kinetic(h, nsteps, checkpoint_every, lo, hi, grad_force, loss):
+    _check(load().lb_adjoint_kinetic(h, int(nsteps), int(checkpoint_every), _int3(lo), _int3(hi),
+                                     _ptr(grad_force), _ptr(loss)))
 
 
 def lb_version() -> str:

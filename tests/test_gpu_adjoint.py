@@ -1,0 +1,150 @@
+"""GPU parity of the hand-written adjoint (kT = 0) against the FP64 oracle's
+reverse pass, through the C ABI, plus the autograd wrapper.
+
+Tolerances (FP32 adjoint against the FP64 reverse pass): one adjoint step to
+1e-5 relative L2; whole reverse passes to 1e-3 relative per significant entry
+and cosine similarity >= 0.99999.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_0803_2826_gb300 import adjoint, inputs  # noqa: E402
+from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+
+GAM = dict(gamma_shear=0.2, gamma_bulk=-0.3, gamma_odd=0.4, gamma_even=-0.1)
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def cos(a, b):
+    return float(np.dot(a.ravel(), b.ravel()) / (np.linalg.norm(a) * np.linalg.norm(b)))
+
+
+def dev(x, dt=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(x)).to(dt).cuda()
+
+
+def _lam_dev(lat, lam):
+    """(19, nz, ny, nx) host array -> padded [19][pitch] device FP32 buffer."""
+    pitch = L.lb_plane_pitch(lat.params)
+    t = torch.zeros((19, pitch), dtype=torch.float32, device="cuda")
+    t[:, :lat.n_nodes] = dev(lam.reshape(19, -1))
+    return t
+
+
+def _lam_host(lat, t):
+    return t[:, :lat.n_nodes].cpu().numpy().astype(np.float64).reshape((19,) + lat.shape[::-1])
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_one_adjoint_step_parity(ora, walls):
+    shape = (7, 5, 9)
+    bf = (2e-4, -1e-4, 0.0 if walls else 1e-4)
+    u = inputs.gaussian_field(shape, 3, 5e-3, seed=1)
+    f = inputs.gaussian_field(shape, 3, 1e-3, seed=2).astype(np.float32)
+    lam = inputs.gaussian_field(shape, 19, 1.0, seed=3)
+    if walls:
+        u[:, 0] = u[:, -1] = 0
+        f[:, 0] = f[:, -1] = 0
+        lam[:, 0] = lam[:, -1] = 0
+    p = ora.make_params(shape, walls=walls, body_force=bf, **GAM)
+    s0 = ora.equilibrium(p, None, u)
+    want_lam, want_g = ora.adjoint_step(p, s0, lam, f.astype(np.float64))
+    ft = dev(f)
+    lat = L.Lattice(shape, walls=walls, body_force=bf, force=ft, **GAM)
+    lat.set_populations(dev(s0, torch.float64))
+    cur, _ = L.lb_state_buffers(lat.h)
+    lin = _lam_dev(lat, lam)
+    lout = torch.zeros_like(lin)
+    g = torch.zeros((3,) + shape[::-1], dtype=torch.float32, device="cuda")
+    L.lb_adjoint_step(lat.h, cur, lin, lout, g)
+    got_lam = _lam_host(lat, lout)
+    fl = slice(1, shape[2] - 1) if walls else slice(None)
+    assert rel(got_lam[:, fl], want_lam[:, fl]) < 1e-5
+    assert rel(g.cpu().numpy()[:, fl], want_g[:, fl]) < 1e-5
+    lat.sync()
+
+
+def test_reverse_pass_parity_and_autograd(ora):
+    """Kinetic energy of the central 8^3 of a 16^3 box after 40 steps from rest,
+    f ~ N(0, 1e-5): library reverse pass (checkpoints every 10) vs the FP64
+    oracle reverse pass (all states stored)."""
+    shape, T, K = (16, 16, 16), 40, 10
+    lo, hi = (4, 4, 4), (12, 12, 12)
+    f = inputs.gaussian_field(shape, 3, 1e-5, seed=0).astype(np.float32)
+    p = ora.make_params(shape)
+    s0 = ora.equilibrium(p)
+    Lw, gw = ora.kinetic_energy_and_grad(p, s0, f.astype(np.float64), T, lo, hi)
+    ft = torch.zeros((3,) + shape[::-1], dtype=torch.float32, device="cuda")
+    lat = L.Lattice(shape, force=ft)
+    lat.init_equilibrium()
+    x = dev(f).requires_grad_(True)
+    loss = adjoint.kinetic_energy(x, lat, T, lo, hi, K)
+    loss.backward()
+    g = x.grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() / Lw - 1) < 1e-4
+    assert cos(g, gw) > 0.99999
+    big = np.abs(gw) > 1e-3 * np.abs(gw).max()
+    assert np.max(np.abs(g[big] - gw[big]) / np.abs(gw[big])) < 1e-3
+    assert lat.step_index == T
+    lat.sync()
+
+
+def test_adjoint_requires_deterministic_run():
+    lat = L.Lattice((8, 8, 8), kT=1e-4, force=torch.zeros((3, 8, 8, 8), device="cuda"))
+    g = torch.zeros((3, 8, 8, 8), device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LBError) as ei:
+        L.lb_adjoint_kinetic(lat.h, 4, 2, (0, 0, 0), (8, 8, 8), g, loss)
+    assert ei.value.status == L.LB_EUNSUPPORTED
+
+
+@pytest.mark.slow
+def test_config_64cubed_500_steps(ora):
+    """The differentiable workload at full size: 64^3 periodic, kT = 0, learnable
+    force field f ~ N(0, 1e-5), loss = kinetic energy of the central 16^3 after
+    500 steps, checkpoints every 50.  Library gradient vs the FP64 oracle reverse
+    pass (checkpointed), and vs central differences of the library's own
+    forward (eps = 1e-3) on 32 random entries."""
+    shape, T, K = (64, 64, 64), 500, 50
+    lo, hi = (24, 24, 24), (40, 40, 40)
+    f = inputs.gaussian_field(shape, 3, 1e-5, seed=0).astype(np.float32)
+    p = ora.make_params(shape)
+    s0 = ora.equilibrium(p)
+    Lw, gw = ora.kinetic_energy_and_grad(p, s0, f.astype(np.float64), T, lo, hi, checkpoint_every=K)
+    ft = torch.zeros((3,) + shape[::-1], dtype=torch.float32, device="cuda")
+    lat = L.Lattice(shape, force=ft)
+
+    def run(field, want_grad):
+        lat.init_equilibrium()
+        lat.step_index = 0
+        ft.copy_(field)
+        g = torch.empty_like(ft)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        L.lb_adjoint_kinetic(lat.h, T, K, lo, hi, g, loss)
+        return loss.item(), g.cpu().numpy().astype(np.float64)
+
+    Lg, g = run(dev(f), True)
+    print("64^3 adjoint: L gpu %.6e oracle %.6e, cosine %.7f" % (Lg, Lw, cos(g, gw)))
+    assert abs(Lg / Lw - 1) < 1e-4
+    assert cos(g, gw) > 0.99999
+    big = np.abs(gw) > 1e-3 * np.abs(gw).max()
+    assert np.max(np.abs(g[big] - gw[big]) / np.abs(gw[big])) < 1e-3
+    rng = np.random.default_rng(1)
+    eps = 1e-3
+    errs = []
+    for _ in range(32):
+        c, z, y, x = (int(rng.integers(0, 3)), int(rng.integers(16, 48)), int(rng.integers(16, 48)),
+                      int(rng.integers(16, 48)))
+        fp, fm = f.copy(), f.copy()
+        fp[c, z, y, x] += eps
+        fm[c, z, y, x] -= eps
+        fd = (run(dev(fp), False)[0] - run(dev(fm), False)[0]) / (2 * eps)
+        errs.append(abs(fd - gw[c, z, y, x]) / max(abs(gw[c, z, y, x]), 1e-3 * np.abs(gw).max()))
+    print("64^3 finite differences: max rel err %.2e" % max(errs))
+    assert max(errs) < 1e-2

@@ -56,3 +56,13 @@ def test_adjoint_linear_in_lambda_and_transposes_step(ora):
     jv = (ora.step(p, s0 + h * v, f) - ora.step(p, s0 - h * v, f)) / (2 * h)
     jt, _ = ora.adjoint_step(p, s0, lam, f)
     assert np.isclose(np.sum(lam * jv), np.sum(jt * v), rtol=1e-8)
+
+
+def test_checkpointed_reverse_pass_is_identical(ora):
+    shape = (5, 6, 4)
+    p = ora.make_params(shape, gamma_shear=0.1)
+    f = inputs.gaussian_field(shape, 3, 1e-3, seed=9)
+    s0 = ora.equilibrium(p, None, inputs.gaussian_field(shape, 3, 1e-2, seed=8))
+    L1, g1 = ora.kinetic_energy_and_grad(p, s0, f, 7, (0, 0, 0), (5, 6, 4))
+    L2, g2 = ora.kinetic_energy_and_grad(p, s0, f, 7, (0, 0, 0), (5, 6, 4), checkpoint_every=3)
+    assert L1 == L2 and np.array_equal(g1, g2)
