@@ -266,6 +266,69 @@ lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[
 lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
                              float *grad_force, double *loss);
 
+/* ---- batched replicas: one persistent launch over many boxes ---------------- */
+
+/* Many independent periodic boxes (replicas) of different sizes advanced
+ * together: replica r is the box per_replica[r] (its nx, ny, nz, seed and
+ * replica counter word; dtype and all physics parameters must equal those of
+ * replica 0; walls are not supported; each replica has fewer than 2^24 nodes).
+ * Population buffer layout: replica r occupies 19 * lb_plane_pitch(&per_replica[r])
+ * elements starting right after replica r-1, planes as for one box.  Every
+ * replica follows exactly the single-box update of lb_step with its own
+ * parameters, so replica r of a batch reproduces a single box created from
+ * per_replica[r]. */
+typedef struct lb_batch lb_batch;
+
+/* Launch shape of the persistent kernel: threads per block, nodes per tile
+ * (a run of consecutive nodes of one replica), blocks per SM; grid is an
+ * output (resident blocks).  Chosen by lb_batch_autotune or set directly. */
+typedef struct {
+    int threads;
+    int tile_nodes;
+    int blocks_per_sm;
+    int grid;
+} lb_batch_config;
+
+/* Bytes of one batch population buffer (0 on invalid parameters). */
+size_t lb_batch_population_bytes(const lb_params *per_replica, int n);
+
+/* Create a batch over two caller-owned device buffers of
+ * lb_batch_population_bytes bytes (256-byte aligned).  The state starts in
+ * pops_a at step 0.  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_batch_create(const lb_params *per_replica, int n, void *pops_a, void *pops_b, void *stream,
+                          lb_batch **out);
+lb_status lb_batch_destroy(lb_batch *b);
+
+/* Advance every replica nsteps steps in ONE cooperative persistent launch:
+ * resident blocks take tiles in a strided order, then meet at a grid barrier
+ * per step.  The barrier spins at most lb_batch_set_barrier_limit times
+ * (default 2^22 polls) and then stops the run, which lb_batch_sync reports as
+ * LB_ETIMEOUT.  use_graph != 0 records the launch in a CUDA graph (once per
+ * nsteps value) and replays it.  Asynchronous. */
+lb_status lb_batch_step(lb_batch *b, int nsteps, int use_graph);
+
+/* Synchronise; report (and clear) the device error word: LB_ETIMEOUT after a
+ * barrier timeout (the populations are then undefined), LB_EDEVICE else. */
+lb_status lb_batch_sync(lb_batch *b, uint32_t *bits);
+
+/* Time trial_steps steps for every launch shape of a small grid (threads
+ * 128/256/512, tiles 512..8192 nodes, 1..8 blocks per SM) with CUDA events
+ * and keep the fastest; the trial steps advance the state like lb_batch_step.
+ * Synchronises.  Returns the chosen shape and its time per step. */
+lb_status lb_batch_autotune(lb_batch *b, int trial_steps, lb_batch_config *chosen, double *best_ms_per_step);
+lb_status lb_batch_set_config(lb_batch *b, const lb_batch_config *c);
+lb_status lb_batch_get_config(const lb_batch *b, lb_batch_config *c);
+lb_status lb_batch_set_barrier_limit(lb_batch *b, uint32_t spins);
+lb_status lb_batch_get_step(const lb_batch *b, uint32_t *step);
+lb_status lb_batch_get_launch_count(const lb_batch *b, uint64_t *count);
+
+/* Per-replica state access and moments (replica = -1 in init: all replicas,
+ * with rho / u then NULL); layouts as for one box of that replica's size. */
+lb_status lb_batch_init_equilibrium(lb_batch *b, int replica, const double *rho, const double *u);
+lb_status lb_batch_set_populations(lb_batch *b, int replica, const double *n);
+lb_status lb_batch_get_populations(lb_batch *b, int replica, double *n);
+lb_status lb_batch_moments(lb_batch *b, int replica, float *rho, float *j, float *pi, double *sums);
+
 /* ---- noise streams (for verification) --------------------------------------- */
 
 /* Raw Philox4x32-10 words and their Box-Muller Gaussians as the kernels draw

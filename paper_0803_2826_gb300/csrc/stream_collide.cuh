@@ -21,6 +21,77 @@ namespace lbi {
 
 constexpr int kBX = 128;  // threads per block along x
 
+// Collision of one node (Sec. 3.4, 3.5, 3.7) from its pulled populations n
+// (deviations n_i - a_i rho0) and the force density (fx, fy, fz) to the
+// post-collision deviations out.  Physics constants come from a; the noise
+// stream is Philox with round keys rk and counter (node, a.step, b, replica).
+template <bool NOISE>
+__device__ __forceinline__ void collide_node(const float n[19], float fx, float fy, float fz, const StepArgs &a,
+                                             const lbd::RoundKeys &rk, uint32_t node, uint32_t replica,
+                                             float out[19])
+{
+    float m[19];
+    lbd::forward(n, m);
+    const float rho = a.rho0 + m[0];
+    const float inv_rho = 1.0f / rho;
+    const float ux = (m[1] + 0.5f * fx) * inv_rho;
+    const float uy = (m[2] + 0.5f * fy) * inv_rho;
+    const float uz = (m[3] + 0.5f * fz) * inv_rho;
+
+    // ---- relaxation in moment space ----------------------------------------
+    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+    const float u2 = uxx + uyy + uzz;
+    const float meq4 = rho * u2;
+    const float meq5 = rho * (3.0f * uxx - u2);
+    const float meq6 = rho * (uyy - uzz);
+    const float meq7 = rho * ux * uy;
+    const float meq8 = rho * uy * uz;
+    const float meq9 = rho * uz * ux;
+    // forcing moments of Delta'' (Sigma of Eq. (moment_two_external_force))
+    const float uf = ux * fx + uy * fy + uz * fz;
+    const float gs1 = 1.0f + a.g_shear;
+    const float F4 = (1.0f + a.g_bulk) * uf;
+    const float F5 = gs1 * (3.0f * ux * fx - uf);
+    const float F6 = gs1 * (uy * fy - uz * fz);
+    const float F7 = 0.5f * gs1 * (ux * fy + uy * fx);
+    const float F8 = 0.5f * gs1 * (uy * fz + uz * fy);
+    const float F9 = 0.5f * gs1 * (uz * fx + ux * fz);
+
+    float M[19];  // post-collision moments divided by w_k
+    M[0] = m[0];
+    M[1] = 3.0f * (m[1] + fx);
+    M[2] = 3.0f * (m[2] + fy);
+    M[3] = 3.0f * (m[3] + fz);
+    M[4] = lbd::inv_w(4) * (meq4 + a.g_bulk * (m[4] - meq4) + F4);
+    M[5] = lbd::inv_w(5) * (meq5 + a.g_shear * (m[5] - meq5) + F5);
+    M[6] = lbd::inv_w(6) * (meq6 + a.g_shear * (m[6] - meq6) + F6);
+    M[7] = lbd::inv_w(7) * (meq7 + a.g_shear * (m[7] - meq7) + F7);
+    M[8] = lbd::inv_w(8) * (meq8 + a.g_shear * (m[8] - meq8) + F8);
+    M[9] = lbd::inv_w(9) * (meq9 + a.g_shear * (m[9] - meq9) + F9);
+#pragma unroll
+    for (int k = 10; k < 16; ++k) M[k] = lbd::inv_w(k) * (a.g_odd * m[k]);
+#pragma unroll
+    for (int k = 16; k < 19; ++k) M[k] = lbd::inv_w(k) * (a.g_even * m[k]);
+
+    if (NOISE) {
+        float g[16];
+        lbd::gaussians16(rk, node, a.step, 0u, replica, g);
+        const float rn = a.noise_rho0 ? a.rho0 : rho;
+        const float s = sqrtf(a.mu * rn);
+        // sqrt(mu rho w_k) phi_k r_k, divided by w_k: sqrt(mu rho / w_k) phi_k r_k
+        const float sb = s * a.phi_bulk, ss = s * a.phi_shear, so = s * a.phi_odd, se = s * a.phi_even;
+        M[4] += sb * lbd::sqrt_inv_w(4) * g[0];
+#pragma unroll
+        for (int k = 5; k < 10; ++k) M[k] += ss * lbd::sqrt_inv_w(k) * g[k - 4];
+#pragma unroll
+        for (int k = 10; k < 16; ++k) M[k] += so * lbd::sqrt_inv_w(k) * g[k - 4];
+#pragma unroll
+        for (int k = 16; k < 19; ++k) M[k] += se * lbd::sqrt_inv_w(k) * g[k - 4];
+    }
+
+    lbd::backward(M, out);
+}
+
 template <int DT, bool NOISE, bool FIELD, bool WALLS>
 __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Store<DT>::T *__restrict__ src,
                                                         typename lbd::Store<DT>::T *__restrict__ dst,
@@ -65,9 +136,7 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
         }
     }
 
-    // ---- moments and force -----------------------------------------------
-    float m[19];
-    lbd::forward(n, m);
+    // ---- force and collision -----------------------------------------------
     float fx = a.fx, fy = a.fy, fz = a.fz;
     if (FIELD) {
         if (ffield) {  // caller's field, component stride N
@@ -81,65 +150,8 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
             fz += __ldg(facc + 2 * P + self);
         }
     }
-    const float rho = a.rho0 + m[0];
-    const float inv_rho = 1.0f / rho;
-    const float ux = (m[1] + 0.5f * fx) * inv_rho;
-    const float uy = (m[2] + 0.5f * fy) * inv_rho;
-    const float uz = (m[3] + 0.5f * fz) * inv_rho;
-
-    // ---- relaxation in moment space ----------------------------------------
-    const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
-    const float u2 = uxx + uyy + uzz;
-    const float meq4 = rho * u2;
-    const float meq5 = rho * (3.0f * uxx - u2);
-    const float meq6 = rho * (uyy - uzz);
-    const float meq7 = rho * ux * uy;
-    const float meq8 = rho * uy * uz;
-    const float meq9 = rho * uz * ux;
-    // forcing moments of Delta'' (Sigma of Eq. (moment_two_external_force))
-    const float uf = ux * fx + uy * fy + uz * fz;
-    const float gs1 = 1.0f + a.g_shear;
-    const float F4 = (1.0f + a.g_bulk) * uf;
-    const float F5 = gs1 * (3.0f * ux * fx - uf);
-    const float F6 = gs1 * (uy * fy - uz * fz);
-    const float F7 = 0.5f * gs1 * (ux * fy + uy * fx);
-    const float F8 = 0.5f * gs1 * (uy * fz + uz * fy);
-    const float F9 = 0.5f * gs1 * (uz * fx + ux * fz);
-
-    float M[19];  // post-collision moments divided by w_k
-    M[0] = m[0];
-    M[1] = 3.0f * (m[1] + fx);
-    M[2] = 3.0f * (m[2] + fy);
-    M[3] = 3.0f * (m[3] + fz);
-    M[4] = lbd::inv_w(4) * (meq4 + a.g_bulk * (m[4] - meq4) + F4);
-    M[5] = lbd::inv_w(5) * (meq5 + a.g_shear * (m[5] - meq5) + F5);
-    M[6] = lbd::inv_w(6) * (meq6 + a.g_shear * (m[6] - meq6) + F6);
-    M[7] = lbd::inv_w(7) * (meq7 + a.g_shear * (m[7] - meq7) + F7);
-    M[8] = lbd::inv_w(8) * (meq8 + a.g_shear * (m[8] - meq8) + F8);
-    M[9] = lbd::inv_w(9) * (meq9 + a.g_shear * (m[9] - meq9) + F9);
-#pragma unroll
-    for (int k = 10; k < 16; ++k) M[k] = lbd::inv_w(k) * (a.g_odd * m[k]);
-#pragma unroll
-    for (int k = 16; k < 19; ++k) M[k] = lbd::inv_w(k) * (a.g_even * m[k]);
-
-    if (NOISE) {
-        float g[16];
-        lbd::gaussians16(a.rk, self, a.step, 0u, a.replica, g);
-        const float rn = a.noise_rho0 ? a.rho0 : rho;
-        const float s = sqrtf(a.mu * rn);
-        // sqrt(mu rho w_k) phi_k r_k, divided by w_k: sqrt(mu rho / w_k) phi_k r_k
-        const float sb = s * a.phi_bulk, ss = s * a.phi_shear, so = s * a.phi_odd, se = s * a.phi_even;
-        M[4] += sb * lbd::sqrt_inv_w(4) * g[0];
-#pragma unroll
-        for (int k = 5; k < 10; ++k) M[k] += ss * lbd::sqrt_inv_w(k) * g[k - 4];
-#pragma unroll
-        for (int k = 10; k < 16; ++k) M[k] += so * lbd::sqrt_inv_w(k) * g[k - 4];
-#pragma unroll
-        for (int k = 16; k < 19; ++k) M[k] += se * lbd::sqrt_inv_w(k) * g[k - 4];
-    }
-
     float out[19];
-    lbd::backward(M, out);
+    collide_node<NOISE>(n, fx, fy, fz, a, a.rk, self, a.replica, out);
 #pragma unroll
     for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
 }

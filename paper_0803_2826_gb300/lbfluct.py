@@ -34,8 +34,16 @@ EXPORTS = (
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
-    "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic", "lb_version",
+    "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
+    "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
+    "lb_batch_autotune", "lb_batch_set_config", "lb_batch_get_config", "lb_batch_set_barrier_limit",
+    "lb_batch_get_step", "lb_batch_get_launch_count", "lb_batch_init_equilibrium", "lb_batch_set_populations",
+    "lb_batch_get_populations", "lb_batch_moments", "lb_version",
 )
+
+
+class lb_batch_config(C.Structure):
+    _fields_ = [("threads", C.c_int), ("tile_nodes", C.c_int), ("blocks_per_sm", C.c_int), ("grid", C.c_int)]
 
 
 class LBError(RuntimeError):
@@ -120,6 +128,21 @@ def load(path: str | None = None):
             "lb_adjoint_step": (i, [H, vp, vp, vp, vp]),
             "lb_adjoint_seed_kinetic": (i, [H, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, vp]),
             "lb_adjoint_kinetic": (i, [H, i, i, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp]),
+            "lb_batch_population_bytes": (C.c_size_t, [P, i]),
+            "lb_batch_create": (i, [P, i, vp, vp, vp, C.POINTER(H)]),
+            "lb_batch_destroy": (i, [H]),
+            "lb_batch_step": (i, [H, i, i]),
+            "lb_batch_sync": (i, [H, C.POINTER(u32)]),
+            "lb_batch_autotune": (i, [H, i, C.POINTER(lb_batch_config), C.POINTER(C.c_double)]),
+            "lb_batch_set_config": (i, [H, C.POINTER(lb_batch_config)]),
+            "lb_batch_get_config": (i, [H, C.POINTER(lb_batch_config)]),
+            "lb_batch_set_barrier_limit": (i, [H, u32]),
+            "lb_batch_get_step": (i, [H, C.POINTER(u32)]),
+            "lb_batch_get_launch_count": (i, [H, C.POINTER(u64)]),
+            "lb_batch_init_equilibrium": (i, [H, i, vp, vp]),
+            "lb_batch_set_populations": (i, [H, i, vp]),
+            "lb_batch_get_populations": (i, [H, i, vp]),
+            "lb_batch_moments": (i, [H, i, vp, vp, vp, vp]),
             "lb_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -296,6 +319,134 @@ def lb_adjoint_seed_kinetic(h, state, lo, hi, lambda_out, grad_force, loss):
 def lb_adjoint_kinetic(h, nsteps, checkpoint_every, lo, hi, grad_force, loss):
     _check(load().lb_adjoint_kinetic(h, int(nsteps), int(checkpoint_every), _int3(lo), _int3(hi),
                                      _ptr(grad_force), _ptr(loss)))
+
+
+def _params_array(plist):
+    arr = (lb_params * len(plist))()
+    for k, p in enumerate(plist):
+        arr[k] = p
+    return arr
+
+
+def lb_batch_population_bytes(plist) -> int:
+    return load().lb_batch_population_bytes(_params_array(plist), len(plist))
+
+
+def lb_batch_create(plist, pops_a, pops_b, stream=None):
+    b = C.c_void_p()
+    _check(load().lb_batch_create(_params_array(plist), len(plist), _ptr(pops_a), _ptr(pops_b), _stream(stream),
+                                  C.byref(b)))
+    return b
+
+
+def lb_batch_destroy(b):
+    _check(load().lb_batch_destroy(b))
+
+
+def lb_batch_step(b, nsteps, use_graph=True):
+    _check(load().lb_batch_step(b, int(nsteps), int(bool(use_graph))))
+
+
+def lb_batch_sync(b, raise_on_error=True):
+    bits = C.c_uint32(0)
+    st = load().lb_batch_sync(b, C.byref(bits))
+    if raise_on_error:
+        _check(st)
+    return st, bits.value
+
+
+def lb_batch_autotune(b, trial_steps=5):
+    cfg = lb_batch_config()
+    ms = C.c_double()
+    _check(load().lb_batch_autotune(b, int(trial_steps), C.byref(cfg), C.byref(ms)))
+    return cfg, ms.value
+
+
+def lb_batch_set_config(b, threads, tile_nodes, blocks_per_sm):
+    cfg = lb_batch_config(int(threads), int(tile_nodes), int(blocks_per_sm), 0)
+    _check(load().lb_batch_set_config(b, C.byref(cfg)))
+
+
+def lb_batch_get_config(b):
+    cfg = lb_batch_config()
+    _check(load().lb_batch_get_config(b, C.byref(cfg)))
+    return cfg
+
+
+def lb_batch_set_barrier_limit(b, spins):
+    _check(load().lb_batch_set_barrier_limit(b, int(spins)))
+
+
+def lb_batch_get_step(b) -> int:
+    v = C.c_uint32()
+    _check(load().lb_batch_get_step(b, C.byref(v)))
+    return v.value
+
+
+def lb_batch_get_launch_count(b) -> int:
+    v = C.c_uint64()
+    _check(load().lb_batch_get_launch_count(b, C.byref(v)))
+    return v.value
+
+
+def lb_batch_init_equilibrium(b, replica=-1, rho=None, u=None):
+    _check(load().lb_batch_init_equilibrium(b, int(replica), _ptr(rho), _ptr(u)))
+
+
+def lb_batch_set_populations(b, replica, n):
+    _check(load().lb_batch_set_populations(b, int(replica), _ptr(n)))
+
+
+def lb_batch_get_populations(b, replica, n):
+    _check(load().lb_batch_get_populations(b, int(replica), _ptr(n)))
+
+
+def lb_batch_moments(b, replica, rho=None, j=None, pi=None, sums=None):
+    _check(load().lb_batch_moments(b, int(replica), _ptr(rho), _ptr(j), _ptr(pi), _ptr(sums)))
+
+
+class Batch:
+    """Owns the two batch population buffers (torch uint8 device tensors) and a batch handle."""
+
+    def __init__(self, shapes, *, seeds=None, replicas=None, device="cuda", stream=None, **kw):
+        import torch
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]
+        n = len(self.shapes)
+        seeds = list(range(n)) if seeds is None else list(seeds)
+        replicas = list(range(n)) if replicas is None else list(replicas)
+        self.params = [make_params(s, seed=seeds[k], replica=replicas[k], **kw) for k, s in enumerate(self.shapes)]
+        nbytes = lb_batch_population_bytes(self.params)
+        if nbytes == 0:
+            raise LBError(LB_EINVAL, lb_last_error())
+        self.device = torch.device(device)
+        self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device) for _ in range(2)]
+        self.b = lb_batch_create(self.params, self._bufs[0], self._bufs[1], stream)
+
+    def close(self):
+        if getattr(self, "b", None) is not None:
+            lb_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_populations(self, r):
+        import torch
+        nx, ny, nz = self.shapes[r]
+        out = torch.empty((19, nz, ny, nx), dtype=torch.float64, device=self.device)
+        lb_batch_get_populations(self.b, r, out)
+        return out
+
+    def moments(self, r):
+        import torch
+        nx, ny, nz = self.shapes[r]
+        rho = torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+        j = torch.empty((3, nz, ny, nx), dtype=torch.float32, device=self.device)
+        lb_batch_moments(self.b, r, rho, j)
+        return rho, j
 
 
 def lb_version() -> str:
