@@ -50,6 +50,8 @@ def _args():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched / adjoint / reduced-precision measurements")
     ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--kernel-only", action="store_true",
                     help="time lb_step alone (no particles) on --shape for each --kT and --dtype")
@@ -350,16 +352,125 @@ def run_ours(args):
         "clocks": clk,
         "wall_s": wall,
     }
+    if world == 1 and not args.no_forms:
+        lat.close()
+        torch.cuda.empty_cache()
+        line["forms"] = _forms(peak)
     if world == 1 and not args.no_cpu_baseline:
         mlups, steps, el, cores = _cpu_sample()
         line["cpu_baseline"] = {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                                 "sample": "%d steps of a 256x256x4 slab + 1 x 256-monomer chain (%.1f s)"
                                           % (steps, el)}
     print(json.dumps(line))
-    lat.close()
+    if lat.h is not None:
+        lat.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def _forms(peak):
+    """The three further forms, each timed with CUDA events against the plain
+    FP32 form on the same box:
+      batched   512 periodic replicas, edges from {16,24,32,48,64} drawn with
+                seed 7, replica r keyed by seed r, kT = 1e-4, FP32: autotuned,
+                then 2000 steps in one graph-replayed persistent launch;
+      adjoint   64^3, kT = 0, force field ~ N(0, 1e-5), kinetic energy of the
+                central 16^3 after 500 steps, checkpoints every 50: forward +
+                reverse ms per step vs 500 plain FP32 steps;
+      precision 512^3 between walls, g = 1e-6, kT = 1e-4: ms per LB step with
+                FP16 / BF16 storage vs FP32 storage (no particles)."""
+    import numpy as np
+    import torch
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    out = {}
+    stream = torch.cuda.Stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    # batched replicas
+    edges = inputs.replica_edges(512, 7)
+    B = L.Batch([(e, e, e) for e in edges], kT=KT, stream=stream)
+    with torch.cuda.stream(stream):
+        L.lb_batch_init_equilibrium(B.b)
+    cfg, _ = L.lb_batch_autotune(B.b, 2)
+    with torch.cuda.stream(stream):
+        L.lb_batch_step(B.b, 5, True)
+    torch.cuda.synchronize()
+    nsteps = 2000
+    with torch.cuda.stream(stream):
+        L.lb_batch_step(B.b, nsteps, True)  # records the graph for this length
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        L.lb_batch_step(B.b, nsteps, True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    L.lb_batch_sync(B.b)
+    ms = a.elapsed_time(b)
+    nodes = int(sum(e ** 3 for e in edges))
+    out["batched"] = {"replicas": 512, "nodes": nodes, "steps": nsteps, "launches": 1,
+                      "mlups": nodes * nsteps / (ms * 1e-3) / 1e6,
+                      "hbm_frac": 152 * nodes * nsteps / (ms * 1e-3) / 1e9 / peak,
+                      "config": {"threads": cfg.threads, "tile_nodes": cfg.tile_nodes,
+                                 "blocks_per_sm": cfg.blocks_per_sm, "grid": cfg.grid}}
+    B.close()
+
+    # adjoint vs plain forward
+    shape, T, K = (64, 64, 64), 500, 50
+    f = torch.as_tensor(inputs.gaussian_field(shape, 3, 1e-5, seed=0).astype(np.float32)).cuda()
+    lat = L.Lattice(shape, force=f, stream=stream)
+    g = torch.empty_like(f)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        lat.step(20)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        lat.step(T)
+        b.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / T
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        L.lb_adjoint_kinetic(lat.h, T, K, (24, 24, 24), (40, 40, 40), g, loss)
+    torch.cuda.synchronize()
+    adj_ms = (time.perf_counter() - t0) * 1e3 / T
+    out["adjoint"] = {"shape": list(shape), "steps": T, "checkpoint_every": K,
+                      "fwd_plus_adj_ms_per_step": adj_ms, "plain_fp32_ms_per_step": fwd_ms,
+                      "ratio": adj_ms / fwd_ms, "loss": loss.item(),
+                      "timing": "wall clock around lb_adjoint_kinetic (includes its checkpoint allocations)"}
+    lat.close()
+
+    # reduced-precision storage
+    shape = (512, 512, 512)
+    prec = {}
+    for name, code, esz in (("f32", L.LB_F32, 4), ("f16", L.LB_F16, 2), ("bf16", L.LB_BF16, 2)):
+        lat = L.Lattice(shape, dtype=code, kT=KT, seed=3, walls=True, body_force=(1e-6, 0, 0), stream=stream)
+        with torch.cuda.stream(stream):
+            lat.init_equilibrium()
+            lat.step(3)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            lat.step(20)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 20
+        nfl = 512 * 512 * 510
+        prec[name] = {"ms_per_step": ms, "mlups": nfl / (ms * 1e-3) / 1e6,
+                      "hbm_frac": 2 * 19 * esz * nfl / (ms * 1e-3) / 1e9 / peak}
+        lat.close()
+        torch.cuda.empty_cache()
+    for name in ("f16", "bf16"):
+        prec[name]["speedup_vs_f32"] = prec["f32"]["ms_per_step"] / prec[name]["ms_per_step"]
+    out["precision"] = {"shape": list(shape), "walls": True, "kT": KT, **prec}
+    return out
 
 
 def _profiled_traffic():

@@ -1,0 +1,127 @@
+"""Reduced-precision population storage (deviations n_i - a_i rho0 scaled by
+2^10, stored as FP16 or BF16 with round-to-nearest-even, FP32 collision)
+against the FP64 oracle and against FP32 storage.
+
+Workload: plane Poiseuille flow between bounce-back walls at z = 0 and
+z = nz - 1 driven by a body force g along x, thermal noise kT = 1e-4, free
+point particles with Gamma = 2 (20 in MD units), started on the analytic
+parabola.  At 128^3 the force is scaled by (510/126)^2 so the flow speed
+matches the 512^3 case; the particle number is scaled with the volume.
+Errors reported: relative L2 of the velocity field, of the non-equilibrium
+stress pi - pi^eq, and the largest relative deviation of a non-conserved
+mode's mean square.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_0803_2826_gb300 import inputs  # noqa: E402
+from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+
+NU = 1.0 / 6.0
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _metrics(ora, p, pops, e):
+    """velocity, non-equilibrium stress and mode mean squares of fluid nodes."""
+    rho, j, pi = ora.moments(p, pops)
+    fl = slice(1, p.nz - 1)
+    u = (j / rho)[:, fl]
+    eye = [(0, 0), (1, 1), (2, 2), (0, 1), (1, 2), (2, 0)]
+    uu = j / rho
+    pieq = np.stack([rho * ((1 / 3) if a_ == b_ else 0) + rho * uu[a_] * uu[b_] for a_, b_ in eye])
+    m = ora.modes(p, pops)[:, fl].reshape(19, -1)
+    return u, (pi - pieq)[:, fl], (m[4:] ** 2).mean(1)
+
+
+def _run_gpu(shape, dtype, g, kT, u0, pos, mom, nsteps, seed):
+    lat = L.Lattice(shape, dtype=dtype, kT=kT, seed=seed, walls=True, body_force=(g, 0, 0))
+    lat.init_equilibrium(None, torch.as_tensor(u0).cuda())
+    gpos = torch.as_tensor(pos).cuda()
+    gmom = torch.as_tensor(mom, dtype=torch.float32).cuda()
+    parts = L.particles(pos.shape[0], gpos, gmom, mass0=1.0, gamma0=2.0)
+    for t in range(nsteps):
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=seed + 1, md_step0=10 * t)
+        L.lb_couple_particles(lat.h, parts, cp)
+        lat.step(1)
+    out = lat.get_populations().cpu().numpy()
+    assert lat.sync() == (L.LB_OK, 0)
+    lat.close()
+    return out
+
+
+def test_reduced_precision_vs_oracle_128(ora):
+    shape, nsteps, kT, seed = (128, 128, 128), 40, 1e-4, 5
+    g = 1e-6 * (510.0 / 126.0) ** 2
+    u0 = inputs.poiseuille_velocity(shape, g, NU)
+    npart = int(round(100000 * (128 / 512) ** 3))
+    pos = inputs.uniform_particles(npart, shape, seed=6, zrange=(1.0, shape[2] - 2.0))
+    mom = inputs.maxwell_momenta(npart, 1.0, kT, seed=7).astype(np.float32).astype(np.float64)
+    p = ora.make_params(shape, kT=kT, seed=seed, walls=True, body_force=(g, 0, 0))
+    pops = ora.equilibrium(p, None, u0)
+    opos, omom = pos.copy(), mom.copy()
+    for t in range(nsteps):
+        opos, omom, facc, _ = ora.couple(p, pops, opos, omom, 1.0, 2.0, dt=0.1, n_substeps=10, seed=seed + 1,
+                                         md_step0=10 * t)
+        pops = ora.step(p, pops, facc.astype(np.float32).astype(np.float64), t)
+    c, a, e, w, opp = ora.tables()
+    ref = _metrics(ora, p, pops, e)
+    table = {}
+    for name, dt in (("f32", L.LB_F32), ("f16", L.LB_F16), ("bf16", L.LB_BF16)):
+        got = _metrics(ora, p, _run_gpu(shape, dt, g, kT, u0, pos, mom, nsteps, seed), e)
+        table[name] = (rel(got[0], ref[0]), rel(got[1], ref[1]), float(np.max(np.abs(got[2] / ref[2] - 1))))
+    print("128^3 Poiseuille + noise + %d particles, %d steps, error vs FP64 oracle "
+          "(velocity, stress, mode mean squares):" % (npart, nsteps))
+    for k, v in table.items():
+        print("  %-5s %.2e %.2e %.2e" % ((k,) + v))
+    assert max(table["f32"]) < 2e-5
+    assert max(table["f16"]) < 2e-2
+    assert max(table["bf16"]) < 1.5e-1
+
+
+@pytest.mark.slow
+def test_reduced_precision_vs_fp32_512():
+    """512^3, walls at z = 0 and 511, g = 1e-6, kT = 1e-4, 100000 particles,
+    2000 steps from the analytic profile at the same seed: FP16 and BF16
+    storage against FP32 storage for the x-y averaged velocity profile
+    u_x(z), the shear stress profile pi_xz(z) and the mode mean squares."""
+    shape, nsteps, kT, seed = (512, 512, 512), 2000, 1e-4, 9
+    g = 1e-6
+    u0 = torch.as_tensor(inputs.poiseuille_velocity(shape, g, NU)).cuda()
+    pos = inputs.uniform_particles(100000, shape, seed=1, zrange=(1.0, 510.0))
+    mom = inputs.maxwell_momenta(100000, 1.0, kT, seed=2)
+    prof = {}
+    for name, dt in (("f32", L.LB_F32), ("f16", L.LB_F16), ("bf16", L.LB_BF16)):
+        lat = L.Lattice(shape, dtype=dt, kT=kT, seed=seed, walls=True, body_force=(g, 0, 0))
+        lat.init_equilibrium(None, u0)
+        gpos = torch.as_tensor(pos).cuda()
+        gmom = torch.as_tensor(mom, dtype=torch.float32).cuda()
+        parts = L.particles(100000, gpos, gmom, mass0=1.0, gamma0=2.0)
+        for t in range(nsteps):
+            L.lb_couple_particles(lat.h, parts, L.couple_params(n_substeps=10, dt=0.1, seed=seed + 1,
+                                                                md_step0=10 * t))
+            lat.step(1)
+        rho, j, pi, sums = lat.moments(want_sums=True)
+        ux = (j[0] / rho)[1:-1].mean(dim=(1, 2)).double().cpu().numpy()
+        pxz = pi[5][1:-1].mean(dim=(1, 2)).double().cpu().numpy()
+        nfl = 512 * 512 * 510
+        msq = (sums[19 + 4:].cpu().numpy() / nfl)
+        prof[name] = (ux, pxz, msq)
+        assert lat.sync() == (L.LB_OK, 0)
+        lat.close()
+        del rho, j, pi
+        torch.cuda.empty_cache()
+    ref = prof["f32"]
+    for name in ("f16", "bf16"):
+        ux, pxz, msq = prof[name]
+        eu = rel(ux, ref[0])
+        es = rel(pxz, ref[1])
+        em = float(np.max(np.abs(msq / ref[2] - 1)))
+        print("512^3 %s vs f32 after %d steps: profile %.2e, stress %.2e, modes %.2e" % (name, nsteps, eu, es, em))
+        assert eu < (5e-2 if name == "f16" else 2e-1)
+        assert em < (2e-2 if name == "f16" else 1e-1)
