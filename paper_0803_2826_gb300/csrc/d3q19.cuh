@@ -269,48 +269,20 @@ __device__ __forceinline__ float uniform01(uint32_t x)
     return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
 }
 
-// sin and cos of 2 pi v for a dyadic v in (0, 1): v = q/4 + f exactly with
-// q = rint(4 v) and |f| <= 1/8, so the polynomial argument needs no rounded
-// multiple of pi.  Taylor series of sin(2 pi f) to f^9 and cos(2 pi f) to
-// f^10 (truncation below 2e-9 for |2 pi f| <= pi/4), then the quadrant q.
-__device__ __forceinline__ void sincos_2pi(float v, float &sn, float &cs)
-{
-    constexpr double T = 6.283185307179586476925286766559;
-    constexpr float S1 = (float)T;
-    constexpr float S3 = (float)(-T * T * T / 6.0);
-    constexpr float S5 = (float)(T * T * T * T * T / 120.0);
-    constexpr float S7 = (float)(-T * T * T * T * T * T * T / 5040.0);
-    constexpr float S9 = (float)(T * T * T * T * T * T * T * T * T / 362880.0);
-    constexpr float C2 = (float)(-T * T / 2.0);
-    constexpr float C4 = (float)(T * T * T * T / 24.0);
-    constexpr float C6 = (float)(-T * T * T * T * T * T / 720.0);
-    constexpr float C8 = (float)(T * T * T * T * T * T * T * T / 40320.0);
-    constexpr float C10 = (float)(-T * T * T * T * T * T * T * T * T * T / 3628800.0);
-    const float q = rintf(4.0f * v);
-    const float f = fmaf(q, -0.25f, v);
-    const float f2 = f * f;
-    const float s = f * fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, S9, S7), S5), S3), S1);
-    const float c = fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, fmaf(f2, C10, C8), C6), C4), C2), 1.0f);
-    const int qi = (int)q;
-    float cq = (qi & 1) ? s : c;
-    float sq = (qi & 1) ? c : s;
-    if ((qi + 1) & 2) cq = -cq;  // quadrants 1, 2
-    if (qi & 2) sq = -sq;        // quadrants 2, 3
-    sn = sq;
-    cs = cq;
-}
-
 // Box-Muller pair from two raw words: sqrt(-2 ln v1) (cos, sin)(2 pi v2).
+// The angle is centred, 2 pi v2 = pi + 2 pi (v2 - 1/2) with v2 - 1/2 exact,
+// so the hardware sine / cosine see an argument in (-pi, pi), where their
+// absolute error is below 2^-21; cos and sin of the shifted angle change sign.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
     const float v1 = uniform01(a);
-    const float v2 = uniform01(b);
+    const float w = uniform01(b) - 0.5f;
     const float L = -2.0f * logf(v1);  // > 0 since v1 <= 1 - 2^-24
     const float r = L * rsqrtf(L);
     float s, c;
-    sincos_2pi(v2, s, c);
-    g0 = r * c;
-    g1 = r * s;
+    __sincosf(6.283185307179586f * w, &s, &c);
+    g0 = -r * c;
+    g1 = -r * s;
 }
 
 // Sixteen Gaussians for counter word 0, step, domain, replica: Philox blocks

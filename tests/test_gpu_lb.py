@@ -129,7 +129,9 @@ def test_noise_words_bitwise(ora):
         want = ora.raw_words(seed, 1000 + q, 77, domain=0, replica=3, nblocks=4)
         assert np.array_equal(W[q].ravel(), want)
         g = ora.gaussians(seed, 1000 + q, 77, domain=0, replica=3, nblocks=4)
-        assert np.allclose(G[q].ravel(), g, rtol=0, atol=2e-6)
+        # FP32 logarithm and hardware sine / cosine (absolute error < 2^-21
+        # on the centred angle) times a radius of at most ~5.8
+        assert np.allclose(G[q].ravel(), g, rtol=0, atol=4e-6)
     # particle domain, one block
     L.lb_noise_words(5, 0, 9, 1, 0, n, 1, words, None)
     torch.cuda.synchronize()
