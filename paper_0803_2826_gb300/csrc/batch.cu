@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "d3q19.cuh"
+#include "grid_barrier.cuh"
 #include "lbf_internal.h"
 #include "stream_collide.cuh"
 
@@ -91,37 +92,11 @@ struct BatchArgs {
     unsigned int spin_limit;
 };
 
-// Bounded grid barrier.  Returns false if the run must stop (a barrier timed
-// out here or elsewhere).
-__device__ __forceinline__ bool grid_barrier(const BatchArgs &a)
+// Bounded grid barrier (grid_barrier.cuh).  Returns false if the run must
+// stop (a barrier timed out here or elsewhere).
+__device__ __forceinline__ bool batch_barrier(const BatchArgs &a)
 {
-    __shared__ int stop;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int *vbar = a.bar;
-        const unsigned int gen = vbar[1];
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&a.bar[0], 1u) + 1u;
-        if (arrived == gridDim.x) {
-            a.bar[0] = 0u;
-            __threadfence();
-            atomicAdd(&a.bar[1], 1u);
-        } else {
-            unsigned int spins = 0;
-            while (vbar[1] == gen && vbar[2] == 0u) {
-                if (++spins > a.spin_limit) {
-                    atomicOr(a.err, LB_DERR_BARRIER);
-                    atomicExch(&a.bar[2], 1u);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-        stop = vbar[2] != 0u;
-    }
-    __syncthreads();
-    return !stop;
+    return lbi::grid_barrier(a.bar, a.err, a.spin_limit);
 }
 
 template <int DT, bool NOISE>
@@ -172,7 +147,7 @@ __global__ void k_batch(BatchArgs a)
             for (uint32_t k = threadIdx.x; k < tl.count; k += blockDim.x)
                 batch_node<DT, NOISE>(d, tl.begin + k, src, dst, a.phys, step);
         }
-        if (!grid_barrier(a)) return;
+        if (!batch_barrier(a)) return;
         cur ^= 1u;
         step += 1u;
     }

@@ -22,6 +22,7 @@
 #include <cstdio>
 
 #include "d3q19.cuh"
+#include "grid_barrier.cuh"
 #include "lbf_internal.h"
 
 namespace lbi {
@@ -44,6 +45,10 @@ struct Particles {
     unsigned int *flags = nullptr;  // two rebuild-request slots
     uint32_t sub_counter = 0;
     int nlist_n = -1;            // particle count the list was built for
+    size_t rec_off = 0;          // offset of the live records in `records`
+    int last_nsub = 0;           // sub-steps of the previous call
+    bool persistent = true;      // use the persistent kernel when it fits
+    unsigned int *bar = nullptr; // grid barrier words of the persistent kernel
 };
 
 namespace {
@@ -537,6 +542,7 @@ void free_parts(Particles *P)
     cudaFree(P->ncount);
     cudaFree(P->ref);
     cudaFree(P->flags);
+    cudaFree(P->bar);
     delete P;
 }
 
@@ -577,24 +583,30 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
         P->nlist_n = -1;
     }
     if (!P->flags) {
-        cudaError_t e = cudaMalloc((void **)&P->flags, 2 * sizeof(unsigned int));
+        // [0], [1]: rebuild slots of the multi-kernel path; [2], [3]: build
+        // request and rebuild epoch of the persistent path
+        cudaError_t e = cudaMalloc((void **)&P->flags, 4 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->bar, 3 * sizeof(unsigned int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->flags, 0, 4 * sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->bar, 0, 3 * sizeof(unsigned int), h->stream);
         if (e != cudaSuccess) {
             set_error("lb_couple_particles: flag allocation failed");
             return LB_ENOMEM;
         }
     }
     const size_t need = (size_t)n * (size_t)nsub;
-    if (P->rec_cap < P->n_records + need) {
-        // grow, keeping the records not yet cleared
+    if (P->rec_cap < P->rec_off + P->n_records + need || P->rec_cap < 2 * need) {
+        // grow, keeping the records not yet cleared (moved to offset 0)
         int *nr = nullptr;
-        const size_t cap = (P->n_records + need) * 2;
+        const size_t cap = std::max((P->n_records + need) * 2, 2 * need);
         cudaError_t e = cudaMalloc((void **)&nr, cap * sizeof(int));
         if (e != cudaSuccess) {
             set_error("lb_couple_particles: record allocation failed");
             return LB_ENOMEM;
         }
         if (P->n_records) {
-            e = cudaMemcpyAsync(nr, P->records, P->n_records * sizeof(int), cudaMemcpyDeviceToDevice, h->stream);
+            e = cudaMemcpyAsync(nr, P->records + P->rec_off, P->n_records * sizeof(int), cudaMemcpyDeviceToDevice,
+                                h->stream);
             if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
             e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
@@ -602,8 +614,263 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
         cudaFree(P->records);
         P->records = nr;
         P->rec_cap = cap;
+        P->rec_off = 0;
     }
     return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent variant: one cooperative launch runs all sub-steps of a call.
+// Each group of 8 lanes owns one particle for the whole call (position,
+// momentum and the fluid velocity of its 8 stencil nodes stay in registers;
+// the velocities are re-gathered only when the particle changes cell).  Sub-
+// steps are separated by the bounded grid barrier.  The Verlet list is built
+// by k_build_nlist before the launch when the previous call asked for it; if a
+// particle still moves more than half the skin during the call, every group
+// rebuilds its own list in place (a slower scan, no barrier needed).
+// ---------------------------------------------------------------------------
+struct PersistArgs {
+    CoupleArgs c;
+    int nsub;
+    const void *src;
+    const float *ffield;
+    double *pos;
+    float *mom;
+    const float *mass, *gamma;
+    float4 *sh[2];
+    int *nlist, *ncount;
+    float4 *ref;
+    float *facc;
+    int *records;            // this call: [nsub][n]
+    const int *stale;        // previous call's records to clear: [nstale_sub][n], or NULL
+    int nstale_sub;
+    unsigned int *flags;     // [0] build before the next call, [1] rebuild epoch request
+    uint32_t epoch0;         // epoch of this call's first sub-step
+    unsigned int *bar;
+    unsigned int *err;
+    unsigned int spin_limit;
+};
+
+// Shadow positions from the caller's double positions, when a list build is
+// requested (the positions may have been changed between calls).
+__global__ void k_shadow_from_pos(const double *pos, float4 *shadow, const unsigned int *flag, unsigned int *err,
+                                  CoupleArgs c)
+{
+    if (*flag == 0u) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.n) return;
+    const double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+    CPos q;
+    if (!split(r, c.g, q)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    shadow[p] = pack(q);
+}
+
+__device__ __forceinline__ void rebuild_own_list(const PersistArgs &a, int p, int q, const CPos &me,
+                                                 const float4 *sh)
+{
+    const int n = a.c.n;
+    const int per = (n + kChunks - 1) / kChunks;
+    const int j0 = q * per, j1 = min(n, j0 + per);
+    int *mine = a.nlist + ((size_t)p * kChunks + q) * kMaxNb;
+    int cnt = 0;
+    bool full = false;
+    for (int j = j0; j < j1; ++j) {
+        if (j == p) continue;
+        float d[3];
+        separation(me, unpack(sh[j]), a.c.g, d);
+        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < a.c.rlist2) {
+            if (cnt < kMaxNb) mine[cnt] = j;
+            else full = true;
+            ++cnt;
+        }
+    }
+    a.ncount[(size_t)p * kChunks + q] = cnt < kMaxNb ? cnt : kMaxNb;
+    if (full) atomicOr(a.err, LB_DERR_NLIST_FULL);
+    if (q == 0) a.ref[p] = pack(me);
+}
+
+template <int DT>
+__global__ void __launch_bounds__(kPartThreads, 8) k_couple_persistent(PersistArgs a)
+{
+    using S = lbd::Store<DT>;
+    const CoupleArgs &c = a.c;
+    const StepArgs &g = c.g;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid >> 3, q = tid & 7;
+    const bool active = p < c.n;
+    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
+    const typename S::T *src = static_cast<const typename S::T *>(a.src);
+    if (c.use_wca && blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0u;  // the pre-launch build has run
+
+    // phase 0: clear the previous call's impulses, first half drift
+    CPos me{};
+    float pm[3] = {0.f, 0.f, 0.f};
+    float m = 1.f, G = 1.f, C1 = c.C1, C2 = c.C2, C3 = c.C3;
+    if (active) {
+        for (int s = 0; s < a.nstale_sub; ++s) {
+            const int base = a.stale[(size_t)s * c.n + p];
+            CPos bq{};
+            bq.c[0] = base % g.nx;
+            bq.c[1] = (base / g.nx) % g.ny;
+            bq.c[2] = base / (g.nx * g.ny);
+            int x, y, z;
+            (void)stencil_node(bq, q, g, x, y, z);
+            const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+            a.facc[node] = 0.0f;
+            a.facc[g.pitch + node] = 0.0f;
+            a.facc[2 * g.pitch + node] = 0.0f;
+        }
+        m = a.mass ? a.mass[p] : c.mass0;
+        G = a.gamma ? a.gamma[p] : c.gamma0;
+        if (!c.uniform_coef) {
+            const float x1 = G * c.dt / m;
+            C1 = expf(-x1);
+            C2 = (m / G) * (-expm1f(-x1));
+            C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+        }
+        double r[3] = {a.pos[3 * p], a.pos[3 * p + 1], a.pos[3 * p + 2]};
+        pm[0] = a.mom[3 * p];
+        pm[1] = a.mom[3 * p + 1];
+        pm[2] = a.mom[3 * p + 2];
+        const double h = 0.5 * (double)c.dt / (double)m;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] += h * (double)pm[k];
+        confine_d(r, pm, g);
+        if (!split(r, g, me) && q == 0) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+        if (q == 0) a.sh[0][p] = pack(me);
+    }
+    if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+
+    int cache_cell = -1;
+    float uc[3] = {0.f, 0.f, 0.f};
+    const float h = 0.5f * c.dt / m;
+    for (int s = 0; s < a.nsub; ++s) {
+        const float4 *shin = a.sh[s & 1];
+        float4 *shout = a.sh[(s + 1) & 1];
+        if (active) {
+            if (c.use_wca && ((volatile unsigned int *)a.flags)[1] == a.epoch0 + (uint32_t)s)
+                rebuild_own_list(a, p, q, me, shin);
+
+            float F[3] = {0.f, 0.f, 0.f};
+            if (c.use_wca) {
+                const size_t li = (size_t)p * kChunks + q;
+                const int nc = a.ncount[li];
+                const int *lst = a.nlist + li * kMaxNb;
+                for (int k = 0; k < nc; ++k) {
+                    float d[3];
+                    separation(me, unpack(shin[lst[k]]), g, d);
+                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 < c.rc2) {
+                        const float sr2 = c.sigma2 / r2;
+                        const float sr6 = sr2 * sr2 * sr2;
+                        const float mag = 24.0f * c.eps * (2.0f * sr6 * sr6 - sr6) / r2;
+                        F[0] += mag * d[0];
+                        F[1] += mag * d[1];
+                        F[2] += mag * d[2];
+                    }
+                }
+            }
+            if (c.chain_len > 1 && q < 2) {
+                const int k = p % c.chain_len;
+                const int j = q == 0 ? p - 1 : p + 1;
+                const bool bonded = (q == 0) ? (k > 0) : (k < c.chain_len - 1 && j < c.n);
+                if (bonded) {
+                    float d[3];
+                    separation(me, unpack(shin[j]), g, d);
+                    const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
+                    if (x >= 1.0f) {
+                        atomicOr(a.err, LB_DERR_FENE_BROKEN);
+                    } else {
+                        const float mag = -c.k_fene / (1.0f - x);
+                        F[0] += mag * d[0];
+                        F[1] += mag * d[1];
+                        F[2] += mag * d[2];
+                    }
+                }
+            }
+
+            // fluid velocity: lane q caches node q of the current cell
+            int x, y, z;
+            const float w = stencil_node(me, q, g, x, y, z);
+            const int cell = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+            if (cell != cache_cell) {
+                node_velocity<DT>(src, a.ffield, x, y, z, g, uc);
+                cache_cell = cell;
+            }
+            float up[3] = {w * uc[0], w * uc[1], w * uc[2]};
+#pragma unroll
+            for (int o = 1; o < 8; o <<= 1) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    up[k] += __shfl_xor_sync(gmask, up[k], o);
+                    F[k] += __shfl_xor_sync(gmask, F[k], o);
+                }
+            }
+
+            float th[3] = {0.f, 0.f, 0.f};
+            if (g.kT > 0.0f) {
+                const lbd::U4 wv = lbd::philox10(
+                    lbd::U4{(uint32_t)p, c.md_step + (uint32_t)s, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
+                if (c.noise_kind == 1) {
+                    const uint32_t ws[3] = {wv.x, wv.y, wv.z};
+                    const float s3 = 1.7320508075688772f;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        const uint64_t kk = 2ull * (uint64_t)(ws[k] >> 9) + 1ull;
+                        th[k] = (6ull * kk < (1ull << 24)) ? -s3 : ((6ull * kk > 5ull * (1ull << 24)) ? s3 : 0.0f);
+                    }
+                } else {
+                    float g3;
+                    lbd::box_muller(wv.x, wv.y, th[0], th[1]);
+                    lbd::box_muller(wv.z, wv.w, th[2], g3);
+                }
+            }
+            float pn[3], J[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
+                J[k] = pn[k] - pm[k] - C2 * F[k];
+            }
+            {
+                const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+                atomicAdd(a.facc + node, -J[0] * w);
+                atomicAdd(a.facc + g.pitch + node, -J[1] * w);
+                atomicAdd(a.facc + 2 * g.pitch + node, -J[2] * w);
+            }
+            if (q == 0) a.records[(size_t)s * c.n + p] = cell;
+
+            // drift (every lane computes the same new position)
+            const bool last = (s == a.nsub - 1);
+            bool ok = drift(me, pn, h, g);
+            if (last) {
+                if (q == 0) {
+                    a.pos[3 * p] = join1(me.c[0], me.f[0]);
+                    a.pos[3 * p + 1] = join1(me.c[1], me.f[1]);
+                    a.pos[3 * p + 2] = join1(me.c[2], me.f[2]);
+                    a.mom[3 * p] = pn[0];
+                    a.mom[3 * p + 1] = pn[1];
+                    a.mom[3 * p + 2] = pn[2];
+                }
+            } else {
+                ok = drift(me, pn, h, g) && ok;
+            }
+            if (!ok && q == 0) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+            pm[0] = pn[0];
+            pm[1] = pn[1];
+            pm[2] = pn[2];
+            if (q == 0) {
+                shout[p] = pack(me);
+                if (c.use_wca) {
+                    float d[3];
+                    separation(me, unpack(a.ref[p]), g, d);
+                    const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (!last && d2 > c.half_skin2) atomicMax(&a.flags[1], a.epoch0 + (uint32_t)s + 1u);
+                    if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
+                }
+            }
+        }
+        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+    }
 }
 
 template <int DT>
@@ -645,6 +912,92 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     const T *src = static_cast<const T *>(h->pops[h->cur]);
     const bool need_nlist = cp->use_wca != 0;
 
+    // persistent path when every particle group can be resident at once
+    const int pblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
+    int per_sm = 0;
+    if (P->persistent && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>,
+                                                                       kPartThreads, 0) == cudaSuccess &&
+        pblocks <= per_sm * device_sm_count()) {
+        cudaError_t e = cudaSuccess;
+        if (need_nlist && P->nlist_n != n) {
+            const unsigned int init[4] = {0u, 0u, 1u, 0u};  // [2]: build before the launch, [3]: epoch
+            e = cudaMemcpyAsync(P->flags, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) return e;
+            P->nlist_n = n;
+        }
+        const bool fold_clear = h->facc_stale && P->n_records == (size_t)n * (size_t)P->last_nsub &&
+                                P->n_records <= P->rec_cap / 2 && (size_t)n * cp->n_substeps <= P->rec_cap / 2;
+        if (h->facc_stale && !fold_clear) {
+            e = clear_particle_forces(h);
+            if (e != cudaSuccess) return e;
+            h->facc_stale = 0;
+        }
+        if (need_nlist) {
+            k_shadow_from_pos<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, P->shadow[1], P->flags + 2, h->d_err,
+                                                                       c);
+            dim3 bgrid((n + kTile - 1) / kTile, kChunks);
+            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(P->shadow[1], P->nlist, P->ncount, P->ref, P->flags,
+                                                          h->d_err, c, 2u);
+            h->launches += 2;
+        }
+        PersistArgs a;
+        a.c = c;
+        a.nsub = cp->n_substeps;
+        a.src = src;
+        a.ffield = h->force;
+        a.pos = pp->pos;
+        a.mom = pp->mom;
+        a.mass = pp->mass;
+        a.gamma = pp->gamma;
+        a.sh[0] = P->shadow[0];
+        a.sh[1] = P->shadow[1];
+        a.nlist = P->nlist;
+        a.ncount = P->ncount;
+        a.ref = P->ref;
+        a.facc = h->facc;
+        // the record buffer has two halves: the stale records (cleared in the
+        // kernel's first phase) stay in one, this call's go to the other
+        const size_t half = P->rec_cap / 2;
+        const size_t new_off = fold_clear ? (P->rec_off == 0 ? half : 0) : P->rec_off + P->n_records;
+        a.stale = fold_clear ? P->records + P->rec_off : nullptr;
+        a.nstale_sub = fold_clear ? P->last_nsub : 0;
+        a.records = P->records + new_off;
+        a.flags = P->flags + 2;
+        a.epoch0 = P->sub_counter + 1u;
+        a.bar = P->bar;
+        a.err = h->d_err;
+        a.spin_limit = 1u << 22;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(pblocks);
+        lc.blockDim = dim3(kPartThreads);
+        lc.stream = h->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        void *args[] = {&a};
+        e = cudaLaunchKernelExC(&lc, (const void *)k_couple_persistent<DT>, args);
+        if (e != cudaSuccess) return e;
+        h->launches += 1;
+        if (fold_clear) {
+            P->rec_off = new_off;
+            P->n_records = (size_t)n * (size_t)cp->n_substeps;
+            h->facc_stale = 0;
+        } else {
+            P->n_records += (size_t)n * (size_t)cp->n_substeps;
+        }
+        P->sub_counter += (uint32_t)cp->n_substeps;
+        P->last_nsub = cp->n_substeps;
+        return cudaGetLastError();
+    }
+
+    if (h->facc_stale) {
+        cudaError_t e = clear_particle_forces(h);
+        if (e != cudaSuccess) return e;
+        h->facc_stale = 0;
+    }
     if (need_nlist && P->nlist_n != n) {
         cudaError_t e = cudaMemsetAsync(P->flags, 0xff, 2 * sizeof(unsigned int), h->stream);
         if (e != cudaSuccess) return e;
@@ -663,7 +1016,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         c.md_step = cp->md_step0 + (uint32_t)s;
         c.last = (s == cp->n_substeps - 1);
         c.slot = wr;
-        int *rec = P->records + P->n_records;
+        int *rec = P->records + P->rec_off + P->n_records;
         const int sblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
         k_substep<DT><<<sblocks, kPartThreads, 0, h->stream>>>(
             src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma,
@@ -719,11 +1072,8 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
     lb_status st = ensure_buffers(h, pp->n, cp->n_substeps);
     if (st != LB_OK) return st;
     cudaError_t e;
-    if (h->facc_stale) {  // impulses of the previous call were applied: clear their nodes
-        e = clear_particle_forces(h);
-        if (e != cudaSuccess) return cuda_fail("lb_couple_particles (clear accumulator)", e);
-        h->facc_stale = 0;
-    }
+    // impulses of the previous call that lb_step already applied are cleared
+    // inside run_substeps (by the persistent kernel, or by k_clear_records)
     switch (h->p.dtype) {
     case LB_F32: e = run_substeps<0>(h, pp, cp); break;
     case LB_F16: e = run_substeps<1>(h, pp, cp); break;
@@ -741,9 +1091,10 @@ cudaError_t clear_particle_forces(lb_handle *h)
     if (P->n_records) {
         const StepArgs g = make_args(h);
         int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
-        k_clear_records<<<blocks, 256, 0, h->stream>>>(h->facc, P->records, P->n_records, g);
+        k_clear_records<<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
         h->launches += 1;
         P->n_records = 0;
+        P->rec_off = 0;
     }
     return cudaGetLastError();
 }

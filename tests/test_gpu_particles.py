@@ -152,3 +152,44 @@ def test_coupled_momentum_conservation_gpu(ora):
     P1 = total()
     assert np.allclose(P1, P0, atol=2e-5), (P0, P1)
     assert lat.sync() == (L.LB_OK, 0)
+
+
+def test_many_particles_multi_kernel_path(ora):
+    """200000 free particles do not fit resident as 8-lane groups, so the
+    coupling runs the per-sub-step kernels instead of the persistent one."""
+    shape = (32, 32, 32)
+    pos = inputs.uniform_particles(200000, shape, seed=21)
+    mom = inputs.maxwell_momenta(200000, 1.0, 1e-4, seed=22)
+    r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_fast_wca_particles_rebuild_lists(ora):
+    """WCA particles moving ~0.5 sigma per call (more than half the Verlet
+    skin) force list rebuilds inside and between calls; three calls in a row,
+    each followed by an LB step, against the oracle's brute-force pairs."""
+    shape = (14, 14, 14)
+    n = 600
+    pos = inputs.uniform_particles(n, shape, seed=31)
+    kT = 1e-2
+    mom = inputs.maxwell_momenta(n, 1.0, kT, seed=32).astype(np.float32).astype(np.float64)
+    p = ora.make_params(shape, kT=kT, seed=4)
+    pops = ora.equilibrium(p)
+    md = ora.make_md(0, 0, eps=0.01, sigma=1.0, use_wca=True)
+    lat = L.Lattice(shape, kT=kT, seed=4)
+    lat.init_equilibrium()
+    gpos, gmom = dev(pos), dev(mom, torch.float32)
+    parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
+    opos, omom = pos.copy(), mom.copy()
+    for t in range(3):
+        opos, omom, facc, _ = ora.couple(p, pops, opos, omom, 1.0, 2.0, dt=0.5, n_substeps=10, seed=9,
+                                         md_step0=10 * t, md=md)
+        pops = ora.step(p, pops, facc.astype(np.float32).astype(np.float64), t)
+        cp = L.couple_params(n_substeps=10, dt=0.5, seed=9, md_step0=10 * t, use_wca=True, eps=0.01, sigma=1.0)
+        L.lb_couple_particles(lat.h, parts, cp)
+        lat.step(1)
+    assert lat.sync() == (L.LB_OK, 0)
+    assert _pos_err(gpos.cpu().numpy(), opos, shape) < 2e-5
+    assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 1e-3
