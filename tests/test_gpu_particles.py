@@ -172,7 +172,7 @@ def test_fast_wca_particles_rebuild_lists(ora):
     each followed by an LB step, against the oracle's brute-force pairs."""
     shape = (14, 14, 14)
     n = 600
-    pos = inputs.uniform_particles(n, shape, seed=31)
+    pos = inputs.random_walk_chains(n, 1, shape, min_dist=1.0, seed=31)  # no overlaps
     kT = 1e-2
     mom = inputs.maxwell_momenta(n, 1.0, kT, seed=32).astype(np.float32).astype(np.float64)
     p = ora.make_params(shape, kT=kT, seed=4)
