@@ -284,7 +284,7 @@ __global__ void k_half_drift(const double *pos, float *mom, const float *mass, f
 }
 
 // Verlet-list build over all pairs.  Particles j are split into kChunks
-// contiguous chunks; block (bi, c) tests 128 particles i against chunk c
+// chunks by j mod kChunks; block (bi, c) tests 128 particles i against chunk c
 // (tiled through shared memory) and writes the partial list of (i, c), so no
 // atomics or clearing are needed and the sub-step kernel's lane c reads
 // chunk c.  Returns at once unless a rebuild was requested in slot `rd`.
@@ -297,9 +297,9 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const float4 *shadow, int
     if (flags[rd] == 0u) return;
     __shared__ float4 sp[kTile];
     const int i = blockIdx.x * kTile + threadIdx.x;
-    const int chunk = blockIdx.y;
-    const int per = (c.n + kChunks - 1) / kChunks;
-    const int j0 = chunk * per, j1 = min(c.n, j0 + per);
+    const int chunk = blockIdx.y;  // particles j with j % kChunks == chunk (neighbours of a
+                                   // chain spread evenly over the 8 lanes that read them)
+    const int per = (c.n - chunk + kChunks - 1) / kChunks;
     CPos pi{};
     float4 raw = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < c.n) {
@@ -309,14 +309,14 @@ __global__ void __launch_bounds__(kTile) k_build_nlist(const float4 *shadow, int
     int cnt = 0;
     bool full = false;
     int *mine = nlist + ((size_t)i * kChunks + chunk) * kMaxNb;
-    for (int base = j0; base < j1; base += kTile) {
-        const int j = base + threadIdx.x;
-        if (j < j1) sp[threadIdx.x] = shadow[j];
+    for (int base = 0; base < per; base += kTile) {
+        const int t = base + threadIdx.x;
+        if (t < per) sp[threadIdx.x] = shadow[chunk + kChunks * t];
         __syncthreads();
-        const int lim = min(kTile, j1 - base);
+        const int lim = min(kTile, per - base);
         if (i < c.n) {
             for (int q = 0; q < lim; ++q) {
-                const int jj = base + q;
+                const int jj = chunk + kChunks * (base + q);
                 if (jj == i) continue;
                 float d[3];
                 separation(pi, unpack(sp[q]), c.g, d);
@@ -669,12 +669,10 @@ __device__ __forceinline__ void rebuild_own_list(const PersistArgs &a, int p, in
                                                  const float4 *sh)
 {
     const int n = a.c.n;
-    const int per = (n + kChunks - 1) / kChunks;
-    const int j0 = q * per, j1 = min(n, j0 + per);
     int *mine = a.nlist + ((size_t)p * kChunks + q) * kMaxNb;
     int cnt = 0;
     bool full = false;
-    for (int j = j0; j < j1; ++j) {
+    for (int j = q; j < n; j += kChunks) {  // the chunk k_build_nlist assigns to lane q
         if (j == p) continue;
         float d[3];
         separation(me, unpack(sh[j]), a.c.g, d);

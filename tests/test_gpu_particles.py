@@ -170,24 +170,26 @@ def test_fast_wca_particles_rebuild_lists(ora):
     """WCA particles moving ~0.5 sigma per call (more than half the Verlet
     skin) force list rebuilds inside and between calls; three calls in a row,
     each followed by an LB step, against the oracle's brute-force pairs."""
+    # heavy particles (m = 10) launched fast (|v| ~ 0.27) in a cold fluid: they
+    # keep moving ~0.3 sigma per call while WCA collisions stay integrable
     shape = (14, 14, 14)
     n = 600
     pos = inputs.random_walk_chains(n, 1, shape, min_dist=1.0, seed=31)  # no overlaps
-    kT = 1e-2
-    mom = inputs.maxwell_momenta(n, 1.0, kT, seed=32).astype(np.float32).astype(np.float64)
+    kT, m = 1e-4, 10.0
+    mom = inputs.maxwell_momenta(n, m, 0.25, seed=32).astype(np.float32).astype(np.float64)
     p = ora.make_params(shape, kT=kT, seed=4)
     pops = ora.equilibrium(p)
     md = ora.make_md(0, 0, eps=0.01, sigma=1.0, use_wca=True)
     lat = L.Lattice(shape, kT=kT, seed=4)
     lat.init_equilibrium()
     gpos, gmom = dev(pos), dev(mom, torch.float32)
-    parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
+    parts = L.particles(n, gpos, gmom, mass0=m, gamma0=2.0)
     opos, omom = pos.copy(), mom.copy()
     for t in range(3):
-        opos, omom, facc, _ = ora.couple(p, pops, opos, omom, 1.0, 2.0, dt=0.5, n_substeps=10, seed=9,
+        opos, omom, facc, _ = ora.couple(p, pops, opos, omom, m, 2.0, dt=0.1, n_substeps=10, seed=9,
                                          md_step0=10 * t, md=md)
         pops = ora.step(p, pops, facc.astype(np.float32).astype(np.float64), t)
-        cp = L.couple_params(n_substeps=10, dt=0.5, seed=9, md_step0=10 * t, use_wca=True, eps=0.01, sigma=1.0)
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=9, md_step0=10 * t, use_wca=True, eps=0.01, sigma=1.0)
         L.lb_couple_particles(lat.h, parts, cp)
         lat.step(1)
     assert lat.sync() == (L.LB_OK, 0)
