@@ -53,6 +53,8 @@ def _args():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched / adjoint / reduced-precision measurements")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--box", type=int, default=SHAPE[0],
+                    help="edge of the coupled box (smaller boxes for profiling runs only)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time lb_step alone (no particles) on --shape for each --kT and --dtype")
     ap.add_argument("--shape", default="256,256,256")
@@ -236,12 +238,13 @@ def run_ours(args):
         if dist:
             dist.barrier()
 
-    nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    shape = (args.box,) * 3
+    nodes = shape[0] * shape[1] * shape[2]
     npart = N_CHAINS * CHAIN_LEN
     with torch.cuda.stream(stream):
-        lat = L.Lattice(SHAPE, kT=KT, seed=rank, replica=rank, stream=stream)
+        lat = L.Lattice(shape, kT=KT, seed=rank, replica=rank, stream=stream)
         lat.init_equilibrium()
-        pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, SHAPE, seed=rank)
+        pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, shape, seed=rank)
         mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000 + rank)
         gpos = torch.as_tensor(pos0).to(dev)
         gmom = torch.as_tensor(mom0, dtype=torch.float32).to(dev)
@@ -253,6 +256,8 @@ def run_ours(args):
 
     def one_step(ev=None):
         cp.md_step0 = (NSUB * t_step[0]) & 0xffffffff
+        if ev is not None:
+            ev[2].record(stream)
         L.lb_couple_particles(lat.h, parts, cp)
         if ev is not None:
             ev[0].record(stream)
@@ -269,7 +274,7 @@ def run_ours(args):
     assert bits == 0, "device error word 0x%x during warm-up" % bits
 
     K = args.steps
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = L.lb_get_launch_count(lat.h)
     clocks = Clocks(local)
@@ -287,7 +292,8 @@ def run_ours(args):
     clk = clocks.stop()
     launches = L.lb_get_launch_count(lat.h) - launches0
     ms_total = t0.elapsed_time(t1)
-    sc_ms = [a.elapsed_time(b) for a, b in evs]
+    sc_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    couple_ms = sum(e[2].elapsed_time(e[0]) for e in evs) / len(evs)
     sc_avg = sum(sc_ms) / len(sc_ms)
     st, bits = lat.sync()
     assert bits == 0, "device error word 0x%x" % bits
@@ -345,6 +351,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_stream_collide",
                      "bytes_per_node": BYTES_PER_NODE, "ms_per_launch": sc_avg,
+                     "coupling_ms_per_step": couple_ms,
                      "peak_source": peak_src},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
