@@ -156,6 +156,130 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
     for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
 }
 
+// Two neighbouring nodes x0 = 2t, x0 + 1 per thread (even nx).  Both pull
+// their populations from the same rows of each plane, so one address per
+// plane serves both (the second is an immediate offset); planes with c_x = 0
+// and all stores move the pair as one 8-byte (FP32) or 4-byte (FP16 / BF16)
+// access.  Collision and noise are those of collide_node, node by node.
+template <int DT>
+struct Pair;
+template <>
+struct Pair<0> {
+    static __device__ __forceinline__ void load(const float *p, float inv, float &a, float &b)
+    {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        a = v.x;
+        b = v.y;
+    }
+    static __device__ __forceinline__ void store(float *p, float a, float b, float)
+    {
+        *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+    }
+};
+template <>
+struct Pair<1> {
+    static __device__ __forceinline__ void load(const __half *p, float inv, float &a, float &b)
+    {
+        const __half2 v = __ldg(reinterpret_cast<const __half2 *>(p));
+        a = __low2float(v) * inv;
+        b = __high2float(v) * inv;
+    }
+    static __device__ __forceinline__ void store(__half *p, float a, float b, float sc)
+    {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a * sc, b * sc);
+    }
+};
+template <>
+struct Pair<2> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16 *p, float inv, float &a, float &b)
+    {
+        const __nv_bfloat162 v = __ldg(reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = __low2float(v) * inv;
+        b = __high2float(v) * inv;
+    }
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float a, float b, float sc)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a * sc, b * sc);
+    }
+};
+
+template <int DT, bool NOISE, bool FIELD, bool WALLS>
+__global__ void __launch_bounds__(kBX) k_stream_collide2(const typename lbd::Store<DT>::T *__restrict__ src,
+                                                         typename lbd::Store<DT>::T *__restrict__ dst,
+                                                         const float *__restrict__ ffield,
+                                                         const float *__restrict__ facc, const StepArgs a)
+{
+    using S = lbd::Store<DT>;
+    using PR = Pair<DT>;
+    const int x0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    if (x0 >= a.nx) return;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z + a.z0;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int xm = (x0 == 0) ? nx - 1 : x0 - 1;       // source of node x0 for c_x = +1
+    const int xp = (x0 + 2 == nx) ? 0 : x0 + 2;       // source of node x0 + 1 for c_x = -1
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int yp = (y == ny - 1) ? 0 : y + 1;
+    int zm, zp;
+    if (WALLS) {
+        zm = z - 1;
+        zp = z + 1;
+    } else {
+        zm = (z == 0) ? nz - 1 : z - 1;
+        zp = (z == nz - 1) ? 0 : z + 1;
+    }
+    const uint32_t P = (uint32_t)a.pitch;
+    const uint32_t self = (uint32_t)((z * ny + y) * nx + x0);
+
+    float n0[19], n1[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+        const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+        bool bounce = false;
+        if (WALLS && lbd::cz(i) != 0) bounce = (sz == 0) || (sz == nz - 1);
+        if (bounce) {
+            PR::load(src + (uint32_t)lbd::opposite(i) * P + self, a.inv_scale, n0[i], n1[i]);
+        } else {
+            const uint32_t row = (uint32_t)i * P + (uint32_t)((sz * ny + sy) * nx);
+            if (lbd::cx(i) == 0) {
+                PR::load(src + row + x0, a.inv_scale, n0[i], n1[i]);
+            } else if (lbd::cx(i) == 1) {
+                n0[i] = S::load(src + row + xm, a.inv_scale);
+                n1[i] = S::load(src + row + x0, a.inv_scale);
+            } else {
+                n0[i] = S::load(src + row + x0 + 1, a.inv_scale);
+                n1[i] = S::load(src + row + xp, a.inv_scale);
+            }
+        }
+    }
+
+    float f0[3] = {a.fx, a.fy, a.fz}, f1[3] = {a.fx, a.fy, a.fz};
+    if (FIELD) {
+        if (ffield) {  // caller's field, component stride N
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                f0[d] += __ldg(ffield + d * a.nn + self);
+                f1[d] += __ldg(ffield + d * a.nn + self + 1);
+            }
+        }
+        if (facc) {  // library accumulator, component stride = plane pitch
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                float u, v;
+                Pair<0>::load(facc + d * (size_t)P + self, 1.0f, u, v);
+                f0[d] += u;
+                f1[d] += v;
+            }
+        }
+    }
+    float out0[19], out1[19];
+    collide_node<NOISE>(n0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
+    collide_node<NOISE>(n1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) PR::store(dst + (uint32_t)i * P + self, out0[i], out1[i], a.scale);
+}
+
 template <int DT>
 cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc)
 {
@@ -169,8 +293,16 @@ cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *
     const bool walls = h->p.walls != 0;
     const T *s = static_cast<const T *>(src);
     T *d = static_cast<T *>(dst);
-#define LBI_SC(NZ, FL, WL) \
-    k_stream_collide<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a)
+    // two nodes per thread when rows pair up and element indices fit 32 bits
+    const bool paired = (a.nx % 2 == 0) && (19.0 * (double)a.pitch < 4294967296.0);
+    if (paired) grid.x = (a.nx / 2 + kBX - 1) / kBX;
+#define LBI_SC(NZ, FL, WL)                                                                             \
+    do {                                                                                               \
+        if (paired)                                                                                    \
+            k_stream_collide2<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a); \
+        else                                                                                           \
+            k_stream_collide<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a);  \
+    } while (0)
     if (noise) {
         if (field) {
             if (walls) LBI_SC(true, true, true); else LBI_SC(true, true, false);
