@@ -160,6 +160,16 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(values, dist=None, device="cpu"):
+    """Element-wise maximum of a list of floats over all ranks (the slowest
+    rank's timings); the identity without a process group."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -327,10 +337,7 @@ def run_ours(args):
     d2h = h2d + L.LB_NSUMS * 8
 
     # max over ranks
-    vals = torch.tensor([ms_total, sc_avg, e2e_ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-    ms_total, sc_avg, e2e_ms = (float(v) for v in vals.cpu())
+    ms_total, sc_avg, e2e_ms, couple_ms = max_over_ranks([ms_total, sc_avg, e2e_ms, couple_ms], dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -483,10 +490,14 @@ def _forms(peak):
 def _profiled_traffic():
     """DRAM bytes per stream-collide launch from the committed ncu summary,
     if it was taken on the current kernel source."""
-    path = os.path.join(ROOT, "profiles", "stream_collide_traffic.json")
+    path = os.path.join(ROOT, "profiles", "stream_collide_traffic.txt")
     try:
+        d = {}
         with open(path) as f:
-            d = json.load(f)
+            for line in f:
+                key, sep, val = line.partition(":")
+                if sep and key.strip() in ("source_hash", "dram_bytes_per_launch"):
+                    d[key.strip()] = val.strip()
         from paper_0803_2826_gb300 import build as B
         if d.get("source_hash") != B.source_hash():
             return None
