@@ -203,10 +203,18 @@ typedef struct {
     uint32_t md_step0;   /* Philox step word of the first sub-step                   */
     int chain_len;       /* > 1: particles k*chain_len..(k+1)*chain_len-1 are a FENE chain */
     int use_wca;         /* purely repulsive LJ between all pairs                    */
-    int reserved;        /* must be 0                                                */
+    int flags;           /* 0, or LB_COUPLE_PER_SUBSTEP                              */
     double eps, sigma;   /* WCA parameters                                           */
     double k_fene, r0;   /* FENE parameters                                          */
 } lb_couple_params;
+
+/* lb_couple_params.flags: run one kernel launch per sub-step instead of one
+ * cooperative launch for the whole call (for callers that cannot guarantee
+ * that the cooperative grid becomes co-resident, e.g. when other work shares
+ * the GPU).  Results agree with the default path to FP32 rounding.  Without
+ * the flag, that path is also taken when the particles do not fit one
+ * co-resident grid. */
+#define LB_COUPLE_PER_SUBSTEP 0x1
 
 /* One LB step's worth of particle motion.  The fluid velocity
  * u = (sum n c + f_ext/2)/rho of the current state is held fixed; for each

@@ -243,6 +243,7 @@ lb_status lb_sync(lb_handle *h, uint32_t *bits)
     if (bits) *bits = v;
     if (v) {
         e = cudaMemsetAsync(h->d_err, 0, sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess && (v & LB_DERR_BARRIER)) e = reset_particle_barrier(h);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail("lb_sync", e);
         set_error("device error word 0x%x%s%s%s%s", v, (v & LB_DERR_FENE_BROKEN) ? " [FENE bond broken]" : "",

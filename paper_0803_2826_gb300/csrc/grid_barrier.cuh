@@ -1,12 +1,17 @@
 // grid_barrier.cuh -- bounded barrier over all blocks of a cooperative launch.
 //
-// bar[0] counts arrivals, bar[1] is the generation, bar[2] the abort flag.
-// The last block to arrive resets the count and advances the generation; the
-// others poll the generation at most `spin_limit` times (with a short sleep),
-// then set LB_DERR_BARRIER in *err and the abort flag and leave.  Every block
-// sees the abort flag after the barrier, so all of them return instead of
-// waiting on a block that will never arrive.  Returns false when the caller
-// must stop.
+// bar[0] is the arrival word, bar[2] the abort flag (bar[1] is unused).  On
+// each barrier block 0 adds 2^31 - (nblocks - 1) to bar[0] and every other
+// block adds 1: together exactly 2^31, and every partial sum stays below
+// 2^31, so the top bit of bar[0] flips at the last arrival and the low 31
+// bits return to zero.  A block waits until the top bit differs from the one
+// its own atomic returned: one atomic and the polling per barrier, no reset
+// and no generation word.  The poll gives up after `spin_limit` rounds (with
+// a short sleep each), sets LB_DERR_BARRIER in *err and the abort flag, which
+// the other blocks check while they wait, so that all of them return instead
+// of waiting on a block that will never arrive.  After a timeout the low bits
+// are no longer zero: the owner resets bar[] to zero before the next launch.
+// Returns false when the caller must stop.
 #pragma once
 
 #include "lbfluct.h"
@@ -18,27 +23,28 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *er
     __shared__ int stop;
     __syncthreads();
     if (threadIdx.x == 0) {
+        const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
+        const bool first = (blockIdx.x | blockIdx.y | blockIdx.z) == 0;
+        __threadfence();  // this block's writes before its arrival
+        const unsigned int old = atomicAdd(&bar[0], first ? 0x80000000u - (nb - 1u) : 1u);
         volatile unsigned int *vbar = bar;
-        const unsigned int gen = vbar[1];
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar[0], 1u) + 1u;
-        if (arrived == gridDim.x * gridDim.y * gridDim.z) {
-            bar[0] = 0u;
-            __threadfence();
-            atomicAdd(&bar[1], 1u);
-        } else {
-            unsigned int spins = 0;
-            while (vbar[1] == gen && vbar[2] == 0u) {
-                if (++spins > spin_limit) {
-                    atomicOr(err, LB_DERR_BARRIER);
-                    atomicExch(&bar[2], 1u);
-                    break;
-                }
-                __nanosleep(64);
+        unsigned int spins = 0;
+        int s = 0;
+        while (((vbar[0] ^ old) & 0x80000000u) == 0u) {
+            if (++spins > spin_limit) {
+                atomicOr(err, LB_DERR_BARRIER);
+                atomicExch(&bar[2], 1u);
+                s = 1;
+                break;
             }
+            if ((spins & 63u) == 0u && vbar[2] != 0u) {  // another block gave up
+                s = 1;
+                break;
+            }
+            __nanosleep(32);
         }
-        __threadfence();
-        stop = vbar[2] != 0u;
+        __threadfence();  // the other blocks' writes after it
+        stop = s;
     }
     __syncthreads();
     return !stop;

@@ -78,6 +78,7 @@ cudaError_t launch_moments(const lb_handle *h, const void *src, float *rho, floa
 lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
 lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out);
 cudaError_t clear_particle_forces(lb_handle *h);
+cudaError_t reset_particle_barrier(lb_handle *h);
 void destroy_particles(lb_handle *h);
 
 }  // namespace lbi

@@ -27,11 +27,12 @@
 
 namespace lbi {
 
-constexpr int kMaxNb = 48;          // Verlet-list capacity per particle and chunk
-constexpr int kChunks = 8;          // neighbour-list chunks = lanes per particle
+constexpr int kMaxNb = 64;          // Verlet-list capacity per particle
+constexpr int kChunks = 8;          // lanes per particle in the per-sub-step kernels
 constexpr float kSkin = 0.4f;       // Verlet skin in units of sigma
 constexpr int kPartThreads = 128;
 constexpr int kMaxCellDim = 1024;   // cells are packed in 10-bit fields
+constexpr int kFlagWords = 5;       // [0], [1]: per-sub-step kernels; [2..4]: persistent kernel
 
 struct Particles {
     int cap = 0;
@@ -39,16 +40,21 @@ struct Particles {
     int *records = nullptr;      // base node of each (sub-step, particle) stencil
     size_t rec_cap = 0;
     size_t n_records = 0;
-    int *nlist = nullptr;        // [cap][kChunks][kMaxNb]
-    int *ncount = nullptr;       // [cap][kChunks]
+    int *nlist = nullptr;        // [cap][kMaxNb], ascending
+    int *ncount = nullptr;       // [cap]
     float4 *ref = nullptr;       // [cap] shadow positions at the last build
-    unsigned int *flags = nullptr;  // two rebuild-request slots
+    unsigned int *flags = nullptr;  // rebuild requests (kFlagWords words)
     uint32_t sub_counter = 0;
     int nlist_n = -1;            // particle count the list was built for
     size_t rec_off = 0;          // offset of the live records in `records`
     int last_nsub = 0;           // sub-steps of the previous call
-    bool persistent = true;      // use the persistent kernel when it fits
     unsigned int *bar = nullptr; // grid barrier words of the persistent kernel
+    // cell list of the Verlet-list build: particles binned into cells of edge
+    // >= r_list, cells hashed into `nbuckets` linked-list buckets
+    int *head = nullptr;         // [nbuckets] first particle of a bucket, -1 = empty
+    int *next = nullptr;         // [cap] next particle in the same bucket
+    int *bucket_of = nullptr;    // [cap] bucket of each particle (to empty it again)
+    int nb_log2 = 0;             // log2 nbuckets
 };
 
 namespace {
@@ -68,6 +74,9 @@ struct CoupleArgs {
     uint32_t md_step;
     int last;              // last sub-step of this call
     uint32_t slot;         // rebuild slot written by this sub-step
+    int ncell[3];          // cell-list cells per axis (edge L / ncell >= r_list)
+    float cinv[3];         // ncell / L
+    int nb_log2;           // log2 of the bucket count
 };
 
 // ---- cell + offset positions -----------------------------------------------
@@ -161,7 +170,13 @@ __device__ __forceinline__ bool drift(CPos &q, float p[3], float h, const StepAr
             q.f[k] = 0.0f;
             q.c[k] += 1;
         }
-        if (!(k == 2 && walls)) q.c[k] = ((q.c[k] % L[k]) + L[k]) % L[k];
+        if (!(k == 2 && walls)) {
+            int v = q.c[k];
+            if (v < 0) v += L[k];
+            else if (v >= L[k]) v -= L[k];
+            if ((unsigned)v >= (unsigned)L[k]) v = ((v % L[k]) + L[k]) % L[k];  // boxes narrower than a step
+            q.c[k] = v;
+        }
     }
     if (walls) {
         const int hi = g.nz - 2;
@@ -283,72 +298,255 @@ __global__ void k_half_drift(const double *pos, float *mom, const float *mass, f
     mom[3 * p + 2] = pm[2];
 }
 
-// Verlet-list build over all pairs.  Particles j are split into kChunks
-// chunks by j mod kChunks; block (bi, c) tests 128 particles i against chunk c
-// (tiled through shared memory) and writes the partial list of (i, c), so no
-// atomics or clearing are needed and the sub-step kernel's lane c reads
-// chunk c.  Returns at once unless a rebuild was requested in slot `rd`.
-constexpr int kTile = 128;
+// Verlet-list build from a cell list.  The box is cut into ncell[k] cells per
+// axis of edge >= r_list, so every pair closer than r_list lies in the same or
+// adjacent cells (periodically adjacent, except across the walls); cells are
+// hashed into 2^nb_log2 buckets, each a linked list (head / next) filled with
+// atomicExch.  Particle p is served by 8 lanes that split the (up to 27)
+// cells around p and append every j within r_list to one shared-memory list;
+// lane 0 sorts it and drops duplicates (two cells may share a bucket): the
+// same list as a test of all pairs, in O(n) work.
+__device__ __forceinline__ void cell_of(const CPos &q, const CoupleArgs &c, int cc[3])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int v = (int)(((float)q.c[k] + q.f[k]) * c.cinv[k]);
+        cc[k] = min(max(v, 0), c.ncell[k] - 1);
+    }
+}
 
-__global__ void __launch_bounds__(kTile) k_build_nlist(const float4 *shadow, int *nlist, int *ncount, float4 *ref,
-                                                       const unsigned int *flags, unsigned int *err, CoupleArgs c,
-                                                       uint32_t rd)
+// Fibonacci hashing of the linear cell index.
+__device__ __forceinline__ int bucket_of_cell(int x, int y, int z, const CoupleArgs &c)
+{
+    const uint32_t lin = ((uint32_t)z * (uint32_t)c.ncell[1] + (uint32_t)y) * (uint32_t)c.ncell[0] + (uint32_t)x;
+    return (int)((lin * 2654435761u) >> (32 - c.nb_log2));
+}
+
+// Cells adjacent to cell v along one axis (itself included), each once.
+__device__ __forceinline__ int adjacent_cells(int v, int nc, bool wall, int out[3])
+{
+    if (wall) {
+        int m = 0;
+        if (v > 0) out[m++] = v - 1;
+        out[m++] = v;
+        if (v < nc - 1) out[m++] = v + 1;
+        return m;
+    }
+    if (nc < 3) {
+        out[0] = 0;
+        out[1] = 1;
+        return nc;
+    }
+    out[0] = v == 0 ? nc - 1 : v - 1;
+    out[1] = v;
+    out[2] = v == nc - 1 ? 0 : v + 1;
+    return 3;
+}
+
+// Put particle p (cell + offset q) into its bucket.
+__device__ __forceinline__ void bin_particle(int p, const CPos &q, const CoupleArgs &c, int *head, int *next,
+                                             int *bucket_of)
+{
+    int cc[3];
+    cell_of(q, c, cc);
+    const int b = bucket_of_cell(cc[0], cc[1], cc[2], c);
+    bucket_of[p] = b;
+    next[p] = atomicExch(head + b, p);
+}
+
+// Binning of the shadows a build will read (the multi-kernel path; the
+// persistent path bins in k_shadow_from_pos).
+__global__ void k_bin(const float4 *shadow, int *head, int *next, int *bucket_of, const unsigned int *flags,
+                      CoupleArgs c, uint32_t rd)
 {
     if (flags[rd] == 0u) return;
-    __shared__ float4 sp[kTile];
-    const int i = blockIdx.x * kTile + threadIdx.x;
-    const int chunk = blockIdx.y;  // particles j with j % kChunks == chunk (neighbours of a
-                                   // chain spread evenly over the 8 lanes that read them)
-    const int per = (c.n - chunk + kChunks - 1) / kChunks;
-    CPos pi{};
-    float4 raw = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < c.n) {
-        raw = shadow[i];
-        pi = unpack(raw);
-    }
-    int cnt = 0;
-    bool full = false;
-    int *mine = nlist + ((size_t)i * kChunks + chunk) * kMaxNb;
-    for (int base = 0; base < per; base += kTile) {
-        const int t = base + threadIdx.x;
-        if (t < per) sp[threadIdx.x] = shadow[chunk + kChunks * t];
-        __syncthreads();
-        const int lim = min(kTile, per - base);
-        if (i < c.n) {
-            for (int q = 0; q < lim; ++q) {
-                const int jj = chunk + kChunks * (base + q);
-                if (jj == i) continue;
-                float d[3];
-                separation(pi, unpack(sp[q]), c.g, d);
-                const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                if (r2 < c.rlist2) {
-                    if (cnt < kMaxNb) mine[cnt] = jj;
-                    else full = true;
-                    ++cnt;
-                }
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.n) return;
+    bin_particle(p, unpack(shadow[p]), c, head, next, bucket_of);
+}
+
+// The buckets are emptied again by the kernel that consumes the lists (each
+// particle resets the head of its own bucket), so no clearing pass is needed.
+__device__ __forceinline__ void unbin_particle(int p, int *head, const int *bucket_of) { head[bucket_of[p]] = -1; }
+
+__global__ void __launch_bounds__(kPartThreads) k_build_nlist(const float4 *shadow, const int *head,
+                                                              const int *next, int *nlist, int *ncount, float4 *ref,
+                                                              const unsigned int *flags, unsigned int *err,
+                                                              CoupleArgs c, uint32_t rd)
+{
+    if (flags[rd] == 0u) return;
+    constexpr int kGroups = kPartThreads / kChunks;
+    __shared__ int lst[kMaxNb][kGroups];  // column per particle: conflict-free
+    __shared__ int fill[kGroups];
+    const int t = threadIdx.x, grp = t >> 3;
+    const int tid = blockIdx.x * blockDim.x + t;
+    const int p = tid >> 3, q = tid & 7;
+    if (p >= c.n) return;  // whole groups of eight leave together
+    const unsigned gmask = 0xFFu << (t & 24);
+    if (q == 0) fill[grp] = 0;
+    __syncwarp(gmask);
+    const float4 raw = shadow[p];
+    const CPos me = unpack(raw);
+    int cc[3], cx[3], cy[3], cz[3];
+    cell_of(me, c, cc);
+    const int mx = adjacent_cells(cc[0], c.ncell[0], false, cx);
+    const int my = adjacent_cells(cc[1], c.ncell[1], false, cy);
+    const int mz = adjacent_cells(cc[2], c.ncell[2], c.g.z0 > 0, cz);
+    bool full = false, broken = false;
+    for (int k = q; k < mx * my * mz; k += kChunks) {
+        const int ix = k % mx, iy = (k / mx) % my, iz = k / (mx * my);
+        int hops = 0;
+        for (int j = head[bucket_of_cell(cx[ix], cy[iy], cz[iz], c)]; j >= 0; j = next[j]) {
+            if (j >= c.n || ++hops > c.n) {  // cannot happen for a consistent list
+                broken = true;
+                break;
             }
+            if (j == p) continue;
+            float d[3];
+            separation(me, unpack(shadow[j]), c.g, d);
+            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= c.rlist2) continue;
+            const int slot = atomicAdd(&fill[grp], 1);
+            if (slot < kMaxNb) lst[slot][grp] = j;
+            else full = true;
         }
-        __syncthreads();
     }
-    if (i < c.n) {
-        ncount[(size_t)i * kChunks + chunk] = cnt < kMaxNb ? cnt : kMaxNb;
-        if (chunk == 0) ref[i] = raw;
-        if (full) atomicOr(err, LB_DERR_NLIST_FULL);
+    __syncwarp(gmask);
+    if (q == 0) {  // insertion sort, duplicates dropped
+        const int m = min(fill[grp], kMaxNb);
+        int cnt = 0;
+        for (int k = 0; k < m; ++k) {
+            const int j = lst[k][grp];
+            int at = cnt;
+            while (at > 0 && lst[at - 1][grp] > j) {
+                lst[at][grp] = lst[at - 1][grp];
+                --at;
+            }
+            if (at > 0 && lst[at - 1][grp] == j) {  // duplicate: undo the shift
+                for (int r = at; r < cnt; ++r) lst[r][grp] = lst[r + 1][grp];
+                continue;
+            }
+            lst[at][grp] = j;
+            ++cnt;
+        }
+        fill[grp] = cnt;
+        ncount[p] = cnt;
+        ref[p] = raw;
+    }
+    __syncwarp(gmask);
+    const int cnt = fill[grp];
+    int *mine = nlist + (size_t)p * kMaxNb;
+    for (int k = q; k < cnt; k += kChunks) mine[k] = lst[k][grp];
+    if (full || broken) atomicOr(err, LB_DERR_NLIST_FULL);
+}
+
+// The same list for one particle, built by one thread (the persistent
+// kernel's rebuild inside a call), sorted in place in `mine`.
+__device__ int build_own_list(int p, const CPos &me, const float4 *shadow, const int *head, const int *next,
+                              const CoupleArgs &c, int *mine, unsigned int *err)
+{
+    int cc[3], cx[3], cy[3], cz[3];
+    cell_of(me, c, cc);
+    const int mx = adjacent_cells(cc[0], c.ncell[0], false, cx);
+    const int my = adjacent_cells(cc[1], c.ncell[1], false, cy);
+    const int mz = adjacent_cells(cc[2], c.ncell[2], c.g.z0 > 0, cz);
+    int cnt = 0;
+    bool full = false, broken = false;
+    for (int k = 0; k < mx * my * mz; ++k) {
+        const int ix = k % mx, iy = (k / mx) % my, iz = k / (mx * my);
+        int hops = 0;
+        for (int j = head[bucket_of_cell(cx[ix], cy[iy], cz[iz], c)]; j >= 0; j = next[j]) {
+            if (j >= c.n || ++hops > c.n) {
+                broken = true;
+                break;
+            }
+            if (j == p) continue;
+            float d[3];
+            separation(me, unpack(shadow[j]), c.g, d);
+            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] >= c.rlist2) continue;
+            int at = cnt;
+            while (at > 0 && mine[at - 1] > j) --at;
+            if (at > 0 && mine[at - 1] == j) continue;
+            if (cnt == kMaxNb) {
+                full = true;
+                continue;
+            }
+            for (int r = cnt; r > at; --r) mine[r] = mine[r - 1];
+            mine[at] = j;
+            ++cnt;
+        }
+    }
+    if (full || broken) atomicOr(err, LB_DERR_NLIST_FULL);
+    return cnt;
+}
+
+// WCA force of b on a (Eq. (ulennardjones), cut and shifted at 2^(1/6) sigma),
+// added to F.
+// `use` false adds nothing; the arithmetic has no branch, so that several
+// pairs can be in flight at once.
+__device__ __forceinline__ void wca_add(const CPos &a, const CPos &b, const CoupleArgs &c, float F[3],
+                                        bool use = true)
+{
+    float d[3];
+    separation(a, b, c.g, d);
+    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const float ir2 = __frcp_rn(r2);
+    const float sr2 = c.sigma2 * ir2;
+    const float sr6 = sr2 * sr2 * sr2;
+    const float mag = (use && r2 < c.rc2) ? 24.0f * c.eps * (2.0f * sr6 * sr6 - sr6) * ir2 : 0.0f;
+    F[0] = fmaf(mag, d[0], F[0]);
+    F[1] = fmaf(mag, d[1], F[1]);
+    F[2] = fmaf(mag, d[2], F[2]);
+}
+
+// FENE force of the bond to b on a (Eq. (ufene)), added to F; false (and no
+// force) for a bond stretched to R0 or beyond.
+__device__ __forceinline__ bool fene_add(const CPos &a, const CPos &b, const CoupleArgs &c, float F[3])
+{
+    float d[3];
+    separation(a, b, c.g, d);
+    const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
+    if (x >= 1.0f) return false;
+    const float mag = -c.k_fene / (1.0f - x);
+    F[0] += mag * d[0];
+    F[1] += mag * d[1];
+    F[2] += mag * d[2];
+    return true;
+}
+
+// The particle noise theta of Eq. (langevin_momentum_update): unit-variance
+// Gaussians (two Box-Muller pairs) or the three-point distribution
+// (-sqrt 3, 0, +sqrt 3 with probabilities 1/6, 2/3, 1/6) from one Philox
+// block, counters (p, step, 1 << 8, replica).
+__device__ __forceinline__ void particle_theta(uint32_t p, uint32_t step, const CoupleArgs &c, float th[3])
+{
+    const lbd::U4 wv = lbd::philox10(lbd::U4{p, step, (1u << 8) | 0u, c.g.replica}, c.pkey0, c.pkey1);
+    if (c.noise_kind == 1) {
+        const uint32_t ws[3] = {wv.x, wv.y, wv.z};
+        const float s3 = 1.7320508075688772f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const uint64_t kk = 2ull * (uint64_t)(ws[k] >> 9) + 1ull;  // uniform = kk / 2^24
+            th[k] = (6ull * kk < (1ull << 24)) ? -s3 : ((6ull * kk > 5ull * (1ull << 24)) ? s3 : 0.0f);
+        }
+    } else {
+        float g3;
+        lbd::box_muller(wv.x, wv.y, th[0], th[1]);
+        lbd::box_muller(wv.z, wv.w, th[2], g3);
     }
 }
 
 // One particle sub-step; eight lanes per particle.  Lane q gathers the fluid
 // velocity of stencil node q (19 loads) and spreads the impulse there; the
-// lanes split the neighbour list (lane q reads chunk q) and the two FENE
-// bonds, and shuffle-reduce u_p and F^c.  Every lane then holds the same
+// lanes split the neighbour list (lane q takes entries q, q + 8, ...) and the
+// two FENE bonds, and shuffle-reduce u_p and F^c.  Every lane then holds the same
 // u_p, F^c and theta and does the (cheap) momentum update; lane 0 writes.
 template <int DT>
 __global__ void __launch_bounds__(kPartThreads)
     k_substep(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
               const float4 *__restrict__ sh_in, float4 *__restrict__ sh_out, double *pos_out, float *mom,
               const float *mass, const float *gamma, const int *nlist, const int *ncount, const float4 *ref,
-              float *facc, int *records, unsigned int *flags, unsigned int *err, CoupleArgs c,
-              uint32_t clear_slot)
+              int *head, const int *bucket_of, float *facc, int *records, unsigned int *flags,
+              unsigned int *err, CoupleArgs c, uint32_t clear_slot)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && c.use_wca) flags[clear_slot] = 0u;  // the list build has run
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -357,46 +555,22 @@ __global__ void __launch_bounds__(kPartThreads)
     if (p >= c.n) return;  // whole groups of eight leave together
     const unsigned gmask = 0xFFu << (threadIdx.x & 24);
     const StepArgs &g = c.g;
+    if (c.use_wca && q == 0) unbin_particle(p, head, bucket_of);
     const CPos me = unpack(sh_in[p]);
     float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
 
     // conservative forces at the half-step positions, split over the lanes
     float F[3] = {0.f, 0.f, 0.f};
     if (c.use_wca) {
-        const size_t li = (size_t)p * kChunks + q;
-        const int nc = ncount[li];
-        const int *lst = nlist + li * kMaxNb;
-        for (int k = 0; k < nc; ++k) {
-            float d[3];
-            separation(me, unpack(sh_in[lst[k]]), g, d);
-            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-            if (r2 < c.rc2) {
-                const float sr2 = c.sigma2 / r2;
-                const float sr6 = sr2 * sr2 * sr2;
-                const float mag = 24.0f * c.eps * (2.0f * sr6 * sr6 - sr6) / r2;
-                F[0] += mag * d[0];
-                F[1] += mag * d[1];
-                F[2] += mag * d[2];
-            }
-        }
+        const int nc = ncount[p];
+        const int *lst = nlist + (size_t)p * kMaxNb;
+        for (int k = q; k < nc; k += kChunks) wca_add(me, unpack(sh_in[lst[k]]), c, F);
     }
     if (c.chain_len > 1 && q < 2) {
         const int k = p % c.chain_len;
         const int j = q == 0 ? p - 1 : p + 1;
         const bool bonded = (q == 0) ? (k > 0) : (k < c.chain_len - 1 && j < c.n);
-        if (bonded) {
-            float d[3];
-            separation(me, unpack(sh_in[j]), g, d);
-            const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
-            if (x >= 1.0f) {
-                atomicOr(err, LB_DERR_FENE_BROKEN);
-            } else {
-                const float mag = -c.k_fene / (1.0f - x);
-                F[0] += mag * d[0];
-                F[1] += mag * d[1];
-                F[2] += mag * d[2];
-            }
-        }
+        if (bonded && !fene_add(me, unpack(sh_in[j]), c, F)) atomicOr(err, LB_DERR_FENE_BROKEN);
     }
 
     // fluid velocity at the particle: lane q takes stencil node q
@@ -425,22 +599,7 @@ __global__ void __launch_bounds__(kPartThreads)
         C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
     }
     float th[3] = {0.f, 0.f, 0.f};
-    if (g.kT > 0.0f) {
-        const lbd::U4 wv = lbd::philox10(lbd::U4{(uint32_t)p, c.md_step, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
-        if (c.noise_kind == 1) {
-            const uint32_t ws[3] = {wv.x, wv.y, wv.z};
-            const float s3 = 1.7320508075688772f;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const uint64_t kk = 2ull * (uint64_t)(ws[k] >> 9) + 1ull;  // uniform = kk / 2^24
-                th[k] = (6ull * kk < (1ull << 24)) ? -s3 : ((6ull * kk > 5ull * (1ull << 24)) ? s3 : 0.0f);
-            }
-        } else {
-            float g3;
-            lbd::box_muller(wv.x, wv.y, th[0], th[1]);
-            lbd::box_muller(wv.z, wv.w, th[2], g3);
-        }
-    }
+    if (g.kT > 0.0f) particle_theta((uint32_t)p, c.md_step, c, th);
     float pn[3], J[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -543,6 +702,9 @@ void free_parts(Particles *P)
     cudaFree(P->ref);
     cudaFree(P->flags);
     cudaFree(P->bar);
+    cudaFree(P->head);
+    cudaFree(P->next);
+    cudaFree(P->bucket_of);
     delete P;
 }
 
@@ -565,15 +727,22 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
         cudaFree(P->nlist);
         cudaFree(P->ncount);
         cudaFree(P->ref);
+        cudaFree(P->next);
+        cudaFree(P->bucket_of);
         P->shadow[0] = P->shadow[1] = nullptr;
         P->nlist = nullptr;
         P->ncount = nullptr;
         P->ref = nullptr;
+        P->next = nullptr;
+        P->bucket_of = nullptr;
         cudaError_t e = cudaMalloc((void **)&P->shadow[0], (size_t)n * sizeof(float4));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->shadow[1], (size_t)n * sizeof(float4));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kChunks * kMaxNb * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * kChunks * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->nlist, (size_t)n * kMaxNb * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->ncount, (size_t)n * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->ref, (size_t)n * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->next, (size_t)n * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->bucket_of, (size_t)n * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->bucket_of, 0, (size_t)n * sizeof(int), h->stream);
         if (e != cudaSuccess) {
             P->cap = 0;
             set_error("lb_couple_particles: particle buffer allocation failed (%s)", cudaGetErrorString(e));
@@ -582,12 +751,30 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
         P->cap = n;
         P->nlist_n = -1;
     }
+    {
+        // at least 2n buckets (a power of two): few cells share one
+        int lg = 10;
+        while ((1 << lg) < 2 * n && lg < 30) ++lg;
+        if (lg > P->nb_log2) {
+            cudaFree(P->head);
+            P->head = nullptr;
+            P->nb_log2 = 0;
+            cudaError_t e = cudaMalloc((void **)&P->head, ((size_t)1 << lg) * sizeof(int));
+            if (e != cudaSuccess) {
+                set_error("lb_couple_particles: cell-list allocation failed (%s)", cudaGetErrorString(e));
+                return LB_ENOMEM;
+            }
+            P->nb_log2 = lg;
+            e = cudaMemsetAsync(P->head, 0xff, ((size_t)1 << lg) * sizeof(int), h->stream);  // all empty
+            if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+        }
+    }
     if (!P->flags) {
-        // [0], [1]: rebuild slots of the multi-kernel path; [2], [3]: build
-        // request and rebuild epoch of the persistent path
-        cudaError_t e = cudaMalloc((void **)&P->flags, 4 * sizeof(unsigned int));
+        // [0], [1]: rebuild slots of the multi-kernel path; [2]: build request
+        // and [3], [4]: rebuild epochs (by sub-step parity) of the persistent path
+        cudaError_t e = cudaMalloc((void **)&P->flags, kFlagWords * sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMalloc((void **)&P->bar, 3 * sizeof(unsigned int));
-        if (e == cudaSuccess) e = cudaMemsetAsync(P->flags, 0, 4 * sizeof(unsigned int), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->flags, 0, kFlagWords * sizeof(unsigned int), h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(P->bar, 0, 3 * sizeof(unsigned int), h->stream);
         if (e != cudaSuccess) {
             set_error("lb_couple_particles: flag allocation failed");
@@ -620,15 +807,24 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
 }
 
 // ---------------------------------------------------------------------------
-// Persistent variant: one cooperative launch runs all sub-steps of a call.
-// Each group of 8 lanes owns one particle for the whole call (position,
-// momentum and the fluid velocity of its 8 stencil nodes stay in registers;
-// the velocities are re-gathered only when the particle changes cell).  Sub-
-// steps are separated by the bounded grid barrier.  The Verlet list is built
-// by k_build_nlist before the launch when the previous call asked for it; if a
-// particle still moves more than half the skin during the call, every group
-// rebuilds its own list in place (a slower scan, no barrier needed).
+// Persistent variant: one cooperative launch runs all sub-steps of a call,
+// one thread per particle, so a warp advances 32 particles with a single
+// instruction stream.  For the cell a particle is in, its thread keeps the
+// fluid velocity of the 8 stencil nodes (re-gathered only when the particle
+// changes cell, by the whole warp: four particles at a time, one node per
+// lane) and the impulses spread to those nodes, summed over the sub-steps
+// spent in the cell and added to the accumulator when the particle leaves
+// the cell or the call ends (the accumulator is read only by the next
+// lb_step).  The first Verlet neighbours stay in registers.  Sub-steps are
+// separated by the bounded grid barrier.  The list comes from k_build_nlist
+// before the launch when the previous call asked for it; if a particle moves
+// more than half the skin during the call, every thread re-bins its particle
+// and rebuilds its list from the cell list at the next sub-step.
 // ---------------------------------------------------------------------------
+constexpr int kPThreads = 128;   // particles per block of the persistent kernel
+constexpr int kNbReg = 16;       // Verlet neighbours held in registers
+constexpr unsigned kFullMask = 0xffffffffu;
+
 struct PersistArgs {
     CoupleArgs c;
     int nsub;
@@ -640,21 +836,23 @@ struct PersistArgs {
     float4 *sh[2];
     int *nlist, *ncount;
     float4 *ref;
+    int *head, *next, *bucket_of;  // cell list; every bucket is empty again when the kernel ends
     float *facc;
     int *records;            // this call: [nsub][n]
     const int *stale;        // previous call's records to clear: [nstale_sub][n], or NULL
     int nstale_sub;
-    unsigned int *flags;     // [0] build before the next call, [1] rebuild epoch request
+    unsigned int *flags;     // [0] build before the next call, [1 + (s & 1)] rebuild epoch of sub-step s
     uint32_t epoch0;         // epoch of this call's first sub-step
     unsigned int *bar;
     unsigned int *err;
     unsigned int spin_limit;
 };
 
-// Shadow positions from the caller's double positions, when a list build is
-// requested (the positions may have been changed between calls).
-__global__ void k_shadow_from_pos(const double *pos, float4 *shadow, const unsigned int *flag, unsigned int *err,
-                                  CoupleArgs c)
+// Shadow positions from the caller's double positions, binned into the cell
+// list, when a list build is requested (the positions may have been changed
+// between calls).
+__global__ void k_shadow_from_pos(const double *pos, float4 *shadow, int *head, int *next, int *bucket_of,
+                                  const unsigned int *flag, unsigned int *err, CoupleArgs c)
 {
     if (*flag == 0u) return;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -663,60 +861,160 @@ __global__ void k_shadow_from_pos(const double *pos, float4 *shadow, const unsig
     CPos q;
     if (!split(r, c.g, q)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
     shadow[p] = pack(q);
+    bin_particle(p, q, c, head, next, bucket_of);
 }
 
-__device__ __forceinline__ void rebuild_own_list(const PersistArgs &a, int p, int q, const CPos &me,
-                                                 const float4 *sh)
+// Fluid velocity u of the 8 stencil nodes of cell `cell` into uc, for every
+// lane with `need`; the whole warp must call this together.  Each round takes
+// up to four such lanes: lane 8 k + q gathers node q of the k-th one and the
+// owners collect their 24 values by shuffles.
+template <int DT>
+__device__ __forceinline__ void warp_gather(bool need, const int cell[3], const typename lbd::Store<DT>::T *src,
+                                            const float *ffield, const StepArgs &g, float uc[8][3])
 {
-    const int n = a.c.n;
-    int *mine = a.nlist + ((size_t)p * kChunks + q) * kMaxNb;
-    int cnt = 0;
-    bool full = false;
-    for (int j = q; j < n; j += kChunks) {  // the chunk k_build_nlist assigns to lane q
-        if (j == p) continue;
-        float d[3];
-        separation(me, unpack(sh[j]), a.c.g, d);
-        if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < a.c.rlist2) {
-            if (cnt < kMaxNb) mine[cnt] = j;
-            else full = true;
-            ++cnt;
+    const int lane = threadIdx.x & 31;
+    unsigned m = __ballot_sync(kFullMask, need);
+    while (m) {
+        int o[4] = {-1, -1, -1, -1};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (m) {
+                o[k] = __ffs(m) - 1;
+                m &= m - 1;
+            }
+        }
+        const int slot = lane >> 3, q = lane & 7;
+        const int owner = slot == 0 ? o[0] : (slot == 1 ? o[1] : (slot == 2 ? o[2] : o[3]));
+        CPos nc{};
+        nc.c[0] = __shfl_sync(kFullMask, cell[0], owner < 0 ? 0 : owner);
+        nc.c[1] = __shfl_sync(kFullMask, cell[1], owner < 0 ? 0 : owner);
+        nc.c[2] = __shfl_sync(kFullMask, cell[2], owner < 0 ? 0 : owner);
+        float u[3] = {0.f, 0.f, 0.f};
+        if (owner >= 0) {
+            int x, y, z;
+            (void)stencil_node(nc, q, g, x, y, z);
+            node_velocity<DT>(src, ffield, x, y, z, g, u);
+        }
+        const int mine = lane == o[0] ? 0 : (lane == o[1] ? 1 : (lane == o[2] ? 2 : (lane == o[3] ? 3 : -1)));
+        const int base = (mine < 0 ? 0 : mine) << 3;
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float v = __shfl_sync(kFullMask, u[k], base | qq);
+                if (mine >= 0) uc[qq][k] = v;
+            }
         }
     }
-    a.ncount[(size_t)p * kChunks + q] = cnt < kMaxNb ? cnt : kMaxNb;
-    if (full) atomicOr(a.err, LB_DERR_NLIST_FULL);
-    if (q == 0) a.ref[p] = pack(me);
+}
+
+// The same for every lane of the warp at once (the start of a call): round r
+// serves lanes 4 r .. 4 r + 3, and kRounds rounds keep their loads in flight
+// together.
+template <int DT>
+__device__ __forceinline__ void warp_gather_all(bool active, const int cell[3],
+                                                const typename lbd::Store<DT>::T *src, const float *ffield,
+                                                const StepArgs &g, float uc[8][3])
+{
+    constexpr int kRounds = 4;
+    const int lane = threadIdx.x & 31, slot = lane >> 3, q = lane & 7;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 8; r0 += kRounds) {
+        float u[kRounds][3];
+#pragma unroll
+        for (int i = 0; i < kRounds; ++i) {
+            const int owner = 4 * (r0 + i) + slot;
+            const int on = __shfl_sync(kFullMask, (int)active, owner);
+            CPos nc{};
+            nc.c[0] = __shfl_sync(kFullMask, cell[0], owner);
+            nc.c[1] = __shfl_sync(kFullMask, cell[1], owner);
+            nc.c[2] = __shfl_sync(kFullMask, cell[2], owner);
+            u[i][0] = u[i][1] = u[i][2] = 0.0f;
+            if (on) {
+                int x, y, z;
+                (void)stencil_node(nc, q, g, x, y, z);
+                node_velocity<DT>(src, ffield, x, y, z, g, u[i]);
+            }
+        }
+        const int from = (lane & 3) << 3;  // the slot that served this lane
+#pragma unroll
+        for (int i = 0; i < kRounds; ++i) {
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float v = __shfl_sync(kFullMask, u[i][k], from | qq);
+                    if ((lane >> 2) == r0 + i) uc[qq][k] = v;
+                }
+            }
+        }
+    }
+}
+
+// Add the impulse sums of the 8 stencil nodes of `cell` to the accumulator
+// and zero them.
+__device__ __forceinline__ void flush_impulses(const int cell[3], float acc[8][3], float *facc, const StepArgs &g)
+{
+    CPos cq{};
+    cq.c[0] = cell[0];
+    cq.c[1] = cell[1];
+    cq.c[2] = cell[2];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        int x, y, z;
+        (void)stencil_node(cq, q, g, x, y, z);
+        const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+        atomicAdd(facc + node, acc[q][0]);
+        atomicAdd(facc + g.pitch + node, acc[q][1]);
+        atomicAdd(facc + 2 * g.pitch + node, acc[q][2]);
+        acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
+    }
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kPartThreads, 8) k_couple_persistent(PersistArgs a)
+__global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
 {
-    using S = lbd::Store<DT>;
+    using T = typename lbd::Store<DT>::T;
     const CoupleArgs &c = a.c;
     const StepArgs &g = c.g;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int p = tid >> 3, q = tid & 7;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < c.n;
-    const unsigned gmask = 0xFFu << (threadIdx.x & 24);
-    const typename S::T *src = static_cast<const typename S::T *>(a.src);
+    const T *src = static_cast<const T *>(a.src);
     if (c.use_wca && blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0u;  // the pre-launch build has run
 
     // phase 0: clear the previous call's impulses, first half drift
-    CPos me{};
+    CPos me{}, refp{};
     float pm[3] = {0.f, 0.f, 0.f};
     float m = 1.f, G = 1.f, C1 = c.C1, C2 = c.C2, C3 = c.C3;
+    // neighbour indices; unused slots (and the bonds of unbonded ends) point
+    // at the particle itself (inactive lanes: particle 0), so that every load
+    // of a sub-step is unconditional
+    const int self = active ? p : 0;
+    int nnb = 0;
+    int nb[kNbReg];
+#pragma unroll
+    for (int k = 0; k < kNbReg; ++k) nb[k] = self;
+    bool bond_lo = false, bond_hi = false;
     if (active) {
+        if (c.use_wca) unbin_particle(p, a.head, a.bucket_of);
+        int prev = -1;
         for (int s = 0; s < a.nstale_sub; ++s) {
             const int base = a.stale[(size_t)s * c.n + p];
+            if (base == prev) continue;  // same cell as the sub-step before
+            prev = base;
             CPos bq{};
             bq.c[0] = base % g.nx;
             bq.c[1] = (base / g.nx) % g.ny;
             bq.c[2] = base / (g.nx * g.ny);
-            int x, y, z;
-            (void)stencil_node(bq, q, g, x, y, z);
-            const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
-            a.facc[node] = 0.0f;
-            a.facc[g.pitch + node] = 0.0f;
-            a.facc[2 * g.pitch + node] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int x, y, z;
+                (void)stencil_node(bq, q, g, x, y, z);
+                const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+                a.facc[node] = 0.0f;
+                a.facc[g.pitch + node] = 0.0f;
+                a.facc[2 * g.pitch + node] = 0.0f;
+            }
         }
         m = a.mass ? a.mass[p] : c.mass0;
         G = a.gamma ? a.gamma[p] : c.gamma0;
@@ -734,94 +1032,112 @@ __global__ void __launch_bounds__(kPartThreads, 8) k_couple_persistent(PersistAr
 #pragma unroll
         for (int k = 0; k < 3; ++k) r[k] += h * (double)pm[k];
         confine_d(r, pm, g);
-        if (!split(r, g, me) && q == 0) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
-        if (q == 0) a.sh[0][p] = pack(me);
+        if (!split(r, g, me)) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+        a.sh[0][p] = pack(me);
+        if (c.use_wca) {
+            nnb = a.ncount[p];
+            const int *lst = a.nlist + (size_t)p * kMaxNb;
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < nnb) nb[k] = lst[k];
+            refp = unpack(a.ref[p]);
+        }
+        if (c.chain_len > 1) {
+            const int k = p % c.chain_len;
+            bond_lo = k > 0;
+            bond_hi = k < c.chain_len - 1 && p + 1 < c.n;
+        }
     }
+    const int jlo = bond_lo ? p - 1 : self, jhi = bond_hi ? p + 1 : self;
+    int kmax = __reduce_max_sync(kFullMask, min(nnb, kNbReg));  // register slots any lane of the warp uses
+    // fluid velocity at the 8 nodes of the cell ccell, and the impulse sums there
+    float uc[8][3], acc[8][3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) uc[q][0] = uc[q][1] = uc[q][2] = acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
+    int ccell[3] = {me.c[0], me.c[1], me.c[2]};
+    warp_gather_all<DT>(active, ccell, src, a.ffield, g, uc);
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
 
-    int cache_cell = -1;
-    float uc[3] = {0.f, 0.f, 0.f};
+    bool binned = false;
     const float h = 0.5f * c.dt / m;
     for (int s = 0; s < a.nsub; ++s) {
         const float4 *shin = a.sh[s & 1];
         float4 *shout = a.sh[(s + 1) & 1];
-        if (active) {
-            if (c.use_wca && ((volatile unsigned int *)a.flags)[1] == a.epoch0 + (uint32_t)s)
-                rebuild_own_list(a, p, q, me, shin);
-
-            float F[3] = {0.f, 0.f, 0.f};
-            if (c.use_wca) {
-                const size_t li = (size_t)p * kChunks + q;
-                const int nc = a.ncount[li];
-                const int *lst = a.nlist + li * kMaxNb;
-                for (int k = 0; k < nc; ++k) {
-                    float d[3];
-                    separation(me, unpack(shin[lst[k]]), g, d);
-                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (r2 < c.rc2) {
-                        const float sr2 = c.sigma2 / r2;
-                        const float sr6 = sr2 * sr2 * sr2;
-                        const float mag = 24.0f * c.eps * (2.0f * sr6 * sr6 - sr6) / r2;
-                        F[0] += mag * d[0];
-                        F[1] += mag * d[1];
-                        F[2] += mag * d[2];
-                    }
-                }
-            }
-            if (c.chain_len > 1 && q < 2) {
-                const int k = p % c.chain_len;
-                const int j = q == 0 ? p - 1 : p + 1;
-                const bool bonded = (q == 0) ? (k > 0) : (k < c.chain_len - 1 && j < c.n);
-                if (bonded) {
-                    float d[3];
-                    separation(me, unpack(shin[j]), g, d);
-                    const float x = (d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) * c.inv_r02;
-                    if (x >= 1.0f) {
-                        atomicOr(a.err, LB_DERR_FENE_BROKEN);
-                    } else {
-                        const float mag = -c.k_fene / (1.0f - x);
-                        F[0] += mag * d[0];
-                        F[1] += mag * d[1];
-                        F[2] += mag * d[2];
-                    }
-                }
-            }
-
-            // fluid velocity: lane q caches node q of the current cell
+        // neighbour positions and the rebuild flag (written before the last
+        // barrier; L1 is bypassed), then the work that needs only this
+        // particle's own state (its noise and stencil weights) while they load
+        float4 v[kNbReg];
+#pragma unroll
+        for (int k = 0; k < kNbReg; ++k)
+            if (k < kmax) v[k] = __ldcg(shin + nb[k]);
+        const float4 vlo = __ldcg(shin + jlo), vhi = __ldcg(shin + jhi);
+        const unsigned int req = c.use_wca ? __ldcg(a.flags + 1 + (s & 1)) : 0u;
+        float th[3] = {0.f, 0.f, 0.f};
+        if (g.kT > 0.0f) particle_theta((uint32_t)p, c.md_step + (uint32_t)s, c, th);
+        float w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
             int x, y, z;
-            const float w = stencil_node(me, q, g, x, y, z);
-            const int cell = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
-            if (cell != cache_cell) {
-                node_velocity<DT>(src, a.ffield, x, y, z, g, uc);
-                cache_cell = cell;
-            }
-            float up[3] = {w * uc[0], w * uc[1], w * uc[2]};
-#pragma unroll
-            for (int o = 1; o < 8; o <<= 1) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    up[k] += __shfl_xor_sync(gmask, up[k], o);
-                    F[k] += __shfl_xor_sync(gmask, F[k], o);
-                }
-            }
+            w[q] = stencil_node(me, q, g, x, y, z);
+        }
 
-            float th[3] = {0.f, 0.f, 0.f};
-            if (g.kT > 0.0f) {
-                const lbd::U4 wv = lbd::philox10(
-                    lbd::U4{(uint32_t)p, c.md_step + (uint32_t)s, (1u << 8) | 0u, g.replica}, c.pkey0, c.pkey1);
-                if (c.noise_kind == 1) {
-                    const uint32_t ws[3] = {wv.x, wv.y, wv.z};
-                    const float s3 = 1.7320508075688772f;
+        if (c.use_wca && req == a.epoch0 + (uint32_t)s) {
+            // a particle moved more than half the skin: re-bin all, rebuild every list
+            if (binned) {
+                if (active) unbin_particle(p, a.head, a.bucket_of);
+                if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+            }
+            if (active) bin_particle(p, me, c, a.head, a.next, a.bucket_of);
+            if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+            binned = true;
+            if (active) {
+                int *mine = a.nlist + (size_t)p * kMaxNb;
+                nnb = build_own_list(p, me, shin, a.head, a.next, c, mine, a.err);
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const uint64_t kk = 2ull * (uint64_t)(ws[k] >> 9) + 1ull;
-                        th[k] = (6ull * kk < (1ull << 24)) ? -s3 : ((6ull * kk > 5ull * (1ull << 24)) ? s3 : 0.0f);
-                    }
-                } else {
-                    float g3;
-                    lbd::box_muller(wv.x, wv.y, th[0], th[1]);
-                    lbd::box_muller(wv.z, wv.w, th[2], g3);
-                }
+                for (int k = 0; k < kNbReg; ++k) nb[k] = k < nnb ? mine[k] : self;
+                a.ncount[p] = nnb;
+                a.ref[p] = pack(me);
+                refp = me;
+            }
+            kmax = __reduce_max_sync(kFullMask, min(nnb, kNbReg));
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < kmax) v[k] = __ldcg(shin + nb[k]);
+        }
+
+        // conservative forces at the half-step positions
+        float F[3] = {0.f, 0.f, 0.f};
+        if (c.use_wca) {
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < kmax) wca_add(me, unpack(v[k]), c, F, k < nnb);
+            for (int k = kNbReg; k < nnb; ++k) wca_add(me, unpack(__ldcg(shin + a.nlist[(size_t)p * kMaxNb + k])), c, F);
+        }
+        if (c.chain_len > 1) {
+            if (bond_lo && !fene_add(me, unpack(vlo), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
+            if (bond_hi && !fene_add(me, unpack(vhi), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
+        }
+
+        // fluid velocity: particles that changed cell hand in their impulse
+        // sums and the warp gathers their new cells
+        const bool moved = active && (me.c[0] != ccell[0] || me.c[1] != ccell[1] || me.c[2] != ccell[2]);
+        if (__any_sync(kFullMask, moved)) {
+            if (moved) {
+                flush_impulses(ccell, acc, a.facc, g);
+                ccell[0] = me.c[0];
+                ccell[1] = me.c[1];
+                ccell[2] = me.c[2];
+            }
+            warp_gather<DT>(moved, ccell, src, a.ffield, g, uc);
+        }
+
+        if (active) {
+            float up[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                up[0] = fmaf(w[q], uc[q][0], up[0]);
+                up[1] = fmaf(w[q], uc[q][1], up[1]);
+                up[2] = fmaf(w[q], uc[q][2], up[2]);
             }
             float pn[3], J[3];
 #pragma unroll
@@ -829,45 +1145,45 @@ __global__ void __launch_bounds__(kPartThreads, 8) k_couple_persistent(PersistAr
                 pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
                 J[k] = pn[k] - pm[k] - C2 * F[k];
             }
-            {
-                const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
-                atomicAdd(a.facc + node, -J[0] * w);
-                atomicAdd(a.facc + g.pitch + node, -J[1] * w);
-                atomicAdd(a.facc + 2 * g.pitch + node, -J[2] * w);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                acc[q][0] = fmaf(-J[0], w[q], acc[q][0]);
+                acc[q][1] = fmaf(-J[1], w[q], acc[q][1]);
+                acc[q][2] = fmaf(-J[2], w[q], acc[q][2]);
             }
-            if (q == 0) a.records[(size_t)s * c.n + p] = cell;
+            a.records[(size_t)s * c.n + p] = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
 
-            // drift (every lane computes the same new position)
+            // second half drift of this sub-step, then the first of the next one
             const bool last = (s == a.nsub - 1);
             bool ok = drift(me, pn, h, g);
             if (last) {
-                if (q == 0) {
-                    a.pos[3 * p] = join1(me.c[0], me.f[0]);
-                    a.pos[3 * p + 1] = join1(me.c[1], me.f[1]);
-                    a.pos[3 * p + 2] = join1(me.c[2], me.f[2]);
-                    a.mom[3 * p] = pn[0];
-                    a.mom[3 * p + 1] = pn[1];
-                    a.mom[3 * p + 2] = pn[2];
-                }
+                a.pos[3 * p] = join1(me.c[0], me.f[0]);
+                a.pos[3 * p + 1] = join1(me.c[1], me.f[1]);
+                a.pos[3 * p + 2] = join1(me.c[2], me.f[2]);
+                a.mom[3 * p] = pn[0];
+                a.mom[3 * p + 1] = pn[1];
+                a.mom[3 * p + 2] = pn[2];
             } else {
                 ok = drift(me, pn, h, g) && ok;
             }
-            if (!ok && q == 0) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+            if (!ok) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
             pm[0] = pn[0];
             pm[1] = pn[1];
             pm[2] = pn[2];
-            if (q == 0) {
-                shout[p] = pack(me);
-                if (c.use_wca) {
-                    float d[3];
-                    separation(me, unpack(a.ref[p]), g, d);
-                    const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    if (!last && d2 > c.half_skin2) atomicMax(&a.flags[1], a.epoch0 + (uint32_t)s + 1u);
-                    if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
-                }
+            shout[p] = pack(me);
+            if (c.use_wca) {
+                float d[3];
+                separation(me, refp, g, d);
+                const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!last && d2 > c.half_skin2) atomicMax(&a.flags[1 + ((s + 1) & 1)], a.epoch0 + (uint32_t)s + 1u);
+                if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
             }
         }
         if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+    }
+    if (active) {
+        flush_impulses(ccell, acc, a.facc, g);
+        if (binned) unbin_particle(p, a.head, a.bucket_of);
     }
 }
 
@@ -905,20 +1221,30 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     c.last = 0;
     c.md_step = cp->md_step0;
     c.slot = 0;
+    {
+        // cells of edge >= r_list (with a margin for the FP32 binning)
+        const int L[3] = {h->p.nx, h->p.ny, h->p.nz};
+        for (int k = 0; k < 3; ++k) {
+            c.ncell[k] = std::max(1, (int)((double)L[k] / (1.001 * rl)));
+            c.cinv[k] = (float)((double)c.ncell[k] / (double)L[k]);
+        }
+        c.nb_log2 = P->nb_log2;
+    }
     const int blocks = (n + kPartThreads - 1) / kPartThreads;
     using T = typename lbd::Store<DT>::T;
     const T *src = static_cast<const T *>(h->pops[h->cur]);
     const bool need_nlist = cp->use_wca != 0;
 
     // persistent path when every particle group can be resident at once
-    const int pblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
+    const int gblocks = (int)(((size_t)n * kChunks + kPartThreads - 1) / kPartThreads);  // 8 lanes a particle
+    const int pblocks = (n + kPThreads - 1) / kPThreads;                                   // one thread a particle
     int per_sm = 0;
-    if (P->persistent && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>,
-                                                                       kPartThreads, 0) == cudaSuccess &&
+    if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>,
+                                                                       kPThreads, 0) == cudaSuccess &&
         pblocks <= per_sm * device_sm_count()) {
         cudaError_t e = cudaSuccess;
         if (need_nlist && P->nlist_n != n) {
-            const unsigned int init[4] = {0u, 0u, 1u, 0u};  // [2]: build before the launch, [3]: epoch
+            const unsigned int init[kFlagWords] = {0u, 0u, 1u, 0u, 0u};  // [2]: build before the launch
             e = cudaMemcpyAsync(P->flags, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
             if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
             if (e != cudaSuccess) return e;
@@ -932,11 +1258,10 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
             h->facc_stale = 0;
         }
         if (need_nlist) {
-            k_shadow_from_pos<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, P->shadow[1], P->flags + 2, h->d_err,
-                                                                       c);
-            dim3 bgrid((n + kTile - 1) / kTile, kChunks);
-            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(P->shadow[1], P->nlist, P->ncount, P->ref, P->flags,
-                                                          h->d_err, c, 2u);
+            k_shadow_from_pos<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, P->shadow[1], P->head, P->next,
+                                                                       P->bucket_of, P->flags + 2, h->d_err, c);
+            k_build_nlist<<<gblocks, kPartThreads, 0, h->stream>>>(P->shadow[1], P->head, P->next, P->nlist,
+                                                                   P->ncount, P->ref, P->flags, h->d_err, c, 2u);
             h->launches += 2;
         }
         PersistArgs a;
@@ -953,6 +1278,9 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         a.nlist = P->nlist;
         a.ncount = P->ncount;
         a.ref = P->ref;
+        a.head = P->head;
+        a.next = P->next;
+        a.bucket_of = P->bucket_of;
         a.facc = h->facc;
         // the record buffer has two halves: the stale records (cleared in the
         // kernel's first phase) stay in one, this call's go to the other
@@ -968,7 +1296,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         a.spin_limit = 1u << 22;
         cudaLaunchConfig_t lc = {};
         lc.gridDim = dim3(pblocks);
-        lc.blockDim = dim3(kPartThreads);
+        lc.blockDim = dim3(kPThreads);
         lc.stream = h->stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;
@@ -1005,20 +1333,22 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     h->launches += 1;
     for (int s = 0; s < cp->n_substeps; ++s) {
         const uint32_t rd = P->sub_counter & 1u, wr = rd ^ 1u;
+        const int sblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
         if (need_nlist) {
-            dim3 bgrid((n + kTile - 1) / kTile, kChunks);
-            k_build_nlist<<<bgrid, kTile, 0, h->stream>>>(P->shadow[s & 1], P->nlist, P->ncount, P->ref, P->flags,
-                                                          h->d_err, c, rd);
-            h->launches += 1;
+            k_bin<<<blocks, kPartThreads, 0, h->stream>>>(P->shadow[s & 1], P->head, P->next, P->bucket_of,
+                                                          P->flags, c, rd);
+            k_build_nlist<<<sblocks, kPartThreads, 0, h->stream>>>(P->shadow[s & 1], P->head, P->next, P->nlist,
+                                                                   P->ncount, P->ref, P->flags, h->d_err, c, rd);
+            h->launches += 2;
         }
         c.md_step = cp->md_step0 + (uint32_t)s;
         c.last = (s == cp->n_substeps - 1);
         c.slot = wr;
         int *rec = P->records + P->rec_off + P->n_records;
-        const int sblocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
         k_substep<DT><<<sblocks, kPartThreads, 0, h->stream>>>(
             src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma,
-            P->nlist, P->ncount, need_nlist ? P->ref : nullptr, h->facc, rec, P->flags, h->d_err, c, rd);
+            P->nlist, P->ncount, need_nlist ? P->ref : nullptr, P->head, P->bucket_of, h->facc, rec, P->flags,
+            h->d_err, c, rd);
         P->n_records += (size_t)n;
         P->sub_counter += 1;
         h->launches += 1;
@@ -1030,8 +1360,8 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
 
 lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
-    if (pp->n < 0 || pp->reserved != 0 || cp->reserved != 0) {
-        set_error("lb_couple_particles: bad particle count or reserved field");
+    if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~LB_COUPLE_PER_SUBSTEP) != 0) {
+        set_error("lb_couple_particles: bad particle count, reserved field or flags");
         return LB_EINVAL;
     }
     if (pp->n == 0) return LB_OK;
@@ -1119,6 +1449,15 @@ lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_interpolate", e);
+}
+
+// After a grid-barrier timeout the arrival word is left mid-count; zero it
+// (stream-ordered) so that the next persistent launch starts clean.
+cudaError_t reset_particle_barrier(lb_handle *h)
+{
+    Particles *P = h->parts;
+    if (!P || !P->bar) return cudaSuccess;
+    return cudaMemsetAsync(P->bar, 0, 3 * sizeof(unsigned int), h->stream);
 }
 
 void destroy_particles(lb_handle *h)

@@ -52,8 +52,10 @@ def random_walk_chains(n_chains, chain_len, box, *, bond=0.97, min_dist=1.0, see
     Lz)``; every further bead sits at distance ``bond`` from its predecessor in
     a uniformly random direction.  A step is redrawn (up to ``max_tries``
     times) when the new bead comes closer than ``min_dist`` to an earlier
-    non-bonded bead, so that the first repulsive forces stay moderate.
-    Returns float64 positions (n_chains * chain_len, 3) in [0, L).
+    non-bonded bead, so that the first repulsive forces stay moderate; a walk
+    that traps itself (no step found) is discarded and the chain regrown, so
+    no two non-bonded beads are closer than ``min_dist``.  Returns float64
+    positions (n_chains * chain_len, 3) in [0, L).
     """
     rng = np.random.default_rng(seed)
     L = np.asarray(box, dtype=np.float64)
@@ -81,14 +83,18 @@ def random_walk_chains(n_chains, chain_len, box, *, bond=0.97, min_dist=1.0, see
                             return True
         return False
 
-    for c in range(n_chains):
-        base = c * chain_len
+    def place(p, i):
+        pos[i] = p
+        grid.setdefault(key(p), []).append(i)
+
+    def grow(base):
         for t in range(max_tries):
             p0 = rng.uniform(0.0, 1.0, 3) * L
             if not too_close(p0, -1):
                 break
-        pos[base] = p0
-        grid.setdefault(key(p0), []).append(base)
+        else:
+            return 0
+        place(p0, base)
         for b in range(1, chain_len):
             prev = pos[base + b - 1]
             for t in range(max_tries):
@@ -97,8 +103,21 @@ def random_walk_chains(n_chains, chain_len, box, *, bond=0.97, min_dist=1.0, see
                 p = (prev + v) % L
                 if not too_close(p, base + b - 1):
                     break
-            pos[base + b] = p
-            grid.setdefault(key(p), []).append(base + b)
+            else:
+                return b
+            place(p, base + b)
+        return chain_len
+
+    for c in range(n_chains):
+        base = c * chain_len
+        for attempt in range(max_tries):
+            done = grow(base)
+            if done == chain_len:
+                break
+            for i in range(base, base + done):  # take the trapped walk out again
+                grid[key(pos[i])].remove(i)
+        else:
+            raise RuntimeError("random_walk_chains: could not place chain %d (box too crowded)" % c)
     return pos
 
 

@@ -23,6 +23,7 @@ LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
 LB_DERR_PARTICLE_RANGE = 16
+LB_COUPLE_PER_SUBSTEP = 1
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
                 5: "LB_ETIMEOUT", 6: "LB_EUNSUPPORTED", 7: "LB_EDEVICE"}
@@ -77,7 +78,7 @@ class lb_couple_params(C.Structure):
     _fields_ = [
         ("n_substeps", C.c_int), ("noise_kind", C.c_int),
         ("dt", C.c_double), ("seed", C.c_uint64), ("md_step0", C.c_uint32),
-        ("chain_len", C.c_int), ("use_wca", C.c_int), ("reserved", C.c_int),
+        ("chain_len", C.c_int), ("use_wca", C.c_int), ("flags", C.c_int),
         ("eps", C.c_double), ("sigma", C.c_double), ("k_fene", C.c_double), ("r0", C.c_double),
     ]
 
@@ -531,10 +532,11 @@ def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_p
 
 
 def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len=0, use_wca=False,
-                  eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5) -> lb_couple_params:
+                  eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5, per_substep=False) -> lb_couple_params:
     c = lb_couple_params()
     c.n_substeps, c.noise_kind, c.dt = int(n_substeps), int(noise_kind), float(dt)
     c.seed, c.md_step0 = int(seed), int(md_step0) & 0xffffffff
-    c.chain_len, c.use_wca, c.reserved = int(chain_len), int(bool(use_wca)), 0
+    c.chain_len, c.use_wca = int(chain_len), int(bool(use_wca))
+    c.flags = LB_COUPLE_PER_SUBSTEP if per_substep else 0
     c.eps, c.sigma, c.k_fene, c.r0 = float(eps), float(sigma), float(k_fene), float(r0)
     return c

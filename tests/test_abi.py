@@ -29,6 +29,14 @@ def test_header_declares_binding_exports(lib):
     assert _declared() == sorted(lib.EXPORTS)
 
 
+def test_header_constants_match_binding(lib):
+    """Every numeric #define of the header has the same value in the binding."""
+    defs = dict(re.findall(r"#define\s+(LB_\w+)\s+(0x[0-9a-fA-F]+|\d+)u?\b", open(HEADER).read()))
+    assert {"LB_DERR_FENE_BROKEN", "LB_NSUMS", "LB_COUPLE_PER_SUBSTEP"} <= set(defs)
+    for name, val in defs.items():
+        assert getattr(lib, name) == int(val, 0), name
+
+
 def test_library_exports_every_symbol(lib):
     out = subprocess.run(["nm", "-D", "--defined-only", lib.LIB_PATH], capture_output=True, text=True,
                          check=True).stdout

@@ -28,7 +28,7 @@ def dev(x, dt=None):
 
 
 def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1, gamma=2.0, mass=1.0,
-         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0)):
+         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0), per_substep=False):
     mom32 = mom.astype(np.float32).astype(np.float64)
     p = ora.make_params(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
     u = inputs.shear_wave(shape, u_amp) + inputs.gaussian_field(shape, 3, 1e-3, seed=8)
@@ -49,7 +49,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
     parts = L.particles(pos.shape[0], gpos, gmom, mass0=mass, gamma0=gamma)
     cp = L.couple_params(n_substeps=nsub, dt=dt, seed=11, md_step0=40, noise_kind=noise_kind,
                          chain_len=chains[1] if chains else 0, use_wca=bool(chains), eps=0.01, sigma=1.0,
-                         k_fene=0.3, r0=1.5)
+                         k_fene=0.3, r0=1.5, per_substep=per_substep)
     L.lb_couple_particles(lat.h, parts, cp)
     facc = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
     L.lb_get_particle_forces(lat.h, facc)
@@ -104,12 +104,42 @@ def test_walls_particles_parity(ora):
     assert rel(r["gfacc"], r["ofacc"]) < 2e-4
 
 
-def test_chains_parity(ora):
-    """Two FENE + WCA chains of 24 beads (bond 0.97) in a 16^3 thermal fluid."""
+@pytest.mark.parametrize("per_substep", [False, True])
+def test_chains_parity(ora, per_substep):
+    """Two FENE + WCA chains of 24 beads (bond 0.97) in a 16^3 thermal fluid,
+    by the persistent kernel and by one launch per sub-step."""
     shape = (16, 16, 16)
     pos = inputs.random_walk_chains(2, 24, shape, seed=7)
     mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
-    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24))
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), per_substep=per_substep)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_wca_narrow_box_between_walls(ora):
+    """WCA particles in a box 4 cells wide in x, where the cell list has only
+    two cells (each visited once), between walls in z (cells not wrapped)."""
+    shape = (4, 20, 14)
+    n = 120
+    pos = inputs.random_walk_chains(n, 1, (4, 20, 11), min_dist=1.0, seed=41)  # no overlaps
+    pos[:, 2] += 1.0  # z in [1, 12) = [1, nz - 2)
+    mom = inputs.maxwell_momenta(n, 1.0, 1e-3, seed=42)
+    r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, chains=(n, 1))
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+@pytest.mark.parametrize("per_substep", [False, True])
+def test_wca_chains_many(ora, per_substep):
+    """100 FENE + WCA chains of 256 beads in a 48^3 box (200 blocks of the
+    persistent kernel; or one launch per sub-step, each after a cell-list
+    build)."""
+    shape = (48, 48, 48)
+    pos = inputs.random_walk_chains(100, 256, shape, seed=43)
+    mom = inputs.maxwell_momenta(25600, 1.0, 1e-4, seed=44)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(100, 256), nsub=3, lb_after=False, per_substep=per_substep)
     assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
     assert rel(r["gmom"], r["omom"]) < 2e-4
     assert rel(r["gfacc"], r["ofacc"]) < 2e-4
@@ -166,7 +196,8 @@ def test_many_particles_multi_kernel_path(ora):
     assert rel(r["gfacc"], r["ofacc"]) < 2e-4
 
 
-def test_fast_wca_particles_rebuild_lists(ora):
+@pytest.mark.parametrize("per_substep", [False, True])
+def test_fast_wca_particles_rebuild_lists(ora, per_substep):
     """WCA particles moving ~0.5 sigma per call (more than half the Verlet
     skin) force list rebuilds inside and between calls; three calls in a row,
     each followed by an LB step, against the oracle's brute-force pairs."""
@@ -189,7 +220,8 @@ def test_fast_wca_particles_rebuild_lists(ora):
         opos, omom, facc, _ = ora.couple(p, pops, opos, omom, m, 2.0, dt=0.1, n_substeps=10, seed=9,
                                          md_step0=10 * t, md=md)
         pops = ora.step(p, pops, facc.astype(np.float32).astype(np.float64), t)
-        cp = L.couple_params(n_substeps=10, dt=0.1, seed=9, md_step0=10 * t, use_wca=True, eps=0.01, sigma=1.0)
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=9, md_step0=10 * t, use_wca=True, eps=0.01, sigma=1.0,
+                             per_substep=per_substep)
         L.lb_couple_particles(lat.h, parts, cp)
         lat.step(1)
     assert lat.sync() == (L.LB_OK, 0)
