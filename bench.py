@@ -38,8 +38,9 @@ DT, NSUB = 0.1, 10              # dt = 0.01 tau_MD
 EPS, SIGMA, K_FENE, R0 = 0.01, 1.0, 0.3, 1.5   # epsilon = 0.01 in lattice energy units
 BYTES_PER_NODE = 19 * 4 * 2 + 3 * 4   # populations read + written, particle impulses read
 FALLBACK_HBM_GBS = 6800.0
-WORKLOAD = ("fluctuating D3Q19 256^3 periodic FP32 kT=1e-4 + 64 FENE/WCA chains x 256 monomers, "
-            "10 MD sub-steps per LB step")
+def workload(box: int = SHAPE[0]) -> str:
+    return ("fluctuating D3Q19 %d^3 periodic FP32 kT=1e-4 + 64 FENE/WCA chains x 256 monomers, "
+            "10 MD sub-steps per LB step" % box)
 SLAB = (256, 256, 4)            # CPU sample: same x-y extent, 4 planes, one chain
 
 
@@ -215,7 +216,7 @@ def run_reference(args):
         "impl": "reference", "metric": "MLUPS", "value": mlups, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": "256x256x4 periodic slab + 1 chain of 256 per step"},
+        "config": {"workload": workload(), "sample": "256x256x4 periodic slab + 1 chain of 256 per step"},
         "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": "%d steps of a 256x256x4 slab + 1 x 256-monomer chain" % steps},
         "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -352,7 +353,7 @@ def run_ours(args):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": nodes, "particles": npart, "substeps": NSUB,
+        "config": {"workload": workload(args.box), "nodes": nodes, "particles": npart, "substeps": NSUB,
                    "l2": "inputs larger than L2 (2.55 GB populations per replica)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -489,7 +490,7 @@ def _forms(peak):
 
 def _profiled_traffic():
     """DRAM bytes per stream-collide launch from the committed ncu summary,
-    if it was taken on the current kernel source."""
+    if it was taken on the current source of that kernel."""
     path = os.path.join(ROOT, "profiles", "stream_collide_traffic.txt")
     try:
         d = {}
@@ -499,7 +500,7 @@ def _profiled_traffic():
                 if sep and key.strip() in ("source_hash", "dram_bytes_per_launch"):
                     d[key.strip()] = val.strip()
         from paper_0803_2826_gb300 import build as B
-        if d.get("source_hash") != B.source_hash():
+        if d.get("source_hash") != B.source_hash(B.STREAM_COLLIDE_FILES):
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:

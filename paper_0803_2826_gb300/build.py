@@ -39,11 +39,17 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def source_hash() -> str:
-    """SHA-1 over the library sources (to tie profiles to the code they measured)."""
+# the files that define the fused stream-collide kernel
+STREAM_COLLIDE_FILES = ("d3q19.cuh", "stream_collide.cuh", "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu", "lbf_internal.h")
+
+
+def source_hash(files=None) -> str:
+    """SHA-1 over the library sources, or over the named files of csrc/ (to
+    tie profiles to the code they measured)."""
     import hashlib
     h = hashlib.sha1()
-    for f in sorted(_deps()):
+    deps = _deps() if files is None else [os.path.join(CSRC, f) for f in files]
+    for f in sorted(deps):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())
