@@ -350,6 +350,13 @@ lb_status lb_batch_moments(lb_batch *b, int replica, float *rho, float *j, float
 lb_status lb_noise_words(uint64_t seed, uint32_t replica, uint32_t step, uint32_t domain, uint32_t index0,
                          int count, int nblocks, uint32_t *words, float *gauss, void *stream);
 
+/* The Box-Muller map of lb_noise_words on caller-given word pairs: for
+ * q < npairs, (gauss[2q], gauss[2q+1]) from (words[2q], words[2q+1]), as the
+ * kernels compute it (for exhaustive checks over all 2^23 uniforms).
+ * words: device uint32 [2 npairs]; gauss: device FP32 [2 npairs].
+ * stream: a cudaStream_t.  Errors: LB_EINVAL, LB_ECUDA. */
+lb_status lb_box_muller(const uint32_t *words, int npairs, float *gauss, void *stream);
+
 /* ---- library information ------------------------------------------------- */
 
 /* "lbfluct <version> sm_103a" */

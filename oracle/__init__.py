@@ -107,6 +107,7 @@ def _load():
                                       C.c_uint32, C.c_int, _U32]
             lib.ora_gaussians.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                           C.c_uint32, C.c_int, _D]
+            lib.ora_box_muller.argtypes = [_U32, C.c_long, _D]
             P = C.POINTER(Params)
             lib.ora_equilibrium.argtypes = [P, _D, _D, _D]
             lib.ora_step.argtypes = [P, _D, _D, _D, C.c_uint32]
@@ -196,6 +197,16 @@ def gaussians(seed, node, step, domain=0, replica=0, nblocks=4):
     lib.ora_gaussians(int(seed), int(node), int(step), int(domain), int(replica),
                       int(nblocks), _dp(g))
     return g[:4 * nblocks]
+
+
+def box_muller(words):
+    """Box-Muller Gaussians of consecutive word pairs (uint32 array of even
+    length), in the order the pairs come."""
+    w = np.ascontiguousarray(words, dtype=np.uint32).ravel()
+    assert w.size % 2 == 0
+    g = np.zeros(w.size)
+    _load().ora_box_muller(w.ctypes.data_as(_U32), w.size // 2, _dp(g))
+    return g
 
 
 def _nodes(p: Params):

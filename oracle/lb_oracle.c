@@ -193,20 +193,32 @@ void ora_raw16(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain,
     }
 }
 
+/* The Box-Muller transform of one pair of raw words (Sec. 3.5 asks for
+ * unit-variance Gaussians): sqrt(-2 ln v1) (cos, sin)(2 pi v2). */
+static void box_muller_pair(uint32_t w1, uint32_t w2, double g[2])
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double v1 = ora_uniform(w1);
+    double v2 = ora_uniform(w2);
+    double rad = sqrt(-2.0 * log(v1));
+    g[0] = rad * cos(two_pi * v2);
+    g[1] = rad * sin(two_pi * v2);
+}
+
+/* The same for npairs word pairs w[2q], w[2q+1]. */
+void ora_box_muller(const uint32_t *w, long npairs, double *g)
+{
+#pragma omp parallel for schedule(static)
+    for (long q = 0; q < npairs; q++) box_muller_pair(w[2 * q], w[2 * q + 1], g + 2 * q);
+}
+
 /* Gaussians by the Box-Muller transform on consecutive uniform pairs. */
 void ora_gaussians(uint64_t seed, uint32_t node, uint32_t step, uint32_t domain,
                    uint32_t replica, int nblocks, double *g)
 {
     uint32_t raw[16];
     ora_raw16(seed, node, step, domain, replica, nblocks, raw);
-    const double two_pi = 6.283185307179586476925286766559;
-    for (int p = 0; p < 2 * nblocks; p++) {
-        double v1 = ora_uniform(raw[2 * p]);
-        double v2 = ora_uniform(raw[2 * p + 1]);
-        double rad = sqrt(-2.0 * log(v1));
-        g[2 * p] = rad * cos(two_pi * v2);
-        g[2 * p + 1] = rad * sin(two_pi * v2);
-    }
+    for (int p = 0; p < 2 * nblocks; p++) box_muller_pair(raw[2 * p], raw[2 * p + 1], g + 2 * p);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -269,6 +269,23 @@ __device__ __forceinline__ float uniform01(uint32_t x)
     return __uint_as_float(0x3F800000u | (x >> 9)) - 0.99999994039535522f;
 }
 
+// -2 ln v for a uniform v = (2k + 1) 2^-24 given with d = 1 - v (both
+// exact), without branches: the hardware log2 (absolute error below 2^-22.6
+// on [0.5, 2], 2 ulp elsewhere) where d >= 2^-5, so |ln v| >= 0.031; below
+// that, where an absolute error would be large against ln v, the Taylor
+// series -ln(1 - d) = d + d^2/2 + ... + d^6/6 (remainder < 2^-32 relative).
+__device__ __forceinline__ float neg2log(float v, float d)
+{
+    const float lg = -1.3862943611198906f * __log2f(v);  // -2 ln 2 log2 v
+    float t = fmaf(d, 1.0f / 6.0f, 0.2f);
+    t = fmaf(d, t, 0.25f);
+    t = fmaf(d, t, 1.0f / 3.0f);
+    t = fmaf(d, t, 0.5f);
+    t = fmaf(d, t, 1.0f);
+    const float s = (2.0f * d) * t;
+    return d < 0.03125f ? s : lg;
+}
+
 // Box-Muller pair from two raw words: sqrt(-2 ln v1) (cos, sin)(2 pi v2).
 // The angle is centred, 2 pi v2 = pi + 2 pi (v2 - 1/2) with v2 - 1/2 exact,
 // so the hardware sine / cosine see an argument in (-pi, pi), where their
@@ -276,8 +293,9 @@ __device__ __forceinline__ float uniform01(uint32_t x)
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
 {
     const float v1 = uniform01(a);
+    const float d1 = 1.0f - v1;  // exact for v1 >= 1/2, the only range where it is used
     const float w = uniform01(b) - 0.5f;
-    const float L = -2.0f * logf(v1);  // > 0 since v1 <= 1 - 2^-24
+    const float L = neg2log(v1, d1);  // >= 2^-23
     const float r = L * rsqrtf(L);
     float s, c;
     __sincosf(6.283185307179586f * w, &s, &c);

@@ -24,7 +24,27 @@ __global__ void k_noise_words(uint32_t k0, uint32_t k1, uint32_t replica, uint32
     }
 }
 
+__global__ void k_box_muller(const uint32_t *words, int npairs, float *gauss)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= npairs) return;
+    lbd::box_muller(words[2 * q], words[2 * q + 1], gauss[2 * q], gauss[2 * q + 1]);
+}
+
 }  // namespace
+
+extern "C" lb_status lb_box_muller(const uint32_t *words, int npairs, float *gauss, void *stream)
+{
+    if (npairs < 0 || (npairs > 0 && (!words || !gauss))) {
+        lbi::set_error("lb_box_muller: need npairs >= 0 and both buffers");
+        return LB_EINVAL;
+    }
+    if (npairs == 0) return LB_OK;
+    const int threads = 256;
+    k_box_muller<<<(npairs + threads - 1) / threads, threads, 0, (cudaStream_t)stream>>>(words, npairs, gauss);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LB_OK : lbi::cuda_fail("lb_box_muller", e);
+}
 
 extern "C" lb_status lb_noise_words(uint64_t seed, uint32_t replica, uint32_t step, uint32_t domain,
                                     uint32_t index0, int count, int nblocks, uint32_t *words, float *gauss,

@@ -33,7 +33,7 @@ EXPORTS = (
     "lb_plane_pitch", "lb_population_bytes", "lb_create", "lb_destroy", "lb_last_error",
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
-    "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words",
+    "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
     "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
     "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
@@ -123,6 +123,7 @@ def load(path: str | None = None):
             "lb_interpolate": (i, [H, i, vp, vp]),
             "lb_get_particle_forces": (i, [H, vp]),
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
+            "lb_box_muller": (i, [vp, i, vp, vp]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
             "lb_moment_sums_static": (i, [P, vp, vp, vp]),
             "lb_step_from": (i, [H, vp, vp, u32]),
@@ -286,6 +287,10 @@ def lb_get_particle_forces(h, out):
 def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, gauss=None, stream=None):
     _check(load().lb_noise_words(int(seed), int(replica), int(step), int(domain), int(index0), int(count),
                                  int(nblocks), _ptr(words), _ptr(gauss), _stream(stream)))
+
+
+def lb_box_muller(words, npairs, gauss, stream=None):
+    _check(load().lb_box_muller(_ptr(words), int(npairs), _ptr(gauss), _stream(stream)))
 
 
 def lb_get_launch_count(h) -> int:

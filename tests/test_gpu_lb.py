@@ -140,6 +140,34 @@ def test_noise_words_bitwise(ora):
         assert np.array_equal(W.reshape(-1)[4 * q:4 * q + 4], ora.raw_words(5, q, 9, domain=1, nblocks=1))
 
 
+def test_box_muller_all_uniforms(ora):
+    """The kernels' Box-Muller map against the FP64 oracle for every one of
+    the 2^23 values of the radial uniform v1 = (2k + 1) 2^-24 (random angle
+    words): finite everywhere, including v1 = 1 - 2^-24, and within the bound
+    of the FP32 logarithm (hardware log2 / series near 1), the rsqrt radius
+    and the hardware sine / cosine times a radius of at most ~5.8."""
+    rng = np.random.default_rng(17)
+    n = 1 << 23
+    w = np.empty(2 * n, dtype=np.uint32)
+    w[0::2] = (np.arange(n, dtype=np.uint32) << 9) | rng.integers(0, 512, n, dtype=np.uint32)
+    w[1::2] = rng.integers(0, 1 << 32, n, dtype=np.uint32)
+    dw = torch.from_numpy(w.view(np.int32)).cuda()
+    dg = torch.empty(2 * n, dtype=torch.float32, device="cuda")
+    L.lb_box_muller(dw, n, dg)
+    torch.cuda.synchronize()
+    got = dg.cpu().numpy().astype(np.float64)
+    want = ora.box_muller(w)
+    assert np.isfinite(got).all()
+    err = np.abs(got - want)
+    assert err.max() < 4e-6, (err.max(), int(err.argmax()))
+    # the radius in relative terms, also where it is tiny (v1 near 1):
+    # g0^2 + g1^2 = -2 ln v1 up to the log2 bound (3.5e-6 relative at the
+    # switch to the series) and the sine / cosine error
+    r2 = got[0::2] ** 2 + got[1::2] ** 2
+    want_r2 = -2.0 * np.log((2.0 * np.arange(n) + 1.0) * 2.0 ** -24)
+    assert np.allclose(r2, want_r2, rtol=1e-5, atol=0)
+
+
 def test_conservation_on_gpu(ora):
     """Mass constant; momentum grows by sum f per step (FP32 storage)."""
     shape = (16, 12, 10)

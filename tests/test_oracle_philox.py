@@ -61,3 +61,10 @@ def test_gaussian_matches_box_muller(ora):
         r = np.sqrt(-2 * np.log(v1))
         assert np.isclose(g[2 * p], r * np.cos(2 * np.pi * v2), rtol=1e-14, atol=1e-15)
         assert np.isclose(g[2 * p + 1], r * np.sin(2 * np.pi * v2), rtol=1e-14, atol=1e-15)
+
+
+def test_box_muller_of_words_matches_gaussians(ora):
+    """The word-pair map is the one the noise streams use, pair by pair."""
+    for node in (0, 7, 123456):
+        w = ora.raw_words(99, node, 5, domain=0, replica=2, nblocks=4)
+        assert np.array_equal(ora.box_muller(w), ora.gaussians(99, node, 5, domain=0, replica=2, nblocks=4))
