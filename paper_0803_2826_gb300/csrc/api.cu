@@ -65,6 +65,13 @@ StepArgs make_args(const lb_handle *h)
     a.phi_bulk = (float)std::sqrt(1.0 - p.gamma_bulk * p.gamma_bulk);
     a.phi_odd = (float)std::sqrt(1.0 - p.gamma_odd * p.gamma_odd);
     a.phi_even = (float)std::sqrt(1.0 - p.gamma_even * p.gamma_even);
+    for (int k = 4; k < 19; ++k) {
+        const double phi = k == 4 ? std::sqrt(1.0 - p.gamma_bulk * p.gamma_bulk)
+                           : k < 10 ? std::sqrt(1.0 - p.gamma_shear * p.gamma_shear)
+                           : k < 16 ? std::sqrt(1.0 - p.gamma_odd * p.gamma_odd)
+                                    : std::sqrt(1.0 - p.gamma_even * p.gamma_even);
+        a.amp[k - 4] = (float)(phi * (double)lbd::sqrt_inv_w(k));
+    }
     a.fx = (float)p.body_force[0];
     a.fy = (float)p.body_force[1];
     a.fz = (float)p.body_force[2];

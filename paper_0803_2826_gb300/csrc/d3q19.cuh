@@ -290,12 +290,13 @@ __device__ __forceinline__ float neg2log(float v, float d)
 // The angle is centred, 2 pi v2 = pi + 2 pi (v2 - 1/2) with v2 - 1/2 exact,
 // so the hardware sine / cosine see an argument in (-pi, pi), where their
 // absolute error is below 2^-21; cos and sin of the shifted angle change sign.
-__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1)
+// With var != 1 the pair has variance var (the radius is sqrt(-2 ln v1 var)).
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, float &g1, float var = 1.0f)
 {
     const float v1 = uniform01(a);
     const float d1 = 1.0f - v1;  // exact for v1 >= 1/2, the only range where it is used
     const float w = uniform01(b) - 0.5f;
-    const float L = neg2log(v1, d1);  // >= 2^-23
+    const float L = neg2log(v1, d1) * var;  // -2 ln v1 >= 2^-23
     const float r = L * rsqrtf(L);
     float s, c;
     __sincosf(6.283185307179586f * w, &s, &c);
@@ -303,16 +304,16 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &g0, fl
     g1 = -r * s;
 }
 
-// Sixteen Gaussians for counter word 0, step, domain, replica: Philox blocks
-// b = 0..3 with counter (w0, step, domain<<8 | b, replica).
+// Sixteen Gaussians of variance var for counter word 0, step, domain,
+// replica: Philox blocks b = 0..3 with counter (w0, step, domain<<8 | b, replica).
 __device__ __forceinline__ void gaussians16(const RoundKeys &rk, uint32_t w0, uint32_t step, uint32_t domain,
-                                            uint32_t replica, float g[16])
+                                            uint32_t replica, float var, float g[16])
 {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         const U4 r = philox10(U4{w0, step, (domain << 8) | (uint32_t)b, replica}, rk);
-        box_muller(r.x, r.y, g[4 * b + 0], g[4 * b + 1]);
-        box_muller(r.z, r.w, g[4 * b + 2], g[4 * b + 3]);
+        box_muller(r.x, r.y, g[4 * b + 0], g[4 * b + 1], var);
+        box_muller(r.z, r.w, g[4 * b + 2], g[4 * b + 3], var);
     }
 }
 

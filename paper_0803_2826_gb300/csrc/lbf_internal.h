@@ -25,6 +25,7 @@ struct StepArgs {
     float mu;              // kT / c_s^2
     float g_shear, g_bulk, g_odd, g_even;
     float phi_shear, phi_bulk, phi_odd, phi_even;  // sqrt(1 - gamma^2)
+    float amp[15];         // noise of mode k = 4..18 per unit sqrt(mu rho): phi_k / sqrt(w_k)
     float fx, fy, fz;      // uniform body force
     float scale, inv_scale;  // storage scale of FP16/BF16 deviations
     int noise_rho0;

@@ -74,19 +74,12 @@ __device__ __forceinline__ void collide_node(const float n[19], float fx, float 
     for (int k = 16; k < 19; ++k) M[k] = lbd::inv_w(k) * (a.g_even * m[k]);
 
     if (NOISE) {
+        // sqrt(mu rho w_k) phi_k r_k, divided by w_k: (phi_k / sqrt(w_k)) times a
+        // Gaussian of variance mu rho (the factor rides in the Box-Muller radius)
         float g[16];
-        lbd::gaussians16(rk, node, a.step, 0u, replica, g);
-        const float rn = a.noise_rho0 ? a.rho0 : rho;
-        const float s = sqrtf(a.mu * rn);
-        // sqrt(mu rho w_k) phi_k r_k, divided by w_k: sqrt(mu rho / w_k) phi_k r_k
-        const float sb = s * a.phi_bulk, ss = s * a.phi_shear, so = s * a.phi_odd, se = s * a.phi_even;
-        M[4] += sb * lbd::sqrt_inv_w(4) * g[0];
+        lbd::gaussians16(rk, node, a.step, 0u, replica, a.mu * (a.noise_rho0 ? a.rho0 : rho), g);
 #pragma unroll
-        for (int k = 5; k < 10; ++k) M[k] += ss * lbd::sqrt_inv_w(k) * g[k - 4];
-#pragma unroll
-        for (int k = 10; k < 16; ++k) M[k] += so * lbd::sqrt_inv_w(k) * g[k - 4];
-#pragma unroll
-        for (int k = 16; k < 19; ++k) M[k] += se * lbd::sqrt_inv_w(k) * g[k - 4];
+        for (int k = 4; k < 19; ++k) M[k] = fmaf(a.amp[k - 4], g[k - 4], M[k]);
     }
 
     lbd::backward(M, out);
