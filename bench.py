@@ -36,7 +36,11 @@ KT = 1e-4
 MASS, GAMMA = 1.0, 2.0          # Gamma = 20 m / tau_MD with h_LB = 0.1 tau_MD
 DT, NSUB = 0.1, 10              # dt = 0.01 tau_MD
 EPS, SIGMA, K_FENE, R0 = 0.01, 1.0, 0.3, 1.5   # epsilon = 0.01 in lattice energy units
-BYTES_PER_NODE = 19 * 4 * 2 + 3 * 4   # populations read + written, particle impulses read
+# algorithmic bytes per node of the timed stream-collide launch: populations
+# read + written, plus the particle impulses when the launch reads them (the
+# serial order); with the overlap the impulse nodes are re-updated by a
+# separate small launch and the timed launch reads no impulse field
+BYTES_PER_NODE = {"serial": 19 * 4 * 2 + 3 * 4, "overlapped": 19 * 4 * 2}
 FALLBACK_HBM_GBS = 6800.0
 def workload(box: int = SHAPE[0]) -> str:
     return ("fluctuating D3Q19 %d^3 periodic FP32 kT=1e-4 + 64 FENE/WCA chains x 256 monomers, "
@@ -54,6 +58,8 @@ def _args():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched / adjoint / reduced-precision measurements")
     ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--serial", action="store_true",
+                    help="run the coupling before the LB update instead of overlapping the two")
     ap.add_argument("--box", type=int, default=SHAPE[0],
                     help="edge of the coupled box (smaller boxes for profiling runs only)")
     ap.add_argument("--kernel-only", action="store_true",
@@ -262,19 +268,13 @@ def run_ours(args):
     torch.cuda.synchronize()
     parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
     cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=7 + rank, chain_len=CHAIN_LEN, use_wca=True,
-                         eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0)
+                         eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=not args.serial)
     t_step = [0]
 
-    def one_step(ev=None):
+    def one_step():
         cp.md_step0 = (NSUB * t_step[0]) & 0xffffffff
-        if ev is not None:
-            ev[2].record(stream)
         L.lb_couple_particles(lat.h, parts, cp)
-        if ev is not None:
-            ev[0].record(stream)
         L.lb_step(lat.h, 1)
-        if ev is not None:
-            ev[1].record(stream)
         t_step[0] += 1
 
     with torch.cuda.stream(stream):
@@ -285,7 +285,10 @@ def run_ours(args):
     assert bits == 0, "device error word 0x%x during warm-up" % bits
 
     K = args.steps
-    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(K)]
+    # the library's kernel timers: CUDA events around each stream-collide
+    # launch and each coupling, on the stream each runs on (with the overlap
+    # the coupling runs on the library's own stream)
+    L.lb_set_timing(lat.h, K)
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches0 = L.lb_get_launch_count(lat.h)
     clocks = Clocks(local)
@@ -296,16 +299,17 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         t0.record(stream)
         for k in range(K):
-            one_step(evs[k])
+            one_step()
         t1.record(stream)
     barrier()
     wall = time.perf_counter() - wall0
     clk = clocks.stop()
     launches = L.lb_get_launch_count(lat.h) - launches0
     ms_total = t0.elapsed_time(t1)
-    sc_ms = [e[0].elapsed_time(e[1]) for e in evs]
-    couple_ms = sum(e[2].elapsed_time(e[0]) for e in evs) / len(evs)
-    sc_avg = sum(sc_ms) / len(sc_ms)
+    sc_sum, sc_n, cp_sum, cp_n = L.lb_get_timing(lat.h)
+    assert sc_n == K and cp_n == K, (sc_n, cp_n)
+    sc_avg, couple_ms = sc_sum / sc_n, cp_sum / cp_n
+    L.lb_set_timing(lat.h, 0)
     st, bits = lat.sync()
     assert bits == 0, "device error word 0x%x" % bits
 
@@ -347,8 +351,9 @@ def run_ours(args):
     value = world * nodes * K / (ms_total * 1e-3) / 1e6
     e2e_value = world * nodes * KE / (e2e_ms * 1e-3) / 1e6
     peak, peak_src = _peak_hbm()
-    achieved = BYTES_PER_NODE * nodes / (sc_avg * 1e-3) / 1e9
-    traffic = _profiled_traffic()
+    bpn = BYTES_PER_NODE["serial" if args.serial else "overlapped"]
+    achieved = bpn * nodes / (sc_avg * 1e-3) / 1e9
+    traffic = _profiled_traffic("serial" if args.serial else "overlapped")
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -358,8 +363,9 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_stream_collide",
-                     "bytes_per_node": BYTES_PER_NODE, "ms_per_launch": sc_avg,
+                     "bytes_per_node": bpn, "ms_per_launch": sc_avg,
                      "coupling_ms_per_step": couple_ms,
+                     "coupling": "serial" if args.serial else "overlapped with the stream-collide launch",
                      "peak_source": peak_src},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -488,19 +494,20 @@ def _forms(peak):
     return out
 
 
-def _profiled_traffic():
+def _profiled_traffic(mode):
     """DRAM bytes per stream-collide launch from the committed ncu summary,
-    if it was taken on the current source of that kernel."""
+    if it was taken on the current source of that kernel, in the same mode
+    (serial or overlapped coupling: the launch reads the impulses or not)."""
     path = os.path.join(ROOT, "profiles", "stream_collide_traffic.txt")
     try:
         d = {}
         with open(path) as f:
             for line in f:
                 key, sep, val = line.partition(":")
-                if sep and key.strip() in ("source_hash", "dram_bytes_per_launch"):
+                if sep and key.strip() in ("source_hash", "dram_bytes_per_launch", "mode"):
                     d[key.strip()] = val.strip()
         from paper_0803_2826_gb300 import build as B
-        if d.get("source_hash") != B.source_hash(B.STREAM_COLLIDE_FILES):
+        if d.get("source_hash") != B.source_hash(B.STREAM_COLLIDE_FILES) or d.get("mode") != mode:
             return None
         return float(d["dram_bytes_per_launch"])
     except Exception:

@@ -216,6 +216,17 @@ typedef struct {
  * co-resident grid. */
 #define LB_COUPLE_PER_SUBSTEP 0x1
 
+/* lb_couple_params.flags: run the coupling on a high-priority library stream
+ * while the next lb_step updates every node without its impulses, then that
+ * lb_step updates again, with the impulses, the nodes of the 8-node stencils
+ * the particles visited (the update of a node depends only on the pre-step
+ * state, its forces and the counter-based noise, so the result is the one a
+ * single update with the impulses gives).  The call returns with the
+ * coupling queued after all work on the handle's stream; the next lb_step, or
+ * any other call on the handle, orders the handle's stream after the
+ * coupling.  Until then the caller must not read pos / mom itself. */
+#define LB_COUPLE_OVERLAP 0x2
+
 /* One LB step's worth of particle motion.  The fluid velocity
  * u = (sum n c + f_ext/2)/rho of the current state is held fixed; for each
  * sub-step: half drift; conservative forces F^c (FENE + WCA); u_p =
@@ -232,6 +243,17 @@ lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_
 /* Interpolated fluid velocity u_p (device FP32 [n][3]) at device positions
  * pos[n][3] (Eq. (ufluid_discrete) with the linear stencil). */
 lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out);
+
+/* Kernel timers for profiling: after lb_set_timing(h, capacity) the library
+ * records CUDA events around each stream-collide launch of lb_step (with
+ * LB_COUPLE_OVERLAP: the update of all nodes, not the re-update of the
+ * impulse nodes) and around the GPU work of each lb_couple_particles, on the
+ * stream that work runs on, for the first `capacity` of each; capacity 0
+ * stops and releases them.  lb_get_timing waits for the recorded work and
+ * returns the summed milliseconds and the counts (any pointer may be NULL).
+ * The paper has no counterpart.  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_set_timing(lb_handle *h, int capacity);
+lb_status lb_get_timing(lb_handle *h, double *ms_step, int *n_step, double *ms_couple, int *n_couple);
 
 /* Copy the impulses the next lb_step will apply (device FP32 [3][N] out;
  * zeros when none are pending). */

@@ -340,6 +340,7 @@ lb_status lb_step_from(lb_handle *h, const void *src, void *dst, uint32_t step)
         set_error("lb_step_from: need a handle and two distinct buffers");
         return LB_EINVAL;
     }
+    join_overlap(h);
     cudaError_t e = step_from(h, src, dst, step);
     h->launches += 1;
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_step_from", e);
@@ -353,6 +354,7 @@ lb_status lb_adjoint_step(lb_handle *h, const void *state, const float *lambda_i
         set_error("lb_adjoint_step: need a state and two distinct adjoint buffers");
         return LB_EINVAL;
     }
+    join_overlap(h);
     cudaError_t e = launch_adjoint(h, state, lambda_in, lambda_out, grad_force);
     h->launches += 1;
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_step", e);
@@ -365,6 +367,7 @@ lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[
         set_error("lb_adjoint_seed_kinetic: NULL argument");
         return LB_EINVAL;
     }
+    join_overlap(h);
     if (!box_ok(h, lo, hi)) {
         set_error("lb_adjoint_seed_kinetic: sub-box outside the lattice");
         return LB_EINVAL;
@@ -385,6 +388,7 @@ lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, con
         set_error("lb_adjoint_kinetic: need nsteps >= 1, checkpoint_every >= 1, a valid sub-box and outputs");
         return LB_EINVAL;
     }
+    join_overlap(h);
     if (h->facc_dirty) {
         set_error("lb_adjoint_kinetic: pending particle impulses are not differentiated");
         return LB_EUNSUPPORTED;

@@ -16,6 +16,15 @@ cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *
 extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *);
 extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const void *, void *, const float *);
 extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *);
+template <int DT>
+cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
+                            int n, int nsub, unsigned int *claim, unsigned int tag);
+extern template cudaError_t launch_patch_dt<0>(const lb_handle *, const void *, void *, const float *, const int *,
+                                               int, int, unsigned int *, unsigned int);
+extern template cudaError_t launch_patch_dt<1>(const lb_handle *, const void *, void *, const float *, const int *,
+                                               int, int, unsigned int *, unsigned int);
+extern template cudaError_t launch_patch_dt<2>(const lb_handle *, const void *, void *, const float *, const int *,
+                                               int, int, unsigned int *, unsigned int);
 
 namespace {
 thread_local char g_msg[512] = "no error";
@@ -87,6 +96,24 @@ StepArgs make_args(const lb_handle *h)
     return a;
 }
 
+// An overlapped coupling is joined by the next lb_step; every other call on
+// the handle first orders its stream after it (the impulses then stay pending
+// and the next lb_step applies them in its single pass).
+void join_overlap(const lb_handle *hc)
+{
+    lb_handle *h = const_cast<lb_handle *>(hc);
+    if (!h || !h->overlap_pending) return;
+    cudaStreamWaitEvent(h->stream, h->ev_couple, 0);
+    h->overlap_pending = 0;
+}
+
+void timer_mark(lb_handle *h, int which, int end, cudaStream_t s)
+{
+    if (!h->timer_cap || h->timer_n[which] >= h->timer_cap) return;
+    cudaEventRecord(h->timer_ev[which][2 * h->timer_n[which] + end], s);
+    if (end) h->timer_n[which] += 1;
+}
+
 }  // namespace lbi
 
 using namespace lbi;
@@ -155,6 +182,19 @@ bool check_params(const lb_params *p)
 }
 
 bool aligned256(const void *ptr) { return ((uintptr_t)ptr & 255u) == 0; }
+
+void free_timers(lb_handle *h)
+{
+    for (int w = 0; w < 2; ++w) {
+        if (!h->timer_ev[w]) continue;
+        for (int i = 0; i < 2 * h->timer_cap; ++i)
+            if (h->timer_ev[w][i]) cudaEventDestroy(h->timer_ev[w][i]);
+        free(h->timer_ev[w]);
+        h->timer_ev[w] = nullptr;
+        h->timer_n[w] = 0;
+    }
+    h->timer_cap = 0;
+}
 
 }  // namespace
 
@@ -226,10 +266,71 @@ lb_status lb_create(const lb_params *p, void *pops_a, void *pops_b, float *force
     return LB_OK;
 }
 
+lb_status lb_set_timing(lb_handle *h, int capacity)
+{
+    if (!h || capacity < 0) {
+        set_error("lb_set_timing: need a handle and capacity >= 0");
+        return LB_EINVAL;
+    }
+    join_overlap(h);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    cudaStreamSynchronize(h->stream);
+    free_timers(h);
+    if (capacity == 0) return LB_OK;
+    for (int w = 0; w < 2; ++w) {
+        h->timer_ev[w] = (cudaEvent_t *)calloc(2 * (size_t)capacity, sizeof(cudaEvent_t));
+        if (!h->timer_ev[w]) {
+            free_timers(h);
+            set_error("lb_set_timing: host allocation failed");
+            return LB_ENOMEM;
+        }
+        for (int i = 0; i < 2 * capacity; ++i) {
+            if (cudaEventCreate(&h->timer_ev[w][i]) != cudaSuccess) {
+                h->timer_cap = capacity;
+                free_timers(h);
+                set_error("lb_set_timing: event creation failed");
+                return LB_ECUDA;
+            }
+        }
+    }
+    h->timer_cap = capacity;
+    return LB_OK;
+}
+
+lb_status lb_get_timing(lb_handle *h, double *ms_step, int *n_step, double *ms_couple, int *n_couple)
+{
+    if (!h) {
+        set_error("lb_get_timing: handle is NULL");
+        return LB_EINVAL;
+    }
+    double sum[2] = {0.0, 0.0};
+    for (int w = 0; w < 2; ++w) {
+        for (int i = 0; i < h->timer_n[w]; ++i) {
+            float ms = 0.0f;
+            cudaError_t e = cudaEventSynchronize(h->timer_ev[w][2 * i + 1]);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->timer_ev[w][2 * i], h->timer_ev[w][2 * i + 1]);
+            if (e != cudaSuccess) return cuda_fail("lb_get_timing", e);
+            sum[w] += ms;
+        }
+    }
+    if (ms_step) *ms_step = sum[0];
+    if (n_step) *n_step = h->timer_n[0];
+    if (ms_couple) *ms_couple = sum[1];
+    if (n_couple) *n_couple = h->timer_n[1];
+    return LB_OK;
+}
+
 lb_status lb_destroy(lb_handle *h)
 {
     if (!h) return LB_OK;
+    free_timers(h);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+    join_overlap(h);
     destroy_particles(h);
+    if (h->claim) cudaFree(h->claim);
+    if (h->ev_main) cudaEventDestroy(h->ev_main);
+    if (h->ev_couple) cudaEventDestroy(h->ev_couple);
+    if (h->aux) cudaStreamDestroy(h->aux);
     if (h->d_err) cudaFree(h->d_err);
     if (h->d_partials) cudaFree(h->d_partials);
     if (h->facc) cudaFree(h->facc);
@@ -243,6 +344,7 @@ lb_status lb_sync(lb_handle *h, uint32_t *bits)
         set_error("lb_sync: handle is NULL");
         return LB_EINVAL;
     }
+    join_overlap(h);
     unsigned int v = 0;
     cudaError_t e = cudaMemcpyAsync(&v, h->d_err, sizeof(v), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -290,6 +392,7 @@ lb_status lb_state_buffers(const lb_handle *h, void **current, void **other)
         set_error("lb_state_buffers: handle is NULL");
         return LB_EINVAL;
     }
+    join_overlap(h);
     if (current) *current = h->pops[h->cur];
     if (other) *other = h->pops[1 - h->cur];
     return LB_OK;
@@ -301,6 +404,7 @@ lb_status lb_init_equilibrium(lb_handle *h, const double *rho, const double *u)
         set_error("lb_init_equilibrium: handle is NULL");
         return LB_EINVAL;
     }
+    join_overlap(h);
     cudaError_t e = launch_init_equilibrium(h, h->pops[h->cur], rho, u);
     h->launches += 1;
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_init_equilibrium", e);
@@ -312,6 +416,7 @@ lb_status lb_set_populations(lb_handle *h, const double *n)
         set_error("lb_set_populations: NULL argument");
         return LB_EINVAL;
     }
+    join_overlap(h);
     cudaError_t e = launch_set_populations(h, h->pops[h->cur], n);
     h->launches += 1;
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_set_populations", e);
@@ -333,6 +438,7 @@ lb_status lb_get_populations(const lb_handle *h, double *n)
         set_error("lb_get_populations: NULL argument");
         return LB_EINVAL;
     }
+    join_overlap(h);
     cudaError_t e = launch_get_populations(h, h->pops[h->cur], n);
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_get_populations", e);
 }
@@ -348,13 +454,48 @@ lb_status lb_step(lb_handle *h, int nsteps)
         return LB_EINVAL;
     }
     for (int t = 0; t < nsteps; ++t) {
-        const float *facc = h->facc_dirty ? h->facc : nullptr;
+        const void *src = h->pops[h->cur];
+        void *dst = h->pops[1 - h->cur];
         cudaError_t e;
-        switch (h->p.dtype) {
-        case LB_F32: e = launch_stream_collide_dt<0>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
-        case LB_F16: e = launch_stream_collide_dt<1>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
-        default: e = launch_stream_collide_dt<2>(h, h->pops[h->cur], h->pops[1 - h->cur], facc); break;
+        if (h->overlap_pending) {
+            // all nodes without the impulses while the coupling runs on aux,
+            // then the nodes it spread impulses to, again with them
+            timer_mark(h, 0, 0, h->stream);
+            switch (h->p.dtype) {
+            case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr); break;
+            case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr); break;
+            default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr); break;
+            }
+            timer_mark(h, 0, 1, h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_couple, 0);
+            h->overlap_pending = 0;
+            if (++h->claim_tag == 0u) {  // wrapped: start the tags again from 1
+                if (e == cudaSuccess) e = cudaMemsetAsync(h->claim, 0, h->n_nodes * sizeof(unsigned int), h->stream);
+                h->claim_tag = 1u;
+            }
+            if (e == cudaSuccess) {
+                switch (h->p.dtype) {
+                case LB_F32: e = launch_patch_dt<0>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+                case LB_F16: e = launch_patch_dt<1>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+                default: e = launch_patch_dt<2>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+                }
+            }
+            if (e != cudaSuccess) return cuda_fail("lb_step", e);
+            h->launches += 2;
+            h->facc_dirty = 0;
+            h->facc_stale = 1;
+            h->cur = 1 - h->cur;
+            h->step += 1;
+            continue;
         }
+        const float *facc = h->facc_dirty ? h->facc : nullptr;
+        timer_mark(h, 0, 0, h->stream);
+        switch (h->p.dtype) {
+        case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, facc); break;
+        case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, facc); break;
+        default: e = launch_stream_collide_dt<2>(h, src, dst, facc); break;
+        }
+        timer_mark(h, 0, 1, h->stream);
         if (e != cudaSuccess) return cuda_fail("lb_step", e);
         h->launches += 1;
         if (facc) {  // applied once; cleared by the next lb_couple_particles
@@ -373,6 +514,7 @@ lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums
         set_error("lb_moments: handle is NULL");
         return LB_EINVAL;
     }
+    join_overlap(h);
     if (!rho && !j && !pi && !sums) return LB_OK;
     cudaError_t e = launch_moments(h, h->pops[h->cur], rho, j, pi, sums);
     h->launches += sums ? 2 : 1;
@@ -394,6 +536,7 @@ lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out)
         set_error("lb_interpolate: bad argument");
         return LB_EINVAL;
     }
+    join_overlap(h);
     return interpolate(h, n, pos, u_out);
 }
 
@@ -403,6 +546,7 @@ lb_status lb_get_particle_forces(lb_handle *h, float *out)
         set_error("lb_get_particle_forces: NULL argument");
         return LB_EINVAL;
     }
+    join_overlap(h);
     const size_t N = h->n_nodes;
     cudaError_t e = cudaSuccess;
     for (int d = 0; d < 3 && e == cudaSuccess; ++d) {

@@ -58,6 +58,21 @@ struct lb_handle {
     int facc_stale;       // facc holds applied impulses not yet cleared
     uint64_t launches;    // kernels launched through this handle
     lbi::Particles *parts;
+    // an overlapped coupling (LB_COUPLE_OVERLAP) runs on `aux` while the next
+    // lb_step updates all nodes without its impulses, then re-updates the
+    // nodes of its stencil records with them
+    cudaStream_t aux;     // high-priority stream, created on first use
+    cudaEvent_t ev_main, ev_couple;
+    int overlap_pending;  // a coupling on aux the next lb_step (or any other call) joins
+    const int *patch_rec; // its stencil records [patch_nsub][patch_n]
+    int patch_n, patch_nsub;
+    unsigned int *claim;  // [n_nodes] tag of the last re-update of each node
+    unsigned int claim_tag;
+    // kernel timers (lb_set_timing): event pairs around stream-collide
+    // launches [0] and coupling calls [1]
+    int timer_cap;
+    int timer_n[2];
+    cudaEvent_t *timer_ev[2];  // [2 * timer_cap] each
 };
 
 namespace lbi {
@@ -79,6 +94,8 @@ cudaError_t launch_moments(const lb_handle *h, const void *src, float *rho, floa
 lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
 lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out);
 cudaError_t clear_particle_forces(lb_handle *h);
+void join_overlap(const lb_handle *h);  // order h->stream after a pending overlapped coupling
+void timer_mark(lb_handle *h, int which, int end, cudaStream_t s);  // record a timer event
 cudaError_t reset_particle_barrier(lb_handle *h);
 void destroy_particles(lb_handle *h);
 

@@ -822,7 +822,7 @@ lb_status ensure_buffers(lb_handle *h, int n, int nsub)
 // and rebuilds its list from the cell list at the next sub-step.
 // ---------------------------------------------------------------------------
 constexpr int kPThreads = 128;   // particles per block of the persistent kernel
-constexpr int kNbReg = 16;       // Verlet neighbours held in registers
+constexpr int kNbReg = 8;        // Verlet neighbours held in registers
 constexpr unsigned kFullMask = 0xffffffffu;
 
 struct PersistArgs {
@@ -1360,7 +1360,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
 
 lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
-    if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~LB_COUPLE_PER_SUBSTEP) != 0) {
+    if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~(LB_COUPLE_PER_SUBSTEP | LB_COUPLE_OVERLAP)) != 0) {
         set_error("lb_couple_particles: bad particle count, reserved field or flags");
         return LB_EINVAL;
     }
@@ -1397,18 +1397,57 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         set_error("lb_couple_particles: misaligned pos or mom");
         return LB_EINVAL;
     }
+    join_overlap(h);  // a coupling of this step that has not been joined yet
+    const bool overlap = (cp->flags & LB_COUPLE_OVERLAP) != 0;
+    cudaStream_t main_stream = h->stream;
+    if (overlap) {
+        // run on the handle's high-priority stream after everything queued on
+        // the main stream so far
+        cudaError_t e = cudaSuccess;
+        if (!h->aux) {
+            int lo = 0, hi = 0;
+            e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+            if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_couple, cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess && !h->claim) {
+            e = cudaMalloc((void **)&h->claim, h->n_nodes * sizeof(unsigned int));
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->claim, 0, h->n_nodes * sizeof(unsigned int), main_stream);
+            h->claim_tag = 0u;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_main, main_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_main, 0);
+        if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
+        h->stream = h->aux;
+    }
+    struct Restore {  // the main stream comes back on every return
+        lb_handle *h;
+        cudaStream_t s;
+        ~Restore() { h->stream = s; }
+    } restore{h, main_stream};
     lb_status st = ensure_buffers(h, pp->n, cp->n_substeps);
     if (st != LB_OK) return st;
     cudaError_t e;
     // impulses of the previous call that lb_step already applied are cleared
     // inside run_substeps (by the persistent kernel, or by k_clear_records)
+    timer_mark(h, 1, 0, h->stream);
     switch (h->p.dtype) {
     case LB_F32: e = run_substeps<0>(h, pp, cp); break;
     case LB_F16: e = run_substeps<1>(h, pp, cp); break;
     default: e = run_substeps<2>(h, pp, cp); break;
     }
+    timer_mark(h, 1, 1, h->stream);
+    if (e == cudaSuccess && overlap) e = cudaEventRecord(h->ev_couple, h->aux);
     if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
     h->facc_dirty = 1;
+    if (overlap) {
+        Particles *P = h->parts;
+        h->overlap_pending = 1;
+        h->patch_n = pp->n;
+        h->patch_nsub = cp->n_substeps;
+        h->patch_rec = P->records + P->rec_off + P->n_records - (size_t)pp->n * (size_t)cp->n_substeps;
+    }
     return LB_OK;
 }
 

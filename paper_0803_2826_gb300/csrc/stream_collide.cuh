@@ -85,17 +85,14 @@ __device__ __forceinline__ void collide_node(const float n[19], float fx, float 
     lbd::backward(M, out);
 }
 
+// The whole update of fluid node (x, y, z): pull, force, collision, store.
 template <int DT, bool NOISE, bool FIELD, bool WALLS>
-__global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Store<DT>::T *__restrict__ src,
-                                                        typename lbd::Store<DT>::T *__restrict__ dst,
-                                                        const float *__restrict__ ffield,
-                                                        const float *__restrict__ facc, const StepArgs a)
+__device__ __forceinline__ void update_node(const typename lbd::Store<DT>::T *__restrict__ src,
+                                            typename lbd::Store<DT>::T *__restrict__ dst,
+                                            const float *__restrict__ ffield, const float *__restrict__ facc,
+                                            const StepArgs &a, int x, int y, int z)
 {
     using S = lbd::Store<DT>;
-    const int x = blockIdx.x * kBX + threadIdx.x;
-    if (x >= a.nx) return;
-    const int y = blockIdx.y;
-    const int z = blockIdx.z + a.z0;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int xm = (x == 0) ? nx - 1 : x - 1;
     const int xp = (x == nx - 1) ? 0 : x + 1;
@@ -147,6 +144,56 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
     collide_node<NOISE>(n, fx, fy, fz, a, a.rk, self, a.replica, out);
 #pragma unroll
     for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
+}
+
+template <int DT, bool NOISE, bool FIELD, bool WALLS>
+__global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Store<DT>::T *__restrict__ src,
+                                                        typename lbd::Store<DT>::T *__restrict__ dst,
+                                                        const float *__restrict__ ffield,
+                                                        const float *__restrict__ facc, const StepArgs a)
+{
+    const int x = blockIdx.x * kBX + threadIdx.x;
+    if (x >= a.nx) return;
+    update_node<DT, NOISE, FIELD, WALLS>(src, dst, ffield, facc, a, x, blockIdx.y, blockIdx.z + a.z0);
+}
+
+// Re-update of the nodes that received particle impulses, after an update of
+// all nodes that left the impulses out (the coupling ran meanwhile): the 8
+// stencil nodes of each cell particle p visited, records[s][p] (linear cell
+// index at sub-step s), are updated again from the same pre-step state with
+// the impulses added.  The update of a node depends only on that state, the
+// forces at the node and the counter-based noise, so the result is the one a
+// single update with the impulses would give.  Thread (p, q) walks p's
+// distinct cells and takes stencil node q of each; a node shared by several
+// particles is updated once, by the thread that raises its tag to `tag`
+// first (tags grow by one per patch, so the array is never cleared).
+template <int DT, bool NOISE, bool WALLS>
+__global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd::Store<DT>::T *__restrict__ src,
+                                                             typename lbd::Store<DT>::T *__restrict__ dst,
+                                                             const float *__restrict__ ffield,
+                                                             const float *__restrict__ facc, const int *records,
+                                                             int n, int nsub, unsigned int *claim, unsigned int tag,
+                                                             const StepArgs a)
+{
+    const int t = blockIdx.x * kBX + threadIdx.x;
+    if (t >= n * 8) return;
+    const int p = t >> 3, q = t & 7;
+    int prev = -1;
+    for (int s = 0; s < nsub; ++s) {
+        const int base = records[(size_t)s * n + p];
+        if (base == prev) continue;  // same cell as the sub-step before
+        prev = base;
+        int x = base % a.nx + (q & 1);
+        int y = (base / a.nx) % a.ny + ((q >> 1) & 1);
+        int z = base / (a.nx * a.ny) + (q >> 2);
+        if (x >= a.nx) x -= a.nx;
+        if (y >= a.ny) y -= a.ny;
+        if (!WALLS && z >= a.nz) z -= a.nz;
+        if (z < a.z0 || z >= a.z1) continue;  // solid node
+        const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
+        if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
+        update_node<DT, NOISE, true, WALLS>(src, dst, ffield, facc, a, x, y, z);
+    }
 }
 
 // Two neighbouring nodes x0 = 2t, x0 + 1 per thread (even nx).  Both pull
@@ -310,6 +357,28 @@ cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *
         }
     }
 #undef LBI_SC
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
+                            int n, int nsub, unsigned int *claim, unsigned int tag)
+{
+    using T = typename lbd::Store<DT>::T;
+    const StepArgs a = make_args(h);
+    if (n <= 0 || nsub <= 0) return cudaSuccess;
+    const unsigned int blocks = (unsigned int)(((size_t)n * 8 + kBX - 1) / kBX);
+    const T *s = static_cast<const T *>(src);
+    T *d = static_cast<T *>(dst);
+    const bool noise = a.kT > 0.0f, walls = h->p.walls != 0;
+#define LBI_PATCH(NZ, WL) \
+    k_patch_impulse_nodes<DT, NZ, WL><<<blocks, kBX, 0, h->stream>>>(s, d, h->force, facc, records, n, nsub, claim, tag, a)
+    if (noise) {
+        if (walls) LBI_PATCH(true, true); else LBI_PATCH(true, false);
+    } else {
+        if (walls) LBI_PATCH(false, true); else LBI_PATCH(false, false);
+    }
+#undef LBI_PATCH
     return cudaGetLastError();
 }
 

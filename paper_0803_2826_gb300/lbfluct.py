@@ -23,7 +23,7 @@ LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
 LB_DERR_PARTICLE_RANGE = 16
-LB_COUPLE_PER_SUBSTEP = 1
+LB_COUPLE_PER_SUBSTEP, LB_COUPLE_OVERLAP = 1, 2
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
                 5: "LB_ETIMEOUT", 6: "LB_EUNSUPPORTED", 7: "LB_EDEVICE"}
@@ -34,6 +34,7 @@ EXPORTS = (
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
+    "lb_set_timing", "lb_get_timing",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
     "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
     "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
@@ -124,6 +125,8 @@ def load(path: str | None = None):
             "lb_get_particle_forces": (i, [H, vp]),
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_box_muller": (i, [vp, i, vp, vp]),
+            "lb_set_timing": (i, [H, i]),
+            "lb_get_timing": (i, [H, C.POINTER(C.c_double), C.POINTER(i), C.POINTER(C.c_double), C.POINTER(i)]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
             "lb_moment_sums_static": (i, [P, vp, vp, vp]),
             "lb_step_from": (i, [H, vp, vp, u32]),
@@ -291,6 +294,18 @@ def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, g
 
 def lb_box_muller(words, npairs, gauss, stream=None):
     _check(load().lb_box_muller(_ptr(words), int(npairs), _ptr(gauss), _stream(stream)))
+
+
+def lb_set_timing(h, capacity):
+    _check(load().lb_set_timing(h, int(capacity)))
+
+
+def lb_get_timing(h):
+    """(ms summed over stream-collide launches, their count, ms over coupling calls, their count)."""
+    a, b = C.c_double(), C.c_double()
+    na, nb = C.c_int(), C.c_int()
+    _check(load().lb_get_timing(h, C.byref(a), C.byref(na), C.byref(b), C.byref(nb)))
+    return a.value, na.value, b.value, nb.value
 
 
 def lb_get_launch_count(h) -> int:
@@ -537,11 +552,12 @@ def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_p
 
 
 def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len=0, use_wca=False,
-                  eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5, per_substep=False) -> lb_couple_params:
+                  eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5, per_substep=False,
+                  overlap=False) -> lb_couple_params:
     c = lb_couple_params()
     c.n_substeps, c.noise_kind, c.dt = int(n_substeps), int(noise_kind), float(dt)
     c.seed, c.md_step0 = int(seed), int(md_step0) & 0xffffffff
     c.chain_len, c.use_wca = int(chain_len), int(bool(use_wca))
-    c.flags = LB_COUPLE_PER_SUBSTEP if per_substep else 0
+    c.flags = (LB_COUPLE_PER_SUBSTEP if per_substep else 0) | (LB_COUPLE_OVERLAP if overlap else 0)
     c.eps, c.sigma, c.k_fene, c.r0 = float(eps), float(sigma), float(k_fene), float(r0)
     return c

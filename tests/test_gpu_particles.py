@@ -227,3 +227,59 @@ def test_fast_wca_particles_rebuild_lists(ora, per_substep):
     assert lat.sync() == (L.LB_OK, 0)
     assert _pos_err(gpos.cpu().numpy(), opos, shape) < 2e-5
     assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 1e-3
+
+
+def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False):
+    """`steps` rounds of couple + step in a thermal fluid: FENE + WCA chains
+    (periodic box) or single WCA particles between walls."""
+    if walls:  # z in [1, nz - 2): no bond may cross the walls
+        n_ch, clen = 192, 1
+        pos = inputs.random_walk_chains(n_ch, 1, (shape[0], shape[1], shape[2] - 3), min_dist=1.0, seed=51)
+        pos[:, 2] += 1.0
+    else:
+        n_ch, clen = 6, 32
+        pos = inputs.random_walk_chains(n_ch, clen, shape, seed=51)
+    n = pos.shape[0]
+    mom = inputs.maxwell_momenta(n, 1.0, 2e-3, seed=52).astype(np.float32)  # fast: cells change
+    lat = L.Lattice(shape, kT=1e-4, seed=6, walls=walls, body_force=(1e-5, 0.0, 0.0))
+    lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+    gpos, gmom = dev(pos), dev(mom, torch.float32)
+    parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
+    forces = []
+    for t in range(steps):
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, chain_len=clen, use_wca=True,
+                             eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=overlap)
+        L.lb_couple_particles(lat.h, parts, cp)
+        if join_early:
+            f = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
+            L.lb_get_particle_forces(lat.h, f)
+            forces.append(f.cpu().numpy())
+        lat.step(1)
+    assert lat.sync() == (L.LB_OK, 0)
+    return lat.get_populations().cpu().numpy(), gpos.cpu().numpy(), gmom.cpu().numpy(), forces
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_overlapped_coupling_matches_serial(walls):
+    """LB_COUPLE_OVERLAP: the step's update of all nodes without the impulses
+    (concurrent with the coupling) plus the re-update of the visited stencil
+    nodes gives the serial result (up to the order of the impulse atomics)."""
+    shape = (20, 18, 16)
+    a = _coupled_run(shape, walls=walls, overlap=False)
+    b = _coupled_run(shape, walls=walls, overlap=True)
+    # FP32 deviations ~1e-2: a few ulps where the impulse sums round differently
+    assert np.abs(a[0] - b[0]).max() < 1e-7
+    assert _pos_err(a[1], b[1], shape) < 1e-7
+    assert np.abs(a[2] - b[2]).max() < 1e-7
+
+
+def test_overlapped_coupling_joined_by_another_call():
+    """A call between the overlapped coupling and lb_step (here
+    lb_get_particle_forces) waits for the coupling; the step then applies
+    the impulses in its single pass."""
+    shape = (20, 18, 16)
+    a = _coupled_run(shape, walls=False, overlap=False, join_early=True)
+    b = _coupled_run(shape, walls=False, overlap=True, join_early=True)
+    for fa, fb in zip(a[3], b[3]):
+        assert np.abs(fa - fb).max() < 1e-9 and np.abs(fa).max() > 0
+    assert np.abs(a[0] - b[0]).max() < 1e-7
