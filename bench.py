@@ -271,10 +271,13 @@ def run_ours(args):
                          eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=not args.serial)
     t_step = [0]
 
-    def one_step():
+    def one_step(sums=None):
         cp.md_step0 = (NSUB * t_step[0]) & 0xffffffff
         L.lb_couple_particles(lat.h, parts, cp)
-        L.lb_step(lat.h, 1)
+        if sums is None:
+            L.lb_step(lat.h, 1)
+        else:  # the step also returns the moment sums of the state it started from
+            L.lb_step_sums(lat.h, 1, sums)
         t_step[0] += 1
 
     with torch.cuda.stream(stream):
@@ -315,7 +318,8 @@ def run_ours(args):
 
     # end to end through the public API with host buffers: per step the
     # particle state goes host -> device from pinned memory, and the particle
-    # state plus the moment sums come back
+    # state plus the moment sums (the 38 sums of lb_moments, accumulated by
+    # the step's stream-collide launch) come back
     KE = min(args.e2e_steps, K)
     hpos = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
     hmom = torch.empty((npart, 3), dtype=torch.float32, pin_memory=True)
@@ -330,8 +334,7 @@ def run_ours(args):
         for _ in range(KE):
             gpos.copy_(hpos, non_blocking=True)
             gmom.copy_(hmom, non_blocking=True)
-            one_step()
-            L.lb_moments(lat.h, None, None, None, dsums)
+            one_step(dsums)
             hpos.copy_(gpos, non_blocking=True)
             hmom.copy_(gmom, non_blocking=True)
             hsums.copy_(dsums, non_blocking=True)

@@ -138,7 +138,9 @@ lb_status lb_state_buffers(const lb_handle *h, void **current, void **other);
 lb_status lb_init_equilibrium(lb_handle *h, const double *rho, const double *u);
 
 /* Copy raw populations n_i (device FP64 [19][N]) into / out of the stored
- * state, converting to / from the storage format. */
+ * state, converting to / from the storage format.  With walls the solid
+ * planes z = 0 and nz-1 hold no state: lb_get_populations reports the rest
+ * state a_i rho0 there. */
 lb_status lb_set_populations(lb_handle *h, const double *n);
 lb_status lb_get_populations(const lb_handle *h, double *n);
 
@@ -156,6 +158,18 @@ lb_status lb_get_populations(const lb_handle *h, double *n);
  * + the impulses spread by the last lb_couple_particles (applied once).
  * Errors: LB_EINVAL, LB_ECUDA. */
 lb_status lb_step(lb_handle *h, int nsteps);
+
+/* lb_step for nsteps >= 1 steps, whose last stream-collide launch also
+ * accumulates the LB_NSUMS moment sums of lb_moments (sum over fluid nodes
+ * of dm_k and dm_k^2, dm_k = sum_i e_ki (n_i - a_i rho0), Table 1) of the
+ * state that last step starts from -- the values lb_moments(..., sums) would
+ * give just before it -- into `sums` (device FP64 [LB_NSUMS]), without a
+ * separate pass over the populations.  Per-block partial sums in library
+ * scratch are reduced in a fixed order, so the result is reproducible
+ * (it differs from lb_moments' in summation order only).  The paper has no
+ * counterpart (a monitoring shortcut).  Errors: LB_EINVAL, LB_ENOMEM, LB_ECUDA;
+ * non-finite sums set LB_DERR_NONFINITE. */
+lb_status lb_step_sums(lb_handle *h, int nsteps, double *sums);
 
 /* Hydrodynamic moments of the pre-collision state (pull of the stored state):
  * rho[N], j[3][N] = sum n c + f_ext/2, pi[6][N] = sum n c c (Eqs. (hmodes_beg)-

@@ -27,7 +27,7 @@
 namespace lbi {
 
 template <int DT>
-cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc);
+cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc, float *partials);
 
 namespace {
 
@@ -298,9 +298,9 @@ cudaError_t step_from(lb_handle *h, const void *src, void *dst, uint32_t step)
     h->step = step;
     cudaError_t e;
     switch (h->p.dtype) {
-    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr); break;
-    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr); break;
-    default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr); break;
+    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr, nullptr); break;
+    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr, nullptr); break;
+    default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr, nullptr); break;
     }
     h->step = saved;
     return e;

@@ -12,10 +12,10 @@
 namespace lbi {
 
 template <int DT>
-cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc);
-extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *);
-extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const void *, void *, const float *);
-extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *);
+cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc, float *partials);
+extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *, float *);
+extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const void *, void *, const float *, float *);
+extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *, float *);
 template <int DT>
 cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
                             int n, int nsub, unsigned int *claim, unsigned int tag);
@@ -196,6 +196,62 @@ void free_timers(lb_handle *h)
     h->timer_cap = 0;
 }
 
+// One step; with partials != NULL the stream-collide launch also writes its
+// per-block moment sums there.
+lb_status step_once(lb_handle *h, float *partials)
+{
+    const void *src = h->pops[h->cur];
+    void *dst = h->pops[1 - h->cur];
+    cudaError_t e;
+    if (h->overlap_pending) {
+        // all nodes without the impulses while the coupling runs on aux,
+        // then the nodes it spread impulses to, again with them
+        timer_mark(h, 0, 0, h->stream);
+        switch (h->p.dtype) {
+        case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr, partials); break;
+        case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr, partials); break;
+        default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr, partials); break;
+        }
+        timer_mark(h, 0, 1, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_couple, 0);
+        h->overlap_pending = 0;
+        if (++h->claim_tag == 0u) {  // wrapped: start the tags again from 1
+            if (e == cudaSuccess) e = cudaMemsetAsync(h->claim, 0, h->n_nodes * sizeof(unsigned int), h->stream);
+            h->claim_tag = 1u;
+        }
+        if (e == cudaSuccess) {
+            switch (h->p.dtype) {
+            case LB_F32: e = launch_patch_dt<0>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+            case LB_F16: e = launch_patch_dt<1>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+            default: e = launch_patch_dt<2>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+            }
+        }
+        if (e != cudaSuccess) return cuda_fail("lb_step", e);
+        h->launches += 2;
+        h->facc_dirty = 0;
+        h->facc_stale = 1;
+        h->cur = 1 - h->cur;
+        h->step += 1;
+        return LB_OK;
+    }
+    const float *facc = h->facc_dirty ? h->facc : nullptr;
+    timer_mark(h, 0, 0, h->stream);
+    switch (h->p.dtype) {
+    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, facc, partials); break;
+    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, facc, partials); break;
+    default: e = launch_stream_collide_dt<2>(h, src, dst, facc, partials); break;
+    }
+    timer_mark(h, 0, 1, h->stream);
+    if (e != cudaSuccess) return cuda_fail("lb_step", e);
+    h->launches += 1;
+    if (facc) {  // applied once; cleared by the next lb_couple_particles
+        h->facc_dirty = 0;
+        h->facc_stale = 1;
+    }
+    h->cur = 1 - h->cur;
+    h->step += 1;
+    return LB_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -328,6 +384,7 @@ lb_status lb_destroy(lb_handle *h)
     join_overlap(h);
     destroy_particles(h);
     if (h->claim) cudaFree(h->claim);
+    if (h->sc_partials) cudaFree(h->sc_partials);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     if (h->ev_couple) cudaEventDestroy(h->ev_couple);
     if (h->aux) cudaStreamDestroy(h->aux);
@@ -454,57 +511,40 @@ lb_status lb_step(lb_handle *h, int nsteps)
         return LB_EINVAL;
     }
     for (int t = 0; t < nsteps; ++t) {
-        const void *src = h->pops[h->cur];
-        void *dst = h->pops[1 - h->cur];
-        cudaError_t e;
-        if (h->overlap_pending) {
-            // all nodes without the impulses while the coupling runs on aux,
-            // then the nodes it spread impulses to, again with them
-            timer_mark(h, 0, 0, h->stream);
-            switch (h->p.dtype) {
-            case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr); break;
-            case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr); break;
-            default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr); break;
-            }
-            timer_mark(h, 0, 1, h->stream);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, h->ev_couple, 0);
-            h->overlap_pending = 0;
-            if (++h->claim_tag == 0u) {  // wrapped: start the tags again from 1
-                if (e == cudaSuccess) e = cudaMemsetAsync(h->claim, 0, h->n_nodes * sizeof(unsigned int), h->stream);
-                h->claim_tag = 1u;
-            }
-            if (e == cudaSuccess) {
-                switch (h->p.dtype) {
-                case LB_F32: e = launch_patch_dt<0>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
-                case LB_F16: e = launch_patch_dt<1>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
-                default: e = launch_patch_dt<2>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
-                }
-            }
-            if (e != cudaSuccess) return cuda_fail("lb_step", e);
-            h->launches += 2;
-            h->facc_dirty = 0;
-            h->facc_stale = 1;
-            h->cur = 1 - h->cur;
-            h->step += 1;
-            continue;
-        }
-        const float *facc = h->facc_dirty ? h->facc : nullptr;
-        timer_mark(h, 0, 0, h->stream);
-        switch (h->p.dtype) {
-        case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, facc); break;
-        case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, facc); break;
-        default: e = launch_stream_collide_dt<2>(h, src, dst, facc); break;
-        }
-        timer_mark(h, 0, 1, h->stream);
-        if (e != cudaSuccess) return cuda_fail("lb_step", e);
-        h->launches += 1;
-        if (facc) {  // applied once; cleared by the next lb_couple_particles
-            h->facc_dirty = 0;
-            h->facc_stale = 1;
-        }
-        h->cur = 1 - h->cur;
-        h->step += 1;
+        const lb_status st = step_once(h, nullptr);
+        if (st != LB_OK) return st;
     }
+    return LB_OK;
+}
+
+lb_status lb_step_sums(lb_handle *h, int nsteps, double *sums)
+{
+    if (!h || !sums || nsteps < 1) {
+        set_error("lb_step_sums: need a handle, a sums buffer and nsteps >= 1");
+        return LB_EINVAL;
+    }
+    const size_t nb = sc_block_count(h);
+    const size_t len = nb * 38 + step_sums_scratch(nb);
+    if (h->sc_partials_len < len) {
+        cudaFree(h->sc_partials);
+        h->sc_partials = nullptr;
+        h->sc_partials_len = 0;
+        const cudaError_t e = cudaMalloc((void **)&h->sc_partials, len * sizeof(float));
+        if (e != cudaSuccess) {
+            set_error("lb_step_sums: scratch allocation failed (%s)", cudaGetErrorString(e));
+            return LB_ENOMEM;
+        }
+        h->sc_partials_len = len;
+    }
+    for (int t = 0; t + 1 < nsteps; ++t) {
+        const lb_status st = step_once(h, nullptr);
+        if (st != LB_OK) return st;
+    }
+    const lb_status st = step_once(h, h->sc_partials);
+    if (st != LB_OK) return st;
+    const cudaError_t e = reduce_step_sums(h, h->sc_partials, nb, h->sc_partials + nb * 38, sums);
+    if (e != cudaSuccess) return cuda_fail("lb_step_sums", e);
+    h->launches += 2;
     return LB_OK;
 }
 

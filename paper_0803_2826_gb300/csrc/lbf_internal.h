@@ -68,6 +68,8 @@ struct lb_handle {
     int patch_n, patch_nsub;
     unsigned int *claim;  // [n_nodes] tag of the last re-update of each node
     unsigned int claim_tag;
+    float *sc_partials;   // lb_step_sums: [blocks][38] per-block sums, then reduction scratch
+    size_t sc_partials_len;
     // kernel timers (lb_set_timing): event pairs around stream-collide
     // launches [0] and coupling calls [1]
     int timer_cap;
@@ -95,6 +97,11 @@ lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_cou
 lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out);
 cudaError_t clear_particle_forces(lb_handle *h);
 void join_overlap(const lb_handle *h);  // order h->stream after a pending overlapped coupling
+// step_sums.cu
+size_t sc_block_count(const lb_handle *h);
+size_t step_sums_scratch(size_t nblocks);
+cudaError_t reduce_step_sums(const lb_handle *h, const float *partials, size_t nblocks, float *scratch,
+                             double *sums);
 void timer_mark(lb_handle *h, int which, int end, cudaStream_t s);  // record a timer event
 cudaError_t reset_particle_barrier(lb_handle *h);
 void destroy_particles(lb_handle *h);

@@ -67,12 +67,15 @@ __global__ void k_get_populations(const typename lbd::Store<DT>::T *src, double 
 {
     using S = lbd::Store<DT>;
     const size_t N = a.nn;
+    const size_t plane = (size_t)a.nx * a.ny;
     for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < N;
          s += (size_t)gridDim.x * blockDim.x) {
+        const int z = (int)(s / plane);
+        const bool solid = z < a.z0 || z >= a.z1;  // wall nodes hold no state: the rest state
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const double ai = (i == 0) ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
-            const float dev = S::cvt(src[(size_t)i * a.pitch + s], a.inv_scale);
+            const float dev = solid ? 0.0f : S::cvt(src[(size_t)i * a.pitch + s], a.inv_scale);
             n[(size_t)i * N + s] = ai * (double)a.rho0 + (double)dev;
         }
     }

@@ -21,17 +21,16 @@ namespace lbi {
 
 constexpr int kBX = 128;  // threads per block along x
 
+
 // Collision of one node (Sec. 3.4, 3.5, 3.7) from its pulled populations n
 // (deviations n_i - a_i rho0) and the force density (fx, fy, fz) to the
 // post-collision deviations out.  Physics constants come from a; the noise
 // stream is Philox with round keys rk and counter (node, a.step, b, replica).
 template <bool NOISE>
-__device__ __forceinline__ void collide_node(const float n[19], float fx, float fy, float fz, const StepArgs &a,
-                                             const lbd::RoundKeys &rk, uint32_t node, uint32_t replica,
-                                             float out[19])
+__device__ __forceinline__ void collide_moments(const float m[19], float fx, float fy, float fz, const StepArgs &a,
+                                                const lbd::RoundKeys &rk, uint32_t node, uint32_t replica,
+                                                float out[19])
 {
-    float m[19];
-    lbd::forward(n, m);
     const float rho = a.rho0 + m[0];
     const float inv_rho = 1.0f / rho;
     const float ux = (m[1] + 0.5f * fx) * inv_rho;
@@ -85,12 +84,96 @@ __device__ __forceinline__ void collide_node(const float n[19], float fx, float 
     lbd::backward(M, out);
 }
 
+// The same from the pulled populations n (deviations n_i - a_i rho0).
+template <bool NOISE>
+__device__ __forceinline__ void collide_node(const float n[19], float fx, float fy, float fz, const StepArgs &a,
+                                             const lbd::RoundKeys &rk, uint32_t node, uint32_t replica,
+                                             float out[19])
+{
+    float m[19];
+    lbd::forward(n, m);
+    collide_moments<NOISE>(m, fx, fy, fz, a, rk, node, replica, out);
+}
+
+// One step of a butterfly reduce-scatter over the warp: each lane keeps one
+// half of its N values (the upper half if `hi`), receives the other lane's
+// copy of that half and adds it, so the lanes now hold disjoint halves.
+template <int N>
+__device__ __forceinline__ void butterfly_half(const float *in, float *out, int offset, bool hi)
+{
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+        const float keep = hi ? in[i + N / 2] : in[i];
+        const float send = hi ? in[i] : in[i + N / 2];
+        out[i] = keep + __shfl_xor_sync(0xffffffffu, send, offset);
+    }
+}
+
+// Moment sums of a warp: lane l holds 38 values (m0_k + m1_k, then
+// m0_k^2 + m1_k^2; zeros where valid is false), the warp needs their 38 sums.
+// Five butterfly steps halve the values per lane (40 -> 20 -> 10 -> 5, padded
+// to 6 -> 3, padded to 4 -> 2), each sum is formed in a fixed order, and the
+// lane that ends with sum k writes it to part[warp][k].  After a
+// __syncthreads the block's sums are part[0] + ... + part[kBX/32 - 1]
+// (block_moment_sums_out).  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_moment_sums(const float m0[19], const float m1[19], bool valid,
+                                                 float (*part)[38])
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float a[40];
+#pragma unroll
+    for (int k = 0; k < 19; ++k) {
+        a[k] = m0[k] + m1[k];
+        a[19 + k] = fmaf(m0[k], m0[k], m1[k] * m1[k]);
+    }
+    a[38] = a[39] = 0.0f;
+    if (!__all_sync(0xffffffffu, valid)) {  // a warp at the end of a row
+#pragma unroll
+        for (int k = 0; k < 38; ++k) a[k] = valid ? a[k] : 0.0f;
+    }
+    float b[20], c[10], d[6], e[4], f[2];
+    butterfly_half<40>(a, b, 16, lane & 16);
+    butterfly_half<20>(b, c, 8, lane & 8);
+    butterfly_half<10>(c, d, 4, lane & 4);
+    d[5] = 0.0f;
+    butterfly_half<6>(d, e, 2, lane & 2);
+    e[3] = 0.0f;
+    butterfly_half<4>(e, f, 1, lane & 1);
+    // lane l holds, for j = 0, 1, the sum of entry k = base + b1 3 + pos of
+    // the 5-entry block base = 20 b4 + 10 b3 + 5 b2, pos = 2 b0 + j (b_i the
+    // bits of l); pos 3 and block entries 5 and beyond are padding
+    const int base = 20 * ((lane >> 4) & 1) + 10 * ((lane >> 3) & 1) + 5 * ((lane >> 2) & 1);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int pos = 2 * (lane & 1) + j;
+        const int idx = 3 * ((lane >> 1) & 1) + pos;
+        const int k = base + idx;
+        if (pos < 3 && idx < 5 && k < 38) part[warp][k] = f[j];
+    }
+}
+
+// FP32 throughout: FP64 arithmetic is slow on this part, and a block that
+// ends in a chain of FP64 adds holds its SM slot meanwhile.
+__device__ __forceinline__ void block_moment_sums_out(const float (*part)[38], float *out)
+{
+    __syncthreads();
+    if (threadIdx.x < 38) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < kBX / 32; ++w) t += part[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+}
+
 // The whole update of fluid node (x, y, z): pull, force, collision, store.
-template <int DT, bool NOISE, bool FIELD, bool WALLS>
+// SUMS: the warp's moment sums go to part (see warp_moment_sums); every
+// lane calls, lanes without a node (valid false) add zeros.
+template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS = false>
 __device__ __forceinline__ void update_node(const typename lbd::Store<DT>::T *__restrict__ src,
                                             typename lbd::Store<DT>::T *__restrict__ dst,
                                             const float *__restrict__ ffield, const float *__restrict__ facc,
-                                            const StepArgs &a, int x, int y, int z)
+                                            const StepArgs &a, int x, int y, int z, bool valid = true,
+                                            float (*part)[38] = nullptr)
 {
     using S = lbd::Store<DT>;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
@@ -140,21 +223,45 @@ __device__ __forceinline__ void update_node(const typename lbd::Store<DT>::T *__
             fz += __ldg(facc + 2 * P + self);
         }
     }
-    float out[19];
-    collide_node<NOISE>(n, fx, fy, fz, a, a.rk, self, a.replica, out);
+    float m[19], out[19];
+    lbd::forward(n, m);
+    if (SUMS) {
+        float none[19];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) none[k] = 0.0f;
+        warp_moment_sums(m, none, valid, part);
+    }
+    if (!valid) return;
+    collide_moments<NOISE>(m, fx, fy, fz, a, a.rk, self, a.replica, out);
 #pragma unroll
     for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
 }
 
-template <int DT, bool NOISE, bool FIELD, bool WALLS>
+__device__ __forceinline__ size_t block_linear()
+{
+    return blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+}
+
+// SUMS: the block also writes the moment sums of its nodes (pre-collision,
+// as lb_moments defines them) to partials[block][38].
+template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS>
 __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Store<DT>::T *__restrict__ src,
                                                         typename lbd::Store<DT>::T *__restrict__ dst,
                                                         const float *__restrict__ ffield,
-                                                        const float *__restrict__ facc, const StepArgs a)
+                                                        const float *__restrict__ facc, const StepArgs a,
+                                                        float *partials)
 {
     const int x = blockIdx.x * kBX + threadIdx.x;
-    if (x >= a.nx) return;
-    update_node<DT, NOISE, FIELD, WALLS>(src, dst, ffield, facc, a, x, blockIdx.y, blockIdx.z + a.z0);
+    if (SUMS) {
+        __shared__ float part[kBX / 32][38];
+        const bool valid = x < a.nx;  // lanes past the row load node 0 of it and store nothing
+        update_node<DT, NOISE, FIELD, WALLS, true>(src, dst, ffield, facc, a, valid ? x : 0, blockIdx.y,
+                                                   blockIdx.z + a.z0, valid, part);
+        block_moment_sums_out(part, partials + 38 * block_linear());
+    } else {
+        if (x >= a.nx) return;
+        update_node<DT, NOISE, FIELD, WALLS>(src, dst, ffield, facc, a, x, blockIdx.y, blockIdx.z + a.z0);
+    }
 }
 
 // Re-update of the nodes that received particle impulses, after an update of
@@ -243,18 +350,15 @@ struct Pair<2> {
     }
 };
 
-template <int DT, bool NOISE, bool FIELD, bool WALLS>
-__global__ void __launch_bounds__(kBX) k_stream_collide2(const typename lbd::Store<DT>::T *__restrict__ src,
-                                                         typename lbd::Store<DT>::T *__restrict__ dst,
-                                                         const float *__restrict__ ffield,
-                                                         const float *__restrict__ facc, const StepArgs a)
+template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS = false>
+__device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__restrict__ src,
+                                            typename lbd::Store<DT>::T *__restrict__ dst,
+                                            const float *__restrict__ ffield, const float *__restrict__ facc,
+                                            const StepArgs &a, int x0, int y, int z, bool valid = true,
+                                            float (*part)[38] = nullptr)
 {
     using S = lbd::Store<DT>;
     using PR = Pair<DT>;
-    const int x0 = 2 * (blockIdx.x * kBX + threadIdx.x);
-    if (x0 >= a.nx) return;
-    const int y = blockIdx.y;
-    const int z = blockIdx.z + a.z0;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int xm = (x0 == 0) ? nx - 1 : x0 - 1;       // source of node x0 for c_x = +1
     const int xp = (x0 + 2 == nx) ? 0 : x0 + 2;       // source of node x0 + 1 for c_x = -1
@@ -314,34 +418,89 @@ __global__ void __launch_bounds__(kBX) k_stream_collide2(const typename lbd::Sto
         }
     }
     float out0[19], out1[19];
-    collide_node<NOISE>(n0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
-    collide_node<NOISE>(n1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
+    if (SUMS) {  // both nodes' moments first, summed before the collisions
+        float m0[19], m1[19];
+        lbd::forward(n0, m0);
+        lbd::forward(n1, m1);
+        warp_moment_sums(m0, m1, valid, part);
+        if (!valid) return;
+        collide_moments<NOISE>(m0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
+        collide_moments<NOISE>(m1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
+    } else {
+        collide_node<NOISE>(n0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
+        collide_node<NOISE>(n1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
+    }
 #pragma unroll
     for (int i = 0; i < 19; ++i) PR::store(dst + (uint32_t)i * P + self, out0[i], out1[i], a.scale);
 }
 
+template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS>
+__global__ void __launch_bounds__(kBX) k_stream_collide2(const typename lbd::Store<DT>::T *__restrict__ src,
+                                                         typename lbd::Store<DT>::T *__restrict__ dst,
+                                                         const float *__restrict__ ffield,
+                                                         const float *__restrict__ facc, const StepArgs a,
+                                                         float *partials)
+{
+    const int x0 = 2 * (blockIdx.x * kBX + threadIdx.x);
+    if (SUMS) {
+        __shared__ float part[kBX / 32][38];
+        const bool valid = x0 < a.nx;  // lanes past the row load nodes 0, 1 of it and store nothing
+        update_pair<DT, NOISE, FIELD, WALLS, true>(src, dst, ffield, facc, a, valid ? x0 : 0, blockIdx.y,
+                                                   blockIdx.z + a.z0, valid, part);
+        block_moment_sums_out(part, partials + 38 * block_linear());
+    } else {
+        if (x0 >= a.nx) return;
+        update_pair<DT, NOISE, FIELD, WALLS>(src, dst, ffield, facc, a, x0, blockIdx.y, blockIdx.z + a.z0);
+    }
+}
+
+// Launch geometry of the stream-collide kernels: two nodes per thread when
+// rows pair up and element indices fit 32 bits.
+inline bool sc_paired(const lb_handle *h)
+{
+    return (h->p.nx % 2 == 0) && (19.0 * (double)h->pitch < 4294967296.0);
+}
+
+inline dim3 sc_grid(const lb_handle *h)
+{
+    const int nzf = h->p.walls ? h->p.nz - 2 : h->p.nz;
+    const int nxt = sc_paired(h) ? h->p.nx / 2 : h->p.nx;
+    return dim3((nxt + kBX - 1) / kBX, h->p.ny, nzf);
+}
+
+// partials != NULL: the launch also writes per-block moment sums
+// (partials[block][38], block = blockIdx.x + gridDim.x (blockIdx.y + gridDim.y blockIdx.z)).
 template <int DT>
-cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc)
+cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *dst, const float *facc,
+                                     float *partials)
 {
     using T = typename lbd::Store<DT>::T;
     const StepArgs a = make_args(h);
-    const int nzf = a.z1 - a.z0;
-    dim3 grid((a.nx + kBX - 1) / kBX, a.ny, nzf);
-    dim3 block(kBX);
+    const dim3 grid = sc_grid(h);
+    const dim3 block(kBX);
     const bool noise = a.kT > 0.0f;
     const bool field = (h->force != nullptr) || (facc != nullptr);
     const bool walls = h->p.walls != 0;
+    const bool paired = sc_paired(h);
     const T *s = static_cast<const T *>(src);
     T *d = static_cast<T *>(dst);
-    // two nodes per thread when rows pair up and element indices fit 32 bits
-    const bool paired = (a.nx % 2 == 0) && (19.0 * (double)a.pitch < 4294967296.0);
-    if (paired) grid.x = (a.nx / 2 + kBX - 1) / kBX;
-#define LBI_SC(NZ, FL, WL)                                                                             \
-    do {                                                                                               \
-        if (paired)                                                                                    \
-            k_stream_collide2<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a); \
-        else                                                                                           \
-            k_stream_collide<DT, NZ, FL, WL><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a);  \
+#define LBI_SC(NZ, FL, WL)                                                                                        \
+    do {                                                                                                          \
+        if (partials) {                                                                                           \
+            if (paired)                                                                                           \
+                k_stream_collide2<DT, NZ, FL, WL, true><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a,   \
+                                                                                        partials);               \
+            else                                                                                                  \
+                k_stream_collide<DT, NZ, FL, WL, true><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a,    \
+                                                                                       partials);                \
+        } else {                                                                                                  \
+            if (paired)                                                                                           \
+                k_stream_collide2<DT, NZ, FL, WL, false><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a,  \
+                                                                                         nullptr);               \
+            else                                                                                                  \
+                k_stream_collide<DT, NZ, FL, WL, false><<<grid, block, 0, h->stream>>>(s, d, h->force, facc, a,   \
+                                                                                        nullptr);                \
+        }                                                                                                         \
     } while (0)
     if (noise) {
         if (field) {

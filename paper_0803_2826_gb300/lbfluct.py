@@ -34,7 +34,7 @@ EXPORTS = (
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
-    "lb_set_timing", "lb_get_timing",
+    "lb_set_timing", "lb_get_timing", "lb_step_sums",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
     "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
     "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
@@ -126,6 +126,7 @@ def load(path: str | None = None):
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_box_muller": (i, [vp, i, vp, vp]),
             "lb_set_timing": (i, [H, i]),
+            "lb_step_sums": (i, [H, i, vp]),
             "lb_get_timing": (i, [H, C.POINTER(C.c_double), C.POINTER(i), C.POINTER(C.c_double), C.POINTER(i)]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
             "lb_moment_sums_static": (i, [P, vp, vp, vp]),
@@ -294,6 +295,10 @@ def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, g
 
 def lb_box_muller(words, npairs, gauss, stream=None):
     _check(load().lb_box_muller(_ptr(words), int(npairs), _ptr(gauss), _stream(stream)))
+
+
+def lb_step_sums(h, nsteps, sums):
+    _check(load().lb_step_sums(h, int(nsteps), _ptr(sums)))
 
 
 def lb_set_timing(h, capacity):
@@ -543,11 +548,14 @@ class Lattice:
 
 
 def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_particles:
+    """The particle set the library updates in place; the struct keeps the
+    tensors alive (it holds only their device pointers otherwise)."""
     s = lb_particles()
     s.n, s.reserved = int(n), 0
     s.pos, s.mom = _ptr(pos), _ptr(mom)
     s.mass, s.gamma = _ptr(mass), _ptr(gamma)
     s.mass0, s.gamma0 = float(mass0), float(gamma0)
+    s._arrays = (pos, mom, mass, gamma)
     return s
 
 

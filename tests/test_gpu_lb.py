@@ -201,3 +201,31 @@ def test_step_counter_and_resume(ora):
     c.step_index = step
     c.step(3)
     assert torch.equal(a.get_populations(), c.get_populations())
+
+
+@pytest.mark.parametrize("shape,walls,dtype", [((24, 10, 12), False, L.LB_F32), ((23, 9, 11), False, L.LB_F32),
+                                                ((20, 8, 14), True, L.LB_F32), ((24, 10, 12), False, L.LB_F16)])
+def test_step_sums_equal_moment_sums(shape, walls, dtype):
+    """lb_step_sums: the sums its last stream-collide launch accumulates equal
+    those of lb_moments on the state that step starts from (paired and
+    single-node kernels, walls, FP16 storage); the state advances as lb_step."""
+    kw = dict(kT=1e-4, seed=3, walls=walls, body_force=(1e-5, 0.0, 0.0), dtype=dtype)
+    a, b = L.Lattice(shape, **kw), L.Lattice(shape, **kw)
+    u = inputs.shear_wave(shape, 0.02) + inputs.gaussian_field(shape, 3, 1e-3, seed=4)
+    if walls:
+        u[:, 0] = 0
+        u[:, -1] = 0
+    for lat in (a, b):
+        lat.init_equilibrium(None, torch.as_tensor(u).cuda())
+    want = torch.empty(L.LB_NSUMS, dtype=torch.float64, device="cuda")
+    got = torch.empty_like(want)
+    a.step(4)
+    L.lb_moments(a.h, None, None, None, want)
+    L.lb_step_sums(b.h, 5, got)
+    a.step(1)
+    torch.cuda.synchronize()
+    w, g = want.cpu().numpy(), got.cpu().numpy()
+    scale = np.abs(w).max()
+    assert np.abs(g - w).max() < 1e-6 * scale, (g, w)
+    assert np.array_equal(a.get_populations().cpu().numpy(), b.get_populations().cpu().numpy())
+    assert a.sync() == (L.LB_OK, 0) and b.sync() == (L.LB_OK, 0)

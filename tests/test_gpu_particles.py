@@ -283,3 +283,26 @@ def test_overlapped_coupling_joined_by_another_call():
     for fa, fb in zip(a[3], b[3]):
         assert np.abs(fa - fb).max() < 1e-9 and np.abs(fa).max() > 0
     assert np.abs(a[0] - b[0]).max() < 1e-7
+
+
+def test_step_sums_with_overlapped_coupling():
+    """The sums of lb_step_sums come from the launch that runs beside an
+    overlapped coupling (forces do not enter them) and equal lb_moments'."""
+    shape = (20, 18, 16)
+    pos = inputs.random_walk_chains(6, 32, shape, seed=61)
+    mom = inputs.maxwell_momenta(192, 1.0, 1e-4, seed=62).astype(np.float32)
+    lat = L.Lattice(shape, kT=1e-4, seed=6)
+    lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+    parts = L.particles(192, dev(pos), dev(mom, torch.float32), mass0=1.0, gamma0=2.0)
+    want = torch.empty(L.LB_NSUMS, dtype=torch.float64, device="cuda")
+    got = torch.empty_like(want)
+    for t in range(3):
+        cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, chain_len=32, use_wca=True,
+                             eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=True)
+        L.lb_moments(lat.h, None, None, None, want)
+        L.lb_couple_particles(lat.h, parts, cp)
+        L.lb_step_sums(lat.h, 1, got)
+        torch.cuda.synchronize()
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        assert np.abs(g - w).max() < 1e-6 * np.abs(w).max()
+    assert lat.sync() == (L.LB_OK, 0)
