@@ -118,6 +118,9 @@ def _load():
             lib.ora_couple.argtypes = [P, _D, _D, C.c_int, _D, _D, _D, _D,
                                        C.POINTER(MD), C.POINTER(CoupleParams), _D]
             lib.ora_couple.restype = C.c_int
+            lib.ora_couple_adjoint.argtypes = [P, _D, _D, C.c_int, _D, _D, _D, _D, C.POINTER(CoupleParams),
+                                               _D, _D, _D, _D, _D]
+            lib.ora_couple_adjoint.restype = C.c_int
             lib.ora_interpolate.argtypes = [P, _D, _D, C.c_int, _D, _D]
             lib.ora_stencil.argtypes = [P, _D, C.POINTER(C.c_longlong), _D]
             lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
@@ -296,6 +299,77 @@ def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_s
                             _dp(gamma), None if md is None else C.byref(md), C.byref(cp),
                             _dp(facc))
     return pos, mom, facc, broken
+
+
+def couple_adjoint(p: Params, pops, pos0, mom0, mass, gamma, *, dt, n_substeps, lam_facc, lam_pos, lam_mom,
+                   lam_pops, grad_f, force=None):
+    """Reverse of couple() at kT = 0 for free particles (no md): from
+    lam_facc = dL/dfacc and lam_pos / lam_mom = dL/d(state after the call),
+    returns (dL/dpos0, dL/dmom0) and adds dL/dpops (through the interpolated
+    u) into lam_pops and dL/dforce into grad_f (both in place)."""
+    lib = _load()
+    n = np.asarray(pos0).shape[0]
+    pos0 = np.ascontiguousarray(pos0, dtype=np.float64)
+    mom0 = np.ascontiguousarray(mom0, dtype=np.float64)
+    mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)))
+    gamma = np.ascontiguousarray(np.broadcast_to(np.asarray(gamma, dtype=np.float64), (n,)))
+    lp = np.array(lam_pos, dtype=np.float64, order="C", copy=True)
+    lm = np.array(lam_mom, dtype=np.float64, order="C", copy=True)
+    cp = CoupleParams()
+    cp.n_substeps, cp.noise_kind, cp.dt = int(n_substeps), 0, float(dt)
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    lf = np.ascontiguousarray(lam_facc, dtype=np.float64)
+    assert lam_pops.flags.c_contiguous and lam_pops.dtype == np.float64
+    assert grad_f.flags.c_contiguous and grad_f.dtype == np.float64
+    st = lib.ora_couple_adjoint(C.byref(p), _dp(src), _dp(f), n, _dp(pos0), _dp(mom0), _dp(mass), _dp(gamma),
+                                C.byref(cp), _dp(lf), _dp(lp), _dp(lm), _dp(lam_pops), _dp(grad_f))
+    if st != 0:
+        raise ValueError("couple_adjoint: a wall reflection with p_z = 0 (sign not recoverable)")
+    return lp, lm
+
+
+def coupled_kinetic_energy(p: Params, pops0, force, pos0, mom0, mass, gamma, *, dt, n_substeps, nsteps, lo, hi):
+    """L after nsteps of (couple, step) from pops0 and the free particles
+    (pos0, mom0), with the force field (forward only; kT = 0)."""
+    pops = np.ascontiguousarray(pops0, dtype=np.float64)
+    pos, mom = np.array(pos0, dtype=np.float64), np.array(mom0, dtype=np.float64)
+    for t in range(nsteps):
+        pos, mom, facc, _ = couple(p, pops, pos, mom, mass, gamma, dt=dt, n_substeps=n_substeps, seed=0,
+                                   force=force)
+        pops = step(p, pops, facc if force is None else force + facc, t)
+    rho, j, _ = moments(p, pops, force)
+    sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+    return float(0.5 * np.sum((j[(slice(None),) + sl] ** 2).sum(0) / rho[sl]))
+
+
+def coupled_kinetic_energy_and_grad(p: Params, pops0, force, pos0, mom0, mass, gamma, *, dt, n_substeps,
+                                    nsteps, lo, hi):
+    """(L, dL/dforce, dL/dpos0, dL/dmom0) of coupled_kinetic_energy by the
+    reverse pass: per step in reverse, the stream-collide adjoint (which gives
+    dL/df of that step, f = force + spread impulses), then the coupling
+    adjoint driven by that dL/df as dL/dfacc."""
+    force = np.zeros((3, p.nz, p.ny, p.nx)) if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    pops = np.ascontiguousarray(pops0, dtype=np.float64)
+    pos, mom = np.array(pos0, dtype=np.float64), np.array(mom0, dtype=np.float64)
+    hist = []
+    for t in range(nsteps):
+        hist.append((pops, pos, mom))
+        pos, mom, facc, _ = couple(p, pops, pos, mom, mass, gamma, dt=dt, n_substeps=n_substeps, seed=0,
+                                   force=force)
+        pops = step(p, pops, force + facc, t)
+        hist[-1] = hist[-1] + (facc,)
+    L, lam, g = kinetic_seed(p, pops, lo, hi, force)
+    lpos, lmom = np.zeros_like(pos), np.zeros_like(mom)
+    for t in range(nsteps - 1, -1, -1):
+        pops_t, pos_t, mom_t, facc_t = hist[t]
+        gstep = np.zeros((3, p.nz, p.ny, p.nx))
+        lam, gstep = adjoint_step(p, pops_t, lam, force + facc_t, gstep)
+        g += gstep
+        lpos, lmom = couple_adjoint(p, pops_t, pos_t, mom_t, mass, gamma, dt=dt, n_substeps=n_substeps,
+                                    lam_facc=gstep, lam_pos=lpos, lam_mom=lmom, lam_pops=lam, grad_f=g,
+                                    force=force)
+    return L, g, lpos, lmom
 
 
 def interpolate(p: Params, pops, pos, force=None):

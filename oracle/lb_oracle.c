@@ -915,3 +915,189 @@ double ora_kinetic_seed(const ora_params *P, const double *state, const double *
     }
     return L;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of the coupling (kT = 0, free particles: no conservative    */
+/* forces).  Each particle is then independent: replay its sub-steps of     */
+/* ora_couple, then walk them back.  Per sub-step (Sec. 4.5), with          */
+/* a = dt / (2 m):                                                          */
+/*   r_h = confine(r + a p)             (a z reflection flips r_z and p_z)   */
+/*   u_p = sum_q w_q(r_h) u_q           (Eqs. Delta, 2point)                 */
+/*   p'  = C1 p~ + C2 Gamma u_p         (p~ = p after the confine)           */
+/*   J   = p' - p~;  facc_q -= J w_q(r_h)                                    */
+/*   r'  = confine(r_h + a p')                                               */
+/* and u_q = (sum_i n_i c_i + f_q / 2) / rho_q from the pulled populations. */
+/* ------------------------------------------------------------------------ */
+
+/* Weight of stencil node (dx, dy, dz) of position p and its gradient in p:
+ * w = prod_d phi2, d phi2 / d p_d = -1 for the lower node, +1 for the upper
+ * (one-sided at integer positions, consistent with the floor). */
+static double stencil_grad(const double p[3], int dx, int dy, int dz, double g[3])
+{
+    const int o[3] = {dx, dy, dz};
+    double ph[3], dph[3];
+    for (int c = 0; c < 3; c++) {
+        double fr = p[c] - floor(p[c]);
+        ph[c] = o[c] ? fr : 1.0 - fr;
+        dph[c] = o[c] ? 1.0 : -1.0;
+    }
+    g[0] = dph[0] * ph[1] * ph[2];
+    g[1] = ph[0] * dph[1] * ph[2];
+    g[2] = ph[0] * ph[1] * dph[2];
+    return ph[0] * ph[1] * ph[2];
+}
+
+/* confine() with the sign it applied to z (+1, or -1 after a reflection). */
+static double confine_sign(const ora_params *P, double p[3], double m[3])
+{
+    double before = m[2];
+    confine(P, p, m);
+    return (before != 0.0 && m[2] == -before) ? -1.0 : 1.0;
+}
+
+/* Given the state at the start of a coupling call (pos0, mom0), the
+ * populations and force field of the step, lam_facc = dL/dfacc ([3][N]) and
+ * lam_pos / lam_mom = dL/d(particle state after the call) ([np][3]): replace
+ * lam_pos / lam_mom by dL/d(state at the start), add dL/dpops through the
+ * interpolated u into lam_pops ([Q][N]) and dL/dforce through u's f/2 term
+ * into grad_f ([3][N]).  Requires kT = 0 and no conservative forces.
+ * Returns -1 (nothing done) if a z reflection happened with p_z = 0, where
+ * the reflection sign cannot be recovered, else 0. */
+int ora_couple_adjoint(const ora_params *P, const double *pops, const double *force, int np,
+                       const double *pos0, const double *mom0, const double *mass, const double *gamma,
+                       const ora_couple_params *C, const double *lam_facc, double *lam_pos, double *lam_mom,
+                       double *lam_pops, double *grad_f)
+{
+    build_tables();
+    size_t N = nodes_of(P);
+    double *u = (double *)malloc(sizeof(double) * 3 * N);
+    double *lam_u = (double *)calloc(3 * N, sizeof(double));
+    node_velocity(P, pops, force, u);
+    const int S = C->n_substeps;
+    const double h = C->dt;
+    double *rh = (double *)malloc(sizeof(double) * 3 * S);   /* r_h of each sub-step */
+    double *pt = (double *)malloc(sizeof(double) * 3 * S);   /* p~ */
+    double *pn = (double *)malloc(sizeof(double) * 3 * S);   /* p' */
+    double *s1 = (double *)malloc(sizeof(double) * S);       /* z sign of the first confine */
+    double *s2 = (double *)malloc(sizeof(double) * S);       /* z sign of the second */
+    int status = 0;
+    for (int p = 0; p < np; p++) {
+        const double m = mass[p], G = gamma[p], a = 0.5 * h / m;
+        const double C1 = exp(-G * h / m), C2 = (m / G) * (1.0 - C1);
+        double r[3], q[3];
+        for (int c = 0; c < 3; c++) { r[c] = pos0[3 * p + c]; q[c] = mom0[3 * p + c]; }
+        /* replay */
+        for (int s = 0; s < S; s++) {
+            for (int c = 0; c < 3; c++) r[c] += a * q[c];
+            if (P->walls && q[2] == 0.0 && (r[2] < 1.0 || r[2] > P->nz - 2)) status = -1;
+            s1[s] = P->walls ? confine_sign(P, r, q) : (confine(P, r, q), 1.0);
+            size_t node[8];
+            double wt[8], up[3] = {0, 0, 0};
+            stencil(P, r, node, wt);
+            for (int k = 0; k < 8; k++)
+                for (int c = 0; c < 3; c++) up[c] += wt[k] * u[3 * node[k] + c];
+            for (int c = 0; c < 3; c++) {
+                rh[3 * s + c] = r[c];
+                pt[3 * s + c] = q[c];
+                q[c] = C1 * q[c] + C2 * G * up[c];
+                pn[3 * s + c] = q[c];
+                r[c] += a * q[c];
+            }
+            if (P->walls && q[2] == 0.0 && (r[2] < 1.0 || r[2] > P->nz - 2)) status = -1;
+            s2[s] = P->walls ? confine_sign(P, r, q) : (confine(P, r, q), 1.0);
+        }
+        /* walk back */
+        double lr[3], lp[3];
+        for (int c = 0; c < 3; c++) { lr[c] = lam_pos[3 * p + c]; lp[c] = lam_mom[3 * p + c]; }
+        for (int s = S - 1; s >= 0; s--) {
+            const double *r_h = rh + 3 * s, *p_t = pt + 3 * s, *p_n = pn + 3 * s;
+            /* second half drift + confine: r' = sz (r_h + a p'), p_stored = sz p' (z only) */
+            double lrh[3], lpn[3];
+            for (int c = 0; c < 3; c++) {
+                double sg = (c == 2) ? s2[s] : 1.0;
+                lrh[c] = sg * lr[c];
+                lpn[c] = sg * (lp[c] + a * lr[c]);
+            }
+            /* spread facc_q -= J w_q and the update p' = C1 p~ + C2 G u_p */
+            double J[3], lJ[3] = {0, 0, 0}, lu[3];
+            for (int c = 0; c < 3; c++) J[c] = p_n[c] - p_t[c];
+            size_t node[8];
+            double wt[8];
+            stencil(P, r_h, node, wt);
+            int k = 0;
+            for (int dz = 0; dz < 2; dz++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++, k++) {
+                        if (wt[k] == 0.0 && P->walls) {
+                            /* a node outside the box: no weight, no gradient */
+                            int nzv = (int)floor(r_h[2]) + dz;
+                            if (nzv < 0 || nzv >= P->nz) continue;
+                        }
+                        double gw[3];
+                        stencil_grad(r_h, dx, dy, dz, gw);
+                        double lf_dot_J = 0.0;
+                        for (int c = 0; c < 3; c++) {
+                            double lf = lam_facc[(size_t)c * N + node[k]];
+                            lJ[c] -= lf * wt[k];
+                            lf_dot_J += lf * J[c];
+                        }
+                        for (int c = 0; c < 3; c++) lrh[c] -= lf_dot_J * gw[c];
+                    }
+            double lpt[3];
+            for (int c = 0; c < 3; c++) {
+                lpn[c] += lJ[c];
+                lpt[c] = -lJ[c] + C1 * lpn[c];
+                lu[c] = C2 * G * lpn[c];
+            }
+            /* u_p = sum_q w_q u_q */
+            k = 0;
+            for (int dz = 0; dz < 2; dz++)
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++, k++) {
+                        if (P->walls) {
+                            int nzv = (int)floor(r_h[2]) + dz;
+                            if (nzv < 0 || nzv >= P->nz) continue;
+                        }
+                        double gw[3];
+                        stencil_grad(r_h, dx, dy, dz, gw);
+                        double udot = 0.0;
+                        for (int c = 0; c < 3; c++) {
+                            lam_u[3 * node[k] + c] += wt[k] * lu[c];
+                            udot += u[3 * node[k] + c] * lu[c];
+                        }
+                        for (int c = 0; c < 3; c++) lrh[c] += udot * gw[c];
+                    }
+            /* first half drift + confine: r_h = sz (r + a p), p~ = sz p */
+            for (int c = 0; c < 3; c++) {
+                double sg = (c == 2) ? s1[s] : 1.0;
+                lr[c] = sg * lrh[c];
+                lp[c] = sg * (lpt[c] + a * lrh[c]);
+            }
+        }
+        for (int c = 0; c < 3; c++) { lam_pos[3 * p + c] = lr[c]; lam_mom[3 * p + c] = lp[c]; }
+    }
+    /* lam_u -> populations (through the pull) and force field */
+    for (int z = 0; z < P->nz; z++) {
+        if (is_solid(P, z)) continue;
+        for (int y = 0; y < P->ny; y++)
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                const double *lu = lam_u + 3 * s;
+                if (lu[0] == 0.0 && lu[1] == 0.0 && lu[2] == 0.0) continue;
+                double n[Q], dn[Q], rho = 0.0;
+                gather(P, pops, x, y, z, n);
+                for (int i = 0; i < Q; i++) rho += n[i];
+                const double *us = u + 3 * s;
+                for (int i = 0; i < Q; i++) {
+                    double v = 0.0;
+                    for (int d = 0; d < 3; d++) v += lu[d] * (g_c[i][d] - us[d]);
+                    dn[i] = v / rho;
+                }
+                push_adjoint(P, lam_pops, x, y, z, dn);
+                if (grad_f)
+                    for (int d = 0; d < 3; d++) grad_f[(size_t)d * N + s] += 0.5 * lu[d] / rho;
+            }
+    }
+    free(u); free(lam_u); free(rh); free(pt); free(pn); free(s1); free(s2);
+    return status;
+}

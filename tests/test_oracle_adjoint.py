@@ -66,3 +66,63 @@ def test_checkpointed_reverse_pass_is_identical(ora):
     L1, g1 = ora.kinetic_energy_and_grad(p, s0, f, 7, (0, 0, 0), (5, 6, 4))
     L2, g2 = ora.kinetic_energy_and_grad(p, s0, f, 7, (0, 0, 0), (5, 6, 4), checkpoint_every=3)
     assert L1 == L2 and np.array_equal(g1, g2)
+
+
+def _coupled_case(ora, walls):
+    from paper_0803_2826_gb300 import inputs
+    shape = (8, 7, 8)
+    p = ora.make_params(shape, kT=0.0, walls=walls)
+    rng = np.random.default_rng(11)
+    force = rng.normal(0.0, 1e-4, size=(3, 8, 7, 8))
+    u = inputs.shear_wave(shape, 0.02) + inputs.gaussian_field(shape, 3, 2e-3, seed=12)
+    if walls:
+        u[:, 0] = 0
+        u[:, -1] = 0
+        force[:, 0] = 0
+        force[:, -1] = 0
+    pops0 = ora.equilibrium(p, None, u)
+    n = 5
+    pos0 = rng.uniform(0.0, 1.0, (n, 3)) * np.array(shape, dtype=float)
+    mom0 = rng.normal(0.0, 0.02, (n, 3))
+    if walls:  # three particles heading into the walls, so that they reflect
+        pos0[:, 2] = rng.uniform(1.2, 5.8, n)
+        pos0[0, 2], mom0[0, 2] = 1.02, -0.3
+        pos0[1, 2], mom0[1, 2] = 5.97, 0.35
+        pos0[2, 2], mom0[2, 2] = 1.05, -0.2
+    kw = dict(dt=0.1, n_substeps=5, nsteps=4, lo=(1, 1, 1), hi=(7, 6, 7))
+    return p, pops0, force, pos0, mom0, kw
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_coupled_reverse_pass_matches_central_differences(ora, walls):
+    """Reverse of (couple free particles at kT = 0, then step) x 4 against
+    central differences of the forward loss in the force field, the initial
+    positions and the initial momenta (Sec. 4.5 with Eqs. Delta, 2point)."""
+    p, pops0, force, pos0, mom0, kw = _coupled_case(ora, walls)
+    L, g, lpos, lmom = ora.coupled_kinetic_energy_and_grad(p, pops0, force, pos0, mom0, 1.0, 2.0, **kw)
+    assert L == pytest.approx(ora.coupled_kinetic_energy(p, pops0, force, pos0, mom0, 1.0, 2.0, **kw), rel=1e-13)
+
+    def fd(fun, x, idx, eps):
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += eps
+        xm[idx] -= eps
+        return (fun(xp) - fun(xm)) / (2 * eps)
+
+    for idx in [(0, 2, 3, 4), (1, 3, 1, 1), (2, 5, 6, 7)]:
+        d = fd(lambda F: ora.coupled_kinetic_energy(p, pops0, F, pos0, mom0, 1.0, 2.0, **kw), force, idx, 1e-4)
+        assert g[idx] == pytest.approx(d, rel=1e-5, abs=1e-9)
+    for idx in [(0, 0), (1, 2), (2, 2), (3, 1)]:
+        d = fd(lambda P: ora.coupled_kinetic_energy(p, pops0, force, P, mom0, 1.0, 2.0, **kw), pos0, idx, 1e-6)
+        assert lpos[idx] == pytest.approx(d, rel=1e-4, abs=1e-10)
+    for idx in [(0, 2), (1, 2), (4, 1)]:
+        d = fd(lambda M: ora.coupled_kinetic_energy(p, pops0, force, pos0, M, 1.0, 2.0, **kw), mom0, idx, 1e-5)
+        assert lmom[idx] == pytest.approx(d, rel=1e-4, abs=1e-10)
+
+
+def test_coupled_reverse_without_particles_is_the_lb_reverse(ora):
+    """With no particles the coupled reverse pass is the plain one."""
+    p, pops0, force, pos0, mom0, kw = _coupled_case(ora, False)
+    L, g, _, _ = ora.coupled_kinetic_energy_and_grad(p, pops0, force, pos0[:0], mom0[:0], 1.0, 2.0, **kw)
+    L2, g2 = ora.kinetic_energy_and_grad(p, pops0, force, kw["nsteps"], kw["lo"], kw["hi"])
+    assert L == pytest.approx(L2, rel=1e-14)
+    assert np.allclose(g, g2, rtol=1e-12, atol=1e-18)
