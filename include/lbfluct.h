@@ -310,6 +310,47 @@ lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[
 lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
                              float *grad_force, double *loss);
 
+/* lb_adjoint_step for a step that also applied particle impulses: impulse
+ * (device FP32 [3][pitch], the layout of the library's accumulator; NULL =
+ * none) is added to f = body_force + force field.  grad_force receives
+ * dL/df of the total f (so also dL/d(impulse)).  Requires kT = 0. */
+lb_status lb_adjoint_step_impulse(lb_handle *h, const void *state, const float *impulse, const float *lambda_in,
+                                  float *lambda_out, float *grad_force);
+
+/* Reverse of one lb_couple_particles call (Sec. 4.5 with the stencil of
+ * Eqs. (Delta), (2point)) for free particles at kT = 0 (chain_len <= 1, no
+ * WCA; LB_EUNSUPPORTED otherwise; n_substeps <= 64).  Per particle the
+ * sub-steps are replayed from `start` (the particle state before the call,
+ * not modified) against the populations `state` (storage format) of that
+ * step, then walked back: half drifts (with the sign flips of wall
+ * reflections), the exact Ornstein-Uhlenbeck update, the spreading of
+ * -J Delta and the interpolation of u.  lambda_facc: dL/d(impulse field)
+ * of the step (device FP32 [3][N], e.g. grad_force of
+ * lb_adjoint_step_impulse); lambda_pos / lambda_mom: device FP32 [n][3],
+ * dL/d(state after the call) in, dL/d(state before it) out.  Adds dL/dstate
+ * through u = (sum n c + f/2)/rho into lambda_pops (FP32 [19][pitch]) and
+ * dL/d(force field) into grad_force ([3][N], may be NULL).
+ * Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_adjoint_couple(lb_handle *h, const void *state, const lb_particles *start, const lb_couple_params *cp,
+                            const float *lambda_facc, float *lambda_pos, float *lambda_mom, float *lambda_pops,
+                            float *grad_force);
+
+/* The reverse pass of "advance nsteps coupled steps (lb_couple_particles,
+ * then lb_step) from the current state and the particles `parts`, then L of
+ * the sub-box" (L as in lb_adjoint_seed_kinetic): the forward steps run as
+ * usual (state and particles advance), with the populations and the
+ * particle state kept every `checkpoint_every` steps; each segment is
+ * recomputed (particle impulses into per-step buffers) and walked back with
+ * lb_adjoint_step_impulse and lb_adjoint_couple.  Writes dL/d(force field)
+ * (device FP32 [3][N]), dL/d(initial positions) and dL/d(initial momenta)
+ * (device FP32 [n][3]) and L (*loss, device double).  Free particles at
+ * kT = 0 only.  Temporaries are allocated for the call and freed before it
+ * returns (it synchronises the stream).
+ * Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp, int nsteps,
+                                     int checkpoint_every, const int lo[3], const int hi[3], float *grad_force,
+                                     float *grad_pos, float *grad_mom, double *loss);
+
 /* ---- batched replicas: one persistent launch over many boxes ---------------- */
 
 /* Many independent periodic boxes (replicas) of different sizes advanced

@@ -72,7 +72,8 @@ __device__ __forceinline__ void pull_source(int i, int x, int y, int z, int xm, 
 template <int DT, bool WALLS>
 __global__ void __launch_bounds__(kAdjBX)
     k_adjoint_step(const typename lbd::Store<DT>::T *__restrict__ state, const float *__restrict__ lam_in,
-                   float *__restrict__ lam_out, const float *__restrict__ ffield, float *grad_f, const StepArgs a)
+                   float *__restrict__ lam_out, const float *__restrict__ ffield, const float *__restrict__ impulse,
+                   float *grad_f, const StepArgs a)
 {
     using S = lbd::Store<DT>;
     const int x = blockIdx.x * kAdjBX + threadIdx.x;
@@ -100,6 +101,11 @@ __global__ void __launch_bounds__(kAdjBX)
         f[0] += ffield[self];
         f[1] += ffield[a.nn + self];
         f[2] += ffield[2 * a.nn + self];
+    }
+    if (impulse) {  // particle impulses of the step ([3][pitch])
+        f[0] += impulse[self];
+        f[1] += impulse[P + self];
+        f[2] += impulse[2 * P + self];
     }
     const float rho = a.rho0 + m[0];
     const float ir = 1.0f / rho;
@@ -245,16 +251,87 @@ __global__ void __launch_bounds__(kAdjBX)
 
 template <int DT>
 cudaError_t launch_adjoint_dt(const lb_handle *h, const void *state, const float *lam_in, float *lam_out,
-                              float *grad_f)
+                              float *grad_f, const float *impulse)
 {
     using T = typename lbd::Store<DT>::T;
     const StepArgs a = make_args(h);
     dim3 grid((a.nx + kAdjBX - 1) / kAdjBX, a.ny, a.z1 - a.z0);
     const T *s = static_cast<const T *>(state);
     if (h->p.walls)
-        k_adjoint_step<DT, true><<<grid, kAdjBX, 0, h->stream>>>(s, lam_in, lam_out, h->force, grad_f, a);
+        k_adjoint_step<DT, true><<<grid, kAdjBX, 0, h->stream>>>(s, lam_in, lam_out, h->force, impulse, grad_f, a);
     else
-        k_adjoint_step<DT, false><<<grid, kAdjBX, 0, h->stream>>>(s, lam_in, lam_out, h->force, grad_f, a);
+        k_adjoint_step<DT, false><<<grid, kAdjBX, 0, h->stream>>>(s, lam_in, lam_out, h->force, impulse, grad_f, a);
+    return cudaGetLastError();
+}
+
+// dL/du at the nodes (lam_u, [3][pitch], set by the coupling reverse pass)
+// into dL/dstate through u = (sum n c + f/2) / rho of the pulled populations:
+// d u_d / d n_i = (c_id - u_d) / rho, added at the stored entry each n_i is
+// pulled from; d u_d / d f_d = 1 / (2 rho) into grad_f ([3][N]).  lam_u is
+// zeroed on the way, so it is clean for the next call.
+template <int DT, bool WALLS>
+__global__ void __launch_bounds__(kAdjBX)
+    k_lambda_u_to_pops(const typename lbd::Store<DT>::T *__restrict__ state, float *lam_u, float *lam_out,
+                       const float *__restrict__ ffield, const float *__restrict__ impulse, float *grad_f,
+                       const StepArgs a)
+{
+    using S = lbd::Store<DT>;
+    const int x = blockIdx.x * kAdjBX + threadIdx.x;
+    if (x >= a.nx) return;
+    const int y = blockIdx.y;
+    const int z = blockIdx.z + a.z0;
+    const size_t P = a.pitch;
+    const uint32_t self = (uint32_t)((z * a.ny + y) * a.nx + x);
+    const float lu[3] = {lam_u[self], lam_u[P + self], lam_u[2 * P + self]};
+    if (lu[0] == 0.0f && lu[1] == 0.0f && lu[2] == 0.0f) return;
+    lam_u[self] = lam_u[P + self] = lam_u[2 * P + self] = 0.0f;
+    int xm, xp, ym, yp, zm, zp;
+    neighbours<WALLS>(x, y, z, a, xm, xp, ym, yp, zm, zp);
+    float n[19];
+    int plane[19];
+    uint32_t src[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        pull_source<WALLS>(i, x, y, z, xm, xp, ym, yp, zm, zp, a, plane[i], src[i]);
+        n[i] = S::load(state + (size_t)plane[i] * P + src[i], a.inv_scale);
+    }
+    float m[19];
+    lbd::forward(n, m);
+    // the velocity the forward coupling interpolated: f = body force + field
+    // (the particle impulses of the step are not part of it)
+    float f[3] = {a.fx, a.fy, a.fz};
+    if (ffield) {
+        f[0] += ffield[self];
+        f[1] += ffield[a.nn + self];
+        f[2] += ffield[2 * a.nn + self];
+    }
+    (void)impulse;
+    const float rho = a.rho0 + m[0];
+    const float ir = 1.0f / rho;
+    const float u[3] = {(m[1] + 0.5f * f[0]) * ir, (m[2] + 0.5f * f[1]) * ir, (m[3] + 0.5f * f[2]) * ir};
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const float v = lu[0] * ((float)lbd::cx(i) - u[0]) + lu[1] * ((float)lbd::cy(i) - u[1]) +
+                        lu[2] * ((float)lbd::cz(i) - u[2]);
+        atomicAdd(lam_out + (size_t)plane[i] * P + src[i], v * ir);
+    }
+    if (grad_f) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) grad_f[d * a.nn + self] += 0.5f * lu[d] * ir;
+    }
+}
+
+template <int DT>
+cudaError_t launch_lambda_u_dt(const lb_handle *h, const void *state, float *lam_u, float *lam_out, float *grad_f)
+{
+    using T = typename lbd::Store<DT>::T;
+    const StepArgs a = make_args(h);
+    dim3 grid((a.nx + kAdjBX - 1) / kAdjBX, a.ny, a.z1 - a.z0);
+    const T *s = static_cast<const T *>(state);
+    if (h->p.walls)
+        k_lambda_u_to_pops<DT, true><<<grid, kAdjBX, 0, h->stream>>>(s, lam_u, lam_out, h->force, nullptr, grad_f, a);
+    else
+        k_lambda_u_to_pops<DT, false><<<grid, kAdjBX, 0, h->stream>>>(s, lam_u, lam_out, h->force, nullptr, grad_f, a);
     return cudaGetLastError();
 }
 
@@ -273,13 +350,30 @@ cudaError_t launch_seed_dt(const lb_handle *h, const void *state, float *lam_out
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint(const lb_handle *h, const void *state, const float *lam_in, float *lam_out, float *grad_f)
+cudaError_t launch_adjoint(const lb_handle *h, const void *state, const float *lam_in, float *lam_out, float *grad_f,
+                           const float *impulse = nullptr)
 {
     switch (h->p.dtype) {
-    case LB_F32: return launch_adjoint_dt<0>(h, state, lam_in, lam_out, grad_f);
-    case LB_F16: return launch_adjoint_dt<1>(h, state, lam_in, lam_out, grad_f);
-    default: return launch_adjoint_dt<2>(h, state, lam_in, lam_out, grad_f);
+    case LB_F32: return launch_adjoint_dt<0>(h, state, lam_in, lam_out, grad_f, impulse);
+    case LB_F16: return launch_adjoint_dt<1>(h, state, lam_in, lam_out, grad_f, impulse);
+    default: return launch_adjoint_dt<2>(h, state, lam_in, lam_out, grad_f, impulse);
     }
+}
+
+cudaError_t launch_lambda_u(const lb_handle *h, const void *state, float *lam_u, float *lam_out, float *grad_f)
+{
+    switch (h->p.dtype) {
+    case LB_F32: return launch_lambda_u_dt<0>(h, state, lam_u, lam_out, grad_f);
+    case LB_F16: return launch_lambda_u_dt<1>(h, state, lam_u, lam_out, grad_f);
+    default: return launch_lambda_u_dt<2>(h, state, lam_u, lam_out, grad_f);
+    }
+}
+
+// a += b over n floats
+__global__ void k_axpy1(float *a, const float *b, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
 }
 
 cudaError_t launch_seed(const lb_handle *h, const void *state, float *lam_out, float *grad_f, double *loss, int3 lo,
@@ -292,15 +386,15 @@ cudaError_t launch_seed(const lb_handle *h, const void *state, float *lam_out, f
     }
 }
 
-cudaError_t step_from(lb_handle *h, const void *src, void *dst, uint32_t step)
+cudaError_t step_from(lb_handle *h, const void *src, void *dst, uint32_t step, const float *impulse = nullptr)
 {
     const uint32_t saved = h->step;
     h->step = step;
     cudaError_t e;
     switch (h->p.dtype) {
-    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, nullptr, nullptr); break;
-    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, nullptr, nullptr); break;
-    default: e = launch_stream_collide_dt<2>(h, src, dst, nullptr, nullptr); break;
+    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, impulse, nullptr); break;
+    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, impulse, nullptr); break;
+    default: e = launch_stream_collide_dt<2>(h, src, dst, impulse, nullptr); break;
     }
     h->step = saved;
     return e;
@@ -449,6 +543,196 @@ lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, con
     seg[0] = nullptr;
     cleanup();
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_kinetic", e);
+}
+
+
+lb_status lb_adjoint_step_impulse(lb_handle *h, const void *state, const float *impulse, const float *lambda_in,
+                                  float *lambda_out, float *grad_force)
+{
+    if (!check_adjoint_handle(h, "lb_adjoint_step_impulse")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
+    if (!state || !lambda_in || !lambda_out || lambda_in == lambda_out) {
+        set_error("lb_adjoint_step_impulse: need a state and two distinct adjoint buffers");
+        return LB_EINVAL;
+    }
+    join_overlap(h);
+    cudaError_t e = launch_adjoint(h, state, lambda_in, lambda_out, grad_force, impulse);
+    h->launches += 1;
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_step_impulse", e);
+}
+
+lb_status lb_adjoint_couple(lb_handle *h, const void *state, const lb_particles *start, const lb_couple_params *cp,
+                            const float *lambda_facc, float *lambda_pos, float *lambda_mom, float *lambda_pops,
+                            float *grad_force)
+{
+    if (!check_adjoint_handle(h, "lb_adjoint_couple")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
+    if (!state || !start || !cp || !lambda_facc || !lambda_pops ||
+        (start->n > 0 && (!lambda_pos || !lambda_mom))) {
+        set_error("lb_adjoint_couple: NULL argument");
+        return LB_EINVAL;
+    }
+    join_overlap(h);
+    if (!h->lam_u) {
+        cudaError_t e = cudaMalloc((void **)&h->lam_u, 3 * h->pitch * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->lam_u, 0, 3 * h->pitch * sizeof(float), h->stream);
+        if (e != cudaSuccess) {
+            set_error("lb_adjoint_couple: scratch allocation failed (%s)", cudaGetErrorString(e));
+            return LB_ENOMEM;
+        }
+    }
+    lb_status st = couple_adjoint(h, state, start, cp, lambda_facc, lambda_pos, lambda_mom, h->lam_u);
+    if (st != LB_OK || start->n == 0) return st;
+    cudaError_t e = launch_lambda_u(h, state, h->lam_u, lambda_pops, grad_force);
+    h->launches += 1;
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_couple", e);
+}
+
+lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp, int nsteps,
+                                     int checkpoint_every, const int lo[3], const int hi[3], float *grad_force,
+                                     float *grad_pos, float *grad_mom, double *loss)
+{
+    if (!check_adjoint_handle(h, "lb_adjoint_kinetic_coupled")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
+    if (!parts || !cp || nsteps < 1 || checkpoint_every < 1 || !lo || !hi || !grad_force || !loss ||
+        !box_ok(h, lo, hi) || (parts->n > 0 && (!grad_pos || !grad_mom))) {
+        set_error("lb_adjoint_kinetic_coupled: need particles, nsteps >= 1, checkpoint_every >= 1, a valid "
+                  "sub-box and outputs");
+        return LB_EINVAL;
+    }
+    if (!adjoint_couple_ok(h, parts, cp, "lb_adjoint_kinetic_coupled")) return LB_EUNSUPPORTED;
+    join_overlap(h);
+    if (h->facc_dirty) {
+        set_error("lb_adjoint_kinetic_coupled: pending particle impulses (call lb_step first)");
+        return LB_EUNSUPPORTED;
+    }
+    lb_couple_params c1 = *cp;
+    c1.flags &= ~LB_COUPLE_OVERLAP;
+    const int n = parts->n;
+    const int K = std::min(checkpoint_every, nsteps);
+    const int nseg = (nsteps + K - 1) / K;
+    const size_t pop_bytes = 19 * h->pitch * h->elem;
+    const size_t lam_bytes = 19 * h->pitch * sizeof(float);
+    const size_t facc_bytes = 3 * h->pitch * sizeof(float);
+    const size_t grad_bytes = 3 * h->n_nodes * sizeof(float);
+    const size_t pos_bytes = (size_t)n * 3 * sizeof(double), mom_bytes = (size_t)n * 3 * sizeof(float);
+    std::vector<void *> ckpt(nseg, nullptr), seg(K, nullptr);
+    std::vector<double *> cpos(nseg, nullptr), spos(K + 1, nullptr);  // particles before step k of a segment
+    std::vector<float *> cmom(nseg, nullptr), smom(K + 1, nullptr), sfacc(K, nullptr);
+    float *lam[2] = {nullptr, nullptr};
+    float *gstep = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        for (void *p : ckpt) cudaFree(p);
+        for (int k = 1; k < K; ++k) cudaFree(seg[k]);
+        for (double *p : cpos) cudaFree(p);
+        for (float *p : cmom) cudaFree(p);
+        for (double *p : spos) cudaFree(p);
+        for (float *p : smom) cudaFree(p);
+        for (float *p : sfacc) cudaFree(p);
+        cudaFree(lam[0]);
+        cudaFree(lam[1]);
+        cudaFree(gstep);
+    };
+    for (int s = 0; s < nseg && e == cudaSuccess; ++s) {
+        e = cudaMalloc(&ckpt[s], pop_bytes);
+        if (e == cudaSuccess && n) e = cudaMalloc((void **)&cpos[s], pos_bytes);
+        if (e == cudaSuccess && n) e = cudaMalloc((void **)&cmom[s], mom_bytes);
+    }
+    for (int k = 0; k <= K && e == cudaSuccess; ++k) {
+        if (k > 0 && k < K) e = cudaMalloc(&seg[k], pop_bytes);
+        if (e == cudaSuccess && n) e = cudaMalloc((void **)&spos[k], pos_bytes);
+        if (e == cudaSuccess && n) e = cudaMalloc((void **)&smom[k], mom_bytes);
+        if (e == cudaSuccess && k < K) e = cudaMalloc((void **)&sfacc[k], facc_bytes);
+    }
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc((void **)&lam[b], lam_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&gstep, grad_bytes);
+    if (e != cudaSuccess) {
+        cleanup();
+        set_error("lb_adjoint_kinetic_coupled: checkpoint allocation failed (%s)", cudaGetErrorString(e));
+        return LB_ENOMEM;
+    }
+    const uint32_t step0 = h->step;
+    // forward pass: populations and particle state checkpointed every K steps
+    for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
+        if (t % K == 0) {
+            e = cudaMemcpyAsync(ckpt[t / K], h->pops[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess && n)
+                e = cudaMemcpyAsync(cpos[t / K], parts->pos, pos_bytes, cudaMemcpyDeviceToDevice, h->stream);
+            if (e == cudaSuccess && n)
+                e = cudaMemcpyAsync(cmom[t / K], parts->mom, mom_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        }
+        lb_status st = (e == cudaSuccess) ? couple_particles(h, parts, &c1) : LB_ECUDA;
+        if (st == LB_OK) st = lb_step(h, 1);
+        if (st != LB_OK) {
+            cleanup();
+            return st;
+        }
+    }
+    // the last step applied its impulses: clear them now, so the recompute
+    // below can reuse the stencil records
+    if (e == cudaSuccess) e = clear_particle_forces(h);
+    h->facc_stale = 0;
+    int cur = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam[0], 0, lam_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam[1], 0, lam_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad_force, 0, grad_bytes, h->stream);
+    if (e == cudaSuccess && n) e = cudaMemsetAsync(grad_pos, 0, (size_t)n * 3 * sizeof(float), h->stream);
+    if (e == cudaSuccess && n) e = cudaMemsetAsync(grad_mom, 0, (size_t)n * 3 * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), h->stream);
+    if (e == cudaSuccess)
+        e = launch_seed(h, h->pops[h->cur], lam[cur], grad_force, loss, make_int3(lo[0], lo[1], lo[2]),
+                        make_int3(hi[0], hi[1], hi[2]));
+    h->launches += 1;
+    for (int sgi = nseg - 1; sgi >= 0 && e == cudaSuccess; --sgi) {
+        const int t0 = sgi * K, t1 = std::min(nsteps, t0 + K);
+        seg[0] = ckpt[sgi];
+        // recompute the segment: populations, the particle state before each
+        // step and each step's impulses
+        if (n) e = cudaMemcpyAsync(spos[0], cpos[sgi], pos_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(smom[0], cmom[sgi], mom_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        for (int t = t0; t < t1 && e == cudaSuccess; ++t) {
+            const int k = t - t0;
+            if (n) {  // the coupling updates in place: run it on a copy in slot k + 1
+                e = cudaMemcpyAsync(spos[k + 1], spos[k], pos_bytes, cudaMemcpyDeviceToDevice, h->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(smom[k + 1], smom[k], mom_bytes, cudaMemcpyDeviceToDevice, h->stream);
+                lb_particles pk = *parts;
+                pk.pos = spos[k + 1];
+                pk.mom = smom[k + 1];
+                if (e == cudaSuccess && couple_on(h, seg[k], &pk, &c1, sfacc[k]) != LB_OK) e = cudaErrorLaunchFailure;
+            } else {
+                e = cudaMemsetAsync(sfacc[k], 0, facc_bytes, h->stream);
+            }
+            if (e == cudaSuccess && t + 1 < t1) {
+                e = step_from(h, seg[k], seg[k + 1], step0 + (uint32_t)t, sfacc[k]);
+                h->launches += 1;
+            }
+        }
+        // reverse through the segment
+        for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
+            const int k = t - t0;
+            e = cudaMemsetAsync(gstep, 0, grad_bytes, h->stream);
+            if (e == cudaSuccess) e = launch_adjoint(h, seg[k], lam[cur], lam[1 - cur], gstep, sfacc[k]);
+            if (e == cudaSuccess) {
+                const size_t cnt = 3 * h->n_nodes;
+                k_axpy1<<<(unsigned int)std::min<size_t>((cnt + 255) / 256, 4096), 256, 0, h->stream>>>(grad_force,
+                                                                                                      gstep, cnt);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess && n) {
+                lb_particles pk = *parts;
+                pk.pos = spos[k];
+                pk.mom = smom[k];
+                if (lb_adjoint_couple(h, seg[k], &pk, &c1, gstep, grad_pos, grad_mom, lam[1 - cur], grad_force) !=
+                    LB_OK)
+                    e = cudaErrorLaunchFailure;
+            }
+            h->launches += 2;
+            cur = 1 - cur;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // temporaries are freed below
+    seg[0] = nullptr;
+    cleanup();
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_kinetic_coupled", e);
 }
 
 }  // extern "C"

@@ -384,6 +384,7 @@ lb_status lb_destroy(lb_handle *h)
     join_overlap(h);
     destroy_particles(h);
     if (h->claim) cudaFree(h->claim);
+    if (h->lam_u) cudaFree(h->lam_u);
     if (h->sc_partials) cudaFree(h->sc_partials);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     if (h->ev_couple) cudaEventDestroy(h->ev_couple);

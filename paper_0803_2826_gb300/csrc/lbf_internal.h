@@ -67,6 +67,7 @@ struct lb_handle {
     const int *patch_rec; // its stencil records [patch_nsub][patch_n]
     int patch_n, patch_nsub;
     unsigned int *claim;  // [n_nodes] tag of the last re-update of each node
+    float *lam_u;         // [3][pitch] dL/du at the nodes (coupling reverse pass), kept zero between calls
     unsigned int claim_tag;
     float *sc_partials;   // lb_step_sums: [blocks][38] per-block sums, then reduction scratch
     size_t sc_partials_len;
@@ -104,6 +105,11 @@ cudaError_t reduce_step_sums(const lb_handle *h, const float *partials, size_t n
                              double *sums);
 void timer_mark(lb_handle *h, int which, int end, cudaStream_t s);  // record a timer event
 cudaError_t reset_particle_barrier(lb_handle *h);
+bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_couple_params *cp, const char *who);
+lb_status couple_adjoint(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
+                         const float *lam_facc, float *lam_pos, float *lam_mom, float *lam_u);
+lb_status couple_on(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
+                    float *facc_out);
 void destroy_particles(lb_handle *h);
 
 }  // namespace lbi

@@ -1187,14 +1187,12 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
     }
 }
 
-template <int DT>
-cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
+// Kernel arguments of a coupling call (everything but the cell list).
+CoupleArgs make_couple_args(const lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
-    Particles *P = h->parts;
-    const int n = pp->n;
     CoupleArgs c;
     c.g = make_args(h);
-    c.n = n;
+    c.n = pp->n;
     c.chain_len = cp->chain_len;
     c.use_wca = cp->use_wca;
     c.noise_kind = cp->noise_kind;
@@ -1221,6 +1219,19 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     c.last = 0;
     c.md_step = cp->md_step0;
     c.slot = 0;
+    c.ncell[0] = c.ncell[1] = c.ncell[2] = 1;
+    c.cinv[0] = c.cinv[1] = c.cinv[2] = 0.0f;
+    c.nb_log2 = 0;
+    return c;
+}
+
+template <int DT>
+cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
+{
+    Particles *P = h->parts;
+    const int n = pp->n;
+    CoupleArgs c = make_couple_args(h, pp, cp);
+    const double rl = 1.122462048309373 * cp->sigma + kSkin * cp->sigma;
     {
         // cells of edge >= r_list (with a margin for the FP32 binning)
         const int L[3] = {h->p.nx, h->p.ny, h->p.nz};
@@ -1356,6 +1367,151 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Reverse mode of the coupling (kT = 0, free particles).  Each particle is
+// independent: its thread replays the sub-steps with the arithmetic of the
+// forward kernels (cell + FP32 offset positions), remembering per sub-step
+// the half-drift position r_h, the momenta p~ (after the first confine) and
+// p', and the z sign each confine applied; then it walks them back:
+//   r' = s2 (r_h + a p'), p_stored = s2 p'          (z only for s2)
+//   facc_q -= J w_q(r_h), J = p' - p~
+//   p' = C1 p~ + C2 Gamma u_p, u_p = sum_q w_q(r_h) u_q
+//   r_h = s1 (r + a p), p~ = s1 p
+// adding dL/du_q into lam_u ([3][pitch], atomics); k_lambda_u_to_pops turns
+// that into dL/dpopulations and dL/dforce.  (Sec. 4.5, Eqs. Delta, 2point.)
+// ---------------------------------------------------------------------------
+constexpr int kMaxAdjSub = 64;  // sub-steps a reverse call can replay
+
+template <int DT>
+__global__ void __launch_bounds__(kPartThreads)
+    k_couple_adjoint(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
+                     const double *pos0, const float *mom0, const float *mass, const float *gamma,
+                     const float *__restrict__ lam_facc, float *lam_pos, float *lam_mom, float *lam_u,
+                     unsigned int *err, CoupleArgs c, int nsub)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.n) return;
+    const StepArgs &g = c.g;
+    const float m = mass ? mass[p] : c.mass0;
+    const float G = gamma ? gamma[p] : c.gamma0;
+    float C1 = c.C1, C2 = c.C2;
+    if (!c.uniform_coef) {
+        const float x1 = G * c.dt / m;
+        C1 = expf(-x1);
+        C2 = (m / G) * (-expm1f(-x1));
+    }
+    const float a = 0.5f * c.dt / m;
+    CPos rh[kMaxAdjSub];
+    float pt[kMaxAdjSub][3], pn[kMaxAdjSub][3], s1[kMaxAdjSub], s2[kMaxAdjSub];
+
+    // replay: first half drift in FP64 as the forward kernel does, then FP32
+    CPos me;
+    float q[3] = {mom0[3 * p], mom0[3 * p + 1], mom0[3 * p + 2]};
+    {
+        double r[3] = {pos0[3 * p], pos0[3 * p + 1], pos0[3 * p + 2]};
+        const double h = 0.5 * (double)c.dt / (double)m;
+        for (int k = 0; k < 3; ++k) r[k] += h * (double)q[k];
+        const float before = q[2];
+        confine_d(r, q, g);
+        s1[0] = (before != 0.0f && q[2] == -before) ? -1.0f : 1.0f;
+        if (!split(r, g, me)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    }
+    for (int s = 0; s < nsub; ++s) {
+        float uc[8][3], w[8];
+        for (int k = 0; k < 8; ++k) {
+            int x, y, z;
+            w[k] = stencil_node(me, k, g, x, y, z);
+            node_velocity<DT>(src, ffield, x, y, z, g, uc[k]);
+        }
+        float up[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < 8; ++k)
+            for (int d = 0; d < 3; ++d) up[d] = fmaf(w[k], uc[k][d], up[d]);
+        rh[s] = me;
+        for (int d = 0; d < 3; ++d) {
+            pt[s][d] = q[d];
+            q[d] = C1 * q[d] + C2 * G * up[d];
+            pn[s][d] = q[d];
+        }
+        float before = q[2];
+        bool ok = drift(me, q, a, g);  // second half drift of sub-step s
+        s2[s] = (before != 0.0f && q[2] == -before) ? -1.0f : 1.0f;
+        if (s + 1 < nsub) {
+            before = q[2];
+            ok = drift(me, q, a, g) && ok;  // first half drift of sub-step s + 1
+            s1[s + 1] = (before != 0.0f && q[2] == -before) ? -1.0f : 1.0f;
+        }
+        if (!ok) atomicOr(err, LB_DERR_PARTICLE_RANGE);
+    }
+
+    // walk back
+    float lr[3] = {lam_pos[3 * p], lam_pos[3 * p + 1], lam_pos[3 * p + 2]};
+    float lp[3] = {lam_mom[3 * p], lam_mom[3 * p + 1], lam_mom[3 * p + 2]};
+    for (int s = nsub - 1; s >= 0; --s) {
+        float lrh[3], lpn[3], lJ[3] = {0.f, 0.f, 0.f};
+        for (int d = 0; d < 3; ++d) {
+            const float sg = d == 2 ? s2[s] : 1.0f;
+            lrh[d] = sg * lr[d];
+            lpn[d] = sg * fmaf(a, lr[d], lp[d]);
+        }
+        const CPos &r = rh[s];
+        float J[3];
+        for (int d = 0; d < 3; ++d) J[d] = pn[s][d] - pt[s][d];
+        float uc[8][3], w[8], gw[8][3];
+        size_t nodes[8];
+        for (int k = 0; k < 8; ++k) {
+            int x, y, z;
+            w[k] = stencil_node(r, k, g, x, y, z);
+            node_velocity<DT>(src, ffield, x, y, z, g, uc[k]);
+            nodes[k] = ((size_t)z * g.ny + y) * g.nx + x;
+            const int o[3] = {k & 1, (k >> 1) & 1, k >> 2};
+            float ph[3], dph[3];
+            for (int d = 0; d < 3; ++d) {
+                ph[d] = o[d] ? r.f[d] : 1.0f - r.f[d];
+                dph[d] = o[d] ? 1.0f : -1.0f;
+            }
+            gw[k][0] = dph[0] * ph[1] * ph[2];
+            gw[k][1] = ph[0] * dph[1] * ph[2];
+            gw[k][2] = ph[0] * ph[1] * dph[2];
+        }
+        // spread
+        for (int k = 0; k < 8; ++k) {
+            float lfJ = 0.0f;
+            for (int d = 0; d < 3; ++d) {
+                const float lf = lam_facc[d * g.nn + nodes[k]];
+                lJ[d] = fmaf(-lf, w[k], lJ[d]);
+                lfJ = fmaf(lf, J[d], lfJ);
+            }
+            for (int d = 0; d < 3; ++d) lrh[d] = fmaf(-lfJ, gw[k][d], lrh[d]);
+        }
+        // update p' = C1 p~ + C2 G u_p
+        float lpt[3], lu[3];
+        for (int d = 0; d < 3; ++d) {
+            lpn[d] += lJ[d];
+            lpt[d] = -lJ[d] + C1 * lpn[d];
+            lu[d] = C2 * G * lpn[d];
+        }
+        // interpolation u_p = sum_q w_q u_q
+        for (int k = 0; k < 8; ++k) {
+            float udot = 0.0f;
+            for (int d = 0; d < 3; ++d) {
+                atomicAdd(lam_u + d * g.pitch + nodes[k], w[k] * lu[d]);
+                udot = fmaf(uc[k][d], lu[d], udot);
+            }
+            for (int d = 0; d < 3; ++d) lrh[d] = fmaf(udot, gw[k][d], lrh[d]);
+        }
+        // first half drift
+        for (int d = 0; d < 3; ++d) {
+            const float sg = d == 2 ? s1[s] : 1.0f;
+            lr[d] = sg * lrh[d];
+            lp[d] = sg * fmaf(a, lrh[d], lpt[d]);
+        }
+    }
+    for (int d = 0; d < 3; ++d) {
+        lam_pos[3 * p + d] = lr[d];
+        lam_mom[3 * p + d] = lp[d];
+    }
+}
+
 }  // namespace
 
 lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
@@ -1488,6 +1644,85 @@ lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_interpolate", e);
+}
+
+// Checks shared by the reverse-mode entry points of the coupling.
+bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_couple_params *cp, const char *who)
+{
+    if (!pp || !cp || pp->n < 0 || pp->reserved != 0 || (pp->n > 0 && (!pp->pos || !pp->mom))) {
+        set_error("%s: bad particle arguments", who);
+        return false;
+    }
+    if (h->p.kT != 0.0 || cp->chain_len > 1 || cp->use_wca) {
+        set_error("%s: the coupling reverse pass covers free particles at kT = 0", who);
+        return false;
+    }
+    if (cp->n_substeps < 1 || cp->n_substeps > kMaxAdjSub || !(cp->dt > 0.0)) {
+        set_error("%s: need 1 <= n_substeps <= %d and dt > 0", who, kMaxAdjSub);
+        return false;
+    }
+    if ((!pp->mass && !(pp->mass0 > 0.0)) || (!pp->gamma && !(pp->gamma0 > 0.0))) {
+        set_error("%s: mass0 and gamma0 must be > 0 when no per-particle arrays are given", who);
+        return false;
+    }
+    return true;
+}
+
+lb_status couple_adjoint(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
+                         const float *lam_facc, float *lam_pos, float *lam_mom, float *lam_u)
+{
+    if (!adjoint_couple_ok(h, pp, cp, "lb_adjoint_couple")) return LB_EUNSUPPORTED;
+    if (pp->n == 0) return LB_OK;
+    const CoupleArgs c = make_couple_args(h, pp, cp);
+    const int blocks = (pp->n + kPartThreads - 1) / kPartThreads;
+    switch (h->p.dtype) {
+    case LB_F32:
+        k_couple_adjoint<0><<<blocks, kPartThreads, 0, h->stream>>>(
+            static_cast<const float *>(state), h->force, pp->pos, pp->mom, pp->mass, pp->gamma, lam_facc, lam_pos,
+            lam_mom, lam_u, h->d_err, c, cp->n_substeps);
+        break;
+    case LB_F16:
+        k_couple_adjoint<1><<<blocks, kPartThreads, 0, h->stream>>>(
+            static_cast<const __half *>(state), h->force, pp->pos, pp->mom, pp->mass, pp->gamma, lam_facc, lam_pos,
+            lam_mom, lam_u, h->d_err, c, cp->n_substeps);
+        break;
+    default:
+        k_couple_adjoint<2><<<blocks, kPartThreads, 0, h->stream>>>(
+            static_cast<const __nv_bfloat16 *>(state), h->force, pp->pos, pp->mom, pp->mass, pp->gamma, lam_facc,
+            lam_pos, lam_mom, lam_u, h->d_err, c, cp->n_substeps);
+        break;
+    }
+    h->launches += 1;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_couple", e);
+}
+
+// A coupling call against the populations `state` whose impulses go to
+// facc_out ([3][pitch], zeroed here) instead of the handle's accumulator; the
+// particles are updated in place.  The handle's accumulator must hold no
+// uncleared impulses (its stencil records are reused here).
+lb_status couple_on(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
+                    float *facc_out)
+{
+    void *saved_pop = h->pops[h->cur];
+    float *saved_facc = h->facc;
+    const int saved_dirty = h->facc_dirty, saved_stale = h->facc_stale;
+    h->pops[h->cur] = const_cast<void *>(state);
+    h->facc = facc_out;
+    h->facc_stale = 0;
+    cudaError_t e = cudaMemsetAsync(facc_out, 0, 3 * h->pitch * sizeof(float), h->stream);
+    lb_couple_params c2 = *cp;
+    c2.flags &= ~LB_COUPLE_OVERLAP;
+    lb_status st = e == cudaSuccess ? couple_particles(h, pp, &c2) : cuda_fail("lb_adjoint_kinetic_coupled", e);
+    if (h->parts) {  // these records index facc_out
+        h->parts->n_records = 0;
+        h->parts->rec_off = 0;
+    }
+    h->pops[h->cur] = saved_pop;
+    h->facc = saved_facc;
+    h->facc_dirty = saved_dirty;
+    h->facc_stale = saved_stale;
+    return st;
 }
 
 // After a grid-barrier timeout the arrival word is left mid-count; zero it

@@ -34,7 +34,8 @@ EXPORTS = (
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
     "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
-    "lb_set_timing", "lb_get_timing", "lb_step_sums",
+    "lb_set_timing", "lb_get_timing", "lb_step_sums", "lb_adjoint_step_impulse", "lb_adjoint_couple",
+    "lb_adjoint_kinetic_coupled",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
     "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
     "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
@@ -127,6 +128,11 @@ def load(path: str | None = None):
             "lb_box_muller": (i, [vp, i, vp, vp]),
             "lb_set_timing": (i, [H, i]),
             "lb_step_sums": (i, [H, i, vp]),
+            "lb_adjoint_step_impulse": (i, [H, vp, vp, vp, vp, vp]),
+            "lb_adjoint_couple": (i, [H, vp, C.POINTER(lb_particles), C.POINTER(lb_couple_params), vp, vp, vp,
+                                      vp, vp]),
+            "lb_adjoint_kinetic_coupled": (i, [H, C.POINTER(lb_particles), C.POINTER(lb_couple_params), i, i,
+                                               C.POINTER(i), C.POINTER(i), vp, vp, vp, vp]),
             "lb_get_timing": (i, [H, C.POINTER(C.c_double), C.POINTER(i), C.POINTER(C.c_double), C.POINTER(i)]),
             "lb_get_launch_count": (i, [H, C.POINTER(u64)]),
             "lb_moment_sums_static": (i, [P, vp, vp, vp]),
@@ -295,6 +301,24 @@ def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, g
 
 def lb_box_muller(words, npairs, gauss, stream=None):
     _check(load().lb_box_muller(_ptr(words), int(npairs), _ptr(gauss), _stream(stream)))
+
+
+def lb_adjoint_step_impulse(h, state, impulse, lam_in, lam_out, grad_force=None):
+    _check(load().lb_adjoint_step_impulse(h, _ptr(state), _ptr(impulse), _ptr(lam_in), _ptr(lam_out),
+                                          _ptr(grad_force)))
+
+
+def lb_adjoint_couple(h, state, start, cp, lam_facc, lam_pos, lam_mom, lam_pops, grad_force=None):
+    _check(load().lb_adjoint_couple(h, _ptr(state), C.byref(start), C.byref(cp), _ptr(lam_facc), _ptr(lam_pos),
+                                    _ptr(lam_mom), _ptr(lam_pops), _ptr(grad_force)))
+
+
+def lb_adjoint_kinetic_coupled(h, parts, cp, nsteps, checkpoint_every, lo, hi, grad_force, grad_pos, grad_mom,
+                               loss):
+    L3 = C.c_int * 3
+    _check(load().lb_adjoint_kinetic_coupled(h, C.byref(parts), C.byref(cp), int(nsteps), int(checkpoint_every),
+                                             L3(*lo), L3(*hi), _ptr(grad_force), _ptr(grad_pos), _ptr(grad_mom),
+                                             _ptr(loss)))
 
 
 def lb_step_sums(h, nsteps, sums):

@@ -148,3 +148,122 @@ def test_config_64cubed_500_steps(ora):
         errs.append(abs(fd - gw[c, z, y, x]) / max(abs(gw[c, z, y, x]), 1e-3 * np.abs(gw).max()))
     print("64^3 finite differences: max rel err %.2e" % max(errs))
     assert max(errs) < 1e-2
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_coupled_reverse_pass_parity(ora, walls):
+    """Reverse pass through coupled steps (free particles at kT = 0, 5
+    sub-steps per LB step, 8 LB steps, checkpoints every 3): the library's
+    dL/dforce, dL/d(initial positions) and dL/d(initial momenta) against the
+    FP64 oracle's reverse pass (Sec. 4.5 with Eqs. Delta, 2point)."""
+    shape, T, K = (12, 10, 12), 8, 3
+    lo, hi = (2, 2, 2), (10, 8, 10)
+    rng = np.random.default_rng(21)
+    f = inputs.gaussian_field(shape, 3, 1e-4, seed=22).astype(np.float32)
+    u0 = inputs.shear_wave(shape, 0.02) + inputs.gaussian_field(shape, 3, 2e-3, seed=23)
+    if walls:
+        f[:, 0] = f[:, -1] = 0
+        u0[:, 0] = u0[:, -1] = 0
+    n = 24
+    pos = rng.uniform(0.0, 1.0, (n, 3)) * np.array(shape, dtype=float)
+    if walls:
+        pos[:, 2] = rng.uniform(1.2, shape[2] - 2.2, n)
+        pos[0, 2] = 1.05
+        pos[1, 2] = shape[2] - 2.05
+    mom = rng.normal(0.0, 0.03, (n, 3)).astype(np.float32).astype(np.float64)
+    if walls:  # two of them head into the walls
+        mom[0, 2], mom[1, 2] = -0.25, 0.25
+    p = ora.make_params(shape, walls=walls)
+    s0 = ora.equilibrium(p, None, u0)
+    L_want, g_want, lp_want, lm_want = ora.coupled_kinetic_energy_and_grad(
+        p, s0, f.astype(np.float64), pos, mom, 1.0, 2.0, dt=0.1, n_substeps=5, nsteps=T, lo=lo, hi=hi)
+
+    lat = L.Lattice(shape, walls=walls, force=dev(f))
+    lat.set_populations(dev(s0, torch.float64))
+    gpos, gmom = dev(pos, torch.float64), dev(mom)
+    parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
+    cp = L.couple_params(n_substeps=5, dt=0.1)
+    g = torch.empty((3,) + shape[::-1], dtype=torch.float32, device="cuda")
+    gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+    gm = torch.empty_like(gp)
+    loss = torch.empty(1, dtype=torch.float64, device="cuda")
+    L.lb_adjoint_kinetic_coupled(lat.h, parts, cp, T, K, lo, hi, g, gp, gm, loss)
+    assert lat.sync() == (L.LB_OK, 0)
+    assert float(loss.item()) == pytest.approx(L_want, rel=1e-4)
+    fl = slice(1, shape[2] - 1) if walls else slice(None)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert cos(gg[:, fl], g_want[:, fl]) > 0.99999
+    assert rel(gg[:, fl], g_want[:, fl]) < 2e-3
+    for got, want in ((gp, lp_want), (gm, lm_want)):
+        got = got.cpu().numpy().astype(np.float64)
+        assert cos(got, want) > 0.99999
+        assert rel(got, want) < 2e-3
+    # the forward part advanced the particles as lb_couple_particles does
+    want_pos = pos.copy()
+    opos, omom, st = pos.copy(), mom.copy(), s0
+    for t in range(T):
+        opos, omom, facc, _ = ora.couple(p, st, opos, omom, 1.0, 2.0, dt=0.1, n_substeps=5, seed=0,
+                                         force=f.astype(np.float64))
+        st = ora.step(p, st, f.astype(np.float64) + facc, t)
+    d = gpos.cpu().numpy() - opos
+    d -= np.array(shape) * np.round(d / np.array(shape))
+    assert np.abs(d).max() < 1e-5, want_pos
+
+
+def test_coupled_reverse_rejects_noise_and_chains():
+    shape = (8, 8, 8)
+    lat = L.Lattice(shape, kT=1e-4)
+    g = torch.zeros((3, 8, 8, 8), dtype=torch.float32, device="cuda")
+    pos = torch.zeros((4, 3), dtype=torch.float64, device="cuda") + 2.5
+    mom = torch.zeros((4, 3), dtype=torch.float32, device="cuda")
+    parts = L.particles(4, pos, mom, mass0=1.0, gamma0=2.0)
+    gp, gm = torch.zeros_like(mom), torch.zeros_like(mom)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LBError) as e:
+        L.lb_adjoint_kinetic_coupled(lat.h, parts, L.couple_params(n_substeps=2, dt=0.1), 2, 1, (0, 0, 0),
+                                     (8, 8, 8), g, gp, gm, loss)
+    assert e.value.status == L.LB_EUNSUPPORTED
+    lat2 = L.Lattice(shape)
+    with pytest.raises(L.LBError) as e:
+        L.lb_adjoint_kinetic_coupled(lat2.h, parts, L.couple_params(n_substeps=2, dt=0.1, chain_len=4,
+                                                                    use_wca=True, r0=1.5, sigma=1.0), 2, 1,
+                                     (0, 0, 0), (8, 8, 8), g, gp, gm, loss)
+    assert e.value.status == L.LB_EUNSUPPORTED
+
+
+def test_coupled_autograd_matches_library_gradients():
+    """adjoint.coupled_kinetic_energy hands the library's gradients to
+    autograd (force field, initial positions and momenta)."""
+    shape, T = (10, 8, 10), 4
+    lo, hi = (2, 2, 2), (8, 6, 8)
+    rng = np.random.default_rng(31)
+    f = dev(inputs.gaussian_field(shape, 3, 1e-4, seed=32))
+    u0 = inputs.shear_wave(shape, 0.02)
+    n = 6
+    pos0 = rng.uniform(0.0, 1.0, (n, 3)) * np.array(shape, dtype=float)
+    mom0 = rng.normal(0.0, 0.03, (n, 3))
+    cp = L.couple_params(n_substeps=4, dt=0.1)
+    grads = []
+    for use_autograd in (False, True):
+        lat = L.Lattice(shape, force=torch.zeros_like(f))
+        lat.init_equilibrium(None, dev(u0, torch.float64))
+        pos, mom = dev(pos0, torch.float64), dev(mom0)
+        if use_autograd:
+            fr = f.clone().requires_grad_(True)
+            pr = pos.clone().requires_grad_(True)
+            mr = mom.clone().requires_grad_(True)
+            loss = adjoint.coupled_kinetic_energy(fr, pr, mr, lat, cp, T, lo, hi, mass0=1.0, gamma0=2.0,
+                                                  checkpoint_every=2)
+            loss.backward()
+            grads.append((fr.grad, pr.grad.float(), mr.grad))
+        else:
+            lat.force.copy_(f)
+            parts = L.particles(n, pos, mom, mass0=1.0, gamma0=2.0)
+            g = torch.empty_like(f)
+            gp = torch.empty((n, 3), dtype=torch.float32, device="cuda")
+            gm = torch.empty_like(gp)
+            ls = torch.empty(1, dtype=torch.float64, device="cuda")
+            L.lb_adjoint_kinetic_coupled(lat.h, parts, cp, T, 2, lo, hi, g, gp, gm, ls)
+            grads.append((g, gp, gm))
+    for a, b in zip(*grads):
+        assert torch.allclose(a, b, rtol=1e-4, atol=1e-9)  # atomics sum in a different order
