@@ -303,6 +303,85 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
     }
 }
 
+// The same for FP32 storage, by a correction of the stored result instead of
+// a second update: the forces enter the collision only through u and the
+// force moments of modes 1..9, and rho and the pre-collision j are
+// recovered from the stored n* (mass is conserved, the stored momentum is
+// j + f).  With f_b the force of the first update and f_n = f_b + the
+// impulse, the stored moments change by dM_1..3 = 3 (f_n - f_b) and, for
+// k = 4..9, dM_k = ((1 - gamma_k) (m^eq_k(u_n) - m^eq_k(u_b)) + F_k(u_n, f_n)
+// - F_k(u_b, f_b)) / w_k; n* += backward(dM).  No pull and no noise; the
+// claim makes sure each node is corrected once.
+template <bool WALLS>
+__global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restrict__ dst, const float *__restrict__ ffield,
+                                                                 const float *__restrict__ facc, const int *records, int n,
+                                                                 int nsub, unsigned int *claim, unsigned int tag,
+                                                                 const StepArgs a)
+{
+    const int t = blockIdx.x * kBX + threadIdx.x;
+    if (t >= n * 8) return;
+    const int p = t >> 3, q = t & 7;
+    const size_t P = a.pitch;
+    int prev = -1;
+    for (int s = 0; s < nsub; ++s) {
+        const int base = records[(size_t)s * n + p];
+        if (base == prev) continue;  // same cell as the sub-step before
+        prev = base;
+        int x = base % a.nx + (q & 1);
+        int y = (base / a.nx) % a.ny + ((q >> 1) & 1);
+        int z = base / (a.nx * a.ny) + (q >> 2);
+        if (x >= a.nx) x -= a.nx;
+        if (y >= a.ny) y -= a.ny;
+        if (!WALLS && z >= a.nz) z -= a.nz;
+        if (z < a.z0 || z >= a.z1) continue;  // solid node
+        const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
+        if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
+        const float df[3] = {facc[node], facc[P + node], facc[2 * P + node]};
+        if (df[0] == 0.0f && df[1] == 0.0f && df[2] == 0.0f) continue;
+        float ns[19], m[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) ns[i] = dst[(size_t)i * P + node];
+        lbd::forward(ns, m);
+        float fb[3] = {a.fx, a.fy, a.fz};
+        if (ffield) {
+            fb[0] += ffield[node];
+            fb[1] += ffield[a.nn + node];
+            fb[2] += ffield[2 * a.nn + node];
+        }
+        const float fn[3] = {fb[0] + df[0], fb[1] + df[1], fb[2] + df[2]};
+        const float rho = a.rho0 + m[0];
+        const float ir = 1.0f / rho;
+        const float j[3] = {m[1] - fb[0], m[2] - fb[1], m[3] - fb[2]};
+        float dM[19];
+#pragma unroll
+        for (int k = 0; k < 19; ++k) dM[k] = 0.0f;
+        dM[1] = 3.0f * df[0];
+        dM[2] = 3.0f * df[1];
+        dM[3] = 3.0f * df[2];
+        const float gs1 = 1.0f + a.g_shear;
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {  // + (u_n, f_n), - (u_b, f_b)
+            const float *f = side ? fb : fn;
+            const float sg = side ? -1.0f : 1.0f;
+            const float ux = (j[0] + 0.5f * f[0]) * ir, uy = (j[1] + 0.5f * f[1]) * ir, uz = (j[2] + 0.5f * f[2]) * ir;
+            const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
+            const float uf = ux * f[0] + uy * f[1] + uz * f[2];
+            dM[4] += sg * ((1.0f - a.g_bulk) * rho * u2 + (1.0f + a.g_bulk) * uf);
+            dM[5] += sg * ((1.0f - a.g_shear) * rho * (3.0f * uxx - u2) + gs1 * (3.0f * ux * f[0] - uf));
+            dM[6] += sg * ((1.0f - a.g_shear) * rho * (uyy - uzz) + gs1 * (uy * f[1] - uz * f[2]));
+            dM[7] += sg * ((1.0f - a.g_shear) * rho * ux * uy + 0.5f * gs1 * (ux * f[1] + uy * f[0]));
+            dM[8] += sg * ((1.0f - a.g_shear) * rho * uy * uz + 0.5f * gs1 * (uy * f[2] + uz * f[1]));
+            dM[9] += sg * ((1.0f - a.g_shear) * rho * uz * ux + 0.5f * gs1 * (uz * f[0] + ux * f[2]));
+        }
+#pragma unroll
+        for (int k = 4; k < 10; ++k) dM[k] *= lbd::inv_w(k);
+        float dn[19];
+        lbd::backward(dM, dn);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) dst[(size_t)i * P + node] = ns[i] + dn[i];
+    }
+}
+
 // Two neighbouring nodes x0 = 2t, x0 + 1 per thread (even nx).  Both pull
 // their populations from the same rows of each plane, so one address per
 // plane serves both (the second is an immediate offset); planes with c_x = 0
@@ -530,6 +609,16 @@ cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, cons
     const T *s = static_cast<const T *>(src);
     T *d = static_cast<T *>(dst);
     const bool noise = a.kT > 0.0f, walls = h->p.walls != 0;
+    if (DT == 0) {  // FP32: correct the stored result in place
+        float *d32 = reinterpret_cast<float *>(dst);
+        if (walls)
+            k_patch_impulse_nodes_f32<true><<<blocks, kBX, 0, h->stream>>>(d32, h->force, facc, records, n, nsub, claim,
+                                                                          tag, a);
+        else
+            k_patch_impulse_nodes_f32<false><<<blocks, kBX, 0, h->stream>>>(d32, h->force, facc, records, n, nsub,
+                                                                           claim, tag, a);
+        return cudaGetLastError();
+    }
 #define LBI_PATCH(NZ, WL) \
     k_patch_impulse_nodes<DT, NZ, WL><<<blocks, kBX, 0, h->stream>>>(s, d, h->force, facc, records, n, nsub, claim, tag, a)
     if (noise) {

@@ -267,10 +267,12 @@ def test_overlapped_coupling_matches_serial(walls):
     shape = (20, 18, 16)
     a = _coupled_run(shape, walls=walls, overlap=False)
     b = _coupled_run(shape, walls=walls, overlap=True)
-    # FP32 deviations ~1e-2: a few ulps where the impulse sums round differently
+    # FP32 deviations ~1e-2: a few ulps where the impulse sums (and, for FP32
+    # storage, the correction of the stored result) round differently; the
+    # particles follow the fluid to a few ulps of their FP32 cell offsets
     assert np.abs(a[0] - b[0]).max() < 1e-7
-    assert _pos_err(a[1], b[1], shape) < 1e-7
-    assert np.abs(a[2] - b[2]).max() < 1e-7
+    assert _pos_err(a[1], b[1], shape) < 1e-6
+    assert np.abs(a[2] - b[2]).max() < 1e-6
 
 
 def test_overlapped_coupling_joined_by_another_call():
