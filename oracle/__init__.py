@@ -85,7 +85,7 @@ class CoupleParams(C.Structure):
     _fields_ = [
         ("n_substeps", C.c_int), ("noise_kind", C.c_int),
         ("dt", C.c_double), ("seed", C.c_uint64),
-        ("md_step0", C.c_uint32), ("pad_", C.c_uint32),
+        ("md_step0", C.c_uint32), ("kernel", C.c_uint32),
     ]
 
 
@@ -122,7 +122,12 @@ def _load():
                                                _D, _D, _D, _D, _D]
             lib.ora_couple_adjoint.restype = C.c_int
             lib.ora_interpolate.argtypes = [P, _D, _D, C.c_int, _D, _D]
+            lib.ora_interpolate_k.argtypes = [P, C.c_int, _D, _D, C.c_int, _D, _D]
             lib.ora_stencil.argtypes = [P, _D, C.POINTER(C.c_longlong), _D]
+            lib.ora_stencil_k.argtypes = [P, C.c_int, _D, C.POINTER(C.c_longlong), _D]
+            lib.ora_stencil_k.restype = C.c_int
+            lib.ora_phi.argtypes = [C.c_int, C.c_double]
+            lib.ora_phi.restype = C.c_double
             lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
             lib.ora_kinetic_seed.argtypes = [P, _D, _D, C.POINTER(C.c_int), C.POINTER(C.c_int), _D, _D]
             lib.ora_kinetic_seed.restype = C.c_double
@@ -280,7 +285,7 @@ def md_forces(p: Params, md: MD, pos):
 
 
 def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_step0=0,
-           md: MD | None = None, force=None, noise_kind=0):
+           md: MD | None = None, force=None, noise_kind=0, kernel=2):
     """One LB step's worth of particle sub-steps.  Returns (pos, mom, facc, broken);
     facc has shape (3, nz, ny, nx) and holds the spread impulses -J Delta."""
     lib = _load()
@@ -292,7 +297,7 @@ def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_s
     facc = np.zeros((3, p.nz, p.ny, p.nx))
     cp = CoupleParams()
     cp.n_substeps, cp.noise_kind, cp.dt = int(n_substeps), int(noise_kind), float(dt)
-    cp.seed, cp.md_step0 = int(seed), int(md_step0)
+    cp.seed, cp.md_step0, cp.kernel = int(seed), int(md_step0), int(kernel)
     src = np.ascontiguousarray(pops, dtype=np.float64)
     f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
     broken = lib.ora_couple(C.byref(p), _dp(src), _dp(f), n, _dp(pos), _dp(mom), _dp(mass),
@@ -372,23 +377,30 @@ def coupled_kinetic_energy_and_grad(p: Params, pops0, force, pos0, mom0, mass, g
     return L, g, lpos, lmom
 
 
-def interpolate(p: Params, pops, pos, force=None):
+def interpolate(p: Params, pops, pos, force=None, kernel=2):
+    """u at the positions with interpolation function phi_kernel (2, 3, 4)."""
     lib = _load()
     pos = np.ascontiguousarray(pos, dtype=np.float64)
     up = np.empty_like(pos)
     src = np.ascontiguousarray(pops, dtype=np.float64)
     f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
-    lib.ora_interpolate(C.byref(p), _dp(src), _dp(f), pos.shape[0], _dp(pos), _dp(up))
+    lib.ora_interpolate_k(C.byref(p), int(kernel), _dp(src), _dp(f), pos.shape[0], _dp(pos), _dp(up))
     return up
 
 
-def stencil(p: Params, pos3):
+def stencil(p: Params, pos3, kernel=2):
+    """The K^3 stencil nodes (linear indices) and weights of phi_kernel."""
     lib = _load()
     pp = np.ascontiguousarray(pos3, dtype=np.float64)
-    node = (C.c_longlong * 8)()
-    wt = np.zeros(8)
-    lib.ora_stencil(C.byref(p), _dp(pp), node, _dp(wt))
-    return np.array(list(node), dtype=np.int64), wt
+    node = (C.c_longlong * 64)()
+    wt = np.zeros(64)
+    nq = lib.ora_stencil_k(C.byref(p), int(kernel), _dp(pp), node, _dp(wt))
+    return np.array(list(node)[:nq], dtype=np.int64), wt[:nq]
+
+
+def phi(kernel, v):
+    """The one-dimensional interpolation function phi_kernel(v)."""
+    return _load().ora_phi(int(kernel), float(v))
 
 
 def adjoint_step(p: Params, state, lam_in, force=None, grad_f=None):

@@ -28,7 +28,10 @@
  *  - conserved-mode eigenvalues gamma_0..3 = 1;
  *  - noise: Philox4x32-10 keyed on (seed) with counter
  *    (node, step, domain<<8 | block, replica), 23-bit odd uniforms,
- *    Box-Muller pairs.
+ *    Box-Muller pairs;
+ *  - interpolation: phi_2 by default, phi_3 / phi_4 on request (Sec. 4.6);
+ *    with walls a particle stays K/2 lattice units from the solid planes,
+ *    K the stencil width.
  */
 #include <math.h>
 #ifdef _OPENMP
@@ -611,15 +614,78 @@ static void stencil(const ora_params *P, const double p[3], size_t node[8], doub
             }
 }
 
+/* phi_3, Eq. (3point): three nodes, moment conditions C1-C3, continuous
+ * first derivative. */
+static double phi3(double v)
+{
+    double a = fabs(v);
+    if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * v * v)) / 3.0;
+    if (a <= 1.5) return (5.0 - 3.0 * a - sqrt(-2.0 + 6.0 * a - 3.0 * v * v)) / 6.0;
+    return 0.0;
+}
+
+/* phi_4, Eq. (4point): four nodes. */
+static double phi4(double v)
+{
+    double a = fabs(v);
+    if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * v * v)) / 8.0;
+    if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * v * v)) / 8.0;
+    return 0.0;
+}
+
+/* Nodes per axis of interpolation function kern (2, 3, 4) and the first of
+ * them for coordinate p: every node with phi(j - p) > 0 lies in [j0, j0 + K). */
+static int kernel_width(int kern) { return kern == 3 ? 3 : (kern == 4 ? 4 : 2); }
+
+static int kernel_first(int kern, double p)
+{
+    if (kern == 3) return (int)floor(p + 0.5) - 1;
+    if (kern == 4) return (int)floor(p) - 1;
+    return (int)floor(p);
+}
+
+static double phi_of(int kern, double v)
+{
+    if (kern == 3) return phi3(v);
+    if (kern == 4) return phi4(v);
+    return phi2(v);
+}
+
+/* The K^3 nodes of Delta (Eq. Delta) with phi_kern around position p and
+ * their weights, x fastest; nodes outside the box (walls) get weight 0.
+ * Returns K^3.  For kern 2 it is stencil() above. */
+static int stencil_k(const ora_params *P, int kern, const double p[3], size_t *node, double *wt)
+{
+    const int K = kernel_width(kern);
+    int b[3];
+    for (int c = 0; c < 3; c++) b[c] = kernel_first(kern, p[c]);
+    int q = 0;
+    for (int dz = 0; dz < K; dz++)
+        for (int dy = 0; dy < K; dy++)
+            for (int dx = 0; dx < K; dx++) {
+                int nxv = b[0] + dx, nyv = b[1] + dy, nzv = b[2] + dz;
+                double w = phi_of(kern, nxv - p[0]) * phi_of(kern, nyv - p[1]) * phi_of(kern, nzv - p[2]);
+                nxv = wrap(nxv, P->nx);
+                nyv = wrap(nyv, P->ny);
+                nzv = P->walls ? nzv : wrap(nzv, P->nz);
+                if (nzv < 0 || nzv >= P->nz) { nzv = 0; w = 0.0; }
+                node[q] = lin(P, nxv, nyv, nzv);
+                wt[q] = w;
+                q++;
+            }
+    return q;
+}
+
 /* Put a position back into the box: periodic wrap in x, y (and z without
- * walls); with walls, specular reflection keeps z in [1, nz-2] so that the
- * stencil touches fluid nodes only (a project reading). */
-static void confine(const ora_params *P, double p[3], double m[3])
+ * walls); with walls, specular reflection keeps z in [b, nz-1-b], b = K/2 for
+ * a stencil K nodes wide, so that the stencil touches fluid nodes only (a
+ * project reading; b = 1 for phi_2). */
+static void confine_band(const ora_params *P, double band, double p[3], double m[3])
 {
     const int L[3] = {P->nx, P->ny, P->nz};
     for (int c = 0; c < 3; c++) {
         if (c == 2 && P->walls) {
-            double lo = 1.0, hi = (double)(P->nz - 2);
+            double lo = band, hi = (double)(P->nz - 1) - band;
             if (p[2] < lo) { p[2] = 2.0 * lo - p[2]; m[2] = -m[2]; }
             if (p[2] > hi) { p[2] = 2.0 * hi - p[2]; m[2] = -m[2]; }
         } else {
@@ -629,13 +695,15 @@ static void confine(const ora_params *P, double p[3], double m[3])
     }
 }
 
+static void confine(const ora_params *P, double p[3], double m[3]) { confine_band(P, 1.0, p, m); }
+
 typedef struct {
     int n_substeps;
     int noise_kind;     /* 0: Gaussian theta; 1: three-point theta in {0, +-sqrt3} */
     double dt;          /* particle time step in lattice units (h = 1 per LB step) */
     uint64_t seed;      /* particle noise key                                      */
     uint32_t md_step0;  /* global index of the first sub-step (noise counter)      */
-    uint32_t pad_;
+    uint32_t kernel;    /* interpolation function phi_2 (0 or 2), phi_3, phi_4     */
 } ora_couple_params;
 
 /* Particle noise theta (3 components) for particle p at sub-step t:
@@ -682,7 +750,7 @@ int ora_couple(const ora_params *P, const double *pops, const double *force, int
     for (int s = 0; s < C->n_substeps; s++) {
         for (int p = 0; p < np; p++) {
             for (int c = 0; c < 3; c++) pos[3 * p + c] += 0.5 * h * mom[3 * p + c] / mass[p];
-            confine(P, pos + 3 * p, mom + 3 * p);
+            confine_band(P, 0.5 * kernel_width((int)C->kernel), pos + 3 * p, mom + 3 * p);
         }
         if (md) broken += ora_md_forces(P, md, np, pos, fc);
         for (int p = 0; p < np; p++) {
@@ -690,11 +758,11 @@ int ora_couple(const ora_params *P, const double *pops, const double *force, int
             double C1 = exp(-G * h / m);
             double C2 = (m / G) * (1.0 - C1);
             double C3 = sqrt(m * P->kT * (1.0 - exp(-2.0 * G * h / m)));
-            size_t node[8];
-            double wt[8];
-            stencil(P, pos + 3 * p, node, wt);
+            size_t node[64];
+            double wt[64];
+            const int nq = stencil_k(P, (int)C->kernel, pos + 3 * p, node, wt);
             double up[3] = {0.0, 0.0, 0.0};
-            for (int q = 0; q < 8; q++)
+            for (int q = 0; q < nq; q++)
                 for (int c = 0; c < 3; c++) up[c] += wt[q] * u[3 * node[q] + c];
             double th[3] = {0.0, 0.0, 0.0};
             if (P->kT > 0.0) particle_theta(P, C, (uint32_t)p, C->md_step0 + (uint32_t)s, th);
@@ -704,13 +772,13 @@ int ora_couple(const ora_params *P, const double *pops, const double *force, int
                 pn[c] = C1 * mom[3 * p + c] + C2 * (Fc + G * up[c]) + C3 * th[c];
                 J[c] = pn[c] - mom[3 * p + c] - C2 * Fc;
             }
-            for (int q = 0; q < 8; q++)
+            for (int q = 0; q < nq; q++)
                 for (int c = 0; c < 3; c++) facc[(size_t)c * N + node[q]] -= J[c] * wt[q];
             for (int c = 0; c < 3; c++) mom[3 * p + c] = pn[c];
         }
         for (int p = 0; p < np; p++) {
             for (int c = 0; c < 3; c++) pos[3 * p + c] += 0.5 * h * mom[3 * p + c] / mass[p];
-            confine(P, pos + 3 * p, mom + 3 * p);
+            confine_band(P, 0.5 * kernel_width((int)C->kernel), pos + 3 * p, mom + 3 * p);
         }
     }
     free(u);
@@ -718,34 +786,50 @@ int ora_couple(const ora_params *P, const double *pops, const double *force, int
     return broken;
 }
 
-/* Interpolated fluid velocity at arbitrary positions (Eq. ufluid_discrete). */
-void ora_interpolate(const ora_params *P, const double *pops, const double *force, int np,
-                     const double *pos, double *up)
+/* Interpolated fluid velocity at arbitrary positions (Eq. ufluid_discrete)
+ * with interpolation function phi_kern. */
+void ora_interpolate_k(const ora_params *P, int kern, const double *pops, const double *force, int np,
+                       const double *pos, double *up)
 {
     build_tables();
     size_t N = nodes_of(P);
     double *u = (double *)malloc(sizeof(double) * 3 * N);
     node_velocity(P, pops, force, u);
     for (int p = 0; p < np; p++) {
-        size_t node[8];
-        double wt[8], pp[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
-        stencil(P, pp, node, wt);
+        size_t node[64];
+        double wt[64], pp[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+        const int nq = stencil_k(P, kern, pp, node, wt);
         for (int c = 0; c < 3; c++) {
             double acc = 0.0;
-            for (int q = 0; q < 8; q++) acc += wt[q] * u[3 * node[q] + c];
+            for (int q = 0; q < nq; q++) acc += wt[q] * u[3 * node[q] + c];
             up[3 * p + c] = acc;
         }
     }
     free(u);
 }
 
-/* Stencil export for the interpolation-kernel tests. */
+void ora_interpolate(const ora_params *P, const double *pops, const double *force, int np,
+                     const double *pos, double *up)
+{
+    ora_interpolate_k(P, 2, pops, force, np, pos, up);
+}
+
+/* Stencil export for the interpolation-kernel tests: K^3 nodes and weights. */
+int ora_stencil_k(const ora_params *P, int kern, const double *p, long long *node, double *wt)
+{
+    size_t nd[64];
+    const int nq = stencil_k(P, kern, p, nd, wt);
+    for (int q = 0; q < nq; q++) node[q] = (long long)nd[q];
+    return nq;
+}
+
 void ora_stencil(const ora_params *P, const double *p, long long *node, double *wt)
 {
-    size_t nd[8];
-    stencil(P, p, nd, wt);
-    for (int q = 0; q < 8; q++) node[q] = (long long)nd[q];
+    ora_stencil_k(P, 2, p, node, wt);
 }
+
+/* phi_kern(v) itself, for the moment-condition tests. */
+double ora_phi(int kern, double v) { return phi_of(kern, v); }
 
 /* ------------------------------------------------------------------------ */
 /* Reverse mode (kT = 0): a hand-derived adjoint of one stream-collide step  */

@@ -1,9 +1,11 @@
 """Pins of the oracle's particle side against what the paper fixes.
 
-- Sec. 4.6 Eqs. (DnormDiscrete), (C1), (C2): the linear stencil sums to one
-  and reproduces the particle position exactly; the product form of Eq. (Delta)
-  interpolates any linear velocity field exactly, and the coupling interpolates
-  u, not j (Sec. 4.5).
+- Sec. 4.6 Eqs. (DnormDiscrete), (C1), (C2): the stencils of phi_2, phi_3
+  and phi_4 sum to one and reproduce the particle position exactly; the
+  product form of Eq. (Delta) interpolates any linear velocity field exactly,
+  and the coupling interpolates u, not j (Sec. 4.5).  Eq. (C3): sum phi^2 is
+  1/2 for phi_3 and 3/8 for phi_4 wherever the particle is; phi_3 has a
+  continuous first derivative.
 - Sec. 4.5: total particle + fluid momentum is conserved by the coupling plus
   the following LB step (pair forces, uniform Gamma/m).
 - Eq. (langevin_momentum_update) is the exact Ornstein-Uhlenbeck solution:
@@ -18,24 +20,57 @@ import pytest
 from paper_0803_2826_gb300 import inputs
 
 
-def test_stencil_moment_conditions(ora):
+@pytest.mark.parametrize("kernel", [2, 3, 4])
+def test_stencil_moment_conditions(ora, kernel):
+    """Eqs. C1, C2 for the 3-d stencil of phi_2, phi_3, phi_4: weights sum to
+    1 and their first moments give the position (unwrapped node coordinates)."""
     p = ora.make_params((8, 9, 10))
     rng = np.random.default_rng(0)
+    K = kernel
     for _ in range(50):
         r = rng.uniform(0, 1, 3) * np.array([8, 9, 10])
-        node, wt = ora.stencil(p, r)
-        assert np.isclose(wt.sum(), 1.0, rtol=0, atol=1e-15)
+        node, wt = ora.stencil(p, r, kernel)
+        assert len(wt) == K ** 3
+        assert np.isclose(wt.sum(), 1.0, rtol=0, atol=1e-14)
         assert np.all(wt >= 0)
-        # sum_j j phi(u - j) = u, per axis, using unwrapped node coordinates
-        b = np.floor(r)
+        b = np.floor(r + 0.5) - 1 if K == 3 else (np.floor(r) - 1 if K == 4 else np.floor(r))
         q = 0
         acc = np.zeros(3)
-        for dz in range(2):
-            for dy in range(2):
-                for dx in range(2):
+        for dz in range(K):
+            for dy in range(K):
+                for dx in range(K):
                     acc += wt[q] * (b + np.array([dx, dy, dz]))
                     q += 1
         assert np.allclose(acc, r, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("kernel,C", [(3, 0.5), (4, 0.375)])
+def test_phi_moment_conditions(ora, kernel, C):
+    """Eqs. C1-C3 in one dimension for phi_3 (Eq. 3point) and phi_4 (Eq.
+    4point): sum phi = 1, sum j phi = u and sum phi^2 = C independent of u
+    (1/2 and 3/8); phi_2 satisfies C1, C2 but not C3."""
+    us = np.linspace(-3.0, 3.0, 611) + 1e-3
+    js = np.arange(-8, 9)
+    for u in us:
+        ph = np.array([ora.phi(kernel, u - j) for j in js])
+        assert abs(ph.sum() - 1.0) < 1e-14
+        assert abs((js * ph).sum() - u) < 1e-13
+        assert abs((ph * ph).sum() - C) < 1e-14
+    s2 = [sum(ora.phi(2, u - j) ** 2 for j in js) for u in us]
+    assert max(s2) - min(s2) > 0.4  # 1/2 .. 1
+
+
+def test_phi3_first_derivative_continuous(ora):
+    """phi_3 has a continuous first derivative (Sec. 4.6), also at the
+    branch points |u| = 1/2 and 3/2; phi_2 has a jump at 0."""
+    h = 1e-7
+    for b in (-1.5, -0.5, 0.5, 1.5):
+        left = (ora.phi(3, b) - ora.phi(3, b - h)) / h
+        right = (ora.phi(3, b + h) - ora.phi(3, b)) / h
+        assert abs(left - right) < 1e-4, (b, left, right)
+    left = (ora.phi(2, 0.0) - ora.phi(2, -h)) / h
+    right = (ora.phi(2, h) - ora.phi(2, 0.0)) / h
+    assert abs(left - right) > 1.9
 
 
 def test_interpolates_linear_u_not_j(ora):
@@ -58,16 +93,19 @@ def test_interpolates_linear_u_not_j(ora):
     rr, jj, _ = ora.moments(p, pops)
     assert np.allclose(jj / rr, u, rtol=1e-12, atol=1e-16)
     pos = inputs.uniform_particles(40, (1, 1, 1), seed=1) * 6 + 3  # interior
-    up = ora.interpolate(p, pops, pos)
-    want = U0[None, :] + pos @ G.T
-    assert np.allclose(up, want, rtol=1e-12, atol=1e-15)
-    # interpolating j and dividing by interpolated rho would not be exact
-    assert np.abs(up - want).max() < 1e-14
+    for kernel in (2, 3, 4):  # Eq. C2 makes every kernel exact for a linear field
+        up = ora.interpolate(p, pops, pos, kernel=kernel)
+        want = U0[None, :] + pos @ G.T
+        assert np.allclose(up, want, rtol=1e-12, atol=1e-15)
+        # interpolating j and dividing by interpolated rho would not be exact
+        assert np.abs(up - want).max() < 1e-14
 
 
-def test_momentum_conservation_coupled(ora):
+@pytest.mark.parametrize("kernel", [2, 3, 4])
+def test_momentum_conservation_coupled(ora, kernel):
     """Sigma p + fluid momentum is unchanged by couple() followed by the LB
-    step that applies the spread impulses (FP64 <= 1e-12 relative)."""
+    step that applies the spread impulses (FP64 <= 1e-12 relative), for each
+    interpolation function (Eq. C1)."""
     shape = (10, 10, 10)
     kT = 1e-4
     p = ora.make_params(shape, kT=kT, seed=1)
@@ -80,13 +118,38 @@ def test_momentum_conservation_coupled(ora):
     fluid0 = pops.reshape(19, -1).sum(1) @ c
     P0 = mom.sum(0) + fluid0
     pos1, mom1, facc, broken = ora.couple(p, pops, pos, mom, 1.0, 2.0, dt=0.1, n_substeps=10,
-                                          seed=9, md=md)
+                                          seed=9, md=md, kernel=kernel)
     assert broken == 0
     # impulse bookkeeping: particles + accumulator conserved
     assert np.allclose(mom1.sum(0) + facc.reshape(3, -1).sum(1), mom.sum(0), rtol=0, atol=1e-14)
     out = ora.step(p, pops, facc, 0)
     P1 = mom1.sum(0) + out.reshape(19, -1).sum(1) @ c
     assert np.allclose(P1, P0, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("kernel", [2, 3, 4])
+def test_wall_band_keeps_stencil_off_solid_planes(ora, kernel):
+    """With walls, positions reflect into z in [K/2, nz-1-K/2] (a project
+    reading) so that the K-node stencil of phi_K never reaches a solid plane:
+    no impulse lands on z = 0 or nz-1, and the impulses still sum to the
+    momentum the particles gave up (Eq. C1)."""
+    shape = (8, 8, 10)
+    p = ora.make_params(shape, walls=True)
+    u = inputs.shear_wave(shape, 0.02)
+    pops = ora.equilibrium(p, None, u)
+    rng = np.random.default_rng(5)
+    n = 60
+    pos = np.column_stack([rng.uniform(0, 8, n), rng.uniform(0, 8, n), rng.uniform(1.0, 8.0, n)])
+    mom = rng.normal(0, 0.5, (n, 3))
+    mom[:, 2] = np.where(pos[:, 2] < 4.5, -1.5, 1.5)  # drive them towards the walls
+    pos1, mom1, facc, _ = ora.couple(p, pops, pos, mom, 1.0, 0.5, dt=0.2, n_substeps=4, seed=2,
+                                     kernel=kernel)
+    b = kernel / 2.0
+    assert np.all(pos1[:, 2] >= b) and np.all(pos1[:, 2] <= shape[2] - 1 - b)
+    assert np.all(facc[:, 0] == 0.0) and np.all(facc[:, -1] == 0.0)
+    assert np.abs(facc).max() > 0
+    # reflections flip p_z, so only x and y of the impulse balance are checked
+    assert np.allclose(mom1.sum(0)[:2] + facc.reshape(3, -1).sum(1)[:2], mom.sum(0)[:2], rtol=0, atol=1e-13)
 
 
 def test_ou_update_stationary(ora):
