@@ -394,7 +394,7 @@ def run_ours(args):
 
 
 def _forms(peak):
-    """The three further forms, each timed with CUDA events against the plain
+    """The further forms, each timed with CUDA events against the plain
     FP32 form on the same box:
       batched   512 periodic replicas, edges from {16,24,32,48,64} drawn with
                 seed 7, replica r keyed by seed r, kT = 1e-4, FP32: autotuned,
@@ -402,6 +402,7 @@ def _forms(peak):
       adjoint   64^3, kT = 0, force field ~ N(0, 1e-5), kinetic energy of the
                 central 16^3 after 500 steps, checkpoints every 50: forward +
                 reverse ms per step vs 500 plain FP32 steps;
+      interpolation  the headline coupled workload with phi_3 and phi_4;
       precision 512^3 between walls, g = 1e-6, kT = 1e-4: ms per LB step with
                 FP16 / BF16 storage vs FP32 storage (no particles)."""
     import numpy as np
@@ -470,6 +471,9 @@ def _forms(peak):
                       "timing": "wall clock around lb_adjoint_kinetic (includes its checkpoint allocations)"}
     lat.close()
 
+    # wider interpolation stencils on the headline workload
+    out["interpolation"] = _interpolation_forms(stream)
+
     # reduced-precision storage
     shape = (512, 512, 512)
     prec = {}
@@ -495,6 +499,58 @@ def _forms(peak):
         prec[name]["speedup_vs_f32"] = prec["f32"]["ms_per_step"] / prec[name]["ms_per_step"]
     out["precision"] = {"shape": list(shape), "walls": True, "kT": KT, **prec}
     return out
+
+
+def _interpolation_forms(stream, steps=100):
+    """The coupled 256^3 workload of the headline line with the three- and
+    four-point interpolation functions (27 / 64 stencil nodes per monomer,
+    per-sub-step kernels, coupling overlapped with the LB update): ms per
+    step and the coupling's ms per step from the library's kernel timers."""
+    import torch
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    npart = N_CHAINS * CHAIN_LEN
+    lat = L.Lattice(SHAPE, kT=KT, seed=0, stream=stream)
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+    pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, SHAPE, seed=0)
+    mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000)
+    res = {"steps": steps, "workload": workload()}
+    for phi in (3, 4):
+        gpos = torch.as_tensor(pos0).cuda()
+        gmom = torch.as_tensor(mom0, dtype=torch.float32).cuda()
+        torch.cuda.synchronize()
+        parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
+        cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=7, chain_len=CHAIN_LEN, use_wca=True, eps=EPS,
+                             sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=True, kernel=phi)
+
+        def run(k, t0):
+            for t in range(k):
+                cp.md_step0 = NSUB * (t0 + t)
+                L.lb_couple_particles(lat.h, parts, cp)
+                L.lb_step(lat.h, 1)
+
+        with torch.cuda.stream(stream):
+            run(5, 0)
+        torch.cuda.synchronize()
+        L.lb_set_timing(lat.h, steps)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            run(steps, 5)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / steps
+        sc_sum, sc_n, cp_sum, cp_n = L.lb_get_timing(lat.h)
+        L.lb_set_timing(lat.h, 0)
+        st, bits = lat.sync()
+        assert bits == 0, "device error word 0x%x (phi_%d)" % (bits, phi)
+        nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
+        res["phi%d" % phi] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6,
+                              "coupling_ms_per_step": cp_sum / cp_n, "stream_collide_ms": sc_sum / sc_n}
+    lat.close()
+    torch.cuda.empty_cache()
+    return res
 
 
 def _profiled_traffic(mode):

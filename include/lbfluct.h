@@ -217,7 +217,7 @@ typedef struct {
     uint32_t md_step0;   /* Philox step word of the first sub-step                   */
     int chain_len;       /* > 1: particles k*chain_len..(k+1)*chain_len-1 are a FENE chain */
     int use_wca;         /* purely repulsive LJ between all pairs                    */
-    int flags;           /* 0, or LB_COUPLE_PER_SUBSTEP                              */
+    int flags;           /* 0, or LB_COUPLE_* bits below                             */
     double eps, sigma;   /* WCA parameters                                           */
     double k_fene, r0;   /* FENE parameters                                          */
 } lb_couple_params;
@@ -241,14 +241,30 @@ typedef struct {
  * coupling.  Until then the caller must not read pos / mom itself. */
 #define LB_COUPLE_OVERLAP 0x2
 
+/* lb_couple_params.flags: interpolate and spread with the three-point
+ * function phi_3 (Sec. 4.6, Eq. (3point)) or the four-point phi_4
+ * (Eq. (4point)) instead of the linear phi_2: 27 or 64 nodes per particle
+ * instead of 8.  Both satisfy the moment conditions C1-C3 (sum phi^2 = 1/2
+ * and 3/8 wherever the particle is), so the friction a particle feels does
+ * not depend on its position within a cell.  With walls a particle is kept
+ * K/2 lattice units from the solid planes (K = 3 or 4, the stencil width;
+ * 1 for phi_2), so nz must be at least K + 1.  These calls take the
+ * per-sub-step kernels (the cooperative kernel covers phi_2 only); at most
+ * one of the two bits may be set; the reverse-mode entry points reject
+ * them. */
+#define LB_COUPLE_PHI3 0x4
+#define LB_COUPLE_PHI4 0x8
+
 /* One LB step's worth of particle motion.  The fluid velocity
  * u = (sum n c + f_ext/2)/rho of the current state is held fixed; for each
  * sub-step: half drift; conservative forces F^c (FENE + WCA); u_p =
- * sum_8 Delta(r - r_p) u(r) with Delta = phi_2 phi_2 phi_2; exact OU update
+ * sum Delta(r - r_p) u(r) with Delta = phi_2 phi_2 phi_2 over 8 nodes (or
+ * phi_3 / phi_4 over 27 / 64, see LB_COUPLE_PHI3); exact OU update
  * p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta; the impulse J = p' - p - C2 F^c
  * is spread as -J Delta(r - r_p) into a library accumulator that the next
  * lb_step applies once; half drift.  Positions wrap periodically (x, y; z
- * without walls) or reflect specularly into z in [1, nz-2] with walls.
+ * without walls) or reflect specularly into z in [1, nz-2] with walls (the
+ * band is K/2 from the solid planes for a stencil K nodes wide).
  * theta: Philox domain 1, counters (p, md_step0 + s, 1<<8, replica), key seed.
  * The caller's pos and mom are updated in place.  Errors: LB_EINVAL,
  * LB_ENOMEM, LB_ECUDA; broken bonds and neighbour overflow set device bits. */
@@ -257,6 +273,11 @@ lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_
 /* Interpolated fluid velocity u_p (device FP32 [n][3]) at device positions
  * pos[n][3] (Eq. (ufluid_discrete) with the linear stencil). */
 lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out);
+
+/* The same with interpolation function phi_kernel, kernel = 2, 3 or 4
+ * (Sec. 4.6, Eqs. (2point), (3point), (4point)); lb_interpolate is
+ * kernel 2.  Positions must lie in the box.  Errors: LB_EINVAL. */
+lb_status lb_interpolate_phi(lb_handle *h, int kernel, int n, const double *pos, float *u_out);
 
 /* Kernel timers for profiling: after lb_set_timing(h, capacity) the library
  * records CUDA events around each stream-collide launch of lb_step (with

@@ -18,13 +18,13 @@ extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const
 extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *, float *);
 template <int DT>
 cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
-                            int n, int nsub, unsigned int *claim, unsigned int tag);
+                            int n, int nsub, int span, unsigned int *claim, unsigned int tag);
 extern template cudaError_t launch_patch_dt<0>(const lb_handle *, const void *, void *, const float *, const int *,
-                                               int, int, unsigned int *, unsigned int);
+                                               int, int, int, unsigned int *, unsigned int);
 extern template cudaError_t launch_patch_dt<1>(const lb_handle *, const void *, void *, const float *, const int *,
-                                               int, int, unsigned int *, unsigned int);
+                                               int, int, int, unsigned int *, unsigned int);
 extern template cudaError_t launch_patch_dt<2>(const lb_handle *, const void *, void *, const float *, const int *,
-                                               int, int, unsigned int *, unsigned int);
+                                               int, int, int, unsigned int *, unsigned int);
 
 namespace {
 thread_local char g_msg[512] = "no error";
@@ -221,9 +221,15 @@ lb_status step_once(lb_handle *h, float *partials)
         }
         if (e == cudaSuccess) {
             switch (h->p.dtype) {
-            case LB_F32: e = launch_patch_dt<0>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
-            case LB_F16: e = launch_patch_dt<1>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
-            default: e = launch_patch_dt<2>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->claim, h->claim_tag); break;
+            case LB_F32: e = launch_patch_dt<0>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->patch_span,
+                                                  h->claim, h->claim_tag);
+                break;
+            case LB_F16: e = launch_patch_dt<1>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->patch_span,
+                                                  h->claim, h->claim_tag);
+                break;
+            default: e = launch_patch_dt<2>(h, src, dst, h->facc, h->patch_rec, h->patch_n, h->patch_nsub, h->patch_span,
+                                                  h->claim, h->claim_tag);
+                break;
             }
         }
         if (e != cudaSuccess) return cuda_fail("lb_step", e);
@@ -573,12 +579,17 @@ lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_
 
 lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out)
 {
-    if (!h || n < 0 || (n > 0 && (!pos || !u_out))) {
+    return lb_interpolate_phi(h, 2, n, pos, u_out);
+}
+
+lb_status lb_interpolate_phi(lb_handle *h, int kernel, int n, const double *pos, float *u_out)
+{
+    if (!h || n < 0 || (n > 0 && (!pos || !u_out)) || kernel < 2 || kernel > 4) {
         set_error("lb_interpolate: bad argument");
         return LB_EINVAL;
     }
     join_overlap(h);
-    return interpolate(h, n, pos, u_out);
+    return interpolate(h, kernel, n, pos, u_out);
 }
 
 lb_status lb_get_particle_forces(lb_handle *h, float *out)

@@ -66,6 +66,7 @@ struct lb_handle {
     int overlap_pending;  // a coupling on aux the next lb_step (or any other call) joins
     const int *patch_rec; // its stencil records [patch_nsub][patch_n]
     int patch_n, patch_nsub;
+    int patch_span;       // nodes per axis around a recorded cell: 2 (phi_2) or 4 (phi_3, phi_4)
     unsigned int *claim;  // [n_nodes] tag of the last re-update of each node
     float *lam_u;         // [3][pitch] dL/du at the nodes (coupling reverse pass), kept zero between calls
     unsigned int claim_tag;
@@ -95,7 +96,7 @@ cudaError_t launch_moments(const lb_handle *h, const void *src, float *rho, floa
                            double *sums);
 // particles.cu
 lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
-lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out);
+lb_status interpolate(lb_handle *h, int kernel, int n, const double *pos, float *u_out);
 cudaError_t clear_particle_forces(lb_handle *h);
 void join_overlap(const lb_handle *h);  // order h->stream after a pending overlapped coupling
 // step_sums.cu

@@ -55,6 +55,7 @@ struct Particles {
     int *next = nullptr;         // [cap] next particle in the same bucket
     int *bucket_of = nullptr;    // [cap] bucket of each particle (to empty it again)
     int nb_log2 = 0;             // log2 nbuckets
+    int rec_span = 2;            // nodes per axis the live records' stencils touch (2, or 4 for phi_3 / phi_4)
 };
 
 namespace {
@@ -77,6 +78,7 @@ struct CoupleArgs {
     int ncell[3];          // cell-list cells per axis (edge L / ncell >= r_list)
     float cinv[3];         // ncell / L
     int nb_log2;           // log2 of the bucket count
+    int kw;                // interpolation stencil width: 2 (phi_2), 3 (phi_3), 4 (phi_4)
 };
 
 // ---- cell + offset positions -----------------------------------------------
@@ -107,16 +109,17 @@ __device__ __forceinline__ CPos unpack(float4 v)
 
 __device__ __forceinline__ double join1(int c, float f) { return (double)c + (double)f; }
 
-// Put a double position into the box (periodic wrap; specular reflection
-// into z in [1, nz-2] with walls, flipping p_z) -- the definition the
-// FP32 path below follows.
-__device__ void confine_d(double r[3], float p[3], const StepArgs &g)
+// Put a double position into the box (periodic wrap; with walls, specular
+// reflection into the band z in [kw/2, nz-1-kw/2], flipping p_z, so that a
+// stencil kw nodes wide touches fluid nodes only) -- the definition the FP32
+// path below follows.
+__device__ void confine_d(double r[3], float p[3], const StepArgs &g, int kw = 2)
 {
     const double L[3] = {(double)g.nx, (double)g.ny, (double)g.nz};
     const bool walls = g.z0 > 0;
     for (int c = 0; c < 3; ++c) {
         if (c == 2 && walls) {
-            const double lo = 1.0, hi = (double)(g.nz - 2);
+            const double lo = 0.5 * kw, hi = (double)(g.nz - 1) - lo;
             if (r[2] < lo) { r[2] = 2.0 * lo - r[2]; p[2] = -p[2]; }
             if (r[2] > hi) { r[2] = 2.0 * hi - r[2]; p[2] = -p[2]; }
         } else {
@@ -148,10 +151,25 @@ __device__ __forceinline__ bool split(const double r[3], const StepArgs &g, CPos
     return ok;
 }
 
+// Whether a cell + offset position lies outside the wall band of a stencil
+// kw nodes wide, z in [kw/2, nz-1-kw/2] (exact: the band edges are whole or
+// half-integer).
+__device__ __forceinline__ bool outside_band(const CPos &q, const StepArgs &g, int kw)
+{
+    const int c = q.c[2];
+    const float f = q.f[2];
+    if (kw & 1) {
+        const int lo = kw >> 1, hi = g.nz - 2 - (kw >> 1);
+        return c < lo || (c == lo && f < 0.5f) || c > hi || (c == hi && f > 0.5f);
+    }
+    const int lo = kw >> 1, hi = g.nz - 1 - (kw >> 1);
+    return c < lo || c > hi || (c == hi && f > 0.0f);
+}
+
 // r += h p (FP32 offset), then wrap / reflect as confine_d does.  A step of
 // more than a few cells, or a non-finite one, is not a valid particle move:
 // the position is clamped into the box and false is returned.
-__device__ __forceinline__ bool drift(CPos &q, float p[3], float h, const StepArgs &g)
+__device__ __forceinline__ bool drift(CPos &q, float p[3], float h, const StepArgs &g, int kw = 2)
 {
     const int L[3] = {g.nx, g.ny, g.nz};
     const bool walls = g.z0 > 0;
@@ -179,10 +197,9 @@ __device__ __forceinline__ bool drift(CPos &q, float p[3], float h, const StepAr
         }
     }
     if (walls) {
-        const int hi = g.nz - 2;
-        if (q.c[2] < 1 || q.c[2] > hi || (q.c[2] == hi && q.f[2] > 0.0f)) {
+        if (outside_band(q, g, kw)) {
             double r[3] = {join1(q.c[0], q.f[0]), join1(q.c[1], q.f[1]), join1(q.c[2], q.f[2])};
-            confine_d(r, p, g);
+            confine_d(r, p, g, kw);
             if (!split(r, g, q)) ok = false;  // split clamps into the box
         }
     }
@@ -273,6 +290,86 @@ __device__ __forceinline__ float stencil_node(const CPos &pos, int q, const Step
     return w;
 }
 
+// One axis of the stencil of phi_KW (Sec. 4.6) for the position c + f:
+// first node o and the KW weights of nodes o, o + 1, ...  phi_2: 1 - f, f.
+// phi_3 (Eq. 3point): with n the nearest node and d = c + f - n in
+// [-1/2, 1/2), the middle weight is (1 + sqrt(1 - 3 d^2)) / 3 and C1, C2
+// give the outer two, (1 - w_0 -+ d) / 2.  phi_4 (Eq. 4point): the nodes
+// c - 1 .. c + 2 carry (3 - 2f - S, 3 - 2f + S, 1 + 2f + S, 1 + 2f - S) / 8
+// with S = sqrt(1 + 4 f (1 - f)), the two branches of phi_4 at the four
+// distances.  Both forms are the paper's functions rewritten so that the
+// weights sum to one and the small outer weights carry no cancellation of
+// large terms.
+template <int KW>
+__device__ __forceinline__ int axis_weights(int c, float f, float w[KW])
+{
+    if constexpr (KW == 2) {
+        w[0] = 1.0f - f;
+        w[1] = f;
+        return c;
+    } else if constexpr (KW == 3) {
+        const bool up = f >= 0.5f;
+        const float d = up ? f - 1.0f : f;  // exact
+        const float w0 = (1.0f + sqrtf(fmaf(-3.0f * d, d, 1.0f))) * (1.0f / 3.0f);
+        w[0] = 0.5f * (1.0f - w0 - d);
+        w[1] = w0;
+        w[2] = 0.5f * (1.0f - w0 + d);
+        return up ? c : c - 1;
+    } else {
+        const float S = sqrtf(fmaf(4.0f * f, 1.0f - f, 1.0f));
+        const float a = 3.0f - 2.0f * f, b = 1.0f + 2.0f * f;
+        w[0] = 0.125f * (a - S);
+        w[1] = 0.125f * (a + S);
+        w[2] = 0.125f * (b + S);
+        w[3] = 0.125f * (b - S);
+        return c - 1;
+    }
+}
+
+template <int KW>
+struct Stencil {
+    int o[3];       // first node per axis (may lie outside the box before wrapping)
+    float w[3][KW]; // weights per axis
+};
+
+template <int KW>
+__device__ __forceinline__ void make_stencil(const CPos &pos, Stencil<KW> &s)
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s.o[k] = axis_weights<KW>(pos.c[k], pos.f[k], s.w[k]);
+}
+
+__device__ __forceinline__ int wrap_node(int v, int L)
+{
+    v = v < 0 ? v + L : (v >= L ? v - L : v);
+    if ((unsigned)v >= (unsigned)L) v = ((v % L) + L) % L;  // boxes narrower than the stencil
+    return v;
+}
+
+// Node q (0 .. KW^3 - 1, x fastest) of a stencil: coordinates and weight
+// Delta = phi(x) phi(y) phi(z) (Eq. Delta).  For KW = 2 this is
+// stencil_node() above, operation for operation.  With walls z is kept in
+// the box (the band keeps the stencil off the solid planes).
+template <int KW>
+__device__ __forceinline__ float stencil_node_k(const Stencil<KW> &s, int q, const StepArgs &g, int &x, int &y,
+                                                int &z)
+{
+    const int dx = q % KW, dy = (q / KW) % KW, dz = q / (KW * KW);
+    float wx = s.w[0][0], wy = s.w[1][0], wz = s.w[2][0];
+#pragma unroll
+    for (int j = 1; j < KW; ++j) {  // selects, no indexed local arrays
+        if (dx == j) wx = s.w[0][j];
+        if (dy == j) wy = s.w[1][j];
+        if (dz == j) wz = s.w[2][j];
+    }
+    x = wrap_node(s.o[0] + dx, g.nx);
+    y = wrap_node(s.o[1] + dy, g.ny);
+    z = s.o[2] + dz;
+    if (g.z0 > 0) z = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
+    else z = wrap_node(z, g.nz);
+    return wx * wy * wz;
+}
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -289,7 +386,7 @@ __global__ void k_half_drift(const double *pos, float *mom, const float *mass, f
     const double h = 0.5 * (double)c.dt / (double)m;
 #pragma unroll
     for (int k = 0; k < 3; ++k) r[k] += h * (double)pm[k];
-    confine_d(r, pm, c.g);
+    confine_d(r, pm, c.g, c.kw);
     CPos q;
     if (!split(r, c.g, q)) atomicOr(err, LB_DERR_PARTICLE_RANGE);
     shadow[p] = pack(q);
@@ -540,7 +637,7 @@ __device__ __forceinline__ void particle_theta(uint32_t p, uint32_t step, const 
 // lanes split the neighbour list (lane q takes entries q, q + 8, ...) and the
 // two FENE bonds, and shuffle-reduce u_p and F^c.  Every lane then holds the same
 // u_p, F^c and theta and does the (cheap) momentum update; lane 0 writes.
-template <int DT>
+template <int DT, int KW>
 __global__ void __launch_bounds__(kPartThreads)
     k_substep(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
               const float4 *__restrict__ sh_in, float4 *__restrict__ sh_out, double *pos_out, float *mom,
@@ -573,12 +670,23 @@ __global__ void __launch_bounds__(kPartThreads)
         if (bonded && !fene_add(me, unpack(sh_in[j]), c, F)) atomicOr(err, LB_DERR_FENE_BROKEN);
     }
 
-    // fluid velocity at the particle: lane q takes stencil node q
-    int x, y, z;
-    const float w = stencil_node(me, q, g, x, y, z);
-    float un[3];
-    node_velocity<DT>(src, ffield, x, y, z, g, un);
-    float up[3] = {w * un[0], w * un[1], w * un[2]};
+    // fluid velocity at the particle: lane q takes stencil nodes q, q + 8, ...
+    constexpr int kNodes = KW * KW * KW, kPerLane = (kNodes + kChunks - 1) / kChunks;
+    Stencil<KW> st;
+    make_stencil<KW>(me, st);
+    float up[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+        const int qq = q + kChunks * i;
+        if (kNodes % kChunks == 0 || qq < kNodes) {
+            int x, y, z;
+            const float w = stencil_node_k<KW>(st, qq, g, x, y, z);
+            float un[3];
+            node_velocity<DT>(src, ffield, x, y, z, g, un);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) up[k] = i == 0 ? w * un[k] : fmaf(w, un[k], up[k]);
+        }
+    }
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
 #pragma unroll
@@ -607,13 +715,19 @@ __global__ void __launch_bounds__(kPartThreads)
         J[k] = pn[k] - pm[k] - C2 * F[k];
     }
 
-    // spread -J Delta: lane q into its own node
-    {
-        const size_t P = g.pitch;
-        const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
-        atomicAdd(facc + s, -J[0] * w);
-        atomicAdd(facc + P + s, -J[1] * w);
-        atomicAdd(facc + 2 * P + s, -J[2] * w);
+    // spread -J Delta: lane q into its own nodes
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+        const int qq = q + kChunks * i;
+        if (kNodes % kChunks == 0 || qq < kNodes) {
+            int x, y, z;
+            const float w = stencil_node_k<KW>(st, qq, g, x, y, z);
+            const size_t P = g.pitch;
+            const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+            atomicAdd(facc + s, -J[0] * w);
+            atomicAdd(facc + P + s, -J[1] * w);
+            atomicAdd(facc + 2 * P + s, -J[2] * w);
+        }
     }
     if (q != 0) return;
     if (records) records[p] = (int)(((size_t)me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0]);
@@ -621,13 +735,13 @@ __global__ void __launch_bounds__(kPartThreads)
     // second half drift of this sub-step, then the first of the next one
     const float h = 0.5f * c.dt / m;
     CPos nx = me;
-    bool ok = drift(nx, pn, h, g);
+    bool ok = drift(nx, pn, h, g, KW);
     if (c.last) {
         pos_out[3 * p] = join1(nx.c[0], nx.f[0]);
         pos_out[3 * p + 1] = join1(nx.c[1], nx.f[1]);
         pos_out[3 * p + 2] = join1(nx.c[2], nx.f[2]);
     } else {
-        ok = drift(nx, pn, h, g) && ok;
+        ok = drift(nx, pn, h, g, KW) && ok;
     }
     if (!ok) atomicOr(err, LB_DERR_PARTICLE_RANGE);
     sh_out[p] = pack(nx);
@@ -641,20 +755,23 @@ __global__ void __launch_bounds__(kPartThreads)
     }
 }
 
-// Zero the eight accumulator nodes around each recorded stencil base.
+// Zero the accumulator nodes around each recorded cell: [b, b + 1] per axis
+// for span 2 (phi_2), [b - 1, b + 2] for span 4 (covers phi_3 and phi_4).
+template <int SPAN>
 __global__ void k_clear_records(float *facc, const int *records, size_t n, StepArgs g)
 {
+    constexpr int lo = SPAN == 4 ? -1 : 0;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const int base = records[q];
         const int x0 = base % g.nx;
         const int y0 = (base / g.nx) % g.ny;
         const int z0 = base / (g.nx * g.ny);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            int x = x0 + (k & 1), y = y0 + ((k >> 1) & 1), z = z0 + (k >> 2);
-            if (x >= g.nx) x -= g.nx;
-            if (y >= g.ny) y -= g.ny;
-            if (z >= g.nz) z = (g.z0 > 0) ? g.nz - 1 : z - g.nz;
+        for (int k = 0; k < SPAN * SPAN * SPAN; ++k) {
+            const int x = wrap_node(x0 + lo + k % SPAN, g.nx), y = wrap_node(y0 + lo + (k / SPAN) % SPAN, g.ny);
+            int z = z0 + lo + k / (SPAN * SPAN);
+            if (g.z0 > 0) z = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
+            else z = wrap_node(z, g.nz);
             const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
             facc[s] = 0.0f;
             facc[g.pitch + s] = 0.0f;
@@ -663,8 +780,9 @@ __global__ void k_clear_records(float *facc, const int *records, size_t n, StepA
     }
 }
 
-// Interpolated velocity at caller positions; eight lanes per position.
-template <int DT>
+// Interpolated velocity at caller positions with phi_KW; eight lanes per
+// position, lane q takes stencil nodes q, q + 8, ...
+template <int DT, int KW>
 __global__ void k_interpolate(const typename lbd::Store<DT>::T *__restrict__ src, const float *__restrict__ ffield,
                               const double *pos, float *u_out, int n, unsigned int *err, StepArgs g)
 {
@@ -675,11 +793,22 @@ __global__ void k_interpolate(const typename lbd::Store<DT>::T *__restrict__ src
     double r[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
     CPos me;
     if (!split(r, g, me) && q == 0) atomicOr(err, LB_DERR_PARTICLE_RANGE);
-    int x, y, z;
-    const float w = stencil_node(me, q, g, x, y, z);
-    float un[3];
-    node_velocity<DT>(src, ffield, x, y, z, g, un);
-    float up[3] = {w * un[0], w * un[1], w * un[2]};
+    constexpr int kNodes = KW * KW * KW, kPerLane = (kNodes + kChunks - 1) / kChunks;
+    Stencil<KW> st;
+    make_stencil<KW>(me, st);
+    float up[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i < kPerLane; ++i) {
+        const int qq = q + kChunks * i;
+        if (kNodes % kChunks == 0 || qq < kNodes) {
+            int x, y, z;
+            const float w = stencil_node_k<KW>(st, qq, g, x, y, z);
+            float un[3];
+            node_velocity<DT>(src, ffield, x, y, z, g, un);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) up[k] = i == 0 ? w * un[k] : fmaf(w, un[k], up[k]);
+        }
+    }
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1)
 #pragma unroll
@@ -1188,6 +1317,14 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
 }
 
 // Kernel arguments of a coupling call (everything but the cell list).
+// Interpolation stencil width selected by lb_couple_params.flags.
+int stencil_width(int flags)
+{
+    if (flags & LB_COUPLE_PHI3) return 3;
+    if (flags & LB_COUPLE_PHI4) return 4;
+    return 2;
+}
+
 CoupleArgs make_couple_args(const lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
     CoupleArgs c;
@@ -1222,6 +1359,7 @@ CoupleArgs make_couple_args(const lb_handle *h, const lb_particles *pp, const lb
     c.ncell[0] = c.ncell[1] = c.ncell[2] = 1;
     c.cinv[0] = c.cinv[1] = c.cinv[2] = 0.0f;
     c.nb_log2 = 0;
+    c.kw = stencil_width(cp->flags);
     return c;
 }
 
@@ -1250,8 +1388,9 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     const int gblocks = (int)(((size_t)n * kChunks + kPartThreads - 1) / kPartThreads);  // 8 lanes a particle
     const int pblocks = (n + kPThreads - 1) / kPThreads;                                   // one thread a particle
     int per_sm = 0;
-    if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>,
-                                                                       kPThreads, 0) == cudaSuccess &&
+    // (phi_3 and phi_4 stencils run on the per-sub-step kernels only)
+    if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && c.kw == 2 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>, kPThreads, 0) == cudaSuccess &&
         pblocks <= per_sm * device_sm_count()) {
         cudaError_t e = cudaSuccess;
         if (need_nlist && P->nlist_n != n) {
@@ -1261,7 +1400,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
             if (e != cudaSuccess) return e;
             P->nlist_n = n;
         }
-        const bool fold_clear = h->facc_stale && P->n_records == (size_t)n * (size_t)P->last_nsub &&
+        const bool fold_clear = h->facc_stale && P->rec_span == 2 && P->n_records == (size_t)n * (size_t)P->last_nsub &&
                                 P->n_records <= P->rec_cap / 2 && (size_t)n * cp->n_substeps <= P->rec_cap / 2;
         if (h->facc_stale && !fold_clear) {
             e = clear_particle_forces(h);
@@ -1356,11 +1495,16 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         c.last = (s == cp->n_substeps - 1);
         c.slot = wr;
         int *rec = P->records + P->rec_off + P->n_records;
-        k_substep<DT><<<sblocks, kPartThreads, 0, h->stream>>>(
-            src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma,
-            P->nlist, P->ncount, need_nlist ? P->ref : nullptr, P->head, P->bucket_of, h->facc, rec, P->flags,
-            h->d_err, c, rd);
+#define LBI_SUBSTEP(KW)                                                                                          \
+    k_substep<DT, KW><<<sblocks, kPartThreads, 0, h->stream>>>(                                                  \
+        src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma, P->nlist, \
+        P->ncount, need_nlist ? P->ref : nullptr, P->head, P->bucket_of, h->facc, rec, P->flags, h->d_err, c, rd)
+        if (c.kw == 3) LBI_SUBSTEP(3);
+        else if (c.kw == 4) LBI_SUBSTEP(4);
+        else LBI_SUBSTEP(2);
+#undef LBI_SUBSTEP
         P->n_records += (size_t)n;
+        if (c.kw > 2) P->rec_span = 4;
         P->sub_counter += 1;
         h->launches += 1;
     }
@@ -1516,8 +1660,14 @@ __global__ void __launch_bounds__(kPartThreads)
 
 lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
-    if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~(LB_COUPLE_PER_SUBSTEP | LB_COUPLE_OVERLAP)) != 0) {
+    const int known = LB_COUPLE_PER_SUBSTEP | LB_COUPLE_OVERLAP | LB_COUPLE_PHI3 | LB_COUPLE_PHI4;
+    if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~known) != 0 ||
+        (cp->flags & (LB_COUPLE_PHI3 | LB_COUPLE_PHI4)) == (LB_COUPLE_PHI3 | LB_COUPLE_PHI4)) {
         set_error("lb_couple_particles: bad particle count, reserved field or flags");
+        return LB_EINVAL;
+    }
+    if (h->p.walls && h->p.nz < stencil_width(cp->flags) + 1) {
+        set_error("lb_couple_particles: the channel is too narrow for the interpolation stencil");
         return LB_EINVAL;
     }
     if (pp->n == 0) return LB_OK;
@@ -1603,6 +1753,7 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         h->patch_n = pp->n;
         h->patch_nsub = cp->n_substeps;
         h->patch_rec = P->records + P->rec_off + P->n_records - (size_t)pp->n * (size_t)cp->n_substeps;
+        h->patch_span = stencil_width(cp->flags) > 2 ? 4 : 2;
     }
     return LB_OK;
 }
@@ -1614,32 +1765,40 @@ cudaError_t clear_particle_forces(lb_handle *h)
     if (P->n_records) {
         const StepArgs g = make_args(h);
         int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
-        k_clear_records<<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
+        if (P->rec_span == 4)
+            k_clear_records<4><<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
+        else
+            k_clear_records<2><<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
         h->launches += 1;
         P->n_records = 0;
         P->rec_off = 0;
+        P->rec_span = 2;
     }
     return cudaGetLastError();
 }
 
-lb_status interpolate(lb_handle *h, int n, const double *pos, float *u_out)
+template <int DT>
+void launch_interpolate(lb_handle *h, int kernel, int n, const double *pos, float *u_out)
 {
-    if (n == 0) return LB_OK;
+    using T = typename lbd::Store<DT>::T;
     const StepArgs g = make_args(h);
     const int blocks = (int)(((size_t)n * 8 + kPartThreads - 1) / kPartThreads);
+    const T *src = static_cast<const T *>(h->pops[h->cur]);
+    if (kernel == 3)
+        k_interpolate<DT, 3><<<blocks, kPartThreads, 0, h->stream>>>(src, h->force, pos, u_out, n, h->d_err, g);
+    else if (kernel == 4)
+        k_interpolate<DT, 4><<<blocks, kPartThreads, 0, h->stream>>>(src, h->force, pos, u_out, n, h->d_err, g);
+    else
+        k_interpolate<DT, 2><<<blocks, kPartThreads, 0, h->stream>>>(src, h->force, pos, u_out, n, h->d_err, g);
+}
+
+lb_status interpolate(lb_handle *h, int kernel, int n, const double *pos, float *u_out)
+{
+    if (n == 0) return LB_OK;
     switch (h->p.dtype) {
-    case LB_F32:
-        k_interpolate<0><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const float *>(h->pops[h->cur]),
-                                                                  h->force, pos, u_out, n, h->d_err, g);
-        break;
-    case LB_F16:
-        k_interpolate<1><<<blocks, kPartThreads, 0, h->stream>>>(static_cast<const __half *>(h->pops[h->cur]),
-                                                                  h->force, pos, u_out, n, h->d_err, g);
-        break;
-    default:
-        k_interpolate<2><<<blocks, kPartThreads, 0, h->stream>>>(
-            static_cast<const __nv_bfloat16 *>(h->pops[h->cur]), h->force, pos, u_out, n, h->d_err, g);
-        break;
+    case LB_F32: launch_interpolate<0>(h, kernel, n, pos, u_out); break;
+    case LB_F16: launch_interpolate<1>(h, kernel, n, pos, u_out); break;
+    default: launch_interpolate<2>(h, kernel, n, pos, u_out); break;
     }
     h->launches += 1;
     cudaError_t e = cudaGetLastError();
@@ -1655,6 +1814,10 @@ bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_coup
     }
     if (h->p.kT != 0.0 || cp->chain_len > 1 || cp->use_wca) {
         set_error("%s: the coupling reverse pass covers free particles at kT = 0", who);
+        return false;
+    }
+    if (cp->flags & (LB_COUPLE_PHI3 | LB_COUPLE_PHI4)) {
+        set_error("%s: the coupling reverse pass covers the phi_2 stencil", who);
         return false;
     }
     if (cp->n_substeps < 1 || cp->n_substeps > kMaxAdjSub || !(cp->dt > 0.0)) {
@@ -1717,6 +1880,7 @@ lb_status couple_on(lb_handle *h, const void *state, const lb_particles *pp, con
     if (h->parts) {  // these records index facc_out
         h->parts->n_records = 0;
         h->parts->rec_off = 0;
+        h->parts->rec_span = 2;
     }
     h->pops[h->cur] = saved_pop;
     h->facc = saved_facc;

@@ -264,14 +264,37 @@ __global__ void __launch_bounds__(kBX) k_stream_collide(const typename lbd::Stor
     }
 }
 
+// Node k (0 .. span^3 - 1, x fastest) of the block of nodes that an impulse
+// stencil can touch around the recorded cell (bx, by, bz): [b, b + 1] per
+// axis for span 2 (phi_2), [b - 1, b + 2] for span 4 (phi_3 and phi_4).
+// Returns false for a node outside the fluid.
+template <bool WALLS>
+__device__ __forceinline__ bool patch_node(int bx, int by, int bz, int k, int span, const StepArgs &a, int &x,
+                                           int &y, int &z)
+{
+    const int sh = span == 4 ? 2 : 1, lo = span == 4 ? -1 : 0, m = span - 1;
+    x = bx + lo + (k & m);
+    y = by + lo + ((k >> sh) & m);
+    z = bz + lo + (k >> (2 * sh));
+    x = x < 0 ? x + a.nx : (x >= a.nx ? x - a.nx : x);
+    y = y < 0 ? y + a.ny : (y >= a.ny ? y - a.ny : y);
+    if ((unsigned)x >= (unsigned)a.nx) x = ((x % a.nx) + a.nx) % a.nx;  // boxes narrower than the stencil
+    if ((unsigned)y >= (unsigned)a.ny) y = ((y % a.ny) + a.ny) % a.ny;
+    if (!WALLS) {
+        z = z < 0 ? z + a.nz : (z >= a.nz ? z - a.nz : z);
+        if ((unsigned)z >= (unsigned)a.nz) z = ((z % a.nz) + a.nz) % a.nz;
+    }
+    return z >= a.z0 && z < a.z1;
+}
+
 // Re-update of the nodes that received particle impulses, after an update of
-// all nodes that left the impulses out (the coupling ran meanwhile): the 8
-// stencil nodes of each cell particle p visited, records[s][p] (linear cell
-// index at sub-step s), are updated again from the same pre-step state with
-// the impulses added.  The update of a node depends only on that state, the
+// all nodes that left the impulses out (the coupling ran meanwhile): the
+// span^3 nodes around each cell particle p visited, records[s][p] (linear
+// cell index at sub-step s), are updated again from the same pre-step state
+// with the impulses added.  The update of a node depends only on that state, the
 // forces at the node and the counter-based noise, so the result is the one a
 // single update with the impulses would give.  Thread (p, q) walks p's
-// distinct cells and takes stencil node q of each; a node shared by several
+// distinct cells and takes nodes q, q + 8, ... of each; a node shared by several
 // particles is updated once, by the thread that raises its tag to `tag`
 // first (tags grow by one per patch, so the array is never cleared).
 template <int DT, bool NOISE, bool WALLS>
@@ -279,27 +302,26 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
                                                              typename lbd::Store<DT>::T *__restrict__ dst,
                                                              const float *__restrict__ ffield,
                                                              const float *__restrict__ facc, const int *records,
-                                                             int n, int nsub, unsigned int *claim, unsigned int tag,
-                                                             const StepArgs a)
+                                                             int n, int nsub, int span, unsigned int *claim,
+                                                             unsigned int tag, const StepArgs a)
 {
     const int t = blockIdx.x * kBX + threadIdx.x;
     if (t >= n * 8) return;
     const int p = t >> 3, q = t & 7;
+    const int nk = span * span * span;
     int prev = -1;
     for (int s = 0; s < nsub; ++s) {
         const int base = records[(size_t)s * n + p];
         if (base == prev) continue;  // same cell as the sub-step before
         prev = base;
-        int x = base % a.nx + (q & 1);
-        int y = (base / a.nx) % a.ny + ((q >> 1) & 1);
-        int z = base / (a.nx * a.ny) + (q >> 2);
-        if (x >= a.nx) x -= a.nx;
-        if (y >= a.ny) y -= a.ny;
-        if (!WALLS && z >= a.nz) z -= a.nz;
-        if (z < a.z0 || z >= a.z1) continue;  // solid node
-        const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
-        if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
-        update_node<DT, NOISE, true, WALLS>(src, dst, ffield, facc, a, x, y, z);
+        const int bx = base % a.nx, by = (base / a.nx) % a.ny, bz = base / (a.nx * a.ny);
+        for (int e = q; e < nk; e += 8) {
+            int x, y, z;
+            if (!patch_node<WALLS>(bx, by, bz, e, span, a, x, y, z)) continue;  // solid node
+            const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
+            if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
+            update_node<DT, NOISE, true, WALLS>(src, dst, ffield, facc, a, x, y, z);
+        }
     }
 }
 
@@ -315,70 +337,69 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
 template <bool WALLS>
 __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restrict__ dst, const float *__restrict__ ffield,
                                                                  const float *__restrict__ facc, const int *records, int n,
-                                                                 int nsub, unsigned int *claim, unsigned int tag,
-                                                                 const StepArgs a)
+                                                                 int nsub, int span, unsigned int *claim,
+                                                                 unsigned int tag, const StepArgs a)
 {
     const int t = blockIdx.x * kBX + threadIdx.x;
     if (t >= n * 8) return;
     const int p = t >> 3, q = t & 7;
     const size_t P = a.pitch;
+    const int nk = span * span * span;
     int prev = -1;
     for (int s = 0; s < nsub; ++s) {
         const int base = records[(size_t)s * n + p];
         if (base == prev) continue;  // same cell as the sub-step before
         prev = base;
-        int x = base % a.nx + (q & 1);
-        int y = (base / a.nx) % a.ny + ((q >> 1) & 1);
-        int z = base / (a.nx * a.ny) + (q >> 2);
-        if (x >= a.nx) x -= a.nx;
-        if (y >= a.ny) y -= a.ny;
-        if (!WALLS && z >= a.nz) z -= a.nz;
-        if (z < a.z0 || z >= a.z1) continue;  // solid node
-        const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
-        if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
-        const float df[3] = {facc[node], facc[P + node], facc[2 * P + node]};
-        if (df[0] == 0.0f && df[1] == 0.0f && df[2] == 0.0f) continue;
-        float ns[19], m[19];
+        const int bx = base % a.nx, by = (base / a.nx) % a.ny, bz = base / (a.nx * a.ny);
+        for (int e = q; e < nk; e += 8) {
+            int x, y, z;
+            if (!patch_node<WALLS>(bx, by, bz, e, span, a, x, y, z)) continue;  // solid node
+            const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
+            if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
+            const float df[3] = {facc[node], facc[P + node], facc[2 * P + node]};
+            if (df[0] == 0.0f && df[1] == 0.0f && df[2] == 0.0f) continue;
+            float ns[19], m[19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) ns[i] = dst[(size_t)i * P + node];
-        lbd::forward(ns, m);
-        float fb[3] = {a.fx, a.fy, a.fz};
-        if (ffield) {
-            fb[0] += ffield[node];
-            fb[1] += ffield[a.nn + node];
-            fb[2] += ffield[2 * a.nn + node];
+            for (int i = 0; i < 19; ++i) ns[i] = dst[(size_t)i * P + node];
+            lbd::forward(ns, m);
+            float fb[3] = {a.fx, a.fy, a.fz};
+            if (ffield) {
+                fb[0] += ffield[node];
+                fb[1] += ffield[a.nn + node];
+                fb[2] += ffield[2 * a.nn + node];
+            }
+            const float fn[3] = {fb[0] + df[0], fb[1] + df[1], fb[2] + df[2]};
+            const float rho = a.rho0 + m[0];
+            const float ir = 1.0f / rho;
+            const float j[3] = {m[1] - fb[0], m[2] - fb[1], m[3] - fb[2]};
+            float dM[19];
+#pragma unroll
+            for (int k = 0; k < 19; ++k) dM[k] = 0.0f;
+            dM[1] = 3.0f * df[0];
+            dM[2] = 3.0f * df[1];
+            dM[3] = 3.0f * df[2];
+            const float gs1 = 1.0f + a.g_shear;
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {  // + (u_n, f_n), - (u_b, f_b)
+                const float *f = side ? fb : fn;
+                const float sg = side ? -1.0f : 1.0f;
+                const float ux = (j[0] + 0.5f * f[0]) * ir, uy = (j[1] + 0.5f * f[1]) * ir, uz = (j[2] + 0.5f * f[2]) * ir;
+                const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
+                const float uf = ux * f[0] + uy * f[1] + uz * f[2];
+                dM[4] += sg * ((1.0f - a.g_bulk) * rho * u2 + (1.0f + a.g_bulk) * uf);
+                dM[5] += sg * ((1.0f - a.g_shear) * rho * (3.0f * uxx - u2) + gs1 * (3.0f * ux * f[0] - uf));
+                dM[6] += sg * ((1.0f - a.g_shear) * rho * (uyy - uzz) + gs1 * (uy * f[1] - uz * f[2]));
+                dM[7] += sg * ((1.0f - a.g_shear) * rho * ux * uy + 0.5f * gs1 * (ux * f[1] + uy * f[0]));
+                dM[8] += sg * ((1.0f - a.g_shear) * rho * uy * uz + 0.5f * gs1 * (uy * f[2] + uz * f[1]));
+                dM[9] += sg * ((1.0f - a.g_shear) * rho * uz * ux + 0.5f * gs1 * (uz * f[0] + ux * f[2]));
+            }
+#pragma unroll
+            for (int k = 4; k < 10; ++k) dM[k] *= lbd::inv_w(k);
+            float dn[19];
+            lbd::backward(dM, dn);
+#pragma unroll
+            for (int i = 0; i < 19; ++i) dst[(size_t)i * P + node] = ns[i] + dn[i];
         }
-        const float fn[3] = {fb[0] + df[0], fb[1] + df[1], fb[2] + df[2]};
-        const float rho = a.rho0 + m[0];
-        const float ir = 1.0f / rho;
-        const float j[3] = {m[1] - fb[0], m[2] - fb[1], m[3] - fb[2]};
-        float dM[19];
-#pragma unroll
-        for (int k = 0; k < 19; ++k) dM[k] = 0.0f;
-        dM[1] = 3.0f * df[0];
-        dM[2] = 3.0f * df[1];
-        dM[3] = 3.0f * df[2];
-        const float gs1 = 1.0f + a.g_shear;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {  // + (u_n, f_n), - (u_b, f_b)
-            const float *f = side ? fb : fn;
-            const float sg = side ? -1.0f : 1.0f;
-            const float ux = (j[0] + 0.5f * f[0]) * ir, uy = (j[1] + 0.5f * f[1]) * ir, uz = (j[2] + 0.5f * f[2]) * ir;
-            const float uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, u2 = uxx + uyy + uzz;
-            const float uf = ux * f[0] + uy * f[1] + uz * f[2];
-            dM[4] += sg * ((1.0f - a.g_bulk) * rho * u2 + (1.0f + a.g_bulk) * uf);
-            dM[5] += sg * ((1.0f - a.g_shear) * rho * (3.0f * uxx - u2) + gs1 * (3.0f * ux * f[0] - uf));
-            dM[6] += sg * ((1.0f - a.g_shear) * rho * (uyy - uzz) + gs1 * (uy * f[1] - uz * f[2]));
-            dM[7] += sg * ((1.0f - a.g_shear) * rho * ux * uy + 0.5f * gs1 * (ux * f[1] + uy * f[0]));
-            dM[8] += sg * ((1.0f - a.g_shear) * rho * uy * uz + 0.5f * gs1 * (uy * f[2] + uz * f[1]));
-            dM[9] += sg * ((1.0f - a.g_shear) * rho * uz * ux + 0.5f * gs1 * (uz * f[0] + ux * f[2]));
-        }
-#pragma unroll
-        for (int k = 4; k < 10; ++k) dM[k] *= lbd::inv_w(k);
-        float dn[19];
-        lbd::backward(dM, dn);
-#pragma unroll
-        for (int i = 0; i < 19; ++i) dst[(size_t)i * P + node] = ns[i] + dn[i];
     }
 }
 
@@ -600,7 +621,7 @@ cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *
 
 template <int DT>
 cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
-                            int n, int nsub, unsigned int *claim, unsigned int tag)
+                            int n, int nsub, int span, unsigned int *claim, unsigned int tag)
 {
     using T = typename lbd::Store<DT>::T;
     const StepArgs a = make_args(h);
@@ -612,15 +633,16 @@ cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, cons
     if (DT == 0) {  // FP32: correct the stored result in place
         float *d32 = reinterpret_cast<float *>(dst);
         if (walls)
-            k_patch_impulse_nodes_f32<true><<<blocks, kBX, 0, h->stream>>>(d32, h->force, facc, records, n, nsub, claim,
-                                                                          tag, a);
+            k_patch_impulse_nodes_f32<true><<<blocks, kBX, 0, h->stream>>>(d32, h->force, facc, records, n, nsub, span,
+                                                                          claim, tag, a);
         else
             k_patch_impulse_nodes_f32<false><<<blocks, kBX, 0, h->stream>>>(d32, h->force, facc, records, n, nsub,
-                                                                           claim, tag, a);
+                                                                           span, claim, tag, a);
         return cudaGetLastError();
     }
 #define LBI_PATCH(NZ, WL) \
-    k_patch_impulse_nodes<DT, NZ, WL><<<blocks, kBX, 0, h->stream>>>(s, d, h->force, facc, records, n, nsub, claim, tag, a)
+    k_patch_impulse_nodes<DT, NZ, WL><<<blocks, kBX, 0, h->stream>>>(s, d, h->force, facc, records, n, nsub, span, claim, \
+                                                     tag, a)
     if (noise) {
         if (walls) LBI_PATCH(true, true); else LBI_PATCH(true, false);
     } else {

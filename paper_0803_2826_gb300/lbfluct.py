@@ -23,7 +23,7 @@ LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
 LB_DERR_PARTICLE_RANGE = 16
-LB_COUPLE_PER_SUBSTEP, LB_COUPLE_OVERLAP = 1, 2
+LB_COUPLE_PER_SUBSTEP, LB_COUPLE_OVERLAP, LB_COUPLE_PHI3, LB_COUPLE_PHI4 = 1, 2, 4, 8
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
                 5: "LB_ETIMEOUT", 6: "LB_EUNSUPPORTED", 7: "LB_EDEVICE"}
@@ -33,7 +33,7 @@ EXPORTS = (
     "lb_plane_pitch", "lb_population_bytes", "lb_create", "lb_destroy", "lb_last_error",
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
-    "lb_couple_particles", "lb_interpolate", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
+    "lb_couple_particles", "lb_interpolate", "lb_interpolate_phi", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
     "lb_set_timing", "lb_get_timing", "lb_step_sums", "lb_adjoint_step_impulse", "lb_adjoint_couple",
     "lb_adjoint_kinetic_coupled",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
@@ -123,6 +123,7 @@ def load(path: str | None = None):
             "lb_moments": (i, [H, vp, vp, vp, vp]),
             "lb_couple_particles": (i, [H, C.POINTER(lb_particles), C.POINTER(lb_couple_params)]),
             "lb_interpolate": (i, [H, i, vp, vp]),
+            "lb_interpolate_phi": (i, [H, i, i, vp, vp]),
             "lb_get_particle_forces": (i, [H, vp]),
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_box_muller": (i, [vp, i, vp, vp]),
@@ -288,6 +289,10 @@ def lb_couple_particles(h, parts: lb_particles, cp: lb_couple_params):
 
 def lb_interpolate(h, n, pos, u_out):
     _check(load().lb_interpolate(h, int(n), _ptr(pos), _ptr(u_out)))
+
+
+def lb_interpolate_phi(h, kernel, n, pos, u_out):
+    _check(load().lb_interpolate_phi(h, int(kernel), int(n), _ptr(pos), _ptr(u_out)))
 
 
 def lb_get_particle_forces(h, out):
@@ -585,11 +590,15 @@ def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_p
 
 def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len=0, use_wca=False,
                   eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5, per_substep=False,
-                  overlap=False) -> lb_couple_params:
+                  overlap=False, kernel=2) -> lb_couple_params:
+    """kernel: interpolation function phi_2 (default), phi_3 or phi_4."""
+    if kernel not in (2, 3, 4):
+        raise ValueError("kernel must be 2, 3 or 4")
     c = lb_couple_params()
     c.n_substeps, c.noise_kind, c.dt = int(n_substeps), int(noise_kind), float(dt)
     c.seed, c.md_step0 = int(seed), int(md_step0) & 0xffffffff
     c.chain_len, c.use_wca = int(chain_len), int(bool(use_wca))
-    c.flags = (LB_COUPLE_PER_SUBSTEP if per_substep else 0) | (LB_COUPLE_OVERLAP if overlap else 0)
+    c.flags = ((LB_COUPLE_PER_SUBSTEP if per_substep else 0) | (LB_COUPLE_OVERLAP if overlap else 0) |
+               {2: 0, 3: LB_COUPLE_PHI3, 4: LB_COUPLE_PHI4}[kernel])
     c.eps, c.sigma, c.k_fene, c.r0 = float(eps), float(sigma), float(k_fene), float(r0)
     return c

@@ -28,7 +28,7 @@ def dev(x, dt=None):
 
 
 def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1, gamma=2.0, mass=1.0,
-         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0), per_substep=False):
+         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0), per_substep=False, kernel=2):
     mom32 = mom.astype(np.float32).astype(np.float64)
     p = ora.make_params(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
     u = inputs.shear_wave(shape, u_amp) + inputs.gaussian_field(shape, 3, 1e-3, seed=8)
@@ -40,7 +40,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
     if chains:
         md = ora.make_md(chains[0], chains[1], eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5)
     opos, omom, ofacc, broken = ora.couple(p, pops, pos, mom32, mass, gamma, dt=dt, n_substeps=nsub, seed=11,
-                                           md_step0=40, md=md, noise_kind=noise_kind)
+                                           md_step0=40, md=md, noise_kind=noise_kind, kernel=kernel)
     assert broken == 0
     lat = L.Lattice(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
     lat.init_equilibrium(None, dev(u))
@@ -49,7 +49,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
     parts = L.particles(pos.shape[0], gpos, gmom, mass0=mass, gamma0=gamma)
     cp = L.couple_params(n_substeps=nsub, dt=dt, seed=11, md_step0=40, noise_kind=noise_kind,
                          chain_len=chains[1] if chains else 0, use_wca=bool(chains), eps=0.01, sigma=1.0,
-                         k_fene=0.3, r0=1.5, per_substep=per_substep)
+                         k_fene=0.3, r0=1.5, per_substep=per_substep, kernel=kernel)
     L.lb_couple_particles(lat.h, parts, cp)
     facc = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
     L.lb_get_particle_forces(lat.h, facc)
@@ -145,18 +145,110 @@ def test_wca_chains_many(ora, per_substep):
     assert rel(r["gfacc"], r["ofacc"]) < 2e-4
 
 
-def test_interpolation_parity(ora):
+@pytest.mark.parametrize("kernel", [2, 3, 4])
+def test_interpolation_parity(ora, kernel):
     shape = (9, 11, 7)
     p = ora.make_params(shape, kT=0.0)
     u = inputs.gaussian_field(shape, 3, 1e-2, seed=9)
     pops = ora.equilibrium(p, None, u)
     pos = inputs.uniform_particles(500, shape, seed=10)
-    want = ora.interpolate(p, pops, pos)
+    # positions on node planes, half-way between them and next to the box
+    # edges, where phi_3 changes branch or the stencil wraps
+    pos[:8] = [[0.0, 0.0, 0.0], [0.5, 1.5, 2.5], [8.999999, 10.5, 6.5], [4.0, 5.0, 6.0],
+               [0.25, 10.75, 0.5], [3.5, 3.5, 3.5], [8.5, 0.5, 6.999], [1e-9, 2.0, 3.0]]
+    want = ora.interpolate(p, pops, pos, kernel=kernel)
     lat = L.Lattice(shape)
     lat.init_equilibrium(None, dev(u))
     out = torch.empty((500, 3), dtype=torch.float32, device="cuda")
-    L.lb_interpolate(lat.h, 500, dev(pos), out)
+    if kernel == 2:
+        L.lb_interpolate(lat.h, 500, dev(pos), out)
+    else:
+        L.lb_interpolate_phi(lat.h, kernel, 500, dev(pos), out)
     assert rel(out.cpu().numpy().astype(np.float64), want) < 1e-6
+    assert np.abs(out.cpu().numpy() - want).max() < 1e-8
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+def test_phi_kernel_free_particles_parity(ora, kernel, kT):
+    """phi_3 / phi_4 stencils (27 / 64 nodes) in the coupling and the LB step
+    that applies their impulses."""
+    shape = (12, 10, 9)
+    pos = inputs.uniform_particles(300, shape, seed=1)
+    mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
+    r = _run(ora, shape, pos, mom, kT=kT, kernel=kernel)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_phi_kernel_walls_parity(ora, kernel):
+    """Between walls the particles stay K/2 from the solid planes; no impulse
+    reaches a solid plane."""
+    shape = (10, 8, 12)
+    b = kernel / 2
+    pos = inputs.uniform_particles(200, shape, seed=5, zrange=(b, shape[2] - 1 - b))
+    mom = inputs.maxwell_momenta(200, 1.0, 1e-2, seed=6)  # fast enough to reach the walls
+    r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, dt=0.5, body_force=(1e-5, 0, 0), kernel=kernel)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-5
+    assert r["gpos"][:, 2].min() >= b and r["gpos"][:, 2].max() <= shape[2] - 1 - b
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    assert np.all(r["gfacc"][:, 0] == 0) and np.all(r["gfacc"][:, -1] == 0)
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_phi_kernel_chains_parity(ora, kernel):
+    """FENE + WCA chains with the wide stencils (per-sub-step kernels)."""
+    shape = (16, 16, 16)
+    pos = inputs.random_walk_chains(2, 24, shape, seed=7)
+    mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), kernel=kernel)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_phi3_many_particles_parity(ora):
+    """200000 particles with phi_3 in a 32^3 box: many particles per node,
+    every stencil shape (both phi_3 branches on every axis)."""
+    shape = (32, 32, 32)
+    pos = inputs.uniform_particles(200000, shape, seed=21)
+    mom = inputs.maxwell_momenta(200000, 1.0, 1e-4, seed=22)
+    r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3, kernel=3)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_phi_kernel_rejections():
+    """Both stencil bits, a channel narrower than the stencil needs, and the
+    reverse pass with a wide stencil are refused."""
+    lat = L.Lattice((8, 8, 4), walls=True)
+    lat.init_equilibrium()
+    pos = dev(np.array([[1.0, 1.0, 1.5]]))
+    mom = dev(np.zeros((1, 3)), torch.float32)
+    parts = L.particles(1, pos, mom, mass0=1.0, gamma0=1.0)
+    cp = L.couple_params(n_substeps=1, dt=0.1)
+    cp.flags = L.LB_COUPLE_PHI3 | L.LB_COUPLE_PHI4
+    with pytest.raises(L.LBError) as ei:
+        L.lb_couple_particles(lat.h, parts, cp)
+    assert ei.value.status == L.LB_EINVAL
+    with pytest.raises(L.LBError) as ei:  # nz = 4 < 4 + 1
+        L.lb_couple_particles(lat.h, parts, L.couple_params(n_substeps=1, dt=0.1, kernel=4))
+    assert ei.value.status == L.LB_EINVAL
+    L.lb_couple_particles(lat.h, parts, L.couple_params(n_substeps=1, dt=0.1, kernel=3))  # nz = 4 fits phi_3
+    with pytest.raises(L.LBError) as ei:
+        L.lb_interpolate_phi(lat.h, 5, 1, pos, torch.empty((1, 3), device="cuda"))
+    assert ei.value.status == L.LB_EINVAL
+    assert lat.sync() == (L.LB_OK, 0)
 
 
 def test_coupled_momentum_conservation_gpu(ora):
@@ -229,7 +321,7 @@ def test_fast_wca_particles_rebuild_lists(ora, per_substep):
     assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 1e-3
 
 
-def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False):
+def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False, kernel=2):
     """`steps` rounds of couple + step in a thermal fluid: FENE + WCA chains
     (periodic box) or single WCA particles between walls."""
     if walls:  # z in [1, nz - 2): no bond may cross the walls
@@ -248,7 +340,7 @@ def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False):
     forces = []
     for t in range(steps):
         cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, chain_len=clen, use_wca=True,
-                             eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=overlap)
+                             eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=overlap, kernel=kernel)
         L.lb_couple_particles(lat.h, parts, cp)
         if join_early:
             f = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
@@ -259,14 +351,15 @@ def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False):
     return lat.get_populations().cpu().numpy(), gpos.cpu().numpy(), gmom.cpu().numpy(), forces
 
 
-@pytest.mark.parametrize("walls", [False, True])
-def test_overlapped_coupling_matches_serial(walls):
+@pytest.mark.parametrize("walls,kernel", [(False, 2), (True, 2), (False, 4), (True, 3)])
+def test_overlapped_coupling_matches_serial(walls, kernel):
     """LB_COUPLE_OVERLAP: the step's update of all nodes without the impulses
     (concurrent with the coupling) plus the re-update of the visited stencil
-    nodes gives the serial result (up to the order of the impulse atomics)."""
+    nodes gives the serial result (up to the order of the impulse atomics);
+    for phi_3 / phi_4 the re-update covers the 4^3 nodes around each cell."""
     shape = (20, 18, 16)
-    a = _coupled_run(shape, walls=walls, overlap=False)
-    b = _coupled_run(shape, walls=walls, overlap=True)
+    a = _coupled_run(shape, walls=walls, overlap=False, kernel=kernel)
+    b = _coupled_run(shape, walls=walls, overlap=True, kernel=kernel)
     # FP32 deviations ~1e-2: a few ulps where the impulse sums (and, for FP32
     # storage, the correction of the stored result) round differently; the
     # particles follow the fluid to a few ulps of their FP32 cell offsets
