@@ -220,6 +220,10 @@ typedef struct {
     int flags;           /* 0, or LB_COUPLE_* bits below                             */
     double eps, sigma;   /* WCA parameters                                           */
     double k_fene, r0;   /* FENE parameters                                          */
+    double fext[3];      /* constant external force on every particle, added to F^c  */
+                         /* (gravity, or the applied force F of the drag experiment  */
+                         /* of Sec. 4.5); the fluid receives it only through the     */
+                         /* friction; 0 for none                                     */
 } lb_couple_params;
 
 /* lb_couple_params.flags: run one kernel launch per sub-step instead of one
@@ -260,8 +264,10 @@ typedef struct {
  * sub-step: half drift; conservative forces F^c (FENE + WCA); u_p =
  * sum Delta(r - r_p) u(r) with Delta = phi_2 phi_2 phi_2 over 8 nodes (or
  * phi_3 / phi_4 over 27 / 64, see LB_COUPLE_PHI3); exact OU update
- * p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta; the impulse J = p' - p - C2 F^c
- * is spread as -J Delta(r - r_p) into a library accumulator that the next
+ * p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta; the impulse of the drag and
+ * random forces over the sub-step, J = p' - p - dt F^c (Eq. (ftotal); F^c,
+ * fext included, is constant during the update), is spread as
+ * -J Delta(r - r_p) into a library accumulator that the next
  * lb_step applies once; half drift.  Positions wrap periodically (x, y; z
  * without walls) or reflect specularly into z in [1, nz-2] with walls (the
  * band is K/2 from the solid planes for a stencil K nodes wide).

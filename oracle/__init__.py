@@ -21,8 +21,10 @@ Function -> passage it follows:
   modes()         Sec. 3.4 Eq. (forward)
   md_forces()     Sec. 2.1 Eqs. (ulennardjones), (ufene)
   couple()        Sec. 4.5 Eqs. (fdrag), (ftotal), (langevin_momentum_update);
-                  Sec. 4.6 Eqs. (ufluid_discrete), (Delta), (2point)
+                  Sec. 4.6 Eqs. (ufluid_discrete), (Delta), (2point), (3point), (4point)
   interpolate()   Sec. 4.6 Eq. (ufluid_discrete)
+  effective_friction()  Sec. 4.5 drag experiment, Eqs. (dragexperiment_particle_equation),
+                  (effsize), (aeff), (aeffcorr); Sec. 4.6 settling test
   adjoint_step()  reverse mode of step() at kT = 0, derived by hand in
                   population space (chain rule through Eq. (original_equil_distrib),
                   the MRT relaxation and Delta'' of Sec. 3.7, then the pull)
@@ -86,6 +88,7 @@ class CoupleParams(C.Structure):
         ("n_substeps", C.c_int), ("noise_kind", C.c_int),
         ("dt", C.c_double), ("seed", C.c_uint64),
         ("md_step0", C.c_uint32), ("kernel", C.c_uint32),
+        ("fext", C.c_double * 3),
     ]
 
 
@@ -285,9 +288,10 @@ def md_forces(p: Params, md: MD, pos):
 
 
 def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_step0=0,
-           md: MD | None = None, force=None, noise_kind=0, kernel=2):
+           md: MD | None = None, force=None, noise_kind=0, kernel=2, fext=None):
     """One LB step's worth of particle sub-steps.  Returns (pos, mom, facc, broken);
-    facc has shape (3, nz, ny, nx) and holds the spread impulses -J Delta."""
+    facc has shape (3, nz, ny, nx) and holds the spread impulses -J Delta.
+    fext: constant external force on every particle (part of F^c)."""
     lib = _load()
     pos = np.array(pos, dtype=np.float64, order="C", copy=True)
     mom = np.array(mom, dtype=np.float64, order="C", copy=True)
@@ -298,6 +302,9 @@ def couple(p: Params, pops, pos, mom, mass, gamma, *, dt, n_substeps, seed, md_s
     cp = CoupleParams()
     cp.n_substeps, cp.noise_kind, cp.dt = int(n_substeps), int(noise_kind), float(dt)
     cp.seed, cp.md_step0, cp.kernel = int(seed), int(md_step0), int(kernel)
+    if fext is not None:
+        for c in range(3):
+            cp.fext[c] = float(fext[c])
     src = np.ascontiguousarray(pops, dtype=np.float64)
     f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
     broken = lib.ora_couple(C.byref(p), _dp(src), _dp(f), n, _dp(pos), _dp(mom), _dp(mass),
@@ -375,6 +382,42 @@ def coupled_kinetic_energy_and_grad(p: Params, pops0, force, pos0, mom0, mass, g
                                     lam_facc=gstep, lam_pos=lpos, lam_mom=lmom, lam_pops=lam, grad_f=g,
                                     force=force)
     return L, g, lpos, lmom
+
+
+def effective_friction(kernel, offset, *, L=16, steps=1500, F=1e-4, a0=1.0, mass=1.0, n_substeps=10,
+                       dt=0.1, check_every=500, gamma_visc=0.0):
+    """The settling test of Sec. 4.6 on couple() and step(): one particle held
+    at the node L/2 plus `offset` (it is put back there before every LB step,
+    so it does not move on the grid) in a periodic L^3 box at kT = 0 with
+    shear and bulk eigenvalue gamma_visc (Eq. (shearviscosity): nu = (1 + gamma)
+    / (6 (1 - gamma)), eta = rho0 nu; 1/6 for 0), pulled along x by the
+    constant force F; a uniform force density -F/L^3 on the fluid makes the
+    net force zero.  The bare friction is Gamma = 6 pi eta a0.  In the
+    steady state the force balance of Eq. (dragexperiment_particle_equation)
+    gives the particle velocity U = F/Gamma + u0, u0 the velocity the coupling
+    interpolates at the particle; then 1/a = 6 pi eta U / F (Stokes) and
+    Eq. (aeffcorr) gives g from 1/(g b) = 1/a + 2.84/L - 1/a0 (b = 1).
+    Returns dict(u0, u0_prev, U, a, g): u0_prev is u0 `check_every` steps
+    before the end (for a convergence check)."""
+    eta = (1.0 + gamma_visc) / (6.0 * (1.0 - gamma_visc))
+    gamma = 6.0 * np.pi * eta * a0
+    p = make_params((L, L, L), body_force=(-F / L ** 3, 0.0, 0.0), gamma_shear=gamma_visc,
+                    gamma_bulk=gamma_visc)
+    pops = equilibrium(p)
+    r0 = np.array([[L / 2 + offset[0], L / 2 + offset[1], L / 2 + offset[2]]], dtype=np.float64)
+    mom = np.zeros((1, 3))
+    u0_prev = None
+    for t in range(steps):
+        if t == steps - check_every:
+            u0_prev = interpolate(p, pops, r0, kernel=kernel)[0, 0]
+        _, mom, facc, _ = couple(p, pops, r0, mom, mass, gamma, dt=dt, n_substeps=n_substeps, seed=0,
+                                 kernel=kernel, fext=(F, 0.0, 0.0))
+        pops = step(p, pops, facc, t)
+    u0 = interpolate(p, pops, r0, kernel=kernel)[0, 0]
+    U = F / gamma + u0
+    a = F / (6.0 * np.pi * eta * U)
+    g = 1.0 / (1.0 / a + 2.84 / L - 1.0 / a0)
+    return dict(u0=u0, u0_prev=u0_prev, U=U, a=a, g=g)
 
 
 def interpolate(p: Params, pops, pos, force=None, kernel=2):

@@ -704,6 +704,7 @@ typedef struct {
     uint64_t seed;      /* particle noise key                                      */
     uint32_t md_step0;  /* global index of the first sub-step (noise counter)      */
     uint32_t kernel;    /* interpolation function phi_2 (0 or 2), phi_3, phi_4     */
+    double fext[3];     /* constant external force on every particle, part of F^c  */
 } ora_couple_params;
 
 /* Particle noise theta (3 components) for particle p at sub-step t:
@@ -732,9 +733,11 @@ static void particle_theta(const ora_params *P, const ora_couple_params *C, uint
 /* Frictional coupling for one LB step (Sec. 4.5, "Langevin integrator"):
  * the fluid velocity field is frozen for the n_substeps particle steps; per
  * sub-step: half drift, conservative forces, exact Ornstein-Uhlenbeck
- * momentum update (Eq. langevin_momentum_update), spreading of the
- * non-conservative impulse J = p' - p - C2 F^c as -J Delta(r - r_half) into
- * facc (layout [3][N]), second half drift.  mass/gamma: per-particle.
+ * momentum update (Eq. langevin_momentum_update), spreading of the impulse
+ * of the drag and random forces over the sub-step as -J Delta(r - r_half)
+ * into facc (layout [3][N]), Eq. (ftotal): F^c is constant during the
+ * momentum update (constant coordinates), so J = p' - p - h F^c; then the
+ * second half drift.  mass/gamma: per-particle.
  * Returns the number of broken FENE bonds met. */
 int ora_couple(const ora_params *P, const double *pops, const double *force, int np,
                double *pos, double *mom, const double *mass, const double *gamma,
@@ -768,9 +771,9 @@ int ora_couple(const ora_params *P, const double *pops, const double *force, int
             if (P->kT > 0.0) particle_theta(P, C, (uint32_t)p, C->md_step0 + (uint32_t)s, th);
             double pn[3], J[3];
             for (int c = 0; c < 3; c++) {
-                double Fc = md ? fc[3 * p + c] : 0.0;
+                double Fc = (md ? fc[3 * p + c] : 0.0) + C->fext[c];
                 pn[c] = C1 * mom[3 * p + c] + C2 * (Fc + G * up[c]) + C3 * th[c];
-                J[c] = pn[c] - mom[3 * p + c] - C2 * Fc;
+                J[c] = pn[c] - mom[3 * p + c] - h * Fc;
             }
             for (int q = 0; q < nq; q++)
                 for (int c = 0; c < 3; c++) facc[(size_t)c * N + node[q]] -= J[c] * wt[q];

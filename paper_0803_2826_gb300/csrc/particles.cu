@@ -1,15 +1,17 @@
 // particles.cu -- frictional point-particle coupling (Sec. 4.5) with the
-// linear interpolation kernel of Sec. 4.6, and the Kremer-Grest forces of
-// Sec. 2.1 for bead-spring chains.
+// interpolation functions phi_2, phi_3, phi_4 of Sec. 4.6, and the
+// Kremer-Grest forces of Sec. 2.1 for bead-spring chains.
 //
 // Per LB step the caller runs n_substeps particle steps against the frozen
 // fluid velocity u = (sum n c + f_ext/2)/rho of the current state.  One
 // kernel launch per sub-step does, for each particle (a group of 8 lanes):
-//   forces      F^c from FENE bonds (chain neighbours p-1, p+1) and WCA pairs
-//               from a Verlet list                          Eqs. (ufene), (ulennardjones)
-//   interpolate u_p = sum_8 phi2 phi2 phi2 u(node)          Eqs. (ufluid_discrete), (Delta), (2point)
+//   forces      F^c from FENE bonds (chain neighbours p-1, p+1), WCA pairs
+//               from a Verlet list and a constant external force   Eqs. (ufene), (ulennardjones)
+//   interpolate u_p = sum phi phi phi u(node) over the K^3 stencil  Eqs. (ufluid_discrete), (Delta)
 //   OU update   p' = C1 p + C2 (F^c + Gamma u_p) + C3 theta  Eq. (langevin_momentum_update)
-//   spread      facc(node) -= J Delta(node - r_p), J = p' - p - C2 F^c   Eq. (ftotal)
+//   spread      facc(node) -= J Delta(node - r_p), J = p' - p - dt F^c, the
+//               impulse of the drag and random forces (F^c is constant
+//               during the update)                         Eq. (ftotal)
 //   drift       second half drift of this sub-step and first half drift of the next
 //
 // Positions are double in the caller's buffer, but inside a coupling call a
@@ -79,6 +81,7 @@ struct CoupleArgs {
     float cinv[3];         // ncell / L
     int nb_log2;           // log2 of the bucket count
     int kw;                // interpolation stencil width: 2 (phi_2), 3 (phi_3), 4 (phi_4)
+    float fext[3];         // constant external force on every particle (part of F^c)
 };
 
 // ---- cell + offset positions -----------------------------------------------
@@ -657,7 +660,8 @@ __global__ void __launch_bounds__(kPartThreads)
     float pm[3] = {mom[3 * p], mom[3 * p + 1], mom[3 * p + 2]};
 
     // conservative forces at the half-step positions, split over the lanes
-    float F[3] = {0.f, 0.f, 0.f};
+    // (lane 0 starts from the external force)
+    float F[3] = {q == 0 ? c.fext[0] : 0.f, q == 0 ? c.fext[1] : 0.f, q == 0 ? c.fext[2] : 0.f};
     if (c.use_wca) {
         const int nc = ncount[p];
         const int *lst = nlist + (size_t)p * kMaxNb;
@@ -712,7 +716,7 @@ __global__ void __launch_bounds__(kPartThreads)
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
-        J[k] = pn[k] - pm[k] - C2 * F[k];
+        J[k] = pn[k] - pm[k] - c.dt * F[k];
     }
 
     // spread -J Delta: lane q into its own nodes
@@ -1234,8 +1238,8 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
                 if (k < kmax) v[k] = __ldcg(shin + nb[k]);
         }
 
-        // conservative forces at the half-step positions
-        float F[3] = {0.f, 0.f, 0.f};
+        // conservative forces at the half-step positions, from the external force
+        float F[3] = {c.fext[0], c.fext[1], c.fext[2]};
         if (c.use_wca) {
 #pragma unroll
             for (int k = 0; k < kNbReg; ++k)
@@ -1272,7 +1276,7 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
-                J[k] = pn[k] - pm[k] - C2 * F[k];
+                J[k] = pn[k] - pm[k] - c.dt * F[k];
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -1360,6 +1364,7 @@ CoupleArgs make_couple_args(const lb_handle *h, const lb_particles *pp, const lb
     c.cinv[0] = c.cinv[1] = c.cinv[2] = 0.0f;
     c.nb_log2 = 0;
     c.kw = stencil_width(cp->flags);
+    for (int k = 0; k < 3; ++k) c.fext[k] = (float)cp->fext[k];
     return c;
 }
 
@@ -1818,6 +1823,10 @@ bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_coup
     }
     if (cp->flags & (LB_COUPLE_PHI3 | LB_COUPLE_PHI4)) {
         set_error("%s: the coupling reverse pass covers the phi_2 stencil", who);
+        return false;
+    }
+    if (cp->fext[0] != 0.0 || cp->fext[1] != 0.0 || cp->fext[2] != 0.0) {
+        set_error("%s: the coupling reverse pass covers particles without an external force", who);
         return false;
     }
     if (cp->n_substeps < 1 || cp->n_substeps > kMaxAdjSub || !(cp->dt > 0.0)) {

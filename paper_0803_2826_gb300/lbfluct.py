@@ -82,6 +82,7 @@ class lb_couple_params(C.Structure):
         ("dt", C.c_double), ("seed", C.c_uint64), ("md_step0", C.c_uint32),
         ("chain_len", C.c_int), ("use_wca", C.c_int), ("flags", C.c_int),
         ("eps", C.c_double), ("sigma", C.c_double), ("k_fene", C.c_double), ("r0", C.c_double),
+        ("fext", C.c_double * 3),
     ]
 
 
@@ -590,8 +591,9 @@ def particles(n, pos, mom, mass=None, gamma=None, mass0=1.0, gamma0=1.0) -> lb_p
 
 def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len=0, use_wca=False,
                   eps=0.0, sigma=1.0, k_fene=0.0, r0=1.5, per_substep=False,
-                  overlap=False, kernel=2) -> lb_couple_params:
-    """kernel: interpolation function phi_2 (default), phi_3 or phi_4."""
+                  overlap=False, kernel=2, fext=(0.0, 0.0, 0.0)) -> lb_couple_params:
+    """kernel: interpolation function phi_2 (default), phi_3 or phi_4;
+    fext: constant external force on every particle."""
     if kernel not in (2, 3, 4):
         raise ValueError("kernel must be 2, 3 or 4")
     c = lb_couple_params()
@@ -601,4 +603,6 @@ def couple_params(*, n_substeps, dt, seed=0, md_step0=0, noise_kind=0, chain_len
     c.flags = ((LB_COUPLE_PER_SUBSTEP if per_substep else 0) | (LB_COUPLE_OVERLAP if overlap else 0) |
                {2: 0, 3: LB_COUPLE_PHI3, 4: LB_COUPLE_PHI4}[kernel])
     c.eps, c.sigma, c.k_fene, c.r0 = float(eps), float(sigma), float(k_fene), float(r0)
+    for k in range(3):
+        c.fext[k] = float(fext[k])
     return c

@@ -28,7 +28,8 @@ def dev(x, dt=None):
 
 
 def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1, gamma=2.0, mass=1.0,
-         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0), per_substep=False, kernel=2):
+         noise_kind=0, u_amp=0.01, lb_after=True, body_force=(0.0, 0.0, 0.0), per_substep=False, kernel=2,
+         fext=(0.0, 0.0, 0.0)):
     mom32 = mom.astype(np.float32).astype(np.float64)
     p = ora.make_params(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
     u = inputs.shear_wave(shape, u_amp) + inputs.gaussian_field(shape, 3, 1e-3, seed=8)
@@ -40,7 +41,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
     if chains:
         md = ora.make_md(chains[0], chains[1], eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5)
     opos, omom, ofacc, broken = ora.couple(p, pops, pos, mom32, mass, gamma, dt=dt, n_substeps=nsub, seed=11,
-                                           md_step0=40, md=md, noise_kind=noise_kind, kernel=kernel)
+                                           md_step0=40, md=md, noise_kind=noise_kind, kernel=kernel, fext=fext)
     assert broken == 0
     lat = L.Lattice(shape, kT=kT, seed=4, walls=walls, body_force=body_force)
     lat.init_equilibrium(None, dev(u))
@@ -49,7 +50,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
     parts = L.particles(pos.shape[0], gpos, gmom, mass0=mass, gamma0=gamma)
     cp = L.couple_params(n_substeps=nsub, dt=dt, seed=11, md_step0=40, noise_kind=noise_kind,
                          chain_len=chains[1] if chains else 0, use_wca=bool(chains), eps=0.01, sigma=1.0,
-                         k_fene=0.3, r0=1.5, per_substep=per_substep, kernel=kernel)
+                         k_fene=0.3, r0=1.5, per_substep=per_substep, kernel=kernel, fext=fext)
     L.lb_couple_particles(lat.h, parts, cp)
     facc = torch.empty((3,) + tuple(shape[::-1]), dtype=torch.float32, device="cuda")
     L.lb_get_particle_forces(lat.h, facc)
@@ -77,6 +78,23 @@ def test_free_particles_parity(ora, kT):
     pos = inputs.uniform_particles(300, shape, seed=1)
     mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
     r = _run(ora, shape, pos, mom, kT=kT)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+
+
+@pytest.mark.parametrize("per_substep,kernel", [(False, 2), (True, 2), (False, 3)])
+def test_external_force_parity(ora, per_substep, kernel):
+    """A constant external force on every particle (part of F^c; the fluid
+    gets only the drag and random impulses, Eq. (ftotal)), on both kernels
+    of the coupling and with phi_3."""
+    shape = (12, 10, 9)
+    pos = inputs.uniform_particles(300, shape, seed=1)
+    mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
+    r = _run(ora, shape, pos, mom, kT=1e-4, per_substep=per_substep, kernel=kernel, fext=(3e-3, -2e-3, 1e-3))
     assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
     assert rel(r["gmom"], r["omom"]) < 2e-4
     assert rel(r["gfacc"], r["ofacc"]) < 2e-4
