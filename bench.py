@@ -42,9 +42,9 @@ EPS, SIGMA, K_FENE, R0 = 0.01, 1.0, 0.3, 1.5   # epsilon = 0.01 in lattice energ
 # separate small launch and the timed launch reads no impulse field
 BYTES_PER_NODE = {"serial": 19 * 4 * 2 + 3 * 4, "overlapped": 19 * 4 * 2}
 FALLBACK_HBM_GBS = 6800.0
-def workload(box: int = SHAPE[0]) -> str:
+def workload(box: int = SHAPE[0], phi: int = 2) -> str:
     return ("fluctuating D3Q19 %d^3 periodic FP32 kT=1e-4 + 64 FENE/WCA chains x 256 monomers, "
-            "10 MD sub-steps per LB step" % box)
+            "10 MD sub-steps per LB step" % box) + ("" if phi == 2 else ", phi_%d interpolation" % phi)
 SLAB = (256, 256, 4)            # CPU sample: same x-y extent, 4 planes, one chain
 
 
@@ -62,6 +62,8 @@ def _args():
                     help="run the coupling before the LB update instead of overlapping the two")
     ap.add_argument("--box", type=int, default=SHAPE[0],
                     help="edge of the coupled box (smaller boxes for profiling runs only)")
+    ap.add_argument("--phi", type=int, choices=[2, 3, 4], default=2,
+                    help="interpolation function of the coupling (phi_2 is the headline workload)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="time lb_step alone (no particles) on --shape for each --kT and --dtype")
     ap.add_argument("--shape", default="256,256,256")
@@ -268,7 +270,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
     cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=7 + rank, chain_len=CHAIN_LEN, use_wca=True,
-                         eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=not args.serial)
+                         eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=not args.serial, kernel=args.phi)
     t_step = [0]
 
     def one_step(sums=None):
@@ -361,7 +363,7 @@ def run_ours(args):
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload(args.box), "nodes": nodes, "particles": npart, "substeps": NSUB,
+        "config": {"workload": workload(args.box, args.phi), "nodes": nodes, "particles": npart, "substeps": NSUB,
                    "l2": "inputs larger than L2 (2.55 GB populations per replica)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -515,7 +517,7 @@ def _interpolation_forms(stream, steps=100):
         lat.init_equilibrium()
     pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, SHAPE, seed=0)
     mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000)
-    res = {"steps": steps, "workload": workload()}
+    res = {"steps": steps}
     for phi in (3, 4):
         gpos = torch.as_tensor(pos0).cuda()
         gmom = torch.as_tensor(mom0, dtype=torch.float32).cuda()
@@ -546,7 +548,7 @@ def _interpolation_forms(stream, steps=100):
         st, bits = lat.sync()
         assert bits == 0, "device error word 0x%x (phi_%d)" % (bits, phi)
         nodes = SHAPE[0] * SHAPE[1] * SHAPE[2]
-        res["phi%d" % phi] = {"ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6,
+        res["phi%d" % phi] = {"workload": workload(phi=phi), "ms_per_step": ms, "mlups": nodes / (ms * 1e-3) / 1e6,
                               "coupling_ms_per_step": cp_sum / cp_n, "stream_collide_ms": sc_sum / sc_n}
     lat.close()
     torch.cuda.empty_cache()

@@ -236,13 +236,15 @@ typedef struct {
 
 /* lb_couple_params.flags: run the coupling on a high-priority library stream
  * while the next lb_step updates every node without its impulses, then that
- * lb_step updates again, with the impulses, the nodes of the 8-node stencils
- * the particles visited (the update of a node depends only on the pre-step
+ * lb_step updates again, with the impulses, the nodes of the stencils the
+ * particles visited (the update of a node depends only on the pre-step
  * state, its forces and the counter-based noise, so the result is the one a
- * single update with the impulses gives).  The call returns with the
- * coupling queued after all work on the handle's stream; the next lb_step, or
- * any other call on the handle, orders the handle's stream after the
- * coupling.  Until then the caller must not read pos / mom itself. */
+ * single update with the impulses gives) and clears their impulses.  The
+ * call returns with the coupling queued after all work on the handle's
+ * stream; the next lb_step, or any other call on the handle, orders the
+ * handle's stream after the coupling.  Until then the caller must not read
+ * pos / mom itself.  A call made while impulses of an earlier call still
+ * wait for a step runs in the serial order (the flag is ignored). */
 #define LB_COUPLE_OVERLAP 0x2
 
 /* lb_couple_params.flags: interpolate and spread with the three-point

@@ -17,13 +17,13 @@ extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const
 extern template cudaError_t launch_stream_collide_dt<1>(const lb_handle *, const void *, void *, const float *, float *);
 extern template cudaError_t launch_stream_collide_dt<2>(const lb_handle *, const void *, void *, const float *, float *);
 template <int DT>
-cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
+cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, float *facc, const int *records,
                             int n, int nsub, int span, unsigned int *claim, unsigned int tag);
-extern template cudaError_t launch_patch_dt<0>(const lb_handle *, const void *, void *, const float *, const int *,
+extern template cudaError_t launch_patch_dt<0>(const lb_handle *, const void *, void *, float *, const int *,
                                                int, int, int, unsigned int *, unsigned int);
-extern template cudaError_t launch_patch_dt<1>(const lb_handle *, const void *, void *, const float *, const int *,
+extern template cudaError_t launch_patch_dt<1>(const lb_handle *, const void *, void *, float *, const int *,
                                                int, int, int, unsigned int *, unsigned int);
-extern template cudaError_t launch_patch_dt<2>(const lb_handle *, const void *, void *, const float *, const int *,
+extern template cudaError_t launch_patch_dt<2>(const lb_handle *, const void *, void *, float *, const int *,
                                                int, int, int, unsigned int *, unsigned int);
 
 namespace {
@@ -235,7 +235,8 @@ lb_status step_once(lb_handle *h, float *partials)
         if (e != cudaSuccess) return cuda_fail("lb_step", e);
         h->launches += 2;
         h->facc_dirty = 0;
-        h->facc_stale = 1;
+        h->facc_stale = 0;  // the patch cleared every impulse node it applied
+        drop_particle_records(h);
         h->cur = 1 - h->cur;
         h->step += 1;
         return LB_OK;

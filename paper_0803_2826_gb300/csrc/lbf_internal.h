@@ -106,6 +106,8 @@ cudaError_t reduce_step_sums(const lb_handle *h, const float *partials, size_t n
                              double *sums);
 void timer_mark(lb_handle *h, int which, int end, cudaStream_t s);  // record a timer event
 cudaError_t reset_particle_barrier(lb_handle *h);
+// Forget the stencil records of applied impulses that are already cleared.
+void drop_particle_records(lb_handle *h);
 bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_couple_params *cp, const char *who);
 lb_status couple_adjoint(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
                          const float *lam_facc, float *lam_pos, float *lam_mom, float *lam_u);

@@ -58,6 +58,15 @@ struct Particles {
     int *bucket_of = nullptr;    // [cap] bucket of each particle (to empty it again)
     int nb_log2 = 0;             // log2 nbuckets
     int rec_span = 2;            // nodes per axis the live records' stencils touch (2, or 4 for phi_3 / phi_4)
+    int rec_n = 0;               // particles per sub-step of the live records (-1: calls with different counts)
+    // fluid velocities at the stencil nodes of each particle, kept over the
+    // sub-steps of a call (the fluid is frozen during a call): [cap][64]
+    // float4, valid while the particle's stencil origin and the call epoch
+    // match its tag
+    float4 *ucache = nullptr;
+    int2 *utag = nullptr;        // [cap] (packed stencil origin, epoch)
+    int ucache_cap = 0;
+    uint32_t epoch = 0;          // coupling calls that used the cache
 };
 
 namespace {
@@ -646,7 +655,8 @@ __global__ void __launch_bounds__(kPartThreads)
               const float4 *__restrict__ sh_in, float4 *__restrict__ sh_out, double *pos_out, float *mom,
               const float *mass, const float *gamma, const int *nlist, const int *ncount, const float4 *ref,
               int *head, const int *bucket_of, float *facc, int *records, unsigned int *flags,
-              unsigned int *err, CoupleArgs c, uint32_t clear_slot)
+              unsigned int *err, float4 *__restrict__ ucache, int2 *__restrict__ utag, int epoch,
+              CoupleArgs c, uint32_t clear_slot)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0 && c.use_wca) flags[clear_slot] = 0u;  // the list build has run
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -675,9 +685,22 @@ __global__ void __launch_bounds__(kPartThreads)
     }
 
     // fluid velocity at the particle: lane q takes stencil nodes q, q + 8, ...
+    // The node velocities of the particle's stencil are cached per call: a
+    // particle keeps its stencil for many sub-steps, so the pull-gathers of
+    // 19 populations per node run only when its stencil origin moves.
     constexpr int kNodes = KW * KW * KW, kPerLane = (kNodes + kChunks - 1) / kChunks;
     Stencil<KW> st;
     make_stencil<KW>(me, st);
+    const int okey = wrap_node(st.o[0], g.nx) | (wrap_node(st.o[1], g.ny) << 10) |
+                     ((g.z0 > 0 ? st.o[2] : wrap_node(st.o[2], g.nz)) << 20);
+    int miss = 1;
+    if (q == 0) {
+        const int2 tag = utag[p];
+        miss = !(tag.x == okey && tag.y == epoch);
+    }
+    // one decision for the group, taken before lane 0 may rewrite the tag
+    const bool hit = __shfl_sync(gmask, miss, 0, kChunks) == 0;
+    float4 *uc = ucache + (size_t)p * 64 + q;
     float up[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < kPerLane; ++i) {
@@ -686,11 +709,20 @@ __global__ void __launch_bounds__(kPartThreads)
             int x, y, z;
             const float w = stencil_node_k<KW>(st, qq, g, x, y, z);
             float un[3];
-            node_velocity<DT>(src, ffield, x, y, z, g, un);
+            if (hit) {
+                const float4 v = __ldcg(uc + kChunks * i);
+                un[0] = v.x;
+                un[1] = v.y;
+                un[2] = v.z;
+            } else {
+                node_velocity<DT>(src, ffield, x, y, z, g, un);
+                __stcg(uc + kChunks * i, make_float4(un[0], un[1], un[2], 0.0f));
+            }
 #pragma unroll
             for (int k = 0; k < 3; ++k) up[k] = i == 0 ? w * un[k] : fmaf(w, un[k], up[k]);
         }
     }
+    if (!hit && q == 0) utag[p] = make_int2(okey, epoch);
 #pragma unroll
     for (int o = 1; o < 8; o <<= 1) {
 #pragma unroll
@@ -784,6 +816,36 @@ __global__ void k_clear_records(float *facc, const int *records, size_t n, StepA
     }
 }
 
+// The same for live records laid out [nsub][n]: eight lanes per particle
+// walk its cells, skip a cell equal to the one before (a particle keeps its
+// cell for many sub-steps) and zero nodes q, q + 8, ... of the block.
+template <int SPAN>
+__global__ void k_clear_records_by_particle(float *facc, const int *records, int n, int nsub, StepArgs g)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)n * 8) return;
+    const int p = (int)(t >> 3), q = (int)(t & 7);
+    constexpr int lo = SPAN == 4 ? -1 : 0, nk = SPAN * SPAN * SPAN;
+    int prev = -1;
+    for (int s = 0; s < nsub; ++s) {
+        const int base = records[(size_t)s * n + p];
+        if (base == prev) continue;
+        prev = base;
+        const int x0 = base % g.nx, y0 = (base / g.nx) % g.ny, z0 = base / (g.nx * g.ny);
+#pragma unroll
+        for (int k = q; k < nk; k += 8) {
+            const int x = wrap_node(x0 + lo + k % SPAN, g.nx), y = wrap_node(y0 + lo + (k / SPAN) % SPAN, g.ny);
+            int z = z0 + lo + k / (SPAN * SPAN);
+            if (g.z0 > 0) z = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
+            else z = wrap_node(z, g.nz);
+            const size_t i = ((size_t)z * g.ny + y) * g.nx + x;
+            facc[i] = 0.0f;
+            facc[g.pitch + i] = 0.0f;
+            facc[2 * g.pitch + i] = 0.0f;
+        }
+    }
+}
+
 // Interpolated velocity at caller positions with phi_KW; eight lanes per
 // position, lane q takes stencil nodes q, q + 8, ...
 template <int DT, int KW>
@@ -838,6 +900,8 @@ void free_parts(Particles *P)
     cudaFree(P->head);
     cudaFree(P->next);
     cudaFree(P->bucket_of);
+    cudaFree(P->ucache);
+    cudaFree(P->utag);
     delete P;
 }
 
@@ -1368,6 +1432,13 @@ CoupleArgs make_couple_args(const lb_handle *h, const lb_particles *pp, const lb
     return c;
 }
 
+void note_records(Particles *P, int n, size_t count)
+{
+    if (P->n_records == 0) P->rec_n = n;
+    else if (P->rec_n != n) P->rec_n = -1;
+    P->n_records += count;
+}
+
 template <int DT>
 cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
 {
@@ -1464,11 +1535,10 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         h->launches += 1;
         if (fold_clear) {
             P->rec_off = new_off;
-            P->n_records = (size_t)n * (size_t)cp->n_substeps;
+            P->n_records = 0;
             h->facc_stale = 0;
-        } else {
-            P->n_records += (size_t)n * (size_t)cp->n_substeps;
         }
+        note_records(P, n, (size_t)n * (size_t)cp->n_substeps);
         P->sub_counter += (uint32_t)cp->n_substeps;
         P->last_nsub = cp->n_substeps;
         return cudaGetLastError();
@@ -1483,6 +1553,24 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         cudaError_t e = cudaMemsetAsync(P->flags, 0xff, 2 * sizeof(unsigned int), h->stream);
         if (e != cudaSuccess) return e;
         P->nlist_n = n;
+    }
+    if (P->ucache_cap < n) {  // node-velocity cache of the per-sub-step kernels
+        cudaFree(P->ucache);
+        cudaFree(P->utag);
+        P->ucache = nullptr;
+        P->utag = nullptr;
+        P->ucache_cap = 0;
+        cudaError_t e = cudaMalloc((void **)&P->ucache, (size_t)n * 64 * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&P->utag, (size_t)n * sizeof(int2));
+        if (e == cudaSuccess) e = cudaMemsetAsync(P->utag, 0, (size_t)n * sizeof(int2), h->stream);
+        if (e != cudaSuccess) return e;
+        P->ucache_cap = n;
+        P->epoch = 0;
+    }
+    if (++P->epoch >= 0x7fffffffu) {  // tags hold the epoch as int: start again from 1
+        cudaError_t e = cudaMemsetAsync(P->utag, 0, (size_t)P->ucache_cap * sizeof(int2), h->stream);
+        if (e != cudaSuccess) return e;
+        P->epoch = 1;
     }
     k_half_drift<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, pp->mom, pp->mass, P->shadow[0], h->d_err, c);
     h->launches += 1;
@@ -1503,12 +1591,13 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
 #define LBI_SUBSTEP(KW)                                                                                          \
     k_substep<DT, KW><<<sblocks, kPartThreads, 0, h->stream>>>(                                                  \
         src, h->force, P->shadow[s & 1], P->shadow[(s + 1) & 1], pp->pos, pp->mom, pp->mass, pp->gamma, P->nlist, \
-        P->ncount, need_nlist ? P->ref : nullptr, P->head, P->bucket_of, h->facc, rec, P->flags, h->d_err, c, rd)
+        P->ncount, need_nlist ? P->ref : nullptr, P->head, P->bucket_of, h->facc, rec, P->flags, h->d_err,         \
+        P->ucache, P->utag, (int)P->epoch, c, rd)
         if (c.kw == 3) LBI_SUBSTEP(3);
         else if (c.kw == 4) LBI_SUBSTEP(4);
         else LBI_SUBSTEP(2);
 #undef LBI_SUBSTEP
-        P->n_records += (size_t)n;
+        note_records(P, n, (size_t)n);
         if (c.kw > 2) P->rec_span = 4;
         P->sub_counter += 1;
         h->launches += 1;
@@ -1709,7 +1798,10 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         return LB_EINVAL;
     }
     join_overlap(h);  // a coupling of this step that has not been joined yet
-    const bool overlap = (cp->flags & LB_COUPLE_OVERLAP) != 0;
+    // impulses of an earlier call that no step has applied yet lie outside
+    // this call's stencil records, which the overlapped step re-updates:
+    // such a call runs in the serial order
+    const bool overlap = (cp->flags & LB_COUPLE_OVERLAP) != 0 && !h->facc_dirty;
     cudaStream_t main_stream = h->stream;
     if (overlap) {
         // run on the handle's high-priority stream after everything queued on
@@ -1769,11 +1861,21 @@ cudaError_t clear_particle_forces(lb_handle *h)
     if (!P || !h->facc) return cudaSuccess;
     if (P->n_records) {
         const StepArgs g = make_args(h);
-        int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
-        if (P->rec_span == 4)
-            k_clear_records<4><<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
-        else
-            k_clear_records<2><<<blocks, 256, 0, h->stream>>>(h->facc, P->records + P->rec_off, P->n_records, g);
+        const int *rec = P->records + P->rec_off;
+        if (P->rec_n > 0 && P->n_records % (size_t)P->rec_n == 0) {  // [nsub][n]: skip repeated cells
+            const int nsub = (int)(P->n_records / (size_t)P->rec_n);
+            const unsigned int blocks = (unsigned int)(((size_t)P->rec_n * 8 + 255) / 256);
+            if (P->rec_span == 4)
+                k_clear_records_by_particle<4><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->rec_n, nsub, g);
+            else
+                k_clear_records_by_particle<2><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->rec_n, nsub, g);
+        } else {
+            int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
+            if (P->rec_span == 4)
+                k_clear_records<4><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->n_records, g);
+            else
+                k_clear_records<2><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->n_records, g);
+        }
         h->launches += 1;
         P->n_records = 0;
         P->rec_off = 0;
@@ -1905,6 +2007,15 @@ cudaError_t reset_particle_barrier(lb_handle *h)
     Particles *P = h->parts;
     if (!P || !P->bar) return cudaSuccess;
     return cudaMemsetAsync(P->bar, 0, 3 * sizeof(unsigned int), h->stream);
+}
+
+void drop_particle_records(lb_handle *h)
+{
+    Particles *P = h->parts;
+    if (!P) return;
+    P->n_records = 0;
+    P->rec_off = 0;
+    P->rec_span = 2;
 }
 
 void destroy_particles(lb_handle *h)

@@ -301,7 +301,7 @@ template <int DT, bool NOISE, bool WALLS>
 __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd::Store<DT>::T *__restrict__ src,
                                                              typename lbd::Store<DT>::T *__restrict__ dst,
                                                              const float *__restrict__ ffield,
-                                                             const float *__restrict__ facc, const int *records,
+                                                             float *__restrict__ facc, const int *records,
                                                              int n, int nsub, int span, unsigned int *claim,
                                                              unsigned int tag, const StepArgs a)
 {
@@ -321,6 +321,10 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
             const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
             if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
             update_node<DT, NOISE, true, WALLS>(src, dst, ffield, facc, a, x, y, z);
+            // the impulses are applied: clear them for the next coupling call
+            facc[node] = 0.0f;
+            facc[a.pitch + node] = 0.0f;
+            facc[2 * a.pitch + node] = 0.0f;
         }
     }
 }
@@ -336,7 +340,7 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
 // claim makes sure each node is corrected once.
 template <bool WALLS>
 __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restrict__ dst, const float *__restrict__ ffield,
-                                                                 const float *__restrict__ facc, const int *records, int n,
+                                                                 float *__restrict__ facc, const int *records, int n,
                                                                  int nsub, int span, unsigned int *claim,
                                                                  unsigned int tag, const StepArgs a)
 {
@@ -399,6 +403,10 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restri
             lbd::backward(dM, dn);
 #pragma unroll
             for (int i = 0; i < 19; ++i) dst[(size_t)i * P + node] = ns[i] + dn[i];
+            // the impulses are applied: clear them for the next coupling call
+            facc[node] = 0.0f;
+            facc[P + node] = 0.0f;
+            facc[2 * P + node] = 0.0f;
         }
     }
 }
@@ -620,7 +628,7 @@ cudaError_t launch_stream_collide_dt(const lb_handle *h, const void *src, void *
 }
 
 template <int DT>
-cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, const float *facc, const int *records,
+cudaError_t launch_patch_dt(const lb_handle *h, const void *src, void *dst, float *facc, const int *records,
                             int n, int nsub, int span, unsigned int *claim, unsigned int tag)
 {
     using T = typename lbd::Store<DT>::T;

@@ -88,6 +88,38 @@ def test_walls_parity(ora, kT):
     assert rel(got[:, fl] - aa, want[:, fl] - aa) < 5e-6
 
 
+@pytest.mark.parametrize("ge", [0.5, -0.5])
+def test_two_rate_poiseuille_gpu(ora, ge):
+    """Two relaxation rates with (tau_e - 1/2)(tau_o - 1/2) = 3/16 (the
+    relation for which the oracle's Poiseuille profile is the exact parabola
+    with half-way no-slip planes): the GPU's steady profile after 20000 steps
+    matches the parabola to FP32 accuracy (1e-5 of the peak), and with
+    gamma_o = 0 it matches the oracle's slipping profile to the same bar."""
+    nz, g = 12, 1e-5
+    te = 1.0 / (1.0 - ge)
+    go = 1.0 - 1.0 / (0.5 + (3.0 / 16.0) / (te - 0.5))
+    nu = (1 + ge) / (6 * (1 - ge))
+    z = np.arange(1, nz - 1)
+    ua = g / (2 * nu) * (z - 0.5) * (nz - 1.5 - z)
+    for gam_o in (go, 0.0):
+        kw = dict(walls=True, body_force=(g, 0.0, 0.0), gamma_shear=ge, gamma_bulk=ge, gamma_even=ge,
+                  gamma_odd=gam_o)
+        lat = L.Lattice((4, 4, nz), **kw)
+        lat.init_equilibrium()
+        lat.step(20000)
+        rho, j, _, _ = lat.moments(want_pi=False)
+        ux = (j[0] / rho)[1:-1].mean(dim=(1, 2)).double().cpu().numpy()
+        assert lat.sync() == (L.LB_OK, 0)
+        if gam_o == go:
+            want = ua
+        else:
+            p = ora.make_params((1, 1, nz), **kw)
+            rr, jj, _ = ora.moments(p, ora.run(p, ora.equilibrium(p), 20000))
+            want = (jj[0] / rr)[1:-1, 0, 0]
+            assert np.abs(want - ua).max() > 1e-3 * ua.max()  # the slip is there
+        assert np.abs(ux - want).max() < 1e-5 * ua.max(), (gam_o, np.abs(ux - want).max() / ua.max())
+
+
 def test_shear_wave_1000_steps(ora):
     """The 32^3 fluctuating shear-wave workload: rho0 = 1, gamma_s = gamma_v = 0
     (nu = 1/6), kT = 1e-4, seed 0, u_x = 0.01 sin(2 pi z / 32), 1000 steps."""

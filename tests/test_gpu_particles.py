@@ -386,6 +386,31 @@ def test_overlapped_coupling_matches_serial(walls, kernel):
     assert np.abs(a[2] - b[2]).max() < 1e-6
 
 
+def test_two_coupling_calls_per_step_with_overlap():
+    """Two coupling calls before one step (5 + 5 sub-steps): the second
+    overlapped call runs in the serial order, so the impulses of both calls
+    reach the fluid; same result as two serial calls."""
+    shape = (20, 18, 16)
+    out = []
+    for overlap in (False, True):
+        pos = inputs.random_walk_chains(6, 32, shape, seed=51)
+        mom = inputs.maxwell_momenta(192, 1.0, 2e-3, seed=52).astype(np.float32)
+        lat = L.Lattice(shape, kT=1e-4, seed=6, body_force=(1e-5, 0.0, 0.0))
+        lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+        gpos, gmom = dev(pos), dev(mom, torch.float32)
+        parts = L.particles(192, gpos, gmom, mass0=1.0, gamma0=2.0)
+        for t in range(3):
+            for half in range(2):
+                cp = L.couple_params(n_substeps=5, dt=0.1, seed=3, md_step0=10 * t + 5 * half, chain_len=32,
+                                     use_wca=True, eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=overlap)
+                L.lb_couple_particles(lat.h, parts, cp)
+            lat.step(1)
+        assert lat.sync() == (L.LB_OK, 0)
+        out.append((lat.get_populations().cpu().numpy(), gpos.cpu().numpy()))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-7
+    assert _pos_err(out[0][1], out[1][1], shape) < 1e-6
+
+
 def test_overlapped_coupling_joined_by_another_call():
     """A call between the overlapped coupling and lb_step (here
     lb_get_particle_forces) waits for the coupling; the step then applies

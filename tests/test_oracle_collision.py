@@ -13,6 +13,9 @@
   variance mu rho0 w_k (mu = kT / c_s^2).
 - Plane Poiseuille flow between bounce-back walls (Sec. 4.1): the steady
   profile has second difference -g / nu and the wall stress balances the force.
+- Two relaxation rates (Sec. 3.4, kinetic eigenvalues): with
+  (tau_e - 1/2)(tau_o - 1/2) = 3/16 the Poiseuille profile is the exact
+  parabola with half-way no-slip planes at every viscosity.
 """
 import numpy as np
 import pytest
@@ -219,3 +222,38 @@ def test_poiseuille(ora):
     again = ora.run(p, pops, 1, step0=6000)
     rho2, j2, _ = ora.moments(p, again)
     assert np.allclose(j2[0][1:-1], j[0][1:-1], rtol=1e-8)
+
+
+def _magic_gamma_odd(ge):
+    """gamma_o with Lambda = (tau_e - 1/2)(tau_o - 1/2) = 3/16, tau = 1/(1 - gamma)."""
+    te = 1.0 / (1.0 - ge)
+    to = 0.5 + (3.0 / 16.0) / (te - 0.5)
+    return 1.0 - 1.0 / to
+
+
+@pytest.mark.parametrize("ge", [0.5, 0.0, -0.5])
+def test_two_rate_poiseuille_is_exact(ora, ge):
+    """Two relaxation rates (Sec. 3.4: gamma_s = gamma_v = gamma_4a = gamma_4b =
+    gamma_e, gamma_3a = gamma_3b = gamma_o) with the relation that the paper
+    leaves to its references, read as (tau_e - 1/2)(tau_o - 1/2) = 3/16:
+    Poiseuille flow between link bounce-back walls is then the exact parabola
+    with no-slip planes half-way between the solid and the first fluid node,
+    for every viscosity nu = (1 + gamma_e)/(6 (1 - gamma_e)) (Eq.
+    shearviscosity); with gamma_o = 0 instead the profile slips by ~0.3 %."""
+    nz, g = 12, 1e-5
+    go = _magic_gamma_odd(ge)
+    nu = (1 + ge) / (6 * (1 - ge))
+    z = np.arange(1, nz - 1)
+    ua = g / (2 * nu) * (z - 0.5) * (nz - 1.5 - z)
+    for gam_o, exact in ((go, True), (0.0, False)):
+        p = ora.make_params((1, 1, nz), walls=True, body_force=(g, 0, 0), gamma_shear=ge, gamma_bulk=ge,
+                            gamma_even=ge, gamma_odd=gam_o)
+        pops = ora.run(p, ora.equilibrium(p), 20000)
+        rho, j, _ = ora.moments(p, pops)
+        ux = (j[0] / rho)[1:-1, 0, 0]
+        dev = np.abs(ux - ua).max() / ua.max()
+        if exact:
+            assert dev < 1e-10, dev
+        else:
+            assert dev > 1e-3, dev
+
