@@ -339,7 +339,7 @@ def test_fast_wca_particles_rebuild_lists(ora, per_substep):
     assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 1e-3
 
 
-def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False, kernel=2):
+def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False, kernel=2, dtype=L.LB_F32):
     """`steps` rounds of couple + step in a thermal fluid: FENE + WCA chains
     (periodic box) or single WCA particles between walls."""
     if walls:  # z in [1, nz - 2): no bond may cross the walls
@@ -351,7 +351,7 @@ def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False, kernel=2):
         pos = inputs.random_walk_chains(n_ch, clen, shape, seed=51)
     n = pos.shape[0]
     mom = inputs.maxwell_momenta(n, 1.0, 2e-3, seed=52).astype(np.float32)  # fast: cells change
-    lat = L.Lattice(shape, kT=1e-4, seed=6, walls=walls, body_force=(1e-5, 0.0, 0.0))
+    lat = L.Lattice(shape, kT=1e-4, seed=6, walls=walls, body_force=(1e-5, 0.0, 0.0), dtype=dtype)
     lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
     gpos, gmom = dev(pos), dev(mom, torch.float32)
     parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
@@ -409,6 +409,51 @@ def test_two_coupling_calls_per_step_with_overlap():
         out.append((lat.get_populations().cpu().numpy(), gpos.cpu().numpy()))
     assert np.abs(out[0][0] - out[1][0]).max() < 1e-7
     assert _pos_err(out[0][1], out[1][1], shape) < 1e-6
+
+
+@pytest.mark.parametrize("dtype,walls,kernel", [(L.LB_F16, False, 3), (L.LB_BF16, True, 2)])
+def test_overlapped_coupling_reduced_precision(dtype, walls, kernel):
+    """FP16 / BF16 storage: the overlapped step re-updates the impulse nodes
+    with the full update (not the FP32 correction), over the 4^3 block for
+    phi_3; same result as the serial order up to storage roundings where the
+    impulse sums (atomics) round differently.  One unit of the stored value
+    (deviation x 2^10, |deviation| < 2e-3) is ~1e-6 in FP16 and ~8e-6 in BF16;
+    the bar is about ten units after four steps."""
+    shape = (20, 18, 16)
+    a = _coupled_run(shape, walls=walls, overlap=False, kernel=kernel, dtype=dtype)
+    b = _coupled_run(shape, walls=walls, overlap=True, kernel=kernel, dtype=dtype)
+    d = np.abs(a[0] - b[0])
+    unit = 1e-6 if dtype == L.LB_F16 else 8e-6
+    assert d.max() < 10 * unit and d.mean() < unit, (d.max(), d.mean())
+    assert _pos_err(a[1], b[1], shape) < 1e-5
+
+
+@pytest.mark.parametrize("shape,kernel", [((3, 3, 3), 4), ((2, 5, 3), 3)])
+def test_stencil_wider_than_box(ora, shape, kernel):
+    """Boxes narrower than the stencil: periodic images of a node receive the
+    weights of every stencil node that wraps onto them (as the oracle
+    does)."""
+    pos = inputs.uniform_particles(20, shape, seed=9)
+    mom = inputs.maxwell_momenta(20, 1.0, 1e-4, seed=10)
+    r = _run(ora, shape, pos, mom, kT=1e-4, nsub=4, kernel=kernel)
+    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
+    assert rel(r["gmom"], r["omom"]) < 2e-4
+    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+
+
+def test_no_particles_is_a_no_op():
+    lat = L.Lattice((8, 8, 8), kT=1e-4, seed=2)
+    lat.init_equilibrium()
+    ref = L.Lattice((8, 8, 8), kT=1e-4, seed=2)
+    ref.init_equilibrium()
+    empty = torch.empty((0, 3), dtype=torch.float64, device="cuda")
+    parts = L.particles(0, empty, empty.float(), mass0=1.0, gamma0=1.0)
+    for overlap in (False, True):
+        L.lb_couple_particles(lat.h, parts, L.couple_params(n_substeps=3, dt=0.1, overlap=overlap, kernel=3))
+        lat.step(1)
+        ref.step(1)
+    assert lat.sync() == (L.LB_OK, 0)
+    assert torch.equal(lat.get_populations(), ref.get_populations())
 
 
 def test_overlapped_coupling_joined_by_another_call():
