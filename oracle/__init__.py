@@ -23,6 +23,8 @@ Function -> passage it follows:
   couple()        Sec. 4.5 Eqs. (fdrag), (ftotal), (langevin_momentum_update);
                   Sec. 4.6 Eqs. (ufluid_discrete), (Delta), (2point), (3point), (4point)
   interpolate()   Sec. 4.6 Eq. (ufluid_discrete)
+  sphere_owner(), sphere_velocity(), step_spheres()  Sec. 4.1 Eq. (MBB); Sec. 4.2
+                  Eqs. (EOMD-1)-(EOMD-3), (force0), (zeta), (EOMUsol) and the U~ equation
   effective_friction()  Sec. 4.5 drag experiment, Eqs. (dragexperiment_particle_equation),
                   (effsize), (aeff), (aeffcorr); Sec. 4.6 settling test
   adjoint_step()  reverse mode of step() at kT = 0, derived by hand in
@@ -129,6 +131,11 @@ def _load():
             lib.ora_stencil.argtypes = [P, _D, C.POINTER(C.c_longlong), _D]
             lib.ora_stencil_k.argtypes = [P, C.c_int, _D, C.POINTER(C.c_longlong), _D]
             lib.ora_stencil_k.restype = C.c_int
+            lib.ora_sphere_owner.argtypes = [P, C.c_int, _D, C.c_double, C.POINTER(C.c_int)]
+            lib.ora_sphere_velocity.argtypes = [_D, C.c_double, _D, _D, _D, _D]
+            lib.ora_step_spheres.argtypes = [P, _D, _D, _D, C.c_uint32, C.POINTER(C.c_int), C.c_int, C.c_double,
+                                             _D, _D, _D, _D, _D]
+            lib.ora_step_spheres.restype = C.c_int
             lib.ora_phi.argtypes = [C.c_int, C.c_double]
             lib.ora_phi.restype = C.c_double
             lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
@@ -418,6 +425,52 @@ def effective_friction(kernel, offset, *, L=16, steps=1500, F=1e-4, a0=1.0, mass
     a = F / (6.0 * np.pi * eta * U)
     g = 1.0 / (1.0 / a + 2.84 / L - 1.0 / a0)
     return dict(u0=u0, u0_prev=u0_prev, U=U, a=a, g=g)
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def sphere_owner(p: Params, R, a):
+    """Solid map (nz, ny, nx): index of the sphere of radius a whose centre
+    lies closer than a to the node (minimum image), -1 for fluid."""
+    lib = _load()
+    R = np.ascontiguousarray(R, dtype=np.float64).reshape(-1, 3)
+    owner = np.empty((p.nz, p.ny, p.nx), dtype=np.int32)
+    lib.ora_sphere_owner(C.byref(p), R.shape[0], _dp(R), float(a), _ip(owner))
+    return owner
+
+
+def sphere_velocity(zeta, m, U, F):
+    """(U(t+h), U~) of Eq. EOMUsol and the consistency equation for
+    m dU/dt = -zeta U + F, zeta a symmetric 3x3 matrix."""
+    lib = _load()
+    z = np.ascontiguousarray(zeta, dtype=np.float64).reshape(9)
+    U = np.ascontiguousarray(U, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    un, ut = np.empty(3), np.empty(3)
+    lib.ora_sphere_velocity(_dp(z), float(m), _dp(U), _dp(F), _dp(un), _dp(ut))
+    return un, ut
+
+
+def step_spheres(p: Params, pops, owner, R, U, a, mass, *, fc=None, force=None, step=0):
+    """One LB step with solid spheres (moving link bounce-back, Sec. 4.1-4.2).
+    Returns (pops, owner, R, U, U~, status); the inputs are not modified.
+    mass: per sphere (<= 0 holds it fixed); fc: external forces [n][3]."""
+    lib = _load()
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    dst = np.empty_like(src)
+    own = np.array(owner, dtype=np.int32, order="C", copy=True)
+    R = np.array(R, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
+    U = np.array(U, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
+    n = R.shape[0]
+    m = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)))
+    f = None if fc is None else np.ascontiguousarray(fc, dtype=np.float64).reshape(-1, 3)
+    ff = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    ut = np.empty((max(n, 1), 3))
+    st = lib.ora_step_spheres(C.byref(p), _dp(src), _dp(dst), _dp(ff), int(step) & 0xffffffff, _ip(own), n,
+                              float(a), _dp(R), _dp(U), _dp(m), _dp(f), _dp(ut))
+    return dst, own, R, U, ut[:n], st
 
 
 def interpolate(p: Params, pops, pos, force=None, kernel=2):

@@ -1188,3 +1188,263 @@ int ora_couple_adjoint(const ora_params *P, const double *pops, const double *fo
     free(u); free(lam_u); free(rh); free(pt); free(pn); free(s1); free(s2);
     return status;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Extended particles: solid spheres with moving link bounce-back            */
+/* (Sec. 4.1, Eqs. MBB, NodeVel; Sec. 4.2, Eqs. EOMD-1..3, force, force0,    */
+/* zeta, EOMUsol and the consistency equation for the velocity U~)           */
+/*                                                                           */
+/* Readings (the paper leaves them open): spheres translate without          */
+/* rotating (Sec. 4.2 treats the linear velocity; Omega = 0, so u_b = U); a  */
+/* node is solid when its distance from the centre is below the radius a     */
+/* (minimum image, periodic box, no walls); rho in Eqs. MBB and zeta is      */
+/* rho0; the velocity update of Eq. EOMUsol is applied in the eigenbasis of  */
+/* the symmetric matrix zeta (the exact solution of m dU/dt = -zeta U + F);  */
+/* a node covered by a moving sphere gives its fluid momentum sum n c to the */
+/* sphere, a node it uncovers starts from n^eq(rho0, U) and the sphere loses */
+/* rho0 U, so total momentum is conserved; spheres must stay apart (a node   */
+/* never passes from one sphere to another).                                 */
+/* ------------------------------------------------------------------------ */
+
+static double periodic_offset(double d, int L) { return d - L * floor(d / L + 0.5); }
+
+static void sphere_map(const ora_params *P, int np, const double *R, double a, int *owner)
+{
+    for (int z = 0; z < P->nz; z++)
+        for (int y = 0; y < P->ny; y++)
+            for (int x = 0; x < P->nx; x++) {
+                int o = -1;
+                for (int p = 0; p < np && o < 0; p++) {
+                    double dx = periodic_offset(x - R[3 * p], P->nx);
+                    double dy = periodic_offset(y - R[3 * p + 1], P->ny);
+                    double dz = periodic_offset(z - R[3 * p + 2], P->nz);
+                    if (dx * dx + dy * dy + dz * dz < a * a) o = p;
+                }
+                owner[lin(P, x, y, z)] = o;
+            }
+}
+
+/* owner[s]: sphere p whose centre lies closer than a to node s, or -1. */
+void ora_sphere_owner(const ora_params *P, int np, const double *R, double a, int *owner)
+{
+    build_tables();
+    sphere_map(P, np, R, a, owner);
+}
+
+/* Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations:
+ * A = V diag(w) V^T, V's columns the eigenvectors. */
+static void jacobi3(const double Ain[3][3], double w[3], double V[3][3])
+{
+    double A[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            A[i][j] = Ain[i][j];
+            V[i][j] = (i == j) ? 1.0 : 0.0;
+        }
+    for (int sweep = 0; sweep < 50; sweep++) {
+        double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+        if (off == 0.0) break;
+        for (int p = 0; p < 2; p++)
+            for (int q = p + 1; q < 3; q++) {
+                if (A[p][q] == 0.0) continue;
+                double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; k++) {  /* A <- A J */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; k++) {  /* A <- J^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; k++) {  /* V <- V J */
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; i++) w[i] = A[i][i];
+}
+
+/* Eq. EOMUsol for m dU/dt = -zeta U + F over h = 1 with zeta, F constant,
+ * and the velocity U~ of the consistency equation, per eigen-direction of
+ * zeta (alpha = lambda / m): U' = e^-alpha U + (1 - e^-alpha) F / lambda,
+ * alpha U~ = (1 - e^-alpha) U + (alpha - (1 - e^-alpha)) F / lambda.  A
+ * direction without links (lambda = 0) takes the limits U' = U + F / m,
+ * U~ = U + F / (2 m). */
+void ora_sphere_velocity(const double zeta[9], double m, const double U[3], const double F[3], double Un[3],
+                         double Ut[3])
+{
+    double Z[3][3], w[3], V[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) Z[i][j] = zeta[3 * i + j];
+    jacobi3(Z, w, V);
+    double ue[3], fe[3];
+    for (int k = 0; k < 3; k++) {
+        ue[k] = V[0][k] * U[0] + V[1][k] * U[1] + V[2][k] * U[2];
+        fe[k] = V[0][k] * F[0] + V[1][k] * F[1] + V[2][k] * F[2];
+    }
+    double une[3], ute[3];
+    for (int k = 0; k < 3; k++) {
+        double al = w[k] / m;
+        if (al < 1e-12) {
+            une[k] = ue[k] + fe[k] / m;
+            ute[k] = ue[k] + 0.5 * fe[k] / m;
+        } else {
+            double e1 = -expm1(-al);  /* 1 - e^-alpha */
+            une[k] = (1.0 - e1) * ue[k] + e1 * fe[k] / w[k];
+            ute[k] = (e1 * ue[k] + (al - e1) * fe[k] / w[k]) / al;
+        }
+    }
+    for (int i = 0; i < 3; i++) {
+        Un[i] = V[i][0] * une[0] + V[i][1] * une[1] + V[i][2] * une[2];
+        Ut[i] = V[i][0] * ute[0] + V[i][1] * ute[1] + V[i][2] * ute[2];
+    }
+}
+
+/* One LB step with np spheres of radius a (h = 1, b = 1).  src: the
+ * post-collision state n*(t); owner: the solid map of the previous step (or
+ * of the initial placement), updated here; R, U: centres and velocities,
+ * updated; mass[p] <= 0 holds sphere p fixed (U, R unchanged, U~ = U); fc:
+ * external forces F^c [np][3] or NULL; Ut_out: U~ [np][3] or NULL.
+ *   1. R_half = R + U / 2                                  Eq. EOMD-1
+ *   2. solid map at R_half; covered nodes give sum n c to their sphere,
+ *      uncovered nodes get n^eq(rho0, U_p(t)) and the sphere loses rho0 U_p(t)
+ *   3. boundary links (fluid r, r + c_b solid of sphere p):
+ *      F0_p = sum 2 n*_b(r) c_b, zeta_p = (2 rho0 / c_s^2) sum a_b c_b c_b^T
+ *                                                          Eqs. force0, zeta
+ *   4. U(t+h) and U~ from F0 + F^c and zeta                Eq. EOMUsol
+ *   5. stream and collide the fluid nodes; a link whose source r - c_i is
+ *      solid (sphere p) returns n_i(r) = n*_{-i}(r) + 2 a_i rho0 U~_p.c_i / c_s^2
+ *                                                          Eq. MBB (c_b = -c_i)
+ *      solid nodes keep their values
+ *   6. R(t+h) = R_half + U(t+h) / 2                        Eq. EOMD-3
+ * Returns 0, -1 when a node passes from one sphere to another, -2 with walls. */
+int ora_step_spheres(const ora_params *P, const double *src, double *dst, const double *force, uint32_t step,
+                     int *owner, int np, double a, double *R, double *U, const double *mass, const double *fc,
+                     double *Ut_out)
+{
+    build_tables();
+    if (P->walls) return -2;  /* spheres live in periodic boxes */
+    size_t N = nodes_of(P);
+    const int L[3] = {P->nx, P->ny, P->nz};
+    double *cur = (double *)malloc(sizeof(double) * Q * N);
+    memcpy(cur, src, sizeof(double) * Q * N);
+    int *nown = (int *)malloc(sizeof(int) * N);
+    double *Rh = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
+    double *Ut = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
+    double *F0 = (double *)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
+    double *Z = (double *)calloc((size_t)9 * (np > 0 ? np : 1), sizeof(double));
+    int status = 0;
+
+    /* 1 */
+    for (int p = 0; p < np; p++)
+        for (int c = 0; c < 3; c++) {
+            double v = R[3 * p + c] + (mass[p] > 0.0 ? 0.5 * U[3 * p + c] : 0.0);
+            v -= L[c] * floor(v / L[c]);
+            Rh[3 * p + c] = v;
+        }
+    /* 2 (new fluid takes the velocity U(t); the exchanges are applied after) */
+    sphere_map(P, np, Rh, a, nown);
+    double *dP = (double *)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
+    for (size_t s = 0; s < N; s++) {
+        int o = owner[s], nn = nown[s];
+        if (o == nn) continue;
+        if (o >= 0 && nn >= 0) { status = -1; continue; }
+        if (nn >= 0) {  /* covered: its fluid momentum goes to the sphere */
+            for (int c = 0; c < 3; c++) {
+                double j = 0.0;
+                for (int i = 0; i < Q; i++) j += cur[(size_t)i * N + s] * g_c[i][c];
+                dP[3 * nn + c] += j;
+            }
+        } else {        /* uncovered: new fluid at the sphere's velocity */
+            double u[3] = {U[3 * o], U[3 * o + 1], U[3 * o + 2]}, ne[Q];
+            equilibrium(P->rho0, u, ne);
+            for (int i = 0; i < Q; i++) cur[(size_t)i * N + s] = ne[i];
+            for (int c = 0; c < 3; c++) dP[3 * o + c] -= P->rho0 * u[c];
+        }
+    }
+    for (int p = 0; p < np; p++)
+        if (mass[p] > 0.0)
+            for (int c = 0; c < 3; c++) U[3 * p + c] += dP[3 * p + c] / mass[p];
+    free(dP);
+    memcpy(owner, nown, sizeof(int) * N);
+    /* 3 */
+    for (int z = 0; z < P->nz; z++)
+        for (int y = 0; y < P->ny; y++)
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                if (owner[s] >= 0) continue;
+                for (int i = 1; i < Q; i++) {
+                    size_t t = lin(P, wrap(x + g_c[i][0], L[0]), wrap(y + g_c[i][1], L[1]),
+                                   wrap(z + g_c[i][2], L[2]));
+                    int p = owner[t];
+                    if (p < 0) continue;
+                    double nb = cur[(size_t)i * N + s];
+                    for (int c = 0; c < 3; c++) {
+                        F0[3 * p + c] += 2.0 * nb * g_c[i][c];
+                        for (int d = 0; d < 3; d++)
+                            Z[9 * p + 3 * c + d] += 2.0 * P->rho0 / CS2 * g_a[i] * g_c[i][c] * g_c[i][d];
+                    }
+                }
+            }
+    /* 4 */
+    for (int p = 0; p < np; p++) {
+        double Fp[3], Un[3];
+        for (int c = 0; c < 3; c++) Fp[c] = F0[3 * p + c] + (fc ? fc[3 * p + c] : 0.0);
+        if (mass[p] > 0.0) {
+            ora_sphere_velocity(Z + 9 * p, mass[p], U + 3 * p, Fp, Un, Ut + 3 * p);
+            for (int c = 0; c < 3; c++) U[3 * p + c] = Un[c];
+        } else {
+            for (int c = 0; c < 3; c++) Ut[3 * p + c] = U[3 * p + c];
+        }
+        if (Ut_out)
+            for (int c = 0; c < 3; c++) Ut_out[3 * p + c] = Ut[3 * p + c];
+    }
+    /* 5 */
+#pragma omp parallel for schedule(static)
+    for (int z = 0; z < P->nz; z++) {
+        for (int y = 0; y < P->ny; y++) {
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                if (owner[s] >= 0) {
+                    for (int i = 0; i < Q; i++) dst[(size_t)i * N + s] = cur[(size_t)i * N + s];
+                    continue;
+                }
+                double n[Q], ns[Q], f[3], g[16];
+                for (int i = 0; i < Q; i++) {
+                    size_t t = lin(P, wrap(x - g_c[i][0], L[0]), wrap(y - g_c[i][1], L[1]),
+                                   wrap(z - g_c[i][2], L[2]));
+                    int p = owner[t];
+                    if (p >= 0) {
+                        double uc = Ut[3 * p] * g_c[i][0] + Ut[3 * p + 1] * g_c[i][1] + Ut[3 * p + 2] * g_c[i][2];
+                        n[i] = cur[(size_t)g_opp[i] * N + s] + 2.0 * g_a[i] * P->rho0 * uc / CS2;
+                    } else {
+                        n[i] = cur[(size_t)i * N + t];
+                    }
+                }
+                node_force(P, force, s, f);
+                const double *r = NULL;
+                if (P->kT > 0.0) {
+                    ora_gaussians(P->seed, (uint32_t)s, step, 0u, P->replica, 4, g);
+                    r = g;
+                }
+                collide(P, n, f, r, ns);
+                for (int i = 0; i < Q; i++) dst[(size_t)i * N + s] = ns[i];
+            }
+        }
+    }
+    /* 6 */
+    for (int p = 0; p < np; p++)
+        for (int c = 0; c < 3; c++) {
+            double v = Rh[3 * p + c] + (mass[p] > 0.0 ? 0.5 * U[3 * p + c] : 0.0);
+            v -= L[c] * floor(v / L[c]);
+            R[3 * p + c] = v;
+        }
+    free(cur); free(nown); free(Rh); free(Ut); free(F0); free(Z);
+    return status;
+}
