@@ -405,6 +405,7 @@ def _forms(peak):
                 central 16^3 after 500 steps, checkpoints every 50: forward +
                 reverse ms per step vs 500 plain FP32 steps;
       interpolation  the headline coupled workload with phi_3 and phi_4;
+      spheres   256^3 with 512 moving solid spheres (moving bounce-back);
       precision 512^3 between walls, g = 1e-6, kT = 1e-4: ms per LB step with
                 FP16 / BF16 storage vs FP32 storage (no particles)."""
     import numpy as np
@@ -475,6 +476,9 @@ def _forms(peak):
 
     # wider interpolation stencils on the headline workload
     out["interpolation"] = _interpolation_forms(stream)
+
+    # extended particles: moving solid spheres
+    out["spheres"] = _sphere_form(stream, peak)
 
     # reduced-precision storage
     shape = (512, 512, 512)
@@ -553,6 +557,58 @@ def _interpolation_forms(stream, steps=100):
     lat.close()
     torch.cuda.empty_cache()
     return res
+
+
+def _sphere_form(stream, peak, steps=200):
+    """256^3 periodic box, kT = 1e-4, 512 solid spheres of radius 4 (volume
+    fraction 0.8 %, neutrally buoyant: m = 4/3 pi a^3 rho0) moving with
+    thermal-scale velocities: ms per lb_step_spheres (moving bounce-back,
+    sphere update, solid-map motion) against a plain lb_step of the same box;
+    algorithmic bytes 152 per node plus the 4-byte solid map."""
+    import math
+    import numpy as np
+    import torch
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    shape, n, rad = (256, 256, 256), 512, 4.0
+    nodes = shape[0] * shape[1] * shape[2]
+    lat = L.Lattice(shape, kT=KT, seed=5, stream=stream)
+    m0 = 4.0 / 3.0 * math.pi * rad ** 3
+    pos = torch.as_tensor(inputs.sphere_centres(n, shape, rad, seed=5)).cuda()
+    vel = torch.as_tensor(np.random.default_rng(6).normal(0.0, 0.01, (n, 3))).cuda()
+    sph = L.spheres(n, pos, vel, rad, mass0=m0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        lat.step(3)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        lat.step(steps)
+        b.record(stream)
+    torch.cuda.synchronize()
+    plain = a.elapsed_time(b) / steps
+    with torch.cuda.stream(stream):
+        L.lb_spheres_place(lat.h, sph)
+        for _ in range(5):
+            L.lb_step_spheres(lat.h, sph)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        for _ in range(steps):
+            L.lb_step_spheres(lat.h, sph)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    st, bits = lat.sync()
+    assert bits == 0, "device error word 0x%x (spheres)" % bits
+    lat.close()
+    torch.cuda.empty_cache()
+    return {"shape": list(shape), "spheres": n, "radius": rad, "steps": steps, "ms_per_step": ms,
+            "mlups": nodes / (ms * 1e-3) / 1e6, "hbm_frac": 156 * nodes / (ms * 1e-3) / 1e9 / peak,
+            "plain_ms_per_step": plain, "ratio": ms / plain}
 
 
 def _profiled_traffic(mode):

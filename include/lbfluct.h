@@ -67,6 +67,8 @@ typedef enum { LB_F32 = 0, LB_F16 = 1, LB_BF16 = 2 } lb_dtype;
 #define LB_DERR_BARRIER       0x8u   /* batched kernel: grid barrier timed out  */
 #define LB_DERR_PARTICLE_RANGE 0x10u /* a particle position outside the box or not
                                         finite (its stencil was clamped)         */
+#define LB_DERR_SPHERE        0x20u  /* spheres: a node claimed by two spheres, or
+                                        a sphere moved more than one node a step */
 
 #define LB_NSUMS 38  /* lb_moments sums: [0..18] sum_r dm_k, [19..37] sum_r dm_k^2 */
 
@@ -301,6 +303,54 @@ lb_status lb_get_timing(lb_handle *h, double *ms_step, int *n_step, double *ms_c
 /* Copy the impulses the next lb_step will apply (device FP32 [3][N] out;
  * zeros when none are pending). */
 lb_status lb_get_particle_forces(lb_handle *h, float *out);
+
+/* ---- extended particles: solid spheres with moving bounce-back ------------- */
+
+/* Spheres of one radius that translate without rotating (Sec. 4.2 treats the
+ * linear velocity).  All pointers are device memory owned by the caller. */
+typedef struct {
+    int n;                /* number of spheres (>= 0)                                */
+    int reserved;         /* must be 0                                               */
+    double radius;        /* a: a node closer than a to a centre is solid            */
+    double *pos;          /* [n][3] centres R in [0, L), updated in place            */
+    double *vel;          /* [n][3] velocities U, updated in place                   */
+    const double *mass;   /* [n] or NULL (mass0); a mass <= 0 holds a sphere fixed:  */
+                          /* R and U stay, its surface moves with U                   */
+    double mass0;
+    const double *force;  /* [n][3] external forces F^c, or NULL                     */
+} lb_spheres;
+
+/* Build the solid map of the spheres at their current centres (no exchange
+ * with the fluid): call once before the first lb_step_spheres, and again
+ * whenever the set of spheres changes.  Requires a periodic box (no walls)
+ * and FP32 storage (LB_EUNSUPPORTED otherwise); spheres must not overlap
+ * (LB_DERR_SPHERE).  The populations of solid nodes are ignored.  Errors:
+ * LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s);
+
+/* One LB step with the spheres (h = 1; Sec. 4.1 Eq. (MBB), Sec. 4.2):
+ *  1. R(t+h/2) = R + U/2 (Eq. EOMD-1); the solid map moves with the
+ *     centres: a covered fluid node gives its momentum sum n c to its
+ *     sphere, an uncovered node starts from n^eq(rho0, U(t)) and the sphere
+ *     loses rho0 U(t);
+ *  2. over the boundary links b (fluid node r, r + c_b solid):
+ *     F0 = sum 2 n*_b c_b, zeta = (2 rho0 / c_s^2) sum a_b c_b c_b^T
+ *     (Eqs. force0, zeta);
+ *  3. U(t+h) = e^-A U + zeta^-1 (1 - e^-A)(F0 + F^c), A = zeta / m
+ *     (Eq. EOMUsol in zeta's eigenbasis), and U~ of the consistency
+ *     equation, so that m (U(t+h) - U(t)) = F0 + F^c - zeta U~;
+ *  4. stream and collide the fluid nodes; a population whose source node is
+ *     solid returns as n_i(r) = n*_-i(r) + 2 a_i rho0 U~.c_i / c_s^2 (Eq. MBB);
+ *  5. R(t+h) = R(t+h/2) + U(t+h)/2 (Eq. EOMD-3).
+ * Total momentum of fluid and spheres is conserved (plus the external
+ * forces).  Sphere velocities must stay below one node per step.  Point
+ * particles are not coupled in the same step (LB_EUNSUPPORTED while
+ * impulses are pending).  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ECUDA;
+ * LB_DERR_SPHERE on the device. */
+lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s);
+
+/* Copy the solid map (device int [N] out: sphere index or -1 for fluid). */
+lb_status lb_get_solid_map(lb_handle *h, int *owner_out);
 
 /* ---- reverse mode (deterministic runs, kT = 0) ------------------------------- */
 

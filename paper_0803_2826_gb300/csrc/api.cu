@@ -316,6 +316,7 @@ lb_status lb_create(const lb_params *p, void *pops_a, void *pops_b, float *force
     h->force = force;
     h->stream = (cudaStream_t)stream;
     h->step = 0;
+    h->sph_n = -1;
     h->red_blocks = 4 * device_sm_count();
     cudaError_t e = cudaMalloc((void **)&h->d_err, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMalloc((void **)&h->d_partials, sizeof(double) * LB_NSUMS * h->red_blocks);
@@ -390,6 +391,7 @@ lb_status lb_destroy(lb_handle *h)
     if (h->aux) cudaStreamSynchronize(h->aux);
     join_overlap(h);
     destroy_particles(h);
+    destroy_spheres(h);
     if (h->claim) cudaFree(h->claim);
     if (h->lam_u) cudaFree(h->lam_u);
     if (h->sc_partials) cudaFree(h->sc_partials);

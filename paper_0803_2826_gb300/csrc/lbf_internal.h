@@ -77,6 +77,14 @@ struct lb_handle {
     int timer_cap;
     int timer_n[2];
     cudaEvent_t *timer_ev[2];  // [2 * timer_cap] each
+    // solid spheres (lb_spheres_place / lb_step_spheres)
+    int *sph_owner;       // [n_nodes] sphere index or -1
+    float *sph_acc;       // [sph_cap][12]: F0 (3), covering momentum (3), zeta (6)
+    double *sph_rh;       // [sph_cap][3] half-step centres
+    float4 *sph_ut;       // [sph_cap] U~
+    int sph_cap;
+    int sph_n;            // spheres of the current solid map (-1: none placed)
+    double sph_a;
 };
 
 namespace lbi {
@@ -114,5 +122,7 @@ lb_status couple_adjoint(lb_handle *h, const void *state, const lb_particles *pp
 lb_status couple_on(lb_handle *h, const void *state, const lb_particles *pp, const lb_couple_params *cp,
                     float *facc_out);
 void destroy_particles(lb_handle *h);
+// spheres.cu
+void destroy_spheres(lb_handle *h);
 
 }  // namespace lbi

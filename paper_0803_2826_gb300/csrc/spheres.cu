@@ -1,0 +1,630 @@
+// spheres.cu -- extended particles: solid spheres that translate through the
+// lattice, coupled to the fluid by the moving link bounce-back of Sec. 4.1
+// (Eq. MBB) and updated as in Sec. 4.2 (Eqs. EOMD-1..3, force0, zeta,
+// EOMUsol and the consistency equation for the velocity U~).
+//
+// One lb_step_spheres call, all on the handle's stream:
+//   k_sph_half     one thread per sphere: R(t+h/2) = R + U/2, accumulators zeroed
+//   k_sph_map      per sphere, the nodes of a box around it: the solid map
+//                  follows R(t+h/2); a covered fluid node gives its momentum
+//                  to the sphere, an uncovered node starts from n^eq(rho0, U)
+//                  and the sphere loses rho0 U
+//   k_sph_links    per sphere, the fluid nodes of its box: F0 = sum 2 n*_b c_b
+//                  and zeta = 6 rho0 sum a_b c_b c_b^T over the boundary links
+//   k_sph_update   one thread per sphere: U(t+h) and U~ (zeta's eigenbasis
+//                  by FP32 Jacobi rotations; U kept in FP64)
+//   the plain stream-collide launch over every node (exact for fluid nodes
+//                  without a solid neighbour), then
+//   k_sph_near_nodes  per sphere, the near fluid nodes of its box again: pull
+//                  streaming in which a population whose source node is solid
+//                  returns as n*_-i(r) + 6 a_i rho0 U~.c_i, then the same
+//                  collision
+//   k_sph_finish   one thread per sphere: R(t+h) = R(t+h/2) + U(t+h)/2
+// The solid map holds the sphere index of a solid node, -2 for a fluid node
+// with a solid neighbour (the only nodes whose pull needs the map) and -1
+// for the other fluid nodes; k_sph_links sets the marks within a + 2.5 of
+// each centre every step (a -2 left further out by a moved sphere is
+// harmless: that node is recomputed with the same result).
+// Spheres translate without rotating (u_b = U), rho in Eqs. MBB and zeta is
+// rho0, and spheres must stay apart; positions and velocities are FP64 (a
+// few values per sphere), the populations FP32 deviations n - a rho0 (the
+// rho0 part of F0 sums to zero over a closed set of links and is left out).
+#include <cmath>
+
+#include "stream_collide.cuh"
+
+namespace lbi {
+
+extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const void *, void *, const float *,
+                                                        float *);
+
+namespace {
+
+constexpr int kSphThreads = 128;
+constexpr int kAcc = 12;  // per sphere: F0 (3), covering momentum (3), zeta xx yy zz xy yz zx
+
+// d - L floor(d / L + 1/2) for d = x - c in (-L, L): the minimum image by
+// comparisons (the same value wherever |d| < L / 2 - 1, which covers every
+// node a sphere of 2 a + 6 <= L can reach).
+__device__ __forceinline__ double periodic_offset(double d, int L)
+{
+    const double h = 0.5 * (double)L;
+    return d >= h ? __dadd_rn(d, -(double)L) : (d < -h ? __dadd_rn(d, (double)L) : d);
+}
+
+__device__ __forceinline__ double wrap_pos(double v, int L) { return __dadd_rn(v, -(double)L * floor(v / (double)L)); }
+
+// v in (-L, 2L): one add or subtract (box offsets are below L).
+__device__ __forceinline__ int wrap_i(int v, int L) { return v < 0 ? v + L : (v >= L ? v - L : v); }
+
+constexpr int kFar = -1, kNear = -2;  // fluid nodes without / with a solid neighbour
+
+// The box of B^3 nodes around a sphere starts at base = floor(c - a) - 2
+// per axis; cf = c - base (FP32, in [2, 3)) places the centre in it.  One
+// block works on one sphere: its first threads fill these in shared memory.
+struct Box {
+    int base[3];
+    float cf[3];
+};
+
+__device__ __forceinline__ void box_setup(Box &b, const double c[3], double a)
+{
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        const int base = (int)floor(c[d] - a) - 2;
+        b.base[d] = base;
+        b.cf[d] = (float)(c[d] - (double)base);
+    }
+    __syncthreads();
+}
+
+// Node k of the box: lattice coordinates and offsets within the box.
+__device__ __forceinline__ void box_node(const Box &b, int B, int k, const StepArgs &g, int &x, int &y, int &z,
+                                         int o[3])
+{
+    o[0] = k % B;
+    o[1] = (k / B) % B;
+    o[2] = k / (B * B);
+    x = wrap_i(b.base[0] + o[0], g.nx);
+    y = wrap_i(b.base[1] + o[1], g.ny);
+    z = wrap_i(b.base[2] + o[2], g.nz);
+}
+
+// |r - c| < a with the minimum image, the arithmetic of the definition
+// written without contractions.
+__device__ __forceinline__ bool inside(int x, int y, int z, const double c[3], double a, const StepArgs &g)
+{
+    const double dx = periodic_offset(__dadd_rn((double)x, -c[0]), g.nx);
+    const double dy = periodic_offset(__dadd_rn((double)y, -c[1]), g.ny);
+    const double dz = periodic_offset(__dadd_rn((double)z, -c[2]), g.nz);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    return d2 < __dmul_rn(a, a);
+}
+
+// inside() decided in FP32 where the squared distance is clearly away from
+// a^2 (the FP32 error is below 1e-5 a^2 for boxes of this size), in FP64
+// otherwise: the same decisions as inside(), mostly without FP64 arithmetic.
+__device__ __forceinline__ bool inside_fast(const Box &b, const int o[3], int x, int y, int z, const double c[3],
+                                            double a, const StepArgs &g)
+{
+    const float dx = (float)o[0] - b.cf[0], dy = (float)o[1] - b.cf[1], dz = (float)o[2] - b.cf[2];
+    const float d2 = dx * dx + dy * dy + dz * dz, a2 = (float)(a * a);
+    if (d2 < a2 * (1.0f - 1e-4f)) return true;
+    if (d2 > a2 * (1.0f + 1e-4f)) return false;
+    return inside(x, y, z, c, a, g);
+}
+
+__global__ void k_sph_place(int *owner, const double *pos, double a, int B, int n, StepArgs g, unsigned int *err)
+{
+    __shared__ Box b;
+    const int p = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const double c[3] = {pos[3 * p], pos[3 * p + 1], pos[3 * p + 2]};
+    box_setup(b, c, a);
+    if (p >= n || k >= B * B * B) return;
+    int x, y, z, o[3];
+    box_node(b, B, k, g, x, y, z, o);
+    if (!inside_fast(b, o, x, y, z, c, a, g)) return;
+    const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+    if (atomicCAS(owner + s, -1, p) != -1) atomicOr(err, LB_DERR_SPHERE);
+}
+
+__global__ void k_sph_half(const double *pos, const double *vel, const double *mass, double mass0, int n, double *rh,
+                           float *acc, StepArgs g, unsigned int *err)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double m = mass ? mass[p] : mass0;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    for (int d = 0; d < 3; ++d) {
+        const double u = vel[3 * p + d];
+        if (!(fabs(u) <= 1.0)) atomicOr(err, LB_DERR_SPHERE);  // also catches NaN
+        rh[3 * p + d] = m > 0.0 ? wrap_pos(__dadd_rn(pos[3 * p + d], 0.5 * u), L[d]) : pos[3 * p + d];
+    }
+    for (int q = 0; q < kAcc; ++q) acc[kAcc * p + q] = 0.0f;
+}
+
+// The solid map follows the half-step centres (uncovered nodes get the
+// equilibrium of the sphere's velocity at time t, which this kernel reads
+// before any update of it).
+__global__ void k_sph_map(int *owner, float *pops, const double *rh, const double *vel, double a, int B, int n,
+                          StepArgs g, float *acc, unsigned int *err)
+{
+    __shared__ Box b;
+    const int p = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
+    box_setup(b, c, a);
+    if (p >= n || k >= B * B * B) return;
+    int x, y, z, o[3];
+    box_node(b, B, k, g, x, y, z, o);
+    const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+    const size_t P = g.pitch;
+    const int old = owner[s];
+    if (inside_fast(b, o, x, y, z, c, a, g)) {
+        if (old == p) return;
+        if (old >= 0) {  // a node passing from one sphere to another
+            atomicOr(err, LB_DERR_SPHERE);
+            return;
+        }
+        float j[3] = {0.f, 0.f, 0.f};  // covered: its fluid momentum goes to the sphere
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const float v = pops[(size_t)i * P + s];
+            if (lbd::cx(i)) j[0] += lbd::cx(i) * v;
+            if (lbd::cy(i)) j[1] += lbd::cy(i) * v;
+            if (lbd::cz(i)) j[2] += lbd::cz(i) * v;
+        }
+        owner[s] = p;
+        for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 3 + d, j[d]);
+    } else if (old == p) {  // uncovered: new fluid at the sphere's velocity
+        owner[s] = kNear;
+        const float u[3] = {(float)vel[3 * p], (float)vel[3 * p + 1], (float)vel[3 * p + 2]};
+        const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const float cu = lbd::cx(i) * u[0] + lbd::cy(i) * u[1] + lbd::cz(i) * u[2];
+            pops[(size_t)i * P + s] = lbd::weight(i) * g.rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * u2);
+        }
+        for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 3 + d, -g.rho0 * u[d]);
+    }
+}
+
+// F0 and zeta of each sphere over its boundary links (fluid node r, r + c_b
+// solid); a block reduces its sums before one atomic per component.  The
+// fluid nodes of the box are marked near (a solid neighbour of any sphere)
+// or far on the way.
+__global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const float *pops, const double *rh,
+                                                            double a, int B, int n, StepArgs g, float *acc)
+{
+    __shared__ float red[kSphThreads / 32][9];
+    __shared__ Box b;
+    const int p = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
+    box_setup(b, c, a);
+    if (p < n && k < B * B * B) {
+        int x, y, z, o[3];
+        box_node(b, B, k, g, x, y, z, o);
+        const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+        const int own = owner[s];
+        const float dx = (float)o[0] - b.cf[0], dy = (float)o[1] - b.cf[1], dz = (float)o[2] - b.cf[2];
+        const float rf = (float)a + 2.5f;
+        if (own < 0 && dx * dx + dy * dy + dz * dz > rf * rf) {
+            // no node of this sphere within two lattice units: no links; the
+            // mark stays (another sphere may be near, and a stale near mark
+            // only costs the exact recomputation of a far node)
+        } else if (own < 0) {
+            bool near = false;
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const int tx = wrap_i(x + lbd::cx(i), g.nx), ty = wrap_i(y + lbd::cy(i), g.ny),
+                          tz = wrap_i(z + lbd::cz(i), g.nz);
+                const int o = owner[((size_t)tz * g.ny + ty) * g.nx + tx];
+                near = near || o >= 0;
+                if (o != p) continue;
+                const float nb = 2.0f * pops[(size_t)i * g.pitch + s];
+                const float cx = (float)lbd::cx(i), cy = (float)lbd::cy(i), cz = (float)lbd::cz(i);
+                const float za = 6.0f * g.rho0 * lbd::weight(i);
+                v[0] += nb * cx;
+                v[1] += nb * cy;
+                v[2] += nb * cz;
+                v[3] += za * cx * cx;
+                v[4] += za * cy * cy;
+                v[5] += za * cz * cz;
+                v[6] += za * cx * cy;
+                v[7] += za * cy * cz;
+                v[8] += za * cz * cx;
+            }
+            const int mark = near ? kNear : kFar;
+            if (own != mark) owner[s] = mark;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+        for (int q = 0; q < 9; ++q) red[w][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < 9 && p < n) {
+        float t = 0.0f;
+        for (int q = 0; q < kSphThreads / 32; ++q) t += red[q][threadIdx.x];
+        if (t != 0.0f) {
+            const int slot = threadIdx.x < 3 ? threadIdx.x : threadIdx.x + 3;  // F0 -> 0..2, zeta -> 6..11
+            atomicAdd(acc + kAcc * p + slot, t);
+        }
+    }
+}
+
+// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// (FP32), until the off-diagonal part is below 1e-7 of the diagonal.
+__device__ void jacobi3(float A[3][3], float w[3], float V[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0f : 0.0f;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
+        const float dia = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
+        if (!(off > 1e-7f * dia)) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (A[p][q] == 0.0f) continue;
+                const float th = (A[q][q] - A[p][p]) / (2.0f * A[p][q]);
+                const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
+                const float c = rsqrtf(t * t + 1.0f), s = t * c;
+                for (int k = 0; k < 3; ++k) {
+                    const float akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const float apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const float vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < 3; ++i) w[i] = A[i][i];
+}
+
+// U(t+h) and U~ per eigen-direction of zeta (alpha = lambda / m), written as
+// increments of U so that FP32 carries only the change:
+//   U' - U = (1 - e^-alpha) (F / lambda - U)                   (Eq. EOMUsol)
+//   U~ - U = ((1 - e^-alpha) / alpha - 1) U + (1 - (1 - e^-alpha) / alpha) F / lambda
+// (the consistency equation); a direction without links takes the limits
+// F / m and F / (2 m).  U stays FP64.
+__global__ void k_sph_update(double *vel, const double *mass, double mass0, const double *force, int n,
+                             const float *acc, float4 *ut)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double m = mass ? mass[p] : mass0;
+    const float *ac = acc + kAcc * p;
+    double U[3] = {vel[3 * p], vel[3 * p + 1], vel[3 * p + 2]};
+    if (!(m > 0.0)) {  // held fixed: the surface moves with U
+        ut[p] = make_float4((float)U[0], (float)U[1], (float)U[2], 0.0f);
+        return;
+    }
+    float F[3], Uf[3];
+    for (int d = 0; d < 3; ++d) {
+        U[d] += (double)ac[3 + d] / m;  // fluid momentum of covered / uncovered nodes
+        F[d] = ac[d] + (force ? (float)force[3 * p + d] : 0.0f);
+        Uf[d] = (float)U[d];
+    }
+    float Z[3][3] = {{ac[6], ac[9], ac[11]}, {ac[9], ac[7], ac[10]}, {ac[11], ac[10], ac[8]}};
+    float w[3], V[3][3];
+    jacobi3(Z, w, V);
+    const float mf = (float)m;
+    float dne[3], dte[3];
+    for (int k = 0; k < 3; ++k) {
+        const float ue = V[0][k] * Uf[0] + V[1][k] * Uf[1] + V[2][k] * Uf[2];
+        const float fe = V[0][k] * F[0] + V[1][k] * F[1] + V[2][k] * F[2];
+        const float al = w[k] / mf;
+        if (al < 1e-6f) {
+            dne[k] = fe / mf;
+            dte[k] = 0.5f * fe / mf;
+        } else {
+            const float e1 = -expm1f(-al), r = e1 / al;
+            dne[k] = e1 * (fe / w[k] - ue);
+            dte[k] = (r - 1.0f) * ue + (1.0f - r) * fe / w[k];
+        }
+    }
+    float Ut[3];
+    for (int i = 0; i < 3; ++i) {
+        vel[3 * p + i] = U[i] + (double)(V[i][0] * dne[0] + V[i][1] * dne[1] + V[i][2] * dne[2]);
+        Ut[i] = Uf[i] + (V[i][0] * dte[0] + V[i][1] * dte[1] + V[i][2] * dte[2]);
+    }
+    ut[p] = make_float4(Ut[0], Ut[1], Ut[2], 0.0f);
+}
+
+__global__ void k_sph_finish(double *pos, const double *vel, const double *mass, double mass0, const double *rh,
+                             int n, StepArgs g)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double m = mass ? mass[p] : mass0;
+    if (!(m > 0.0)) return;
+    const int L[3] = {g.nx, g.ny, g.nz};
+    for (int d = 0; d < 3; ++d) pos[3 * p + d] = wrap_pos(__dadd_rn(rh[3 * p + d], 0.5 * vel[3 * p + d]), L[d]);
+}
+
+// Stream and collide fluid node (x, y, z) whose map entry is own (< 0): a
+// population whose source node is solid (sphere o) returns from the node
+// itself with the moving-wall term, n_i(r) = n*_-i(r) + 2 a_i rho0
+// U~_o.c_i / c_s^2 (Eq. MBB, c_b = -c_i); far fluid nodes pull without
+// looking at the map.
+template <bool NOISE>
+__device__ __forceinline__ void sphere_node(const float *__restrict__ src, float *__restrict__ dst,
+                                            const float *__restrict__ ffield, const int *__restrict__ owner,
+                                            const float4 *__restrict__ ut, const StepArgs &a, int x, int y, int z,
+                                            int own)
+{
+    const size_t self = ((size_t)z * a.ny + y) * a.nx + x;
+    const int xm = (x == 0) ? a.nx - 1 : x - 1, xp = (x == a.nx - 1) ? 0 : x + 1;
+    const int ym = (y == 0) ? a.ny - 1 : y - 1, yp = (y == a.ny - 1) ? 0 : y + 1;
+    const int zm = (z == 0) ? a.nz - 1 : z - 1, zp = (z == a.nz - 1) ? 0 : z + 1;
+    const size_t P = a.pitch;
+    float n[19];
+    if (own == kFar) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const int sx = lbd::cx(i) == 1 ? xm : (lbd::cx(i) == -1 ? xp : x);
+            const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+            const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+            n[i] = __ldg(src + (size_t)i * P + ((size_t)sz * a.ny + sy) * a.nx + sx);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            const int sx = lbd::cx(i) == 1 ? xm : (lbd::cx(i) == -1 ? xp : x);
+            const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+            const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+            const size_t t = ((size_t)sz * a.ny + sy) * a.nx + sx;
+            const int o = i == 0 ? kFar : __ldg(owner + t);
+            if (o >= 0) {
+                const float4 v = __ldg(ut + o);
+                const float uc = lbd::cx(i) * v.x + lbd::cy(i) * v.y + lbd::cz(i) * v.z;
+                n[i] = __ldg(src + (size_t)lbd::opposite(i) * P + self) + 6.0f * lbd::weight(i) * a.rho0 * uc;
+            } else {
+                n[i] = __ldg(src + (size_t)i * P + t);
+            }
+        }
+    }
+    float fx = a.fx, fy = a.fy, fz = a.fz;
+    if (ffield) {
+        fx += __ldg(ffield + self);
+        fy += __ldg(ffield + a.nn + self);
+        fz += __ldg(ffield + 2 * a.nn + self);
+    }
+    float m[19], out[19];
+    lbd::forward(n, m);
+    collide_moments<NOISE>(m, fx, fy, fz, a, a.rk, (uint32_t)self, a.replica, out);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = out[i];
+}
+
+// The near fluid nodes of each sphere's box, after the plain update of all
+// nodes: every fluid node without a solid neighbour is exact from that
+// update (solid nodes hold values nobody reads), the near ones are done
+// again here with the moving bounce-back.  A node near two spheres is
+// written twice with the same value.
+template <bool NOISE>
+__global__ void __launch_bounds__(kSphThreads) k_sph_near_nodes(const float *__restrict__ src, float *__restrict__ dst,
+                                                                 const float *__restrict__ ffield,
+                                                                 const int *__restrict__ owner,
+                                                                 const float4 *__restrict__ ut, const double *rh,
+                                                                 double a, int B, int n, StepArgs g)
+{
+    __shared__ Box b;
+    const int p = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
+    box_setup(b, c, a);
+    if (p >= n || k >= B * B * B) return;
+    int x, y, z, o[3];
+    box_node(b, B, k, g, x, y, z, o);
+    if (__ldg(owner + ((size_t)z * g.ny + y) * g.nx + x) != kNear) return;
+    sphere_node<NOISE>(src, dst, ffield, owner, ut, g, x, y, z, kNear);
+}
+
+int box_edge(double a) { return (int)std::ceil(2.0 * a) + 6; }
+
+// The map as the caller sees it: sphere index or -1.
+__global__ void k_sph_export(const int *owner, int *out, size_t nn)
+{
+    for (size_t s = blockIdx.x * (size_t)blockDim.x + threadIdx.x; s < nn; s += (size_t)gridDim.x * blockDim.x)
+        out[s] = owner[s] >= 0 ? owner[s] : -1;
+}
+
+bool check_spheres(const lb_handle *h, const lb_spheres *s, const char *who)
+{
+    if (!s || s->n < 0 || s->n > 65535 || s->reserved != 0) {
+        set_error("%s: need 0 <= n <= 65535 spheres and reserved = 0", who);
+        return false;
+    }
+    if (s->n > 0 && (!s->pos || !s->vel || ((uintptr_t)s->pos & 7u) || ((uintptr_t)s->vel & 7u))) {
+        set_error("%s: pos and vel must be 8-byte aligned device arrays", who);
+        return false;
+    }
+    const int lmin = std::min(h->p.nx, std::min(h->p.ny, h->p.nz));
+    if (!(s->radius > 0.0) || box_edge(s->radius) > lmin) {
+        set_error("%s: need 0 < radius and 2 radius + 6 <= the shortest box edge (%d)", who, lmin);
+        return false;
+    }
+    return true;
+}
+
+lb_status spheres_supported(const lb_handle *h, const char *who)
+{
+    if (h->p.walls || h->p.dtype != LB_F32) {
+        set_error("%s: spheres need a periodic box with FP32 storage", who);
+        return LB_EUNSUPPORTED;
+    }
+    return LB_OK;
+}
+
+lb_status ensure_sphere_buffers(lb_handle *h, int n)
+{
+    cudaError_t e = cudaSuccess;
+    if (!h->sph_owner) e = cudaMalloc((void **)&h->sph_owner, h->n_nodes * sizeof(int));
+    if (e == cudaSuccess && h->sph_cap < n) {
+        cudaFree(h->sph_acc);
+        cudaFree(h->sph_rh);
+        cudaFree(h->sph_ut);
+        h->sph_acc = nullptr;
+        h->sph_rh = nullptr;
+        h->sph_ut = nullptr;
+        h->sph_cap = 0;
+        e = cudaMalloc((void **)&h->sph_acc, (size_t)n * kAcc * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->sph_rh, (size_t)n * 3 * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->sph_ut, (size_t)n * sizeof(float4));
+        if (e == cudaSuccess) h->sph_cap = n;
+    }
+    if (e != cudaSuccess) {
+        set_error("spheres: device allocation failed (%s)", cudaGetErrorString(e));
+        return LB_ENOMEM;
+    }
+    return LB_OK;
+}
+
+}  // namespace
+
+void destroy_spheres(lb_handle *h)
+{
+    cudaFree(h->sph_owner);
+    cudaFree(h->sph_acc);
+    cudaFree(h->sph_rh);
+    cudaFree(h->sph_ut);
+    h->sph_owner = nullptr;
+    h->sph_acc = nullptr;
+    h->sph_rh = nullptr;
+    h->sph_ut = nullptr;
+    h->sph_cap = 0;
+    h->sph_n = -1;
+}
+
+}  // namespace lbi
+
+using namespace lbi;
+
+extern "C" {
+
+lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s)
+{
+    if (!h || !check_spheres(h, s, "lb_spheres_place")) return LB_EINVAL;
+    lb_status st = spheres_supported(h, "lb_spheres_place");
+    if (st != LB_OK) return st;
+    join_overlap(h);
+    st = ensure_sphere_buffers(h, std::max(s->n, 1));
+    if (st != LB_OK) return st;
+    const StepArgs g = make_args(h);
+    cudaError_t e = cudaMemsetAsync(h->sph_owner, 0xff, h->n_nodes * sizeof(int), h->stream);  // all fluid
+    if (e == cudaSuccess && s->n > 0) {
+        const int B = box_edge(s->radius);
+        const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)s->n);
+        k_sph_place<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, s->pos, s->radius, B, s->n, g, h->d_err);
+        // near / far marks around the placed spheres (the sums go to scratch)
+        e = cudaMemcpyAsync(h->sph_rh, s->pos, (size_t)s->n * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                            h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->sph_acc, 0, (size_t)s->n * kAcc * sizeof(float), h->stream);
+        if (e == cudaSuccess)
+            k_sph_links<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, static_cast<const float *>(h->pops[h->cur]),
+                                                             h->sph_rh, s->radius, B, s->n, g, h->sph_acc);
+        h->launches += 2;
+        if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail("lb_spheres_place", e);
+    h->sph_n = s->n;
+    h->sph_a = s->radius;
+    return LB_OK;
+}
+
+lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
+{
+    if (!h || !check_spheres(h, s, "lb_step_spheres")) return LB_EINVAL;
+    lb_status st = spheres_supported(h, "lb_step_spheres");
+    if (st != LB_OK) return st;
+    if (h->sph_n != s->n || h->sph_a != s->radius) {
+        set_error("lb_step_spheres: the spheres differ from the placed ones (call lb_spheres_place)");
+        return LB_EINVAL;
+    }
+    join_overlap(h);
+    if (h->facc_dirty) {
+        set_error("lb_step_spheres: point-particle impulses are pending; spheres and point particles are not "
+                  "coupled in one step");
+        return LB_EUNSUPPORTED;
+    }
+    const StepArgs g = make_args(h);
+    float *src = static_cast<float *>(h->pops[h->cur]);
+    float *dst = static_cast<float *>(h->pops[1 - h->cur]);
+    const int n = s->n;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        const int B = box_edge(s->radius);
+        const unsigned pb = (unsigned)((n + kSphThreads - 1) / kSphThreads);
+        const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
+        k_sph_half<<<pb, kSphThreads, 0, h->stream>>>(s->pos, s->vel, s->mass, s->mass0, n, h->sph_rh, h->sph_acc, g,
+                                                      h->d_err);
+        k_sph_map<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->vel, s->radius, B, n, g,
+                                                       h->sph_acc, h->d_err);
+        k_sph_links<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g, h->sph_acc);
+        k_sph_update<<<pb, kSphThreads, 0, h->stream>>>(s->vel, s->mass, s->mass0, s->force, n, h->sph_acc, h->sph_ut);
+        h->launches += 4;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {  // every node with the plain update (solid nodes get values nobody reads)
+        e = launch_stream_collide_dt<0>(h, src, dst, nullptr, nullptr);
+        h->launches += 1;
+    }
+    if (e == cudaSuccess && n > 0) {  // then the near fluid nodes with the moving bounce-back
+        const int B = box_edge(s->radius);
+        const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
+        if (g.kT > 0.0f)
+            k_sph_near_nodes<true><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
+                                                                        h->sph_rh, s->radius, B, n, g);
+        else
+            k_sph_near_nodes<false><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
+                                                                         h->sph_rh, s->radius, B, n, g);
+        h->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && n > 0) {
+        k_sph_finish<<<(unsigned)((n + kSphThreads - 1) / kSphThreads), kSphThreads, 0, h->stream>>>(
+            s->pos, s->vel, s->mass, s->mass0, h->sph_rh, n, g);
+        h->launches += 1;
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail("lb_step_spheres", e);
+    h->cur = 1 - h->cur;
+    h->step += 1;
+    return LB_OK;
+}
+
+lb_status lb_get_solid_map(lb_handle *h, int *owner_out)
+{
+    if (!h || !owner_out) {
+        set_error("lb_get_solid_map: NULL argument");
+        return LB_EINVAL;
+    }
+    join_overlap(h);
+    cudaError_t e = cudaSuccess;
+    if (h->sph_owner && h->sph_n >= 0) {
+        k_sph_export<<<(unsigned)std::min<size_t>((h->n_nodes + 255) / 256, 65535), 256, 0, h->stream>>>(
+            h->sph_owner, owner_out, h->n_nodes);
+        h->launches += 1;
+        e = cudaGetLastError();
+    } else {
+        e = cudaMemsetAsync(owner_out, 0xff, h->n_nodes * sizeof(int), h->stream);
+    }
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_get_solid_map", e);
+}
+
+}  // extern "C"

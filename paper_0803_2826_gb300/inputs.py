@@ -1,7 +1,7 @@
 """Seeded synthetic inputs for the fluctuating D3Q19 lattice-Boltzmann workloads.
 
 This module only draws and shapes numbers (velocity fields, random-walk chain
-conformations, particle positions, replica sizes).  It holds none of the
+conformations, particle positions, sphere centres, replica sizes).  It holds none of the
 lattice-Boltzmann arithmetic: both the CUDA library and the CPU oracle turn
 these fields into populations themselves.  Every generator is deterministic in
 its seed (numpy ``default_rng``).
@@ -129,6 +129,27 @@ def uniform_particles(n, box, seed, *, zrange=None):
     if zrange is not None:
         pos[:, 2] = rng.uniform(zrange[0], zrange[1], size=n)
     return pos
+
+
+def sphere_centres(n, box, radius, seed, *, gap=2.0, tries=100000):
+    """n centres uniform in the periodic box, each at least 2 radius + gap
+    from the others (minimum image), by random sequential addition; shape
+    (n, 3).  Raises if the box cannot take them."""
+    rng = np.random.default_rng(seed)
+    L = np.asarray(box, dtype=np.float64)
+    dmin = 2.0 * radius + gap
+    out = np.empty((0, 3))
+    for _ in range(tries):
+        if out.shape[0] == n:
+            return out
+        c = rng.uniform(0.0, 1.0, 3) * L
+        d = out - c
+        d -= L * np.round(d / L)
+        if out.shape[0] == 0 or (d * d).sum(1).min() >= dmin * dmin:
+            out = np.vstack([out, c])
+    if out.shape[0] == n:
+        return out
+    raise ValueError("could not place %d spheres of radius %g in box %s" % (n, radius, tuple(box)))
 
 
 def maxwell_momenta(n, mass, kT, seed):

@@ -23,6 +23,7 @@ LB_F32, LB_F16, LB_BF16 = 0, 1, 2
 LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
 LB_DERR_PARTICLE_RANGE = 16
+LB_DERR_SPHERE = 32
 LB_COUPLE_PER_SUBSTEP, LB_COUPLE_OVERLAP, LB_COUPLE_PHI3, LB_COUPLE_PHI4 = 1, 2, 4, 8
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
@@ -33,7 +34,8 @@ EXPORTS = (
     "lb_plane_pitch", "lb_population_bytes", "lb_create", "lb_destroy", "lb_last_error",
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
-    "lb_couple_particles", "lb_interpolate", "lb_interpolate_phi", "lb_get_particle_forces", "lb_noise_words", "lb_box_muller",
+    "lb_couple_particles", "lb_interpolate", "lb_interpolate_phi", "lb_get_particle_forces",
+    "lb_spheres_place", "lb_step_spheres", "lb_get_solid_map", "lb_noise_words", "lb_box_muller",
     "lb_set_timing", "lb_get_timing", "lb_step_sums", "lb_adjoint_step_impulse", "lb_adjoint_couple",
     "lb_adjoint_kinetic_coupled",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
@@ -73,6 +75,14 @@ class lb_particles(C.Structure):
         ("n", C.c_int), ("reserved", C.c_int),
         ("pos", C.c_void_p), ("mom", C.c_void_p), ("mass", C.c_void_p), ("gamma", C.c_void_p),
         ("mass0", C.c_double), ("gamma0", C.c_double),
+    ]
+
+
+class lb_spheres(C.Structure):
+    _fields_ = [
+        ("n", C.c_int), ("reserved", C.c_int), ("radius", C.c_double),
+        ("pos", C.c_void_p), ("vel", C.c_void_p), ("mass", C.c_void_p), ("mass0", C.c_double),
+        ("force", C.c_void_p),
     ]
 
 
@@ -126,6 +136,9 @@ def load(path: str | None = None):
             "lb_interpolate": (i, [H, i, vp, vp]),
             "lb_interpolate_phi": (i, [H, i, i, vp, vp]),
             "lb_get_particle_forces": (i, [H, vp]),
+            "lb_spheres_place": (i, [H, C.POINTER(lb_spheres)]),
+            "lb_step_spheres": (i, [H, C.POINTER(lb_spheres)]),
+            "lb_get_solid_map": (i, [H, vp]),
             "lb_noise_words": (i, [u64, u32, u32, u32, u32, i, i, vp, vp, vp]),
             "lb_box_muller": (i, [vp, i, vp, vp]),
             "lb_set_timing": (i, [H, i]),
@@ -298,6 +311,30 @@ def lb_interpolate_phi(h, kernel, n, pos, u_out):
 
 def lb_get_particle_forces(h, out):
     _check(load().lb_get_particle_forces(h, _ptr(out)))
+
+
+def spheres(n, pos, vel, radius, *, mass=None, mass0=1.0, force=None) -> lb_spheres:
+    """The sphere set the library updates in place (pos, vel: device FP64
+    [n][3]; mass: FP64 [n] or None; force: FP64 [n][3] or None); the struct
+    keeps the tensors alive."""
+    s = lb_spheres()
+    s.n, s.reserved, s.radius = int(n), 0, float(radius)
+    s.pos, s.vel, s.mass, s.force = _ptr(pos), _ptr(vel), _ptr(mass), _ptr(force)
+    s.mass0 = float(mass0)
+    s._arrays = (pos, vel, mass, force)
+    return s
+
+
+def lb_spheres_place(h, s):
+    _check(load().lb_spheres_place(h, C.byref(s)))
+
+
+def lb_step_spheres(h, s):
+    _check(load().lb_step_spheres(h, C.byref(s)))
+
+
+def lb_get_solid_map(h, out):
+    _check(load().lb_get_solid_map(h, _ptr(out)))
 
 
 def lb_noise_words(seed, replica, step, domain, index0, count, nblocks, words, gauss=None, stream=None):
