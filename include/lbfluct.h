@@ -88,7 +88,12 @@ typedef struct {
     double body_force[3];  /* uniform force density f added at every fluid node     */
     uint64_t seed;         /* Philox key of the fluid noise                          */
     uint32_t replica;      /* fourth Philox counter word (replica index)            */
-    uint32_t reserved;     /* must be 0                                             */
+    uint32_t equilibrium;  /* equilibrium of the collision: 0 the quadratic form of
+                              Eq. (original_equil_distrib); 1 the exponential form of
+                              Eq. (equildist_lagrange), the maximum-entropy populations
+                              at given rho and j (Sec. 3.6) -- lb_step and lb_step_from
+                              only (no step sums, reverse mode, batches or spheres;
+                              couplings run in the serial order)                      */
     double pop_scale;      /* FP16/BF16 storage scale (0 selects 1024)              */
 } lb_params;
 

@@ -32,6 +32,8 @@ Function -> passage it follows:
                   the MRT relaxation and Delta'' of Sec. 3.7, then the pull)
   kinetic_seed()  L = 1/2 sum |j|^2 / rho over a sub-box and dL/dstate
   kinetic_energy_and_grad()  forward + reverse pass of a whole run
+  exp_equilibrium()  Sec. 3.6 Eq. (equildist_lagrange), the maximum-entropy equilibrium
+                  (make_params(equilibrium=1) uses it in the collision)
 """
 from __future__ import annotations
 
@@ -67,7 +69,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [
         ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-        ("walls", C.c_int), ("noise_rho0", C.c_int), ("pad_", C.c_int),
+        ("walls", C.c_int), ("noise_rho0", C.c_int), ("equilibrium", C.c_int),
         ("rho0", C.c_double), ("kT", C.c_double),
         ("gamma_shear", C.c_double), ("gamma_bulk", C.c_double),
         ("gamma_odd", C.c_double), ("gamma_even", C.c_double),
@@ -136,6 +138,7 @@ def _load():
             lib.ora_step_spheres.argtypes = [P, _D, _D, _D, C.c_uint32, C.POINTER(C.c_int), C.c_int, C.c_double,
                                              _D, _D, _D, _D, _D]
             lib.ora_step_spheres.restype = C.c_int
+            lib.ora_exp_equilibrium.argtypes = [C.c_double, _D, _D]
             lib.ora_phi.argtypes = [C.c_int, C.c_double]
             lib.ora_phi.restype = C.c_double
             lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
@@ -154,12 +157,15 @@ def _dp(a):
 
 def make_params(shape, *, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0,
                 gamma_odd=0.0, gamma_even=0.0, body_force=(0.0, 0.0, 0.0), seed=0,
-                replica=0, walls=False, noise_rho0=False) -> Params:
-    """shape = (nx, ny, nz)."""
+                replica=0, walls=False, noise_rho0=False, equilibrium=0) -> Params:
+    """shape = (nx, ny, nz); equilibrium: 0 the quadratic form of Eq.
+    (original_equil_distrib), 1 the exponential form of Eq. (equildist_lagrange)
+    in the collision."""
     p = Params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
     p.walls = int(bool(walls))
     p.noise_rho0 = int(bool(noise_rho0))
+    p.equilibrium = int(equilibrium)
     p.rho0 = rho0
     p.kT = kT
     p.gamma_shear, p.gamma_bulk = gamma_shear, gamma_bulk
@@ -427,6 +433,15 @@ def effective_friction(kernel, offset, *, L=16, steps=1500, F=1e-4, a0=1.0, mass
     return dict(u0=u0, u0_prev=u0_prev, U=U, a=a, g=g)
 
 
+def exp_equilibrium(rho, u):
+    """n^eq of Eq. (equildist_lagrange) for density rho and velocity u (19 values)."""
+    lib = _load()
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(19)
+    lib.ora_exp_equilibrium(float(rho), _dp(uu), _dp(out))
+    return out
+
+
 def _ip(a):
     return a.ctypes.data_as(C.POINTER(C.c_int))
 
@@ -499,8 +514,14 @@ def phi(kernel, v):
     return _load().ora_phi(int(kernel), float(v))
 
 
+def _quadratic_only(p: Params):
+    if p.equilibrium != 0:
+        raise ValueError("the reverse pass is derived for the quadratic equilibrium")
+
+
 def adjoint_step(p: Params, state, lam_in, force=None, grad_f=None):
     """dL/dn*(t) from dL/dn*(t+1) for the step leaving `state`; adds dL/df to grad_f."""
+    _quadratic_only(p)
     lib = _load()
     st = np.ascontiguousarray(state, dtype=np.float64)
     li = np.ascontiguousarray(lam_in, dtype=np.float64)

@@ -232,7 +232,8 @@ typedef struct {
     int nx, ny, nz;
     int walls;          /* 1: solid planes z = 0 and z = nz-1 (link bounce-back) */
     int noise_rho0;     /* 1: noise amplitude uses rho0 instead of local rho      */
-    int pad_;
+    int equilibrium;    /* collision equilibrium: 0 Eq. original_equil_distrib,   */
+                        /* 1 the exponential form of Eq. equildist_lagrange       */
     double rho0;
     double kT;
     double gamma_shear, gamma_bulk, gamma_odd, gamma_even;
@@ -276,6 +277,57 @@ static void equilibrium(double rho, const double u[3], double neq[Q])
         double cu = u[0] * g_c[i][0] + u[1] * g_c[i][1] + u[2] * g_c[i][2];
         neq[i] = g_a[i] * rho * (1.0 + cu / CS2 + cu * cu / (2.0 * CS2 * CS2) - u2 / (2.0 * CS2));
     }
+}
+
+/* Eq. (equildist_lagrange): the equilibrium that maximises the entropy of
+ * Eq. (boltzmann_entropy_function) under the mass and momentum constraints
+ * (Eqs. constraint_mass, constraint_mom): n^eq_i = rho a_i exp(lambda.c_i) / Z,
+ * Z = sum_i a_i exp(lambda.c_i) (the normalisation stands for lambda_rho),
+ * with lambda the root of sum_i a_i c_i exp(lambda.c_i) / Z = u.  The root
+ * is found by Newton's method (the Jacobian is the covariance of c under the
+ * weights a_i exp(lambda.c_i) / Z, positive definite), started from the
+ * first-order value lambda = u / c_s^2. */
+static void exp_equilibrium(double rho, const double u[3], double neq[Q])
+{
+    double lam[3] = {u[0] / CS2, u[1] / CS2, u[2] / CS2};
+    for (int it = 0; it < 60; it++) {
+        double w[Q], Z = 0.0, m[3] = {0, 0, 0}, C[3][3] = {{0}};
+        for (int i = 0; i < Q; i++) {
+            w[i] = g_a[i] * exp(lam[0] * g_c[i][0] + lam[1] * g_c[i][1] + lam[2] * g_c[i][2]);
+            Z += w[i];
+        }
+        for (int i = 0; i < Q; i++)
+            for (int a = 0; a < 3; a++) m[a] += w[i] * g_c[i][a] / Z;
+        for (int i = 0; i < Q; i++)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) C[a][b] += w[i] * (g_c[i][a] - m[a]) * (g_c[i][b] - m[b]) / Z;
+        double r[3] = {u[0] - m[0], u[1] - m[1], u[2] - m[2]};
+        if (fabs(r[0]) + fabs(r[1]) + fabs(r[2]) < 1e-16) break;
+        /* solve C d = r (Cramer's rule on the symmetric 3x3 system) */
+        double det = C[0][0] * (C[1][1] * C[2][2] - C[1][2] * C[2][1]) - C[0][1] * (C[1][0] * C[2][2] - C[1][2] * C[2][0])
+                   + C[0][2] * (C[1][0] * C[2][1] - C[1][1] * C[2][0]);
+        double d[3];
+        for (int k = 0; k < 3; k++) {
+            double M[3][3];
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 3; b++) M[a][b] = (b == k) ? r[a] : C[a][b];
+            d[k] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+                    + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+        }
+        for (int k = 0; k < 3; k++) lam[k] += d[k];
+    }
+    double Z = 0.0, w[Q];
+    for (int i = 0; i < Q; i++) {
+        w[i] = g_a[i] * exp(lam[0] * g_c[i][0] + lam[1] * g_c[i][1] + lam[2] * g_c[i][2]);
+        Z += w[i];
+    }
+    for (int i = 0; i < Q; i++) neq[i] = rho * w[i] / Z;
+}
+
+void ora_exp_equilibrium(double rho, const double *u, double *neq)
+{
+    build_tables();
+    exp_equilibrium(rho, u, neq);
 }
 
 /* Equilibrium populations for given fields rho [N] and u [3][N] (NULL: rho0, 0). */
@@ -351,7 +403,10 @@ static void collide(const ora_params *P, const double n[Q], const double f[3],
     double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
 
     double neq[Q], nneq[Q];
-    equilibrium(rho, u, neq);
+    if (P->equilibrium == 1)
+        exp_equilibrium(rho, u, neq);
+    else
+        equilibrium(rho, u, neq);
     for (int i = 0; i < Q; i++) nneq[i] = n[i] - neq[i];
 
     double m[Q];

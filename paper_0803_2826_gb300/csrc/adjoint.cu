@@ -392,9 +392,18 @@ cudaError_t step_from(lb_handle *h, const void *src, void *dst, uint32_t step, c
     h->step = step;
     cudaError_t e;
     switch (h->p.dtype) {
-    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, impulse, nullptr); break;
-    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, impulse, nullptr); break;
-    default: e = launch_stream_collide_dt<2>(h, src, dst, impulse, nullptr); break;
+    case LB_F32:
+        e = h->p.equilibrium ? launch_stream_collide_exp(h, src, dst, impulse)
+                             : launch_stream_collide_dt<0>(h, src, dst, impulse, nullptr);
+        break;
+    case LB_F16:
+        e = h->p.equilibrium ? launch_stream_collide_exp(h, src, dst, impulse)
+                             : launch_stream_collide_dt<1>(h, src, dst, impulse, nullptr);
+        break;
+    default:
+        e = h->p.equilibrium ? launch_stream_collide_exp(h, src, dst, impulse)
+                             : launch_stream_collide_dt<2>(h, src, dst, impulse, nullptr);
+        break;
     }
     h->step = saved;
     return e;
@@ -408,6 +417,10 @@ bool check_adjoint_handle(const lb_handle *h, const char *who)
     }
     if (h->p.kT != 0.0) {
         set_error("%s: the adjoint is defined for deterministic runs (kT = 0)", who);
+        return false;
+    }
+    if (h->p.equilibrium) {
+        set_error("%s: the adjoint is derived for the quadratic equilibrium", who);
         return false;
     }
     return true;

@@ -174,8 +174,8 @@ bool check_params(const lb_params *p)
         set_error("pop_scale must be >= 0 (0 selects 1024)");
         return false;
     }
-    if (p->reserved != 0) {
-        set_error("lb_params.reserved must be 0");
+    if (p->equilibrium > 1) {
+        set_error("lb_params.equilibrium must be 0 (quadratic) or 1 (exponential)");
         return false;
     }
     return true;
@@ -243,10 +243,14 @@ lb_status step_once(lb_handle *h, float *partials)
     }
     const float *facc = h->facc_dirty ? h->facc : nullptr;
     timer_mark(h, 0, 0, h->stream);
-    switch (h->p.dtype) {
-    case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, facc, partials); break;
-    case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, facc, partials); break;
-    default: e = launch_stream_collide_dt<2>(h, src, dst, facc, partials); break;
+    if (h->p.equilibrium) {
+        e = launch_stream_collide_exp(h, src, dst, facc);
+    } else {
+        switch (h->p.dtype) {
+        case LB_F32: e = launch_stream_collide_dt<0>(h, src, dst, facc, partials); break;
+        case LB_F16: e = launch_stream_collide_dt<1>(h, src, dst, facc, partials); break;
+        default: e = launch_stream_collide_dt<2>(h, src, dst, facc, partials); break;
+        }
     }
     timer_mark(h, 0, 1, h->stream);
     if (e != cudaSuccess) return cuda_fail("lb_step", e);
@@ -532,6 +536,10 @@ lb_status lb_step_sums(lb_handle *h, int nsteps, double *sums)
     if (!h || !sums || nsteps < 1) {
         set_error("lb_step_sums: need a handle, a sums buffer and nsteps >= 1");
         return LB_EINVAL;
+    }
+    if (h->p.equilibrium) {
+        set_error("lb_step_sums: the sums come from the quadratic-equilibrium launch (use lb_step + lb_moments)");
+        return LB_EUNSUPPORTED;
     }
     const size_t nb = sc_block_count(h);
     const size_t len = nb * 38 + step_sums_scratch(nb);

@@ -370,8 +370,8 @@ lb_status lb_batch_create(const lb_params *per_replica, int n, void *pops_a, voi
     }
     for (int r = 0; r < n; ++r) {
         if (!lb_plane_pitch(&per_replica[r])) return LB_EINVAL;
-        if (per_replica[r].walls) {
-            set_error("lb_batch_create: replicas must be periodic");
+        if (per_replica[r].walls || per_replica[r].equilibrium) {
+            set_error("lb_batch_create: replicas must be periodic with the quadratic equilibrium");
             return LB_EUNSUPPORTED;
         }
         if (!same_physics(per_replica[r], per_replica[0])) {

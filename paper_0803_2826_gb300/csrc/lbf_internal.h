@@ -96,6 +96,8 @@ int device_sm_count();
 
 // stream_collide.cu
 cudaError_t launch_stream_collide(const lb_handle *h, const void *src, void *dst, const float *facc);
+// exp_eq.cu: the update with the exponential equilibrium (lb_params.equilibrium = 1)
+cudaError_t launch_stream_collide_exp(const lb_handle *h, const void *src, void *dst, const float *facc);
 // moments.cu
 cudaError_t launch_init_equilibrium(const lb_handle *h, void *dst, const double *rho, const double *u);
 cudaError_t launch_set_populations(const lb_handle *h, void *dst, const double *n);

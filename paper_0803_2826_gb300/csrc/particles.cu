@@ -1801,7 +1801,7 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
     // impulses of an earlier call that no step has applied yet lie outside
     // this call's stencil records, which the overlapped step re-updates:
     // such a call runs in the serial order
-    const bool overlap = (cp->flags & LB_COUPLE_OVERLAP) != 0 && !h->facc_dirty;
+    const bool overlap = (cp->flags & LB_COUPLE_OVERLAP) != 0 && !h->facc_dirty && h->p.equilibrium == 0;
     cudaStream_t main_stream = h->stream;
     if (overlap) {
         // run on the handle's high-priority stream after everything queued on
@@ -1919,8 +1919,8 @@ bool adjoint_couple_ok(const lb_handle *h, const lb_particles *pp, const lb_coup
         set_error("%s: bad particle arguments", who);
         return false;
     }
-    if (h->p.kT != 0.0 || cp->chain_len > 1 || cp->use_wca) {
-        set_error("%s: the coupling reverse pass covers free particles at kT = 0", who);
+    if (h->p.kT != 0.0 || cp->chain_len > 1 || cp->use_wca || h->p.equilibrium) {
+        set_error("%s: the coupling reverse pass covers free particles at kT = 0 (quadratic equilibrium)", who);
         return false;
     }
     if (cp->flags & (LB_COUPLE_PHI3 | LB_COUPLE_PHI4)) {

@@ -464,8 +464,8 @@ bool check_spheres(const lb_handle *h, const lb_spheres *s, const char *who)
 
 lb_status spheres_supported(const lb_handle *h, const char *who)
 {
-    if (h->p.walls || h->p.dtype != LB_F32) {
-        set_error("%s: spheres need a periodic box with FP32 storage", who);
+    if (h->p.walls || h->p.dtype != LB_F32 || h->p.equilibrium) {
+        set_error("%s: spheres need a periodic box with FP32 storage and the quadratic equilibrium", who);
         return LB_EUNSUPPORTED;
     }
     return LB_OK;

@@ -65,7 +65,7 @@ class lb_params(C.Structure):
         ("gamma_shear", C.c_double), ("gamma_bulk", C.c_double),
         ("gamma_odd", C.c_double), ("gamma_even", C.c_double),
         ("body_force", C.c_double * 3),
-        ("seed", C.c_uint64), ("replica", C.c_uint32), ("reserved", C.c_uint32),
+        ("seed", C.c_uint64), ("replica", C.c_uint32), ("equilibrium", C.c_uint32),
         ("pop_scale", C.c_double),
     ]
 
@@ -211,8 +211,8 @@ def _check(st):
 
 def make_params(shape, *, dtype=LB_F32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma_bulk=0.0,
                 gamma_odd=0.0, gamma_even=0.0, body_force=(0.0, 0.0, 0.0), seed=0, replica=0,
-                walls=False, noise_rho0=False, pop_scale=0.0) -> lb_params:
-    """shape = (nx, ny, nz)."""
+                walls=False, noise_rho0=False, pop_scale=0.0, equilibrium=0) -> lb_params:
+    """shape = (nx, ny, nz); equilibrium 1 selects the exponential equilibrium."""
     p = lb_params()
     p.nx, p.ny, p.nz = (int(v) for v in shape)
     p.dtype = int(dtype)
@@ -223,7 +223,7 @@ def make_params(shape, *, dtype=LB_F32, rho0=1.0, kT=0.0, gamma_shear=0.0, gamma
     p.gamma_odd, p.gamma_even = float(gamma_odd), float(gamma_even)
     for d in range(3):
         p.body_force[d] = float(body_force[d])
-    p.seed, p.replica, p.reserved = int(seed), int(replica), 0
+    p.seed, p.replica, p.equilibrium = int(seed), int(replica), int(equilibrium)
     p.pop_scale = float(pop_scale)
     return p
 

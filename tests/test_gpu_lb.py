@@ -120,6 +120,45 @@ def test_two_rate_poiseuille_gpu(ora, ge):
         assert np.abs(ux - want).max() < 1e-5 * ua.max(), (gam_o, np.abs(ux - want).max() / ua.max())
 
 
+@pytest.mark.parametrize("kT,walls", [(0.0, False), (1e-4, False), (1e-4, True)])
+def test_exponential_equilibrium_parity(ora, kT, walls):
+    """lb_params.equilibrium = 1 (Sec. 3.6, Eq. equildist_lagrange): 20
+    steps with a force field against the oracle, velocities up to 0.1 (the
+    exponential and quadratic forms differ there by ~1e-4 of a population)."""
+    shape = (9, 8, 10)
+    u = inputs.gaussian_field(shape, 3, 0.04, seed=11)
+    if walls:
+        u[:, 0] = 0
+        u[:, -1] = 0
+    field = inputs.gaussian_field(shape, 3, 1e-4, seed=12)
+    kw = dict(kT=kT, seed=5, walls=walls, equilibrium=1, **GAMMAS)
+    p, want, got, lat, f64 = _pair(ora, shape, 20, u=u, field=field, **kw)
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None, None, None]
+    fl = slice(1, shape[2] - 1) if walls else slice(None)
+    assert rel(got[:, fl] - aa, want[:, fl] - aa) < 5e-6
+    # and it is not the quadratic update
+    pq, want_q, _, _, _ = _pair(ora, shape, 20, u=u, field=field, **dict(kw, equilibrium=0))
+    assert rel(want_q[:, fl] - aa, want[:, fl] - aa) > 20 * rel(got[:, fl] - aa, want[:, fl] - aa)
+
+
+def test_exponential_equilibrium_rejections():
+    lat = L.Lattice((8, 8, 8), equilibrium=1)
+    lat.init_equilibrium()
+    sums = torch.empty(L.LB_NSUMS, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LBError) as ei:
+        L.lb_step_sums(lat.h, 1, sums)
+    assert ei.value.status == L.LB_EUNSUPPORTED
+    g = torch.zeros((3, 8, 8, 8), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(L.LBError) as ei:
+        L.lb_adjoint_kinetic(lat.h, 2, 1, (2, 2, 2), (6, 6, 6), g, loss)
+    assert ei.value.status == L.LB_EUNSUPPORTED
+    with pytest.raises(L.LBError) as ei:
+        L.Lattice((8, 8, 8), equilibrium=2)
+    assert ei.value.status == L.LB_EINVAL
+
+
 def test_shear_wave_1000_steps(ora):
     """The 32^3 fluctuating shear-wave workload: rho0 = 1, gamma_s = gamma_v = 0
     (nu = 1/6), kT = 1e-4, seed 0, u_x = 0.01 sin(2 pi z / 32), 1000 steps."""
