@@ -69,6 +69,8 @@ def _args():
     ap.add_argument("--shape", default="256,256,256")
     ap.add_argument("--kT", default="0,1e-4")
     ap.add_argument("--dtype", default="f32")
+    ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
+                    help="time only the moving-sphere form for STEPS steps (profiling runs)")
     return ap.parse_args()
 
 
@@ -406,6 +408,7 @@ def _forms(peak):
                 reverse ms per step vs 500 plain FP32 steps;
       interpolation  the headline coupled workload with phi_3 and phi_4;
       spheres   256^3 with 512 moving solid spheres (moving bounce-back);
+      exp_equilibrium  256^3 steps with the exponential vs the quadratic equilibrium;
       precision 512^3 between walls, g = 1e-6, kT = 1e-4: ms per LB step with
                 FP16 / BF16 storage vs FP32 storage (no particles)."""
     import numpy as np
@@ -479,6 +482,27 @@ def _forms(peak):
 
     # extended particles: moving solid spheres
     out["spheres"] = _sphere_form(stream, peak)
+
+    # the exponential equilibrium against the quadratic one, 256^3 FP32 kT = 1e-4
+    exp_eq = {}
+    for name, eq in (("quadratic", 0), ("exponential", 1)):
+        lat = L.Lattice((256, 256, 256), kT=KT, seed=9, equilibrium=eq, stream=stream)
+        with torch.cuda.stream(stream):
+            lat.init_equilibrium(None, torch.as_tensor(inputs.shear_wave((256, 256, 256), 0.05)).cuda())
+            lat.step(3)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            lat.step(50)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 50
+        exp_eq[name] = {"ms_per_step": ms, "mlups": 256 ** 3 / (ms * 1e-3) / 1e6,
+                        "hbm_frac": 152 * 256 ** 3 / (ms * 1e-3) / 1e9 / peak}
+        lat.close()
+        torch.cuda.empty_cache()
+    out["exp_equilibrium"] = exp_eq
 
     # reduced-precision storage
     shape = (512, 512, 512)
@@ -637,6 +661,10 @@ def main():
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.sphere_form:
+        import torch
+        print(json.dumps(_sphere_form(torch.cuda.Stream(), _peak_hbm()[0], steps=args.sphere_form)))
+        return 0
     return run_ours(args)
 
 
