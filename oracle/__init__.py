@@ -136,7 +136,8 @@ def _load():
             lib.ora_sphere_owner.argtypes = [P, C.c_int, _D, C.c_double, C.POINTER(C.c_int)]
             lib.ora_sphere_velocity.argtypes = [_D, C.c_double, _D, _D, _D, _D]
             lib.ora_step_spheres.argtypes = [P, _D, _D, _D, C.c_uint32, C.POINTER(C.c_int), C.c_int, C.c_double,
-                                             _D, _D, _D, _D, _D]
+                                             _D, _D, _D, _D, _D, _D, _D]
+            lib.ora_sphere_velocity6.argtypes = [_D, C.c_double, C.c_double, _D, _D, _D, _D]
             lib.ora_step_spheres.restype = C.c_int
             lib.ora_exp_equilibrium.argtypes = [C.c_double, _D, _D]
             lib.ora_phi.argtypes = [C.c_int, C.c_double]
@@ -468,10 +469,25 @@ def sphere_velocity(zeta, m, U, F):
     return un, ut
 
 
-def step_spheres(p: Params, pops, owner, R, U, a, mass, *, fc=None, force=None, step=0):
+def sphere_velocity6(Z, m, inertia, V, F):
+    """(V(t+h), V~) for M dV/dt = -Z V + F, V = (U, Omega), M = diag(m, m, m,
+    I, I, I), Z a symmetric 6x6 matrix (Eq. EOMUsol and the U~ equation)."""
+    lib = _load()
+    z = np.ascontiguousarray(Z, dtype=np.float64).reshape(36)
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    vn, vt = np.empty(6), np.empty(6)
+    lib.ora_sphere_velocity6(_dp(z), float(m), float(inertia), _dp(V), _dp(F), _dp(vn), _dp(vt))
+    return vn, vt
+
+
+def step_spheres(p: Params, pops, owner, R, U, a, mass, *, omega=None, fc=None, force=None, step=0, forces=None):
     """One LB step with solid spheres (moving link bounce-back, Sec. 4.1-4.2).
-    Returns (pops, owner, R, U, U~, status); the inputs are not modified.
-    mass: per sphere (<= 0 holds it fixed); fc: external forces [n][3]."""
+    Returns (pops, owner, R, U, omega, U~, status); the inputs are not
+    modified.  omega: angular velocities [n][3], or None for spheres that do
+    not rotate (then omega is returned as None); mass: per sphere (<= 0 holds
+    it fixed); fc: external forces [n][3]; forces: an (n, 6) float64 array
+    that receives the hydrodynamic force and torque of the step."""
     lib = _load()
     src = np.ascontiguousarray(pops, dtype=np.float64)
     dst = np.empty_like(src)
@@ -479,13 +495,14 @@ def step_spheres(p: Params, pops, owner, R, U, a, mass, *, fc=None, force=None, 
     R = np.array(R, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
     U = np.array(U, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
     n = R.shape[0]
+    Om = None if omega is None else np.array(omega, dtype=np.float64, order="C", copy=True).reshape(-1, 3)
     m = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, dtype=np.float64), (n,)))
     f = None if fc is None else np.ascontiguousarray(fc, dtype=np.float64).reshape(-1, 3)
     ff = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
     ut = np.empty((max(n, 1), 3))
     st = lib.ora_step_spheres(C.byref(p), _dp(src), _dp(dst), _dp(ff), int(step) & 0xffffffff, _ip(own), n,
-                              float(a), _dp(R), _dp(U), _dp(m), _dp(f), _dp(ut))
-    return dst, own, R, U, ut[:n], st
+                              float(a), _dp(R), _dp(U), _dp(Om), _dp(m), _dp(f), _dp(ut), _dp(forces))
+    return dst, own, R, U, Om, ut[:n], st
 
 
 def interpolate(p: Params, pops, pos, force=None, kernel=2):

@@ -1361,39 +1361,137 @@ void ora_sphere_velocity(const double zeta[9], double m, const double U[3], cons
     }
 }
 
+/* Eigen-decomposition of a symmetric n x n matrix (n <= 6) by cyclic Jacobi
+ * rotations: A = V diag(w) V^T. */
+static void jacobi_n(int n, const double *Ain, double *w, double *V)
+{
+    double A[36];
+    for (int i = 0; i < n * n; i++) A[i] = Ain[i];
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 60; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += fabs(A[p * n + q]);
+        if (off == 0.0) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                if (A[p * n + q] == 0.0) continue;
+                double th = (A[q * n + q] - A[p * n + p]) / (2.0 * A[p * n + q]);
+                double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; k++) {
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - sn * akq;
+                    A[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - sn * aqk;
+                    A[q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {
+                    double vkp = V[k * n + p], vkq = V[k * n + q];
+                    V[k * n + p] = c * vkp - sn * vkq;
+                    V[k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    for (int i = 0; i < n; i++) w[i] = A[i * n + i];
+}
+
+/* Translation and rotation together: M dV/dt = -Z V + F for V = (U, Omega),
+ * M = diag(m, m, m, I, I, I), Z the symmetric 6 x 6 friction matrix.  With
+ * W = M^1/2 V and K = M^-1/2 Z M^-1/2 it is dW/dt = -K W + M^-1/2 F, solved
+ * over h = 1 as Eq. EOMUsol and the U~ equation in K's eigenbasis (kappa the
+ * eigenvalue, G the force component): W' = e^-kappa W + (1 - e^-kappa) G / kappa,
+ * W~ = ((1 - e^-kappa) W + (kappa - (1 - e^-kappa)) G / kappa) / kappa. */
+void ora_sphere_velocity6(const double Z[36], double m, double I, const double V[6], const double F[6],
+                          double Vn[6], double Vt[6])
+{
+    double sq[6], K[36], w[6], E[36];
+    for (int i = 0; i < 6; i++) sq[i] = sqrt(i < 3 ? m : I);
+    for (int i = 0; i < 6; i++)
+        for (int j = 0; j < 6; j++) K[i * 6 + j] = Z[i * 6 + j] / (sq[i] * sq[j]);
+    jacobi_n(6, K, w, E);
+    double we[6], ge[6], wn[6], wt[6];
+    for (int k = 0; k < 6; k++) {
+        we[k] = 0.0;
+        ge[k] = 0.0;
+        for (int i = 0; i < 6; i++) {
+            we[k] += E[i * 6 + k] * sq[i] * V[i];
+            ge[k] += E[i * 6 + k] * F[i] / sq[i];
+        }
+        double ka = w[k];
+        if (ka < 1e-12) {
+            wn[k] = we[k] + ge[k];
+            wt[k] = we[k] + 0.5 * ge[k];
+        } else {
+            double e1 = -expm1(-ka);
+            wn[k] = (1.0 - e1) * we[k] + e1 * ge[k] / ka;
+            wt[k] = (e1 * we[k] + (ka - e1) * ge[k] / ka) / ka;
+        }
+    }
+    for (int i = 0; i < 6; i++) {
+        double sn = 0.0, st = 0.0;
+        for (int k = 0; k < 6; k++) {
+            sn += E[i * 6 + k] * wn[k];
+            st += E[i * 6 + k] * wt[k];
+        }
+        Vn[i] = sn / sq[i];
+        Vt[i] = st / sq[i];
+    }
+}
+
+static void cross3(const double a[3], const double b[3], double out[3])
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
 /* One LB step with np spheres of radius a (h = 1, b = 1).  src: the
  * post-collision state n*(t); owner: the solid map of the previous step (or
  * of the initial placement), updated here; R, U: centres and velocities,
- * updated; mass[p] <= 0 holds sphere p fixed (U, R unchanged, U~ = U); fc:
- * external forces F^c [np][3] or NULL; Ut_out: U~ [np][3] or NULL.
+ * updated; Om: angular velocities [np][3], updated, or NULL for spheres that
+ * do not rotate; mass[p] <= 0 holds sphere p fixed (U, Om, R unchanged,
+ * U~ = U); the moment of inertia is 2/5 m a^2 (a uniform solid sphere);
+ * fc: external forces F^c [np][3] or NULL; Ut_out: U~ [np][3] or NULL;
+ * FT_out: the hydrodynamic force and torque of the step, F0 - Z V~ (the
+ * momentum and its moment the links give the sphere) [np][6], or NULL.
+ * rho_b below is the minimum-image offset from the half-step centre.
  *   1. R_half = R + U / 2                                  Eq. EOMD-1
- *   2. solid map at R_half; covered nodes give sum n c to their sphere,
- *      uncovered nodes get n^eq(rho0, U_p(t)) and the sphere loses rho0 U_p(t)
- *   3. boundary links (fluid r, r + c_b solid of sphere p):
- *      F0_p = sum 2 n*_b(r) c_b, zeta_p = (2 rho0 / c_s^2) sum a_b c_b c_b^T
- *                                                          Eqs. force0, zeta
- *   4. U(t+h) and U~ from F0 + F^c and zeta                Eq. EOMUsol
+ *   2. solid map at R_half; covered nodes give sum n c (and its moment about
+ *      the centre) to their sphere, uncovered nodes get n^eq(rho0, u) with
+ *      u = U + Om x rho (values at time t) and the sphere loses rho0 u
+ *   3. boundary links (fluid r, r + c_b solid of sphere p), r_b = r + c_b/2:
+ *      F0 = sum 2 n*_b c_b, T0 = sum 2 n*_b rho_b x c_b, and the friction
+ *      (2 rho0 / c_s^2) sum a_b g g^T, g = (c_b, rho_b x c_b)   Eqs. force0, zeta
+ *   4. U, Om at t + h and U~, Om~ from F0 + F^c, T0 and the friction
+ *                                                          Eq. EOMUsol
  *   5. stream and collide the fluid nodes; a link whose source r - c_i is
- *      solid (sphere p) returns n_i(r) = n*_{-i}(r) + 2 a_i rho0 U~_p.c_i / c_s^2
- *                                                          Eq. MBB (c_b = -c_i)
+ *      solid (sphere p) returns n_i(r) = n*_{-i}(r) + 2 a_i rho0 u_b.c_i / c_s^2,
+ *      u_b = U~ + Om~ x rho_b at r_b = r - c_i/2     Eqs. MBB, NodeVel (c_b = -c_i)
  *      solid nodes keep their values
  *   6. R(t+h) = R_half + U(t+h) / 2                        Eq. EOMD-3
  * Returns 0, -1 when a node passes from one sphere to another, -2 with walls. */
 int ora_step_spheres(const ora_params *P, const double *src, double *dst, const double *force, uint32_t step,
-                     int *owner, int np, double a, double *R, double *U, const double *mass, const double *fc,
-                     double *Ut_out)
+                     int *owner, int np, double a, double *R, double *U, double *Om, const double *mass,
+                     const double *fc, double *Ut_out, double *FT_out)
 {
     build_tables();
     if (P->walls) return -2;  /* spheres live in periodic boxes */
     size_t N = nodes_of(P);
     const int L[3] = {P->nx, P->ny, P->nz};
+    const int n1 = np > 0 ? np : 1;
     double *cur = (double *)malloc(sizeof(double) * Q * N);
     memcpy(cur, src, sizeof(double) * Q * N);
     int *nown = (int *)malloc(sizeof(int) * N);
-    double *Rh = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
-    double *Ut = (double *)malloc(sizeof(double) * 3 * (np > 0 ? np : 1));
-    double *F0 = (double *)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
-    double *Z = (double *)calloc((size_t)9 * (np > 0 ? np : 1), sizeof(double));
+    double *Rh = (double *)malloc(sizeof(double) * 3 * n1);
+    double *Vt = (double *)calloc((size_t)6 * n1, sizeof(double));
+    double *F0 = (double *)calloc((size_t)6 * n1, sizeof(double));   /* force, torque */
+    double *Z = (double *)calloc((size_t)36 * n1, sizeof(double));
+    double *dP = (double *)calloc((size_t)6 * n1, sizeof(double));
     int status = 0;
 
     /* 1 */
@@ -1403,30 +1501,47 @@ int ora_step_spheres(const ora_params *P, const double *src, double *dst, const 
             v -= L[c] * floor(v / L[c]);
             Rh[3 * p + c] = v;
         }
-    /* 2 (new fluid takes the velocity U(t); the exchanges are applied after) */
+    /* 2 (new fluid takes the velocities at time t; the exchanges are applied after) */
     sphere_map(P, np, Rh, a, nown);
-    double *dP = (double *)calloc((size_t)3 * (np > 0 ? np : 1), sizeof(double));
-    for (size_t s = 0; s < N; s++) {
-        int o = owner[s], nn = nown[s];
-        if (o == nn) continue;
-        if (o >= 0 && nn >= 0) { status = -1; continue; }
-        if (nn >= 0) {  /* covered: its fluid momentum goes to the sphere */
-            for (int c = 0; c < 3; c++) {
-                double j = 0.0;
-                for (int i = 0; i < Q; i++) j += cur[(size_t)i * N + s] * g_c[i][c];
-                dP[3 * nn + c] += j;
+    for (int z = 0; z < P->nz; z++)
+        for (int y = 0; y < P->ny; y++)
+            for (int x = 0; x < P->nx; x++) {
+                size_t s = lin(P, x, y, z);
+                int o = owner[s], nn = nown[s];
+                if (o == nn) continue;
+                if (o >= 0 && nn >= 0) { status = -1; continue; }
+                int p = nn >= 0 ? nn : o;
+                const double rv[3] = {periodic_offset(x - Rh[3 * p], L[0]), periodic_offset(y - Rh[3 * p + 1], L[1]),
+                                      periodic_offset(z - Rh[3 * p + 2], L[2])};
+                double j[3] = {0.0, 0.0, 0.0}, mom[3];
+                if (nn >= 0) {  /* covered: its fluid momentum goes to the sphere */
+                    for (int c = 0; c < 3; c++)
+                        for (int i = 0; i < Q; i++) j[c] += cur[(size_t)i * N + s] * g_c[i][c];
+                } else {        /* uncovered: new fluid at the surface velocity */
+                    double u[3] = {U[3 * p], U[3 * p + 1], U[3 * p + 2]}, ne[Q];
+                    if (Om) {
+                        double w[3];
+                        cross3(Om + 3 * p, rv, w);
+                        for (int c = 0; c < 3; c++) u[c] += w[c];
+                    }
+                    equilibrium(P->rho0, u, ne);
+                    for (int i = 0; i < Q; i++) cur[(size_t)i * N + s] = ne[i];
+                    for (int c = 0; c < 3; c++) j[c] = -P->rho0 * u[c];
+                }
+                cross3(rv, j, mom);
+                for (int c = 0; c < 3; c++) {
+                    dP[6 * p + c] += j[c];
+                    dP[6 * p + 3 + c] += mom[c];
+                }
             }
-        } else {        /* uncovered: new fluid at the sphere's velocity */
-            double u[3] = {U[3 * o], U[3 * o + 1], U[3 * o + 2]}, ne[Q];
-            equilibrium(P->rho0, u, ne);
-            for (int i = 0; i < Q; i++) cur[(size_t)i * N + s] = ne[i];
-            for (int c = 0; c < 3; c++) dP[3 * o + c] -= P->rho0 * u[c];
-        }
-    }
     for (int p = 0; p < np; p++)
-        if (mass[p] > 0.0)
-            for (int c = 0; c < 3; c++) U[3 * p + c] += dP[3 * p + c] / mass[p];
-    free(dP);
+        if (mass[p] > 0.0) {
+            double I = 0.4 * mass[p] * a * a;
+            for (int c = 0; c < 3; c++) {
+                U[3 * p + c] += dP[6 * p + c] / mass[p];
+                if (Om) Om[3 * p + c] += dP[6 * p + 3 + c] / I;
+            }
+        }
     memcpy(owner, nown, sizeof(int) * N);
     /* 3 */
     for (int z = 0; z < P->nz; z++)
@@ -1439,26 +1554,54 @@ int ora_step_spheres(const ora_params *P, const double *src, double *dst, const 
                                    wrap(z + g_c[i][2], L[2]));
                     int p = owner[t];
                     if (p < 0) continue;
-                    double nb = cur[(size_t)i * N + s];
-                    for (int c = 0; c < 3; c++) {
-                        F0[3 * p + c] += 2.0 * nb * g_c[i][c];
-                        for (int d = 0; d < 3; d++)
-                            Z[9 * p + 3 * c + d] += 2.0 * P->rho0 / CS2 * g_a[i] * g_c[i][c] * g_c[i][d];
+                    double nb = cur[(size_t)i * N + s], cb[3] = {g_c[i][0], g_c[i][1], g_c[i][2]};
+                    double rb[3] = {periodic_offset(x + 0.5 * cb[0] - Rh[3 * p], L[0]),
+                                    periodic_offset(y + 0.5 * cb[1] - Rh[3 * p + 1], L[1]),
+                                    periodic_offset(z + 0.5 * cb[2] - Rh[3 * p + 2], L[2])};
+                    double g[6];
+                    g[0] = cb[0];
+                    g[1] = cb[1];
+                    g[2] = cb[2];
+                    cross3(rb, cb, g + 3);
+                    for (int c = 0; c < 6; c++) {
+                        F0[6 * p + c] += 2.0 * nb * g[c];
+                        for (int d = 0; d < 6; d++) Z[36 * p + 6 * c + d] += 2.0 * P->rho0 / CS2 * g_a[i] * g[c] * g[d];
                     }
                 }
             }
     /* 4 */
     for (int p = 0; p < np; p++) {
-        double Fp[3], Un[3];
-        for (int c = 0; c < 3; c++) Fp[c] = F0[3 * p + c] + (fc ? fc[3 * p + c] : 0.0);
+        double Fp[6], Vn[6];
+        for (int c = 0; c < 6; c++) Fp[c] = F0[6 * p + c] + ((fc && c < 3) ? fc[3 * p + c] : 0.0);
         if (mass[p] > 0.0) {
-            ora_sphere_velocity(Z + 9 * p, mass[p], U + 3 * p, Fp, Un, Ut + 3 * p);
-            for (int c = 0; c < 3; c++) U[3 * p + c] = Un[c];
+            if (Om) {
+                double V[6] = {U[3 * p], U[3 * p + 1], U[3 * p + 2], Om[3 * p], Om[3 * p + 1], Om[3 * p + 2]};
+                ora_sphere_velocity6(Z + 36 * p, mass[p], 0.4 * mass[p] * a * a, V, Fp, Vn, Vt + 6 * p);
+                for (int c = 0; c < 3; c++) {
+                    U[3 * p + c] = Vn[c];
+                    Om[3 * p + c] = Vn[3 + c];
+                }
+            } else {
+                double Z3[9];
+                for (int c = 0; c < 3; c++)
+                    for (int d = 0; d < 3; d++) Z3[3 * c + d] = Z[36 * p + 6 * c + d];
+                ora_sphere_velocity(Z3, mass[p], U + 3 * p, Fp, Vn, Vt + 6 * p);
+                for (int c = 0; c < 3; c++) U[3 * p + c] = Vn[c];
+            }
         } else {
-            for (int c = 0; c < 3; c++) Ut[3 * p + c] = U[3 * p + c];
+            for (int c = 0; c < 3; c++) {
+                Vt[6 * p + c] = U[3 * p + c];
+                Vt[6 * p + 3 + c] = Om ? Om[3 * p + c] : 0.0;
+            }
         }
         if (Ut_out)
-            for (int c = 0; c < 3; c++) Ut_out[3 * p + c] = Ut[3 * p + c];
+            for (int c = 0; c < 3; c++) Ut_out[3 * p + c] = Vt[6 * p + c];
+        if (FT_out)
+            for (int c = 0; c < 6; c++) {
+                double zv = 0.0;
+                for (int d = 0; d < 6; d++) zv += Z[36 * p + 6 * c + d] * Vt[6 * p + d];
+                FT_out[6 * p + c] = F0[6 * p + c] - zv;
+            }
     }
     /* 5 */
 #pragma omp parallel for schedule(static)
@@ -1476,7 +1619,16 @@ int ora_step_spheres(const ora_params *P, const double *src, double *dst, const 
                                    wrap(z - g_c[i][2], L[2]));
                     int p = owner[t];
                     if (p >= 0) {
-                        double uc = Ut[3 * p] * g_c[i][0] + Ut[3 * p + 1] * g_c[i][1] + Ut[3 * p + 2] * g_c[i][2];
+                        const double *vt = Vt + 6 * p;
+                        double ub[3] = {vt[0], vt[1], vt[2]};
+                        if (Om) {
+                            double rb[3] = {periodic_offset(x - 0.5 * g_c[i][0] - Rh[3 * p], L[0]),
+                                            periodic_offset(y - 0.5 * g_c[i][1] - Rh[3 * p + 1], L[1]),
+                                            periodic_offset(z - 0.5 * g_c[i][2] - Rh[3 * p + 2], L[2])}, w[3];
+                            cross3(vt + 3, rb, w);
+                            for (int c = 0; c < 3; c++) ub[c] += w[c];
+                        }
+                        double uc = ub[0] * g_c[i][0] + ub[1] * g_c[i][1] + ub[2] * g_c[i][2];
                         n[i] = cur[(size_t)g_opp[i] * N + s] + 2.0 * g_a[i] * P->rho0 * uc / CS2;
                     } else {
                         n[i] = cur[(size_t)i * N + t];
@@ -1500,6 +1652,6 @@ int ora_step_spheres(const ora_params *P, const double *src, double *dst, const 
             v -= L[c] * floor(v / L[c]);
             R[3 * p + c] = v;
         }
-    free(cur); free(nown); free(Rh); free(Ut); free(F0); free(Z);
+    free(cur); free(nown); free(Rh); free(Vt); free(F0); free(Z); free(dP);
     return status;
 }

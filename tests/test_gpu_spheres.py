@@ -41,7 +41,7 @@ def _gpu_run(shape, pops0, R, U, rad, mass, steps, *, fc=None, **kw):
 def _ora_run(ora, p, pops, R, U, rad, mass, steps, fc=None):
     owner = ora.sphere_owner(p, R, rad)
     for t in range(steps):
-        pops, owner, R, U, ut, st = ora.step_spheres(p, pops, owner, R, U, rad, mass, fc=fc, step=t)
+        pops, owner, R, U, _, ut, st = ora.step_spheres(p, pops, owner, R, U, rad, mass, fc=fc, step=t)
         assert st == 0
     return pops, owner, R, U
 
