@@ -311,8 +311,10 @@ lb_status lb_get_particle_forces(lb_handle *h, float *out);
 
 /* ---- extended particles: solid spheres with moving bounce-back ------------- */
 
-/* Spheres of one radius that translate without rotating (Sec. 4.2 treats the
- * linear velocity).  All pointers are device memory owned by the caller. */
+/* Spheres of one radius that translate and, with angular velocities, rotate
+ * (Sec. 4.1 Eq. NodeVel; Sec. 4.2 writes the linear update, the rotational
+ * one follows the same steps).  All pointers are device memory owned by the
+ * caller. */
 typedef struct {
     int n;                /* number of spheres (>= 0)                                */
     int reserved;         /* must be 0                                               */
@@ -323,6 +325,9 @@ typedef struct {
                           /* R and U stay, its surface moves with U                   */
     double mass0;
     const double *force;  /* [n][3] external forces F^c, or NULL                     */
+    double *omega;        /* [n][3] angular velocities, updated in place, or NULL    */
+                          /* for spheres that do not rotate (moment of inertia       */
+                          /* 2/5 m a^2; u_b = U + Omega x (r_b - R), Eq. NodeVel)    */
 } lb_spheres;
 
 /* Build the solid map of the spheres at their current centres (no exchange
@@ -340,7 +345,8 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s);
  *     loses rho0 U(t);
  *  2. over the boundary links b (fluid node r, r + c_b solid):
  *     F0 = sum 2 n*_b c_b, zeta = (2 rho0 / c_s^2) sum a_b c_b c_b^T
- *     (Eqs. force0, zeta);
+ *     (Eqs. force0, zeta); with rotation also the torque and the coupled
+ *     6 x 6 friction of g = (c_b, (r_b - R) x c_b), r_b = r + c_b/2;
  *  3. U(t+h) = e^-A U + zeta^-1 (1 - e^-A)(F0 + F^c), A = zeta / m
  *     (Eq. EOMUsol in zeta's eigenbasis), and U~ of the consistency
  *     equation, so that m (U(t+h) - U(t)) = F0 + F^c - zeta U~;

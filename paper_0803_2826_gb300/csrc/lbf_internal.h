@@ -82,6 +82,7 @@ struct lb_handle {
     float *sph_acc;       // [sph_cap][12]: F0 (3), covering momentum (3), zeta (6)
     double *sph_rh;       // [sph_cap][3] half-step centres
     float4 *sph_ut;       // [sph_cap] U~
+    float4 *sph_uw;       // [sph_cap] Omega~ (0 for spheres that do not rotate)
     int sph_cap;
     int sph_n;            // spheres of the current solid map (-1: none placed)
     double sph_a;

@@ -1,5 +1,5 @@
 // spheres.cu -- extended particles: solid spheres that translate through the
-// lattice, coupled to the fluid by the moving link bounce-back of Sec. 4.1
+// lattice (and may rotate), coupled to the fluid by the moving link bounce-back of Sec. 4.1
 // (Eq. MBB) and updated as in Sec. 4.2 (Eqs. EOMD-1..3, force0, zeta,
 // EOMUsol and the consistency equation for the velocity U~).
 //
@@ -25,8 +25,9 @@
 // for the other fluid nodes; k_sph_links sets the marks within a + 2.5 of
 // each centre every step (a -2 left further out by a moved sphere is
 // harmless: that node is recomputed with the same result).
-// Spheres translate without rotating (u_b = U), rho in Eqs. MBB and zeta is
-// rho0, and spheres must stay apart; positions and velocities are FP64 (a
+// Spheres translate, and rotate when angular velocities are given (u_b = U +
+// Omega x (r_b - R), Eq. NodeVel; moment of inertia 2/5 m a^2); rho in Eqs.
+// MBB and zeta is rho0, and spheres must stay apart; positions and velocities are FP64 (a
 // few values per sphere), the populations FP32 deviations n - a rho0 (the
 // rho0 part of F0 sums to zero over a closed set of links and is left out).
 #include <cmath>
@@ -41,7 +42,10 @@ extern template cudaError_t launch_stream_collide_dt<0>(const lb_handle *, const
 namespace {
 
 constexpr int kSphThreads = 128;
-constexpr int kAcc = 12;  // per sphere: F0 (3), covering momentum (3), zeta xx yy zz xy yz zx
+// per sphere: F0 (3), covering momentum (3), friction TT xx yy zz xy yz zx (6),
+// torque T0 (3), covering angular momentum (3), friction TR row-major (9),
+// friction RR xx yy zz xy yz zx (6)
+constexpr int kAcc = 33;
 
 // d - L floor(d / L + 1/2) for d = x - c in (-L, L): the minimum image by
 // comparisons (the same value wherever |d| < L / 2 - 1, which covers every
@@ -144,11 +148,18 @@ __global__ void k_sph_half(const double *pos, const double *vel, const double *m
     for (int q = 0; q < kAcc; ++q) acc[kAcc * p + q] = 0.0f;
 }
 
+__device__ __forceinline__ void cross3f(const float a[3], const float b[3], float out[3])
+{
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
 // The solid map follows the half-step centres (uncovered nodes get the
-// equilibrium of the sphere's velocity at time t, which this kernel reads
-// before any update of it).
-__global__ void k_sph_map(int *owner, float *pops, const double *rh, const double *vel, double a, int B, int n,
-                          StepArgs g, float *acc, unsigned int *err)
+// equilibrium of the surface velocity U + Omega x rho at time t, which this
+// kernel reads before any update).  om: angular velocities, or NULL.
+__global__ void k_sph_map(int *owner, float *pops, const double *rh, const double *vel, const double *om, double a,
+                          int B, int n, StepArgs g, float *acc, unsigned int *err)
 {
     __shared__ Box b;
     const int p = blockIdx.y;
@@ -161,47 +172,67 @@ __global__ void k_sph_map(int *owner, float *pops, const double *rh, const doubl
     const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
     const size_t P = g.pitch;
     const int old = owner[s];
+    const float rv[3] = {(float)o[0] - b.cf[0], (float)o[1] - b.cf[1], (float)o[2] - b.cf[2]};
+    float j[3] = {0.f, 0.f, 0.f};
     if (inside_fast(b, o, x, y, z, c, a, g)) {
         if (old == p) return;
         if (old >= 0) {  // a node passing from one sphere to another
             atomicOr(err, LB_DERR_SPHERE);
             return;
         }
-        float j[3] = {0.f, 0.f, 0.f};  // covered: its fluid momentum goes to the sphere
 #pragma unroll
-        for (int i = 1; i < 19; ++i) {
+        for (int i = 1; i < 19; ++i) {  // covered: its fluid momentum goes to the sphere
             const float v = pops[(size_t)i * P + s];
             if (lbd::cx(i)) j[0] += lbd::cx(i) * v;
             if (lbd::cy(i)) j[1] += lbd::cy(i) * v;
             if (lbd::cz(i)) j[2] += lbd::cz(i) * v;
         }
         owner[s] = p;
-        for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 3 + d, j[d]);
-    } else if (old == p) {  // uncovered: new fluid at the sphere's velocity
+    } else if (old == p) {  // uncovered: new fluid at the surface velocity
         owner[s] = kNear;
-        const float u[3] = {(float)vel[3 * p], (float)vel[3 * p + 1], (float)vel[3 * p + 2]};
+        float u[3] = {(float)vel[3 * p], (float)vel[3 * p + 1], (float)vel[3 * p + 2]};
+        if (om) {
+            const float w[3] = {(float)om[3 * p], (float)om[3 * p + 1], (float)om[3 * p + 2]};
+            float wr[3];
+            cross3f(w, rv, wr);
+            for (int d = 0; d < 3; ++d) u[d] += wr[d];
+        }
         const float u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const float cu = lbd::cx(i) * u[0] + lbd::cy(i) * u[1] + lbd::cz(i) * u[2];
             pops[(size_t)i * P + s] = lbd::weight(i) * g.rho0 * (3.0f * cu + 4.5f * cu * cu - 1.5f * u2);
         }
-        for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 3 + d, -g.rho0 * u[d]);
+        for (int d = 0; d < 3; ++d) j[d] = -g.rho0 * u[d];
+    } else {
+        return;
+    }
+    for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 3 + d, j[d]);
+    if (om) {
+        float mom[3];
+        cross3f(rv, j, mom);
+        for (int d = 0; d < 3; ++d) atomicAdd(acc + kAcc * p + 15 + d, mom[d]);
     }
 }
 
-// F0 and zeta of each sphere over its boundary links (fluid node r, r + c_b
-// solid); a block reduces its sums before one atomic per component.  The
-// fluid nodes of the box are marked near (a solid neighbour of any sphere)
-// or far on the way.
+// Sums of each sphere over its boundary links (fluid node r, r + c_b solid,
+// r_b = r + c_b/2, rho_b = r_b - R, g = rho_b x c_b): F0 = sum 2 n*_b c_b,
+// the friction blocks 6 rho0 sum a_b (c c^T, and with ROT c g^T, g g^T) and
+// with ROT the torque T0 = sum 2 n*_b g.  A block reduces its sums before one
+// atomic per entry.  The fluid nodes within a + 2.5 of the centre are marked
+// near (a solid neighbour of any sphere) or far on the way.
+template <bool ROT>
 __global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const float *pops, const double *rh,
                                                             double a, int B, int n, StepArgs g, float *acc)
 {
-    __shared__ float red[kSphThreads / 32][9];
+    constexpr int NV = ROT ? 27 : 9;
+    __shared__ float red[kSphThreads / 32][NV];
     __shared__ Box b;
     const int p = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float v[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = 0.0f;
     const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
     box_setup(b, c, a);
     if (p < n && k < B * B * B) {
@@ -221,128 +252,222 @@ __global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const flo
             for (int i = 1; i < 19; ++i) {
                 const int tx = wrap_i(x + lbd::cx(i), g.nx), ty = wrap_i(y + lbd::cy(i), g.ny),
                           tz = wrap_i(z + lbd::cz(i), g.nz);
-                const int o = owner[((size_t)tz * g.ny + ty) * g.nx + tx];
-                near = near || o >= 0;
-                if (o != p) continue;
+                const int ow = owner[((size_t)tz * g.ny + ty) * g.nx + tx];
+                near = near || ow >= 0;
+                if (ow != p) continue;
                 const float nb = 2.0f * pops[(size_t)i * g.pitch + s];
-                const float cx = (float)lbd::cx(i), cy = (float)lbd::cy(i), cz = (float)lbd::cz(i);
+                const float cb[3] = {(float)lbd::cx(i), (float)lbd::cy(i), (float)lbd::cz(i)};
                 const float za = 6.0f * g.rho0 * lbd::weight(i);
-                v[0] += nb * cx;
-                v[1] += nb * cy;
-                v[2] += nb * cz;
-                v[3] += za * cx * cx;
-                v[4] += za * cy * cy;
-                v[5] += za * cz * cz;
-                v[6] += za * cx * cy;
-                v[7] += za * cy * cz;
-                v[8] += za * cz * cx;
+                v[0] += nb * cb[0];
+                v[1] += nb * cb[1];
+                v[2] += nb * cb[2];
+                v[3] += za * cb[0] * cb[0];
+                v[4] += za * cb[1] * cb[1];
+                v[5] += za * cb[2] * cb[2];
+                v[6] += za * cb[0] * cb[1];
+                v[7] += za * cb[1] * cb[2];
+                v[8] += za * cb[2] * cb[0];
+                if (ROT) {
+                    const float rb[3] = {dx + 0.5f * cb[0], dy + 0.5f * cb[1], dz + 0.5f * cb[2]};
+                    float gv[3];
+                    cross3f(rb, cb, gv);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) v[9 + d] += nb * gv[d];
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int d = 0; d < 3; ++d) v[12 + 3 * r + d] += za * cb[r] * gv[d];
+                    v[21] += za * gv[0] * gv[0];
+                    v[22] += za * gv[1] * gv[1];
+                    v[23] += za * gv[2] * gv[2];
+                    v[24] += za * gv[0] * gv[1];
+                    v[25] += za * gv[1] * gv[2];
+                    v[26] += za * gv[2] * gv[0];
+                }
             }
             const int mark = near ? kNear : kFar;
             if (own != mark) owner[s] = mark;
         }
     }
 #pragma unroll
-    for (int q = 0; q < 9; ++q)
+    for (int q = 0; q < NV; ++q)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0)
-        for (int q = 0; q < 9; ++q) red[w][q] = v[q];
+        for (int q = 0; q < NV; ++q) red[w][q] = v[q];
     __syncthreads();
-    if (threadIdx.x < 9 && p < n) {
+    if (threadIdx.x < NV && p < n) {
         float t = 0.0f;
         for (int q = 0; q < kSphThreads / 32; ++q) t += red[q][threadIdx.x];
         if (t != 0.0f) {
-            const int slot = threadIdx.x < 3 ? threadIdx.x : threadIdx.x + 3;  // F0 -> 0..2, zeta -> 6..11
+            // F0 -> 0..2, friction TT -> 6..11, T0 -> 12..14, TR -> 18..26, RR -> 27..32
+            const int q = threadIdx.x;
+            const int slot = q < 3 ? q : (q < 9 ? q + 3 : (q < 12 ? q + 3 : q + 6));
             atomicAdd(acc + kAcc * p + slot, t);
         }
     }
 }
 
-// Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations
+// Eigen-decomposition of a symmetric N x N matrix by cyclic Jacobi rotations
 // (FP32), until the off-diagonal part is below 1e-7 of the diagonal.
-__device__ void jacobi3(float A[3][3], float w[3], float V[3][3])
+template <int N>
+__device__ void jacobi(float A[N][N], float w[N], float V[N][N])
 {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0f : 0.0f;
-    for (int sweep = 0; sweep < 12; ++sweep) {
-        const float off = fabsf(A[0][1]) + fabsf(A[0][2]) + fabsf(A[1][2]);
-        const float dia = fabsf(A[0][0]) + fabsf(A[1][1]) + fabsf(A[2][2]);
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) V[i][j] = (i == j) ? 1.0f : 0.0f;
+    for (int sweep = 0; sweep < 15; ++sweep) {
+        float off = 0.0f, dia = 0.0f;
+#pragma unroll
+        for (int p = 0; p < N; ++p) {
+            dia += fabsf(A[p][p]);
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) off += fabsf(A[p][q]);
+        }
         if (!(off > 1e-7f * dia)) break;
-        for (int p = 0; p < 2; ++p)
-            for (int q = p + 1; q < 3; ++q) {
+#pragma unroll
+        for (int p = 0; p < N - 1; ++p)
+#pragma unroll
+            for (int q = p + 1; q < N; ++q) {
                 if (A[p][q] == 0.0f) continue;
                 const float th = (A[q][q] - A[p][p]) / (2.0f * A[p][q]);
                 const float t = copysignf(1.0f, th) / (fabsf(th) + sqrtf(th * th + 1.0f));
                 const float c = rsqrtf(t * t + 1.0f), s = t * c;
-                for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
                     const float akp = A[k][p], akq = A[k][q];
                     A[k][p] = c * akp - s * akq;
                     A[k][q] = s * akp + c * akq;
                 }
-                for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
                     const float apk = A[p][k], aqk = A[q][k];
                     A[p][k] = c * apk - s * aqk;
                     A[q][k] = s * apk + c * aqk;
                 }
-                for (int k = 0; k < 3; ++k) {
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
                     const float vkp = V[k][p], vkq = V[k][q];
                     V[k][p] = c * vkp - s * vkq;
                     V[k][q] = s * vkp + c * vkq;
                 }
             }
     }
-    for (int i = 0; i < 3; ++i) w[i] = A[i][i];
+#pragma unroll
+    for (int i = 0; i < N; ++i) w[i] = A[i][i];
 }
 
-// U(t+h) and U~ per eigen-direction of zeta (alpha = lambda / m), written as
-// increments of U so that FP32 carries only the change:
-//   U' - U = (1 - e^-alpha) (F / lambda - U)                   (Eq. EOMUsol)
-//   U~ - U = ((1 - e^-alpha) / alpha - 1) U + (1 - (1 - e^-alpha) / alpha) F / lambda
-// (the consistency equation); a direction without links takes the limits
-// F / m and F / (2 m).  U stays FP64.
-__global__ void k_sph_update(double *vel, const double *mass, double mass0, const double *force, int n,
-                             const float *acc, float4 *ut)
+// The velocity update of N components (3: translation; 6: translation and
+// rotation) in the variables W = M^1/2 V, where dW/dt = -K W + G with
+// K = M^-1/2 Z M^-1/2 and G = M^-1/2 F; per eigen-direction of K (kappa),
+// written as increments of W so that FP32 carries only the change:
+//   W' - W = (1 - e^-kappa) (G / kappa - W)                       (Eq. EOMUsol)
+//   W~ - W = ((1 - e^-kappa) / kappa - 1) W + (1 - (1 - e^-kappa) / kappa) G / kappa
+// (the consistency equation); a direction without links takes the limits G
+// and G / 2.  V is FP64, V' = V + M^-1/2 (W' - W).
+template <int N>
+__device__ void velocity_update(const float Z[N][N], const float sq[N], double V[N], const float F[N], float Vt[N])
+{
+    float K[N][N], Q[N][N], w[N], Wf[N], G[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        Wf[i] = sq[i] * (float)V[i];
+        G[i] = F[i] / sq[i];
+#pragma unroll
+        for (int j = 0; j < N; ++j) K[i][j] = Z[i][j] / (sq[i] * sq[j]);
+    }
+    jacobi<N>(K, w, Q);
+    float dn[N], dt[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        float we = 0.0f, ge = 0.0f;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            we += Q[i][k] * Wf[i];
+            ge += Q[i][k] * G[i];
+        }
+        const float ka = w[k];
+        if (ka < 1e-6f) {
+            dn[k] = ge;
+            dt[k] = 0.5f * ge;
+        } else {
+            const float e1 = -expm1f(-ka), r = e1 / ka;
+            dn[k] = e1 * (ge / ka - we);
+            dt[k] = (r - 1.0f) * we + (1.0f - r) * ge / ka;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float sn = 0.0f, st = 0.0f;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            sn += Q[i][k] * dn[k];
+            st += Q[i][k] * dt[k];
+        }
+        Vt[i] = (float)V[i] + st / sq[i];
+        V[i] += (double)(sn / sq[i]);
+    }
+}
+
+// U(t+h), U~ (and with om Omega(t+h), Omega~) of each sphere; the moment of
+// inertia is 2/5 m a^2.
+__global__ void k_sph_update(double *vel, double *om, const double *mass, double mass0, double a, const double *force,
+                             int n, const float *acc, float4 *ut, float4 *uw)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const double m = mass ? mass[p] : mass0;
     const float *ac = acc + kAcc * p;
-    double U[3] = {vel[3 * p], vel[3 * p + 1], vel[3 * p + 2]};
-    if (!(m > 0.0)) {  // held fixed: the surface moves with U
-        ut[p] = make_float4((float)U[0], (float)U[1], (float)U[2], 0.0f);
+    if (!(m > 0.0)) {  // held fixed: the surface moves with U (+ Omega x rho)
+        ut[p] = make_float4((float)vel[3 * p], (float)vel[3 * p + 1], (float)vel[3 * p + 2], 0.0f);
+        uw[p] = om ? make_float4((float)om[3 * p], (float)om[3 * p + 1], (float)om[3 * p + 2], 0.0f)
+                   : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
-    float F[3], Uf[3];
-    for (int d = 0; d < 3; ++d) {
-        U[d] += (double)ac[3 + d] / m;  // fluid momentum of covered / uncovered nodes
-        F[d] = ac[d] + (force ? (float)force[3 * p + d] : 0.0f);
-        Uf[d] = (float)U[d];
-    }
-    float Z[3][3] = {{ac[6], ac[9], ac[11]}, {ac[9], ac[7], ac[10]}, {ac[11], ac[10], ac[8]}};
-    float w[3], V[3][3];
-    jacobi3(Z, w, V);
-    const float mf = (float)m;
-    float dne[3], dte[3];
-    for (int k = 0; k < 3; ++k) {
-        const float ue = V[0][k] * Uf[0] + V[1][k] * Uf[1] + V[2][k] * Uf[2];
-        const float fe = V[0][k] * F[0] + V[1][k] * F[1] + V[2][k] * F[2];
-        const float al = w[k] / mf;
-        if (al < 1e-6f) {
-            dne[k] = fe / mf;
-            dte[k] = 0.5f * fe / mf;
-        } else {
-            const float e1 = -expm1f(-al), r = e1 / al;
-            dne[k] = e1 * (fe / w[k] - ue);
-            dte[k] = (r - 1.0f) * ue + (1.0f - r) * fe / w[k];
+    const double I = 0.4 * m * a * a;
+    if (om) {
+        double V[6];
+        float F[6], Z[6][6], sq[6], Vt[6];
+        for (int d = 0; d < 3; ++d) {
+            V[d] = vel[3 * p + d] + (double)ac[3 + d] / m;  // covered / uncovered nodes
+            V[3 + d] = om[3 * p + d] + (double)ac[15 + d] / I;
+            F[d] = ac[d] + (force ? (float)force[3 * p + d] : 0.0f);
+            F[3 + d] = ac[12 + d];
+            sq[d] = sqrtf((float)m);
+            sq[3 + d] = sqrtf((float)I);
         }
+        const float tt[3][3] = {{ac[6], ac[9], ac[11]}, {ac[9], ac[7], ac[10]}, {ac[11], ac[10], ac[8]}};
+        const float rr[3][3] = {{ac[27], ac[30], ac[32]}, {ac[30], ac[28], ac[31]}, {ac[32], ac[31], ac[29]}};
+        for (int r = 0; r < 3; ++r)
+            for (int d = 0; d < 3; ++d) {
+                Z[r][d] = tt[r][d];
+                Z[3 + r][3 + d] = rr[r][d];
+                Z[r][3 + d] = ac[18 + 3 * r + d];
+                Z[3 + d][r] = ac[18 + 3 * r + d];
+            }
+        velocity_update<6>(Z, sq, V, F, Vt);
+        for (int d = 0; d < 3; ++d) {
+            vel[3 * p + d] = V[d];
+            om[3 * p + d] = V[3 + d];
+        }
+        ut[p] = make_float4(Vt[0], Vt[1], Vt[2], 0.0f);
+        uw[p] = make_float4(Vt[3], Vt[4], Vt[5], 0.0f);
+        return;
     }
-    float Ut[3];
-    for (int i = 0; i < 3; ++i) {
-        vel[3 * p + i] = U[i] + (double)(V[i][0] * dne[0] + V[i][1] * dne[1] + V[i][2] * dne[2]);
-        Ut[i] = Uf[i] + (V[i][0] * dte[0] + V[i][1] * dte[1] + V[i][2] * dte[2]);
+    double V[3];
+    float F[3], sq[3], Vt[3];
+    for (int d = 0; d < 3; ++d) {
+        V[d] = vel[3 * p + d] + (double)ac[3 + d] / m;
+        F[d] = ac[d] + (force ? (float)force[3 * p + d] : 0.0f);
+        sq[d] = sqrtf((float)m);
     }
-    ut[p] = make_float4(Ut[0], Ut[1], Ut[2], 0.0f);
+    const float Z[3][3] = {{ac[6], ac[9], ac[11]}, {ac[9], ac[7], ac[10]}, {ac[11], ac[10], ac[8]}};
+    velocity_update<3>(Z, sq, V, F, Vt);
+    for (int d = 0; d < 3; ++d) vel[3 * p + d] = V[d];
+    ut[p] = make_float4(Vt[0], Vt[1], Vt[2], 0.0f);
+    uw[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 }
 
 __global__ void k_sph_finish(double *pos, const double *vel, const double *mass, double mass0, const double *rh,
@@ -356,16 +481,25 @@ __global__ void k_sph_finish(double *pos, const double *vel, const double *mass,
     for (int d = 0; d < 3; ++d) pos[3 * p + d] = wrap_pos(__dadd_rn(rh[3 * p + d], 0.5 * vel[3 * p + d]), L[d]);
 }
 
+// Minimum image of d along an axis of length L (|d| < L).
+__device__ __forceinline__ float image_f(float d, int L)
+{
+    const float h = 0.5f * (float)L;
+    return d > h ? d - (float)L : (d < -h ? d + (float)L : d);
+}
+
 // Stream and collide fluid node (x, y, z) whose map entry is own (< 0): a
 // population whose source node is solid (sphere o) returns from the node
 // itself with the moving-wall term, n_i(r) = n*_-i(r) + 2 a_i rho0
-// U~_o.c_i / c_s^2 (Eq. MBB, c_b = -c_i); far fluid nodes pull without
-// looking at the map.
+// u_b.c_i / c_s^2 with u_b = U~_o + Omega~_o x (r_b - R_o), r_b = r - c_i / 2
+// (Eqs. MBB, NodeVel; c_b = -c_i); far fluid nodes pull without looking at
+// the map.  rot: the spheres rotate (uw, rh are read).
 template <bool NOISE>
 __device__ __forceinline__ void sphere_node(const float *__restrict__ src, float *__restrict__ dst,
                                             const float *__restrict__ ffield, const int *__restrict__ owner,
-                                            const float4 *__restrict__ ut, const StepArgs &a, int x, int y, int z,
-                                            int own)
+                                            const float4 *__restrict__ ut, const float4 *__restrict__ uw,
+                                            const double *__restrict__ rh, bool rot, const StepArgs &a, int x, int y,
+                                            int z, int own)
 {
     const size_t self = ((size_t)z * a.ny + y) * a.nx + x;
     const int xm = (x == 0) ? a.nx - 1 : x - 1, xp = (x == a.nx - 1) ? 0 : x + 1;
@@ -391,7 +525,18 @@ __device__ __forceinline__ void sphere_node(const float *__restrict__ src, float
             const int o = i == 0 ? kFar : __ldg(owner + t);
             if (o >= 0) {
                 const float4 v = __ldg(ut + o);
-                const float uc = lbd::cx(i) * v.x + lbd::cy(i) * v.y + lbd::cz(i) * v.z;
+                float ub[3] = {v.x, v.y, v.z};
+                if (rot) {
+                    const float4 w = __ldg(uw + o);
+                    const float rb[3] = {image_f((float)((double)x - 0.5 * lbd::cx(i) - rh[3 * o]), a.nx),
+                                         image_f((float)((double)y - 0.5 * lbd::cy(i) - rh[3 * o + 1]), a.ny),
+                                         image_f((float)((double)z - 0.5 * lbd::cz(i) - rh[3 * o + 2]), a.nz)};
+                    const float wv[3] = {w.x, w.y, w.z};
+                    float wr[3];
+                    cross3f(wv, rb, wr);
+                    for (int d = 0; d < 3; ++d) ub[d] += wr[d];
+                }
+                const float uc = lbd::cx(i) * ub[0] + lbd::cy(i) * ub[1] + lbd::cz(i) * ub[2];
                 n[i] = __ldg(src + (size_t)lbd::opposite(i) * P + self) + 6.0f * lbd::weight(i) * a.rho0 * uc;
             } else {
                 n[i] = __ldg(src + (size_t)i * P + t);
@@ -420,8 +565,9 @@ template <bool NOISE>
 __global__ void __launch_bounds__(kSphThreads) k_sph_near_nodes(const float *__restrict__ src, float *__restrict__ dst,
                                                                  const float *__restrict__ ffield,
                                                                  const int *__restrict__ owner,
-                                                                 const float4 *__restrict__ ut, const double *rh,
-                                                                 double a, int B, int n, StepArgs g)
+                                                                 const float4 *__restrict__ ut,
+                                                                 const float4 *__restrict__ uw, const double *rh,
+                                                                 bool rot, double a, int B, int n, StepArgs g)
 {
     __shared__ Box b;
     const int p = blockIdx.y;
@@ -432,7 +578,7 @@ __global__ void __launch_bounds__(kSphThreads) k_sph_near_nodes(const float *__r
     int x, y, z, o[3];
     box_node(b, B, k, g, x, y, z, o);
     if (__ldg(owner + ((size_t)z * g.ny + y) * g.nx + x) != kNear) return;
-    sphere_node<NOISE>(src, dst, ffield, owner, ut, g, x, y, z, kNear);
+    sphere_node<NOISE>(src, dst, ffield, owner, ut, uw, rh, rot, g, x, y, z, kNear);
 }
 
 int box_edge(double a) { return (int)std::ceil(2.0 * a) + 6; }
@@ -450,8 +596,9 @@ bool check_spheres(const lb_handle *h, const lb_spheres *s, const char *who)
         set_error("%s: need 0 <= n <= 65535 spheres and reserved = 0", who);
         return false;
     }
-    if (s->n > 0 && (!s->pos || !s->vel || ((uintptr_t)s->pos & 7u) || ((uintptr_t)s->vel & 7u))) {
-        set_error("%s: pos and vel must be 8-byte aligned device arrays", who);
+    if (s->n > 0 && (!s->pos || !s->vel || ((uintptr_t)s->pos & 7u) || ((uintptr_t)s->vel & 7u) ||
+                     ((uintptr_t)s->omega & 7u))) {
+        set_error("%s: pos, vel (and omega) must be 8-byte aligned device arrays", who);
         return false;
     }
     const int lmin = std::min(h->p.nx, std::min(h->p.ny, h->p.nz));
@@ -479,13 +626,16 @@ lb_status ensure_sphere_buffers(lb_handle *h, int n)
         cudaFree(h->sph_acc);
         cudaFree(h->sph_rh);
         cudaFree(h->sph_ut);
+        cudaFree(h->sph_uw);
         h->sph_acc = nullptr;
         h->sph_rh = nullptr;
         h->sph_ut = nullptr;
+        h->sph_uw = nullptr;
         h->sph_cap = 0;
         e = cudaMalloc((void **)&h->sph_acc, (size_t)n * kAcc * sizeof(float));
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->sph_rh, (size_t)n * 3 * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->sph_ut, (size_t)n * sizeof(float4));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->sph_uw, (size_t)n * sizeof(float4));
         if (e == cudaSuccess) h->sph_cap = n;
     }
     if (e != cudaSuccess) {
@@ -503,6 +653,8 @@ void destroy_spheres(lb_handle *h)
     cudaFree(h->sph_acc);
     cudaFree(h->sph_rh);
     cudaFree(h->sph_ut);
+    cudaFree(h->sph_uw);
+    h->sph_uw = nullptr;
     h->sph_owner = nullptr;
     h->sph_acc = nullptr;
     h->sph_rh = nullptr;
@@ -536,8 +688,8 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s)
                             h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->sph_acc, 0, (size_t)s->n * kAcc * sizeof(float), h->stream);
         if (e == cudaSuccess)
-            k_sph_links<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, static_cast<const float *>(h->pops[h->cur]),
-                                                             h->sph_rh, s->radius, B, s->n, g, h->sph_acc);
+            k_sph_links<false><<<grid, kSphThreads, 0, h->stream>>>(
+                h->sph_owner, static_cast<const float *>(h->pops[h->cur]), h->sph_rh, s->radius, B, s->n, g, h->sph_acc);
         h->launches += 2;
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -573,10 +725,16 @@ lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
         const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
         k_sph_half<<<pb, kSphThreads, 0, h->stream>>>(s->pos, s->vel, s->mass, s->mass0, n, h->sph_rh, h->sph_acc, g,
                                                       h->d_err);
-        k_sph_map<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->vel, s->radius, B, n, g,
-                                                       h->sph_acc, h->d_err);
-        k_sph_links<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g, h->sph_acc);
-        k_sph_update<<<pb, kSphThreads, 0, h->stream>>>(s->vel, s->mass, s->mass0, s->force, n, h->sph_acc, h->sph_ut);
+        k_sph_map<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->vel, s->omega, s->radius, B, n,
+                                                       g, h->sph_acc, h->d_err);
+        if (s->omega)
+            k_sph_links<true><<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g,
+                                                                   h->sph_acc);
+        else
+            k_sph_links<false><<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g,
+                                                                    h->sph_acc);
+        k_sph_update<<<pb, kSphThreads, 0, h->stream>>>(s->vel, s->omega, s->mass, s->mass0, s->radius, s->force, n,
+                                                        h->sph_acc, h->sph_ut, h->sph_uw);
         h->launches += 4;
         e = cudaGetLastError();
     }
@@ -587,12 +745,13 @@ lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
     if (e == cudaSuccess && n > 0) {  // then the near fluid nodes with the moving bounce-back
         const int B = box_edge(s->radius);
         const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
+        const bool rot = s->omega != nullptr;
         if (g.kT > 0.0f)
             k_sph_near_nodes<true><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
-                                                                        h->sph_rh, s->radius, B, n, g);
+                                                                        h->sph_uw, h->sph_rh, rot, s->radius, B, n, g);
         else
             k_sph_near_nodes<false><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
-                                                                         h->sph_rh, s->radius, B, n, g);
+                                                                         h->sph_uw, h->sph_rh, rot, s->radius, B, n, g);
         h->launches += 1;
         e = cudaGetLastError();
     }

@@ -82,7 +82,7 @@ class lb_spheres(C.Structure):
     _fields_ = [
         ("n", C.c_int), ("reserved", C.c_int), ("radius", C.c_double),
         ("pos", C.c_void_p), ("vel", C.c_void_p), ("mass", C.c_void_p), ("mass0", C.c_double),
-        ("force", C.c_void_p),
+        ("force", C.c_void_p), ("omega", C.c_void_p),
     ]
 
 
@@ -313,15 +313,16 @@ def lb_get_particle_forces(h, out):
     _check(load().lb_get_particle_forces(h, _ptr(out)))
 
 
-def spheres(n, pos, vel, radius, *, mass=None, mass0=1.0, force=None) -> lb_spheres:
-    """The sphere set the library updates in place (pos, vel: device FP64
-    [n][3]; mass: FP64 [n] or None; force: FP64 [n][3] or None); the struct
-    keeps the tensors alive."""
+def spheres(n, pos, vel, radius, *, mass=None, mass0=1.0, force=None, omega=None) -> lb_spheres:
+    """The sphere set the library updates in place (pos, vel, omega: device
+    FP64 [n][3], omega None for spheres that do not rotate; mass: FP64 [n] or
+    None; force: FP64 [n][3] or None); the struct keeps the tensors alive."""
     s = lb_spheres()
     s.n, s.reserved, s.radius = int(n), 0, float(radius)
     s.pos, s.vel, s.mass, s.force = _ptr(pos), _ptr(vel), _ptr(mass), _ptr(force)
+    s.omega = _ptr(omega)
     s.mass0 = float(mass0)
-    s._arrays = (pos, vel, mass, force)
+    s._arrays = (pos, vel, mass, force, omega)
     return s
 
 

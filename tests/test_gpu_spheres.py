@@ -20,30 +20,33 @@ def rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
 
-def _gpu_run(shape, pops0, R, U, rad, mass, steps, *, fc=None, **kw):
+def _gpu_run(shape, pops0, R, U, rad, mass, steps, *, fc=None, omega=None, **kw):
     lat = L.Lattice(shape, **kw)
     lat.set_populations(torch.as_tensor(pops0).cuda())
     pos = torch.as_tensor(np.array(R, dtype=np.float64)).cuda()
     vel = torch.as_tensor(np.array(U, dtype=np.float64)).cuda()
     m = torch.as_tensor(np.array(mass, dtype=np.float64)).cuda()
     f = None if fc is None else torch.as_tensor(np.array(fc, dtype=np.float64)).cuda()
-    s = L.spheres(len(mass), pos, vel, rad, mass=m, force=f)
+    om = None if omega is None else torch.as_tensor(np.array(omega, dtype=np.float64)).cuda()
+    s = L.spheres(len(mass), pos, vel, rad, mass=m, force=f, omega=om)
     L.lb_spheres_place(lat.h, s)
     for _ in range(steps):
         L.lb_step_spheres(lat.h, s)
     own = torch.empty(lat.n_nodes, dtype=torch.int32, device="cuda")
     L.lb_get_solid_map(lat.h, own)
     st = lat.sync()
-    return (lat.get_populations().cpu().numpy(), own.cpu().numpy().reshape(shape[::-1]), pos.cpu().numpy(),
-            vel.cpu().numpy(), st, lat)
+    out = (lat.get_populations().cpu().numpy(), own.cpu().numpy().reshape(shape[::-1]), pos.cpu().numpy(),
+           vel.cpu().numpy(), st, lat)
+    return out if om is None else out + (om.cpu().numpy(),)
 
 
-def _ora_run(ora, p, pops, R, U, rad, mass, steps, fc=None):
+def _ora_run(ora, p, pops, R, U, rad, mass, steps, fc=None, omega=None):
     owner = ora.sphere_owner(p, R, rad)
     for t in range(steps):
-        pops, owner, R, U, _, ut, st = ora.step_spheres(p, pops, owner, R, U, rad, mass, fc=fc, step=t)
+        pops, owner, R, U, omega, ut, st = ora.step_spheres(p, pops, owner, R, U, rad, mass, fc=fc, step=t,
+                                                            omega=omega)
         assert st == 0
-    return pops, owner, R, U
+    return pops, owner, R, U, omega
 
 
 @pytest.mark.parametrize("kT,shape", [(0.0, (16, 16, 16)), (1e-4, (16, 16, 16)), (1e-4, (17, 16, 15))])
@@ -67,6 +70,32 @@ def test_moving_spheres_parity(ora, kT, shape):
     assert rel(got[0][:, fl] - aa, want[0][:, fl] - aa) < 2e-6
     assert np.abs(got[2] - want[2]).max() < 1e-6
     assert rel(got[3], want[3]) < 1e-5
+
+
+@pytest.mark.parametrize("kT", [0.0, 1e-4])
+def test_rotating_spheres_parity(ora, kT):
+    """Spheres with angular velocities (Eq. NodeVel): maps, populations,
+    velocities and angular velocities against the oracle."""
+    shape = (16, 16, 16)
+    kw = dict(kT=kT, seed=3, gamma_shear=0.1)
+    p = ora.make_params(shape, **kw)
+    pops0 = ora.equilibrium(p, None, inputs.shear_wave(shape, 0.01))
+    R = np.array([[4.3, 5.1, 6.2], [11.2, 10.7, 9.9]])
+    U = np.array([[0.05, -0.03, 0.02], [-0.04, 0.02, 0.06]])
+    Om = np.array([[0.01, -0.02, 0.015], [0.0, 0.02, -0.01]])
+    mass = [40.0, 60.0]
+    want = _ora_run(ora, p, pops0, R, U, 2.6, mass, 12, omega=Om)
+    got = _gpu_run(shape, pops0, R, U, 2.6, mass, 12, omega=Om, **kw)
+    assert got[4] == (L.LB_OK, 0)
+    assert np.array_equal(got[1], want[1])
+    fl = want[1] < 0
+    c, a, e, w, opp = ora.tables()
+    aa = a[:, None]
+    assert rel(got[0][:, fl] - aa, want[0][:, fl] - aa) < 2e-6
+    assert np.abs(got[2] - want[2]).max() < 1e-6
+    assert rel(got[3], want[3]) < 1e-5
+    assert rel(got[6], want[4]) < 1e-5
+    assert np.abs(want[4] - Om).max() > 1e-4
 
 
 def test_spheres_conserve_momentum_gpu(ora):
