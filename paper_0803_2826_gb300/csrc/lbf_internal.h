@@ -83,6 +83,9 @@ struct lb_handle {
     double *sph_rh;       // [sph_cap][3] half-step centres
     float4 *sph_ut;       // [sph_cap] U~
     float4 *sph_uw;       // [sph_cap] Omega~ (0 for spheres that do not rotate)
+    int *sph_list;        // near fluid nodes of the current step (linear indices)
+    size_t sph_list_cap;
+    unsigned int *sph_count;  // entries in sph_list
     int sph_cap;
     int sph_n;            // spheres of the current solid map (-1: none placed)
     double sph_a;

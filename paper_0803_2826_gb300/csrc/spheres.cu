@@ -15,7 +15,7 @@
 //                  by FP32 Jacobi rotations; U kept in FP64)
 //   the plain stream-collide launch over every node (exact for fluid nodes
 //                  without a solid neighbour), then
-//   k_sph_near_nodes  per sphere, the near fluid nodes of its box again: pull
+//   k_sph_near_nodes  the near fluid nodes (listed by k_sph_links) again: pull
 //                  streaming in which a population whose source node is solid
 //                  returns as n*_-i(r) + 6 a_i rho0 U~.c_i, then the same
 //                  collision
@@ -134,9 +134,10 @@ __global__ void k_sph_place(int *owner, const double *pos, double a, int B, int 
 }
 
 __global__ void k_sph_half(const double *pos, const double *vel, const double *mass, double mass0, int n, double *rh,
-                           float *acc, StepArgs g, unsigned int *err)
+                           float *acc, unsigned int *count, StepArgs g, unsigned int *err)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p == 0) *count = 0u;  // the near-node list of this step
     if (p >= n) return;
     const double m = mass ? mass[p] : mass0;
     const int L[3] = {g.nx, g.ny, g.nz};
@@ -223,7 +224,8 @@ __global__ void k_sph_map(int *owner, float *pops, const double *rh, const doubl
 // near (a solid neighbour of any sphere) or far on the way.
 template <bool ROT>
 __global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const float *pops, const double *rh,
-                                                            double a, int B, int n, StepArgs g, float *acc)
+                                                            double a, int B, int n, StepArgs g, float *acc,
+                                                            int *list, unsigned int *count)
 {
     constexpr int NV = ROT ? 27 : 9;
     __shared__ float red[kSphThreads / 32][NV];
@@ -235,10 +237,12 @@ __global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const flo
     for (int q = 0; q < NV; ++q) v[q] = 0.0f;
     const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
     box_setup(b, c, a);
+    bool add = false;  // a near node for the list of the re-update
+    size_t s = 0;
     if (p < n && k < B * B * B) {
         int x, y, z, o[3];
         box_node(b, B, k, g, x, y, z, o);
-        const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
+        s = ((size_t)z * g.ny + y) * g.nx + x;
         const int own = owner[s];
         const float dx = (float)o[0] - b.cf[0], dy = (float)o[1] - b.cf[1], dz = (float)o[2] - b.cf[2];
         const float rf = (float)a + 2.5f;
@@ -287,6 +291,18 @@ __global__ void __launch_bounds__(kSphThreads) k_sph_links(int *owner, const flo
             }
             const int mark = near ? kNear : kFar;
             if (own != mark) owner[s] = mark;
+            add = near;
+        }
+    }
+    {  // append the near nodes, one atomic per warp (a node near two spheres
+       // appears twice and is recomputed with the same value)
+        const unsigned ball = __ballot_sync(0xffffffffu, add);
+        if (ball) {
+            const int lane = threadIdx.x & 31, leader = __ffs(ball) - 1;
+            unsigned int base = 0;
+            if (lane == leader) base = atomicAdd(count, (unsigned int)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (add) list[base + __popc(ball & ((1u << lane) - 1u))] = (int)s;
         }
     }
 #pragma unroll
@@ -556,29 +572,26 @@ __device__ __forceinline__ void sphere_node(const float *__restrict__ src, float
     for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = out[i];
 }
 
-// The near fluid nodes of each sphere's box, after the plain update of all
-// nodes: every fluid node without a solid neighbour is exact from that
-// update (solid nodes hold values nobody reads), the near ones are done
-// again here with the moving bounce-back.  A node near two spheres is
-// written twice with the same value.
+// The near fluid nodes (the list k_sph_links built this step), after the
+// plain update of all nodes: every fluid node without a solid neighbour is
+// exact from that update (solid nodes hold values nobody reads), the near
+// ones are done again here with the moving bounce-back.  Grid-stride over
+// the list.
 template <bool NOISE>
 __global__ void __launch_bounds__(kSphThreads) k_sph_near_nodes(const float *__restrict__ src, float *__restrict__ dst,
                                                                  const float *__restrict__ ffield,
                                                                  const int *__restrict__ owner,
                                                                  const float4 *__restrict__ ut,
                                                                  const float4 *__restrict__ uw, const double *rh,
-                                                                 bool rot, double a, int B, int n, StepArgs g)
+                                                                 bool rot, const int *list,
+                                                                 const unsigned int *count, StepArgs g)
 {
-    __shared__ Box b;
-    const int p = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const double c[3] = {rh[3 * p], rh[3 * p + 1], rh[3 * p + 2]};
-    box_setup(b, c, a);
-    if (p >= n || k >= B * B * B) return;
-    int x, y, z, o[3];
-    box_node(b, B, k, g, x, y, z, o);
-    if (__ldg(owner + ((size_t)z * g.ny + y) * g.nx + x) != kNear) return;
-    sphere_node<NOISE>(src, dst, ffield, owner, ut, uw, rh, rot, g, x, y, z, kNear);
+    const unsigned int nl = *count;
+    for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < nl; q += gridDim.x * blockDim.x) {
+        const int s = list[q];
+        const int x = s % g.nx, y = (s / g.nx) % g.ny, z = s / (g.nx * g.ny);
+        sphere_node<NOISE>(src, dst, ffield, owner, ut, uw, rh, rot, g, x, y, z, kNear);
+    }
 }
 
 int box_edge(double a) { return (int)std::ceil(2.0 * a) + 6; }
@@ -618,10 +631,20 @@ lb_status spheres_supported(const lb_handle *h, const char *who)
     return LB_OK;
 }
 
-lb_status ensure_sphere_buffers(lb_handle *h, int n)
+lb_status ensure_sphere_buffers(lb_handle *h, int n, double radius)
 {
     cudaError_t e = cudaSuccess;
     if (!h->sph_owner) e = cudaMalloc((void **)&h->sph_owner, h->n_nodes * sizeof(int));
+    if (e == cudaSuccess && !h->sph_count) e = cudaMalloc((void **)&h->sph_count, sizeof(unsigned int));
+    const int B = box_edge(radius);
+    const size_t need = (size_t)n * B * B * B;  // every box node of every sphere at most once
+    if (e == cudaSuccess && h->sph_list_cap < need) {
+        cudaFree(h->sph_list);
+        h->sph_list = nullptr;
+        h->sph_list_cap = 0;
+        e = cudaMalloc((void **)&h->sph_list, need * sizeof(int));
+        if (e == cudaSuccess) h->sph_list_cap = need;
+    }
     if (e == cudaSuccess && h->sph_cap < n) {
         cudaFree(h->sph_acc);
         cudaFree(h->sph_rh);
@@ -654,7 +677,12 @@ void destroy_spheres(lb_handle *h)
     cudaFree(h->sph_rh);
     cudaFree(h->sph_ut);
     cudaFree(h->sph_uw);
+    cudaFree(h->sph_list);
+    cudaFree(h->sph_count);
     h->sph_uw = nullptr;
+    h->sph_list = nullptr;
+    h->sph_count = nullptr;
+    h->sph_list_cap = 0;
     h->sph_owner = nullptr;
     h->sph_acc = nullptr;
     h->sph_rh = nullptr;
@@ -675,7 +703,7 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s)
     lb_status st = spheres_supported(h, "lb_spheres_place");
     if (st != LB_OK) return st;
     join_overlap(h);
-    st = ensure_sphere_buffers(h, std::max(s->n, 1));
+    st = ensure_sphere_buffers(h, std::max(s->n, 1), s->radius);
     if (st != LB_OK) return st;
     const StepArgs g = make_args(h);
     cudaError_t e = cudaMemsetAsync(h->sph_owner, 0xff, h->n_nodes * sizeof(int), h->stream);  // all fluid
@@ -687,9 +715,11 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s)
         e = cudaMemcpyAsync(h->sph_rh, s->pos, (size_t)s->n * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
                             h->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(h->sph_acc, 0, (size_t)s->n * kAcc * sizeof(float), h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->sph_count, 0, sizeof(unsigned int), h->stream);
         if (e == cudaSuccess)
             k_sph_links<false><<<grid, kSphThreads, 0, h->stream>>>(
-                h->sph_owner, static_cast<const float *>(h->pops[h->cur]), h->sph_rh, s->radius, B, s->n, g, h->sph_acc);
+                h->sph_owner, static_cast<const float *>(h->pops[h->cur]), h->sph_rh, s->radius, B, s->n, g, h->sph_acc,
+                h->sph_list, h->sph_count);
         h->launches += 2;
         if (e == cudaSuccess) e = cudaGetLastError();
     }
@@ -723,16 +753,16 @@ lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
         const int B = box_edge(s->radius);
         const unsigned pb = (unsigned)((n + kSphThreads - 1) / kSphThreads);
         const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
-        k_sph_half<<<pb, kSphThreads, 0, h->stream>>>(s->pos, s->vel, s->mass, s->mass0, n, h->sph_rh, h->sph_acc, g,
-                                                      h->d_err);
+        k_sph_half<<<pb, kSphThreads, 0, h->stream>>>(s->pos, s->vel, s->mass, s->mass0, n, h->sph_rh, h->sph_acc,
+                                                      h->sph_count, g, h->d_err);
         k_sph_map<<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->vel, s->omega, s->radius, B, n,
                                                        g, h->sph_acc, h->d_err);
         if (s->omega)
             k_sph_links<true><<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g,
-                                                                   h->sph_acc);
+                                                                   h->sph_acc, h->sph_list, h->sph_count);
         else
             k_sph_links<false><<<grid, kSphThreads, 0, h->stream>>>(h->sph_owner, src, h->sph_rh, s->radius, B, n, g,
-                                                                    h->sph_acc);
+                                                                    h->sph_acc, h->sph_list, h->sph_count);
         k_sph_update<<<pb, kSphThreads, 0, h->stream>>>(s->vel, s->omega, s->mass, s->mass0, s->radius, s->force, n,
                                                         h->sph_acc, h->sph_ut, h->sph_uw);
         h->launches += 4;
@@ -743,15 +773,16 @@ lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
         h->launches += 1;
     }
     if (e == cudaSuccess && n > 0) {  // then the near fluid nodes with the moving bounce-back
-        const int B = box_edge(s->radius);
-        const dim3 grid((unsigned)((B * B * B + kSphThreads - 1) / kSphThreads), (unsigned)n);
+        const unsigned grid = (unsigned)(4 * device_sm_count());
         const bool rot = s->omega != nullptr;
         if (g.kT > 0.0f)
             k_sph_near_nodes<true><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
-                                                                        h->sph_uw, h->sph_rh, rot, s->radius, B, n, g);
+                                                                        h->sph_uw, h->sph_rh, rot, h->sph_list,
+                                                                        h->sph_count, g);
         else
             k_sph_near_nodes<false><<<grid, kSphThreads, 0, h->stream>>>(src, dst, h->force, h->sph_owner, h->sph_ut,
-                                                                         h->sph_uw, h->sph_rh, rot, s->radius, B, n, g);
+                                                                         h->sph_uw, h->sph_rh, rot, h->sph_list,
+                                                                         h->sph_count, g);
         h->launches += 1;
         e = cudaGetLastError();
     }
