@@ -40,7 +40,7 @@ def _deps():
 
 
 # the files that define the fused stream-collide kernel
-STREAM_COLLIDE_FILES = ("d3q19.cuh", "stream_collide.cuh", "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu", "lbf_internal.h")
+STREAM_COLLIDE_FILES = ("d3q19.cuh", "stream_collide.cuh", "sc_f32.cu", "sc_f16.cu", "sc_bf16.cu", "step_args.h")
 
 
 def source_hash(files=None) -> str:
