@@ -14,7 +14,7 @@ Function -> passage it follows:
   tables()        Sec. 3.3 (D3Q19 weights), Sec. 3.4 Table 1 and Eq. (weights_unweighted)
   philox()        Philox4x32-10 of Salmon et al., SC'11 (noise source for Sec. 3.5)
   equilibrium()   Sec. 3.3, Eq. (original_equil_distrib)
-  step()          Eq. (LBE) streaming; Sec. 3.4-3.5 MRT collision with noise,
+  step(), step_nodes()  Eq. (LBE) streaming; Sec. 3.4-3.5 MRT collision with noise,
                   Eqs. (lco_update), (stochupdaterule1), (detailedbalance1);
                   Sec. 3.7 forcing; Sec. 4.1 Eq. (MBB) with u_b = 0 for walls
   moments()       Sec. 3.4 Eqs. (hmodes_beg)-(hmodes_end); Sec. 3.7 for j
@@ -140,6 +140,7 @@ def _load():
             lib.ora_sphere_velocity6.argtypes = [_D, C.c_double, C.c_double, _D, _D, _D, _D]
             lib.ora_step_spheres.restype = C.c_int
             lib.ora_exp_equilibrium.argtypes = [C.c_double, _D, _D]
+            lib.ora_step_nodes.argtypes = [P, _D, _D, C.c_uint32, C.c_int, C.POINTER(C.c_longlong), _D]
             lib.ora_phi.argtypes = [C.c_int, C.c_double]
             lib.ora_phi.restype = C.c_double
             lib.ora_adjoint_step.argtypes = [P, _D, _D, _D, _D, _D]
@@ -432,6 +433,19 @@ def effective_friction(kernel, offset, *, L=16, steps=1500, F=1e-4, a0=1.0, mass
     a = F / (6.0 * np.pi * eta * U)
     g = 1.0 / (1.0 / a + 2.84 / L - 1.0 / a0)
     return dict(u0=u0, u0_prev=u0_prev, U=U, a=a, g=g)
+
+
+def step_nodes(p: Params, pops, idx, force=None, step_index=0):
+    """step() evaluated at the listed fluid nodes only (linear indices):
+    returns (len(idx), 19) post-collision populations."""
+    lib = _load()
+    src = np.ascontiguousarray(pops, dtype=np.float64)
+    f = None if force is None else np.ascontiguousarray(force, dtype=np.float64)
+    ix = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.empty((ix.shape[0], 19))
+    lib.ora_step_nodes(C.byref(p), _dp(src), _dp(f), int(step_index) & 0xffffffff, ix.shape[0],
+                       ix.ctypes.data_as(C.POINTER(C.c_longlong)), _dp(out))
+    return out
 
 
 def exp_equilibrium(rho, u):

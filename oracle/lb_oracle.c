@@ -1655,3 +1655,28 @@ int ora_step_spheres(const ora_params *P, const double *src, double *dst, const 
     free(cur); free(nown); free(Rh); free(Vt); free(F0); free(Z); free(dP);
     return status;
 }
+
+/* The step of ora_step restricted to the listed nodes (linear indices of
+ * fluid nodes): the same pull, force and collision with the noise of the
+ * node; out[k][19] receives the post-collision populations of node idx[k].
+ * Lets a test check sampled nodes of a box too large to step whole. */
+void ora_step_nodes(const ora_params *P, const double *src, const double *force, uint32_t step, int nsel,
+                    const long long *idx, double *out)
+{
+    build_tables();
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nsel; k++) {
+        size_t s = (size_t)idx[k];
+        int x = (int)(s % (size_t)P->nx), y = (int)((s / (size_t)P->nx) % (size_t)P->ny);
+        int z = (int)(s / ((size_t)P->nx * P->ny));
+        double n[Q], f[3], g[16];
+        gather(P, src, x, y, z, n);
+        node_force(P, force, s, f);
+        const double *r = NULL;
+        if (P->kT > 0.0) {
+            ora_gaussians(P->seed, (uint32_t)s, step, 0u, P->replica, 4, g);
+            r = g;
+        }
+        collide(P, n, f, r, out + (size_t)Q * k);
+    }
+}

@@ -257,3 +257,17 @@ def test_two_rate_poiseuille_is_exact(ora, ge):
         else:
             assert dev > 1e-3, dev
 
+
+
+def test_step_nodes_is_step_at_those_nodes(ora):
+    """step_nodes (used to check sampled nodes of large boxes) returns step()'s
+    values at the listed nodes, with walls, noise and a force field."""
+    shape = (7, 6, 9)
+    p = ora.make_params(shape, kT=1e-4, seed=3, walls=True, gamma_shear=0.1)
+    pops = ora.equilibrium(p, None, inputs.shear_wave(shape, 0.02))
+    field = inputs.gaussian_field(shape, 3, 1e-4, seed=4)
+    full = ora.step(p, pops, field, 5)
+    rng = np.random.default_rng(0)
+    idx = rng.choice(np.arange(shape[0] * shape[1], shape[0] * shape[1] * (shape[2] - 1)), 40, replace=False)
+    part = ora.step_nodes(p, pops, idx, field, 5)
+    assert np.array_equal(part, full.reshape(19, -1)[:, idx].T)
