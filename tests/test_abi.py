@@ -92,3 +92,29 @@ def test_null_handles_rejected(lib):
     assert raw.lb_moments(None, None, None, None, None) == lib.LB_EINVAL
     assert raw.lb_destroy(None) == lib.LB_OK
     assert raw.lb_noise_words(0, 0, 0, 0, 0, 4, 5, None, None, None) == lib.LB_EINVAL
+
+
+def test_struct_layouts_match_header(lib, tmp_path):
+    """Size and every field offset of the ABI structs, from the C compiler
+    (gcc on include/lbfluct.h) against the ctypes binding."""
+    import shutil
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    structs = [lib.lb_params, lib.lb_particles, lib.lb_couple_params, lib.lb_spheres, lib.lb_batch_config]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "lbfluct.h"', "int main(void) {"]
+    for st in structs:
+        name = st.__name__
+        lines.append('printf("%%zu\\n", sizeof(%s));' % name)
+        for field in st._fields_:
+            lines.append('printf("%%zu\\n", offsetof(%s, %s));' % (name, field[0]))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = []
+    for st in structs:
+        want.append(C.sizeof(st))
+        want += [getattr(st, f[0]).offset for f in st._fields_]
+    assert got == want
