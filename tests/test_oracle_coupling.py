@@ -243,3 +243,24 @@ def test_wca_cutoff_and_fene_limits(ora):
     pos = np.array([[5.0, 5.0, 5.0], [6.6, 5.0, 5.0]])  # bond beyond R0
     F, broken = ora.md_forces(p, md, pos)
     assert broken == 2  # counted once from each end
+
+
+def test_particles_thermalise_with_the_fluid_at_weak_friction(ora):
+    """Sec. 4.5: the coupled fluid-particle system satisfies the
+    fluctuation-dissipation theorem, so free particles in a thermal fluid
+    reach <p^2>/(3m) = kT.  At weak friction (Gamma mu_inf ~ 0.06) the
+    discrete scheme (fluid frozen over the LB step, u without the particles'
+    own half force) gives kT to a few per cent; the temperature at stronger
+    friction is a measured property of the scheme, not a pin."""
+    shape, kT, n = (8, 8, 8), 1e-3, 200
+    p = ora.make_params(shape, kT=kT, seed=1)
+    pops = ora.equilibrium(p)
+    pos = inputs.uniform_particles(n, shape, seed=2)
+    mom = np.zeros((n, 3))
+    T = []
+    for t in range(600):
+        pos, mom, facc, _ = ora.couple(p, pops, pos, mom, 1.0, 0.2, dt=0.1, n_substeps=10, seed=3, md_step0=10 * t)
+        pops = ora.step(p, pops, facc, t)
+        if t >= 200:
+            T.append((mom ** 2).mean())
+    assert abs(np.mean(T) / kT - 1) < 0.06
