@@ -31,7 +31,12 @@
  *    Box-Muller pairs;
  *  - interpolation: phi_2 by default, phi_3 / phi_4 on request (Sec. 4.6);
  *    with walls a particle stays K/2 lattice units from the solid planes,
- *    K the stencil width.
+ *    K the stencil width;
+ *  - the fluid receives the impulse of the drag and random forces of each
+ *    sub-step, J = p' - p - h F^c (Eq. ftotal);
+ *  - the exponential equilibrium (Eq. equildist_lagrange) replaces the
+ *    quadratic one in the collision when params.equilibrium = 1;
+ *  - solid spheres: see the section on extended particles below.
  */
 #include <math.h>
 #ifdef _OPENMP
