@@ -21,6 +21,33 @@ namespace lbi {
 
 namespace {
 
+// x_i = exp(lambda.c_i) - 1 for the 18 moving directions from three
+// expm1 values: with e_d = exp(+-lambda_d) - 1 (exp(-a) - 1 = -x / (1 + x)
+// for x = exp(a) - 1) and (1 + x)(1 + e) - 1 = x + e + x e over the (one or
+// two) non-zero components of c_i.
+__device__ __forceinline__ void exp_dirs(const float l[3], float x[19])
+{
+    float ep[3], em[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        ep[d] = expm1f(l[d]);
+        em[d] = -ep[d] / (1.0f + ep[d]);
+    }
+    x[0] = 0.0f;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const int c3[3] = {lbd::cx(i), lbd::cy(i), lbd::cz(i)};
+        float xi = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (c3[d] != 0) {
+                const float e = c3[d] > 0 ? ep[d] : em[d];
+                xi = xi + e + xi * e;
+            }
+        x[i] = xi;
+    }
+}
+
 // Deviation moments meq[k] of n^eq - a rho0 (Table 1 transform).
 __device__ __forceinline__ void exp_eq_moments(float drho, float rho, float ux, float uy, float uz, float meq[19])
 {
@@ -30,10 +57,11 @@ __device__ __forceinline__ void exp_eq_moments(float drho, float rho, float ux, 
 #pragma unroll 1
     for (int it = 0; it < 2; ++it) {
         float s = 0.0f, m[3] = {0.f, 0.f, 0.f}, C[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        exp_dirs(l, x);
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const float cx = lbd::cx(i), cy = lbd::cy(i), cz = lbd::cz(i);
-            const float xi = expm1f(l[0] * cx + l[1] * cy + l[2] * cz);
+            const float xi = x[i];
             const float w = lbd::weight(i) * xi;
             s += w;
             m[0] += w * cx;
@@ -63,12 +91,9 @@ __device__ __forceinline__ void exp_eq_moments(float drho, float rho, float ux, 
         l[2] += id * (c02 * r[0] + c12 * r[1] + c22 * r[2]);
     }
     float s = 0.0f;
-    x[0] = 0.0f;
+    exp_dirs(l, x);
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        x[i] = expm1f(l[0] * lbd::cx(i) + l[1] * lbd::cy(i) + l[2] * lbd::cz(i));
-        s += lbd::weight(i) * x[i];
-    }
+    for (int i = 1; i < 19; ++i) s += lbd::weight(i) * x[i];
     const float g = rho / (1.0f + s);
     float d[19];
 #pragma unroll
