@@ -340,18 +340,22 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s);
 
 /* One LB step with the spheres (h = 1; Sec. 4.1 Eq. (MBB), Sec. 4.2):
  *  1. R(t+h/2) = R + U/2 (Eq. EOMD-1); the solid map moves with the
- *     centres: a covered fluid node gives its momentum sum n c to its
- *     sphere, an uncovered node starts from n^eq(rho0, U(t)) and the sphere
- *     loses rho0 U(t);
+ *     centres: a covered fluid node gives its momentum sum n c (and its
+ *     moment about the centre) to its sphere, an uncovered node starts from
+ *     n^eq(rho0, u) with u = U(t) (+ Omega(t) x (r - R)) and the sphere loses
+ *     rho0 u;
  *  2. over the boundary links b (fluid node r, r + c_b solid):
  *     F0 = sum 2 n*_b c_b, zeta = (2 rho0 / c_s^2) sum a_b c_b c_b^T
  *     (Eqs. force0, zeta); with rotation also the torque and the coupled
  *     6 x 6 friction of g = (c_b, (r_b - R) x c_b), r_b = r + c_b/2;
  *  3. U(t+h) = e^-A U + zeta^-1 (1 - e^-A)(F0 + F^c), A = zeta / m
  *     (Eq. EOMUsol in zeta's eigenbasis), and U~ of the consistency
- *     equation, so that m (U(t+h) - U(t)) = F0 + F^c - zeta U~;
+ *     equation, so that m (U(t+h) - U(t)) = F0 + F^c - zeta U~ (with
+ *     rotation the same for (U, Omega) with the 6 x 6 friction and
+ *     M = diag(m, m, m, I, I, I));
  *  4. stream and collide the fluid nodes; a population whose source node is
- *     solid returns as n_i(r) = n*_-i(r) + 2 a_i rho0 U~.c_i / c_s^2 (Eq. MBB);
+ *     solid returns as n_i(r) = n*_-i(r) + 2 a_i rho0 u_b.c_i / c_s^2 with
+ *     u_b = U~ (+ Omega~ x (r_b - R)) (Eqs. MBB, NodeVel);
  *  5. R(t+h) = R(t+h/2) + U(t+h)/2 (Eq. EOMD-3).
  * Total momentum of fluid and spheres is conserved (plus the external
  * forces).  Sphere velocities must stay below one node per step.  Point
