@@ -4,12 +4,17 @@ times: 256^3 fluctuating FP32 fluid (kT = 1e-4) with 64 FENE/WCA chains x
 update on the cooperative kernel.  After two coupled steps on the GPU, a
 third one is checked against the FP64 oracle:
 
-- every particle's position (1e-6 absolute) and momentum (2e-4 relative),
-  the oracle running the whole coupling call from the GPU's state;
+- every particle's position and momentum, the oracle running the whole
+  coupling call from the GPU's state (momenta ~1e-5 relative, the FP32
+  rounding of the positions amplified by the steep WCA force);
 - the post-step populations at sampled nodes, which the oracle evaluates one
-  by one (step_nodes): 2e-6 relative at nodes without particle impulses, and
-  2e-4 at impulse nodes, where the FP32 impulses (about 1e-4 relative from
-  the oracle's) enter through the force term.
+  by one (step_nodes), at nodes without particle impulses and at impulse
+  nodes, where the FP32 impulses enter through the force term.
+
+Each check asserts the relative L2 error and the worst element at about
+three times the errors measured on a GB300 (positions 3.9e-7; momenta
+9.5e-6 / 1.4e-5; populations 1.7e-7 / 1.8e-7 without and 8.3e-7 / 1.3e-6
+with impulses).
 """
 import numpy as np
 import pytest
@@ -19,6 +24,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_0803_2826_gb300 import inputs  # noqa: E402
 from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+from parity_util import check, check_pos  # noqa: E402
 
 
 def rel(a, b):
@@ -55,10 +61,8 @@ def test_bench_workload_parity(ora):
     opos, omom, facc, broken = ora.couple(p, state, pos, mom, mass, gamma, dt=dt, n_substeps=nsub, seed=7,
                                           md_step0=nsub * 2, md=md)
     assert broken == 0
-    d = gpos.cpu().numpy() - opos
-    d -= 256.0 * np.round(d / 256.0)
-    assert np.abs(d).max() < 1e-6
-    assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 2e-4
+    check_pos("fullsize positions", gpos.cpu().numpy(), opos, shape, 1.2e-6)
+    check("fullsize momenta", gmom.cpu().numpy().astype(np.float64), omom, 3e-5, 4.5e-5)
 
     f32 = facc.astype(np.float32).astype(np.float64)
     hit = np.flatnonzero(np.abs(f32).sum(0).ravel() > 0)
@@ -67,6 +71,6 @@ def test_bench_workload_parity(ora):
     busy = rng.choice(hit, 400, replace=False)
     c, a, e, w, opp = ora.tables()
     got = lat.get_populations().cpu().numpy().reshape(19, -1)
-    for idx, tol in ((quiet, 2e-6), (busy, 2e-4)):
+    for tag, idx, bar in (("quiet", quiet, (5e-7, 6e-7)), ("busy", busy, (2.5e-6, 4e-6))):
         want = ora.step_nodes(p, state, idx, f32, 2)
-        assert rel(got[:, idx].T - a, want - a) < tol, (tol, rel(got[:, idx].T - a, want - a))
+        check("fullsize populations at %s nodes" % tag, got[:, idx].T - a, want - a, *bar)

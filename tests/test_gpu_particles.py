@@ -1,11 +1,21 @@
 """GPU parity of the point-particle coupling (Sec. 4.5, 4.6) and the
 Kremer-Grest forces (Sec. 2.1) against the FP64 oracle, through the C ABI.
 
-Tolerances: positions to 1e-6 absolute (FP64 positions, FP32 increments);
-momenta and spread impulses to 2e-4 relative (FP32 arithmetic for the
-interpolation and the OU update); the LB step that applies the impulses to
-the same 2e-6 as the plain step.
+Every comparison asserts the field-wide relative L2 error and the worst
+element (relative to the field's largest entry); the bars are about three
+times the errors measured on a GB300:
+  - positions: 1e-6 absolute (FP32 cell offsets: ~3e-7 measured);
+  - free particles (no pair forces): momenta, spread impulses and the
+    populations after the LB step that applies them at ~2e-7 relative
+    (FP32 rounding of the interpolation and the OU update);
+  - FENE/WCA chains: momenta ~1e-5, impulses ~3e-6.  The WCA force is steep
+    (d ln F / d ln r ~ 14 at r ~ sigma), so the ~2e-7 rounding of the FP32
+    offsets over the sub-steps becomes ~3e-6 in a force and ~1e-5 in the
+    momentum it accumulates; the impulses to the fluid, which see the forces
+    only through (C2 - dt) F^c, stay smaller.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -14,6 +24,30 @@ pytestmark = pytest.mark.gpu
 
 from paper_0803_2826_gb300 import inputs  # noqa: E402
 from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+from parity_util import check, check_pos  # noqa: E402
+
+# Bars (relative L2, worst element relative to the field's largest entry);
+# see the module docstring.
+MOM = (6e-7, 1e-6)          # free particles
+FACC = (1.2e-6, 3e-6)
+NEXT = (6e-7, 1.2e-6)
+CHAIN_MOM = (3e-5, 4e-5)    # FENE/WCA chains
+CHAIN_FACC = (1e-5, 1.2e-5)
+
+
+def tid():
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split("::")[-1].split(" ")[0]
+
+
+def _check_run(r, shape, pos_tol, next_bar=NEXT, mom=MOM, facc=FACC):
+    t = tid()
+    check_pos(t + " positions", r["gpos"], r["opos"], shape, pos_tol)
+    check(t + " momenta", r["gmom"], r["omom"], *mom)
+    check(t + " impulses", r["gfacc"], r["ofacc"], *facc)
+    if "got_next" in r and next_bar is not None:
+        c, a, e, w, opp = r["tables"]
+        aa = a[:, None, None, None]
+        check(t + " next populations", r["got_next"] - aa, r["want_next"] - aa, *next_bar)
 
 
 def rel(a, b):
@@ -61,6 +95,7 @@ def _run(ora, shape, pos, mom, *, kT, walls=False, chains=None, nsub=10, dt=0.1,
         lat.step(1)
         out["want_next"] = ora.step(p, pops, ofacc.astype(np.float32).astype(np.float64), 0)
         out["got_next"] = lat.get_populations().cpu().numpy()
+        out["tables"] = ora.tables()
     assert lat.sync() == (L.LB_OK, 0)
     return out
 
@@ -78,12 +113,7 @@ def test_free_particles_parity(ora, kT):
     pos = inputs.uniform_particles(300, shape, seed=1)
     mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
     r = _run(ora, shape, pos, mom, kT=kT)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
-    c, a, e, w, opp = ora.tables()
-    aa = a[:, None, None, None]
-    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+    _check_run(r, shape, 1e-6)
 
 
 @pytest.mark.parametrize("per_substep,kernel", [(False, 2), (True, 2), (False, 3)])
@@ -95,12 +125,7 @@ def test_external_force_parity(ora, per_substep, kernel):
     pos = inputs.uniform_particles(300, shape, seed=1)
     mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
     r = _run(ora, shape, pos, mom, kT=1e-4, per_substep=per_substep, kernel=kernel, fext=(3e-3, -2e-3, 1e-3))
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
-    c, a, e, w, opp = ora.tables()
-    aa = a[:, None, None, None]
-    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+    _check_run(r, shape, 1e-6)
 
 
 def test_three_point_noise_parity(ora):
@@ -108,7 +133,7 @@ def test_three_point_noise_parity(ora):
     pos = inputs.uniform_particles(200, shape, seed=3)
     mom = np.zeros((200, 3))
     r = _run(ora, shape, pos, mom, kT=1e-4, noise_kind=1, lb_after=False)
-    assert rel(r["gmom"], r["omom"]) < 2e-4
+    check(tid() + " momenta", r["gmom"], r["omom"], *MOM)
 
 
 def test_walls_particles_parity(ora):
@@ -116,10 +141,8 @@ def test_walls_particles_parity(ora):
     pos = inputs.uniform_particles(200, shape, seed=5, zrange=(1.0, 10.0))
     mom = inputs.maxwell_momenta(200, 1.0, 1e-2, seed=6)  # fast enough to reach the walls
     r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, dt=0.5, body_force=(1e-5, 0, 0))
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-5
+    _check_run(r, shape, 1e-6, next_bar=None)
     assert r["gpos"][:, 2].min() >= 1.0 and r["gpos"][:, 2].max() <= 10.0
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
 
 
 @pytest.mark.parametrize("per_substep", [False, True])
@@ -130,9 +153,7 @@ def test_chains_parity(ora, per_substep):
     pos = inputs.random_walk_chains(2, 24, shape, seed=7)
     mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
     r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), per_substep=per_substep)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None, mom=CHAIN_MOM, facc=CHAIN_FACC)
 
 
 def test_wca_narrow_box_between_walls(ora):
@@ -144,9 +165,7 @@ def test_wca_narrow_box_between_walls(ora):
     pos[:, 2] += 1.0  # z in [1, 12) = [1, nz - 2)
     mom = inputs.maxwell_momenta(n, 1.0, 1e-3, seed=42)
     r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, chains=(n, 1))
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1.2e-6, next_bar=None, mom=(2.5e-6, 5e-6), facc=(1e-6, 2e-6))
 
 
 @pytest.mark.parametrize("per_substep", [False, True])
@@ -158,9 +177,7 @@ def test_wca_chains_many(ora, per_substep):
     pos = inputs.random_walk_chains(100, 256, shape, seed=43)
     mom = inputs.maxwell_momenta(25600, 1.0, 1e-4, seed=44)
     r = _run(ora, shape, pos, mom, kT=1e-4, chains=(100, 256), nsub=3, lb_after=False, per_substep=per_substep)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None, mom=(1.1e-5, 1.4e-5), facc=(4e-6, 5e-6))
 
 
 @pytest.mark.parametrize("kernel", [2, 3, 4])
@@ -195,12 +212,7 @@ def test_phi_kernel_free_particles_parity(ora, kernel, kT):
     pos = inputs.uniform_particles(300, shape, seed=1)
     mom = inputs.maxwell_momenta(300, 1.0, 1e-4, seed=2)
     r = _run(ora, shape, pos, mom, kT=kT, kernel=kernel)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
-    c, a, e, w, opp = ora.tables()
-    aa = a[:, None, None, None]
-    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
+    _check_run(r, shape, 1e-6)
 
 
 @pytest.mark.parametrize("kernel", [3, 4])
@@ -212,14 +224,9 @@ def test_phi_kernel_walls_parity(ora, kernel):
     pos = inputs.uniform_particles(200, shape, seed=5, zrange=(b, shape[2] - 1 - b))
     mom = inputs.maxwell_momenta(200, 1.0, 1e-2, seed=6)  # fast enough to reach the walls
     r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, dt=0.5, body_force=(1e-5, 0, 0), kernel=kernel)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-5
+    _check_run(r, shape, 1.2e-6)
     assert r["gpos"][:, 2].min() >= b and r["gpos"][:, 2].max() <= shape[2] - 1 - b
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
     assert np.all(r["gfacc"][:, 0] == 0) and np.all(r["gfacc"][:, -1] == 0)
-    c, a, e, w, opp = ora.tables()
-    aa = a[:, None, None, None]
-    assert rel(r["got_next"] - aa, r["want_next"] - aa) < 2e-6
 
 
 @pytest.mark.parametrize("kernel", [3, 4])
@@ -229,9 +236,7 @@ def test_phi_kernel_chains_parity(ora, kernel):
     pos = inputs.random_walk_chains(2, 24, shape, seed=7)
     mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
     r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), kernel=kernel)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None, mom=CHAIN_MOM, facc=CHAIN_FACC)
 
 
 def test_phi3_many_particles_parity(ora):
@@ -241,9 +246,7 @@ def test_phi3_many_particles_parity(ora):
     pos = inputs.uniform_particles(200000, shape, seed=21)
     mom = inputs.maxwell_momenta(200000, 1.0, 1e-4, seed=22)
     r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3, kernel=3)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None)
 
 
 def test_phi_kernel_rejections():
@@ -301,9 +304,7 @@ def test_many_particles_multi_kernel_path(ora):
     pos = inputs.uniform_particles(200000, shape, seed=21)
     mom = inputs.maxwell_momenta(200000, 1.0, 1e-4, seed=22)
     r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None)
 
 
 @pytest.mark.parametrize("per_substep", [False, True])
@@ -335,8 +336,8 @@ def test_fast_wca_particles_rebuild_lists(ora, per_substep):
         L.lb_couple_particles(lat.h, parts, cp)
         lat.step(1)
     assert lat.sync() == (L.LB_OK, 0)
-    assert _pos_err(gpos.cpu().numpy(), opos, shape) < 2e-5
-    assert rel(gmom.cpu().numpy().astype(np.float64), omom) < 1e-3
+    check_pos(tid() + " positions", gpos.cpu().numpy(), opos, shape, 2.2e-6)
+    check(tid() + " momenta", gmom.cpu().numpy().astype(np.float64), omom, 2e-6, 5e-6)
 
 
 def _coupled_run(shape, *, walls, overlap, steps=4, join_early=False, kernel=2, dtype=L.LB_F32):
@@ -436,9 +437,7 @@ def test_stencil_wider_than_box(ora, shape, kernel):
     pos = inputs.uniform_particles(20, shape, seed=9)
     mom = inputs.maxwell_momenta(20, 1.0, 1e-4, seed=10)
     r = _run(ora, shape, pos, mom, kT=1e-4, nsub=4, kernel=kernel)
-    assert _pos_err(r["gpos"], r["opos"], shape) < 1e-6
-    assert rel(r["gmom"], r["omom"]) < 2e-4
-    assert rel(r["gfacc"], r["ofacc"]) < 2e-4
+    _check_run(r, shape, 1e-6, next_bar=None)
 
 
 def test_no_particles_is_a_no_op():

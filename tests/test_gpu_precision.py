@@ -9,7 +9,16 @@ parabola.  At 128^3 the force is scaled by (510/126)^2 so the flow speed
 matches the 512^3 case; the particle number is scaled with the volume.
 Errors reported: relative L2 of the velocity field, of the non-equilibrium
 stress pi - pi^eq, and the largest relative deviation of a non-conserved
-mode's mean square.
+mode's mean square.  Each is asserted at about three times its value
+measured on a GB300:
+
+  128^3, 40 steps, vs the FP64 oracle    velocity  stress   modes
+    FP32                                 1.05e-6   4.9e-7   3.4e-6
+    FP16                                 1.10e-4   7.7e-4   6.6e-5
+    BF16                                 9.0e-4    6.2e-3   8.1e-4
+  512^3, 2000 steps, vs FP32 storage     profile   stress   modes
+    FP16                                 1.08e-4   3.2e-4   3.6e-4
+    BF16                                 5.3e-3    6.8e-3   1.8e-2
 """
 import numpy as np
 import pytest
@@ -79,9 +88,9 @@ def test_reduced_precision_vs_oracle_128(ora):
           "(velocity, stress, mode mean squares):" % (npart, nsteps))
     for k, v in table.items():
         print("  %-5s %.2e %.2e %.2e" % ((k,) + v))
-    assert max(table["f32"]) < 2e-5
-    assert max(table["f16"]) < 2e-2
-    assert max(table["bf16"]) < 1.5e-1
+    bars = {"f32": (3e-6, 1.5e-6, 1e-5), "f16": (3.3e-4, 2.3e-3, 2e-4), "bf16": (2.7e-3, 1.9e-2, 2.4e-3)}
+    for k, bar in bars.items():
+        assert all(v < b for v, b in zip(table[k], bar)), (k, table[k], bar)
 
 
 @pytest.mark.slow
@@ -123,5 +132,5 @@ def test_reduced_precision_vs_fp32_512():
         es = rel(pxz, ref[1])
         em = float(np.max(np.abs(msq / ref[2] - 1)))
         print("512^3 %s vs f32 after %d steps: profile %.2e, stress %.2e, modes %.2e" % (name, nsteps, eu, es, em))
-        assert eu < (5e-2 if name == "f16" else 2e-1)
-        assert em < (2e-2 if name == "f16" else 1e-1)
+        bar = (3.3e-4, 1e-3, 1.1e-3) if name == "f16" else (1.6e-2, 2e-2, 5.3e-2)
+        assert eu < bar[0] and es < bar[1] and em < bar[2], (name, (eu, es, em), bar)
