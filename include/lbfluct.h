@@ -196,7 +196,8 @@ lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums
  * mid-run), which also rules out lb_create.  Its reduction scratch is a
  * static 1.2 MiB device array that every GPU loading the library keeps until
  * exit.  Boxes of more than 2^28 nodes are rejected with LB_EINVAL.  The first
- * call on a device looks up that array's device address, so make that first
+ * call on a device (and the first after its context changed, e.g. after
+ * cudaDeviceReset) looks up that array's device address, so make that first
  * call before any stream capture.  All calls share the array: calls that
  * overlap on the GPU (different streams or threads) race and must be
  * serialised by the caller.  stream: a cudaStream_t.  No force field is

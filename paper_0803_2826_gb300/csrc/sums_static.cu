@@ -9,6 +9,7 @@
 // the parameters directly and allocates nothing.  Its reduction scratch is the
 // file-scope array below, which every GPU that loads the library holds until
 // the process exits.
+#include <cuda.h>
 #include <mutex>
 
 #include "d3q19.cuh"
@@ -27,7 +28,44 @@ static __device__ __align__(256) double g_static_partials[kStaticMaxBlocks * LB_
 
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double *g_partials_ptr[kMaxDevices] = {nullptr};
+
+// The array's device address, per device, together with the unique id of
+// the context it was looked up in: after cudaDeviceReset (or under another
+// context) the address of the old context is no longer valid, so a changed
+// id repeats the lookup.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double *ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+// Unique id of the calling thread's current context, through the driver
+// entry points the runtime exposes (no link against the driver library).
+// Returns false when there is no current context or the driver lacks the
+// calls.
+bool current_context_id(unsigned long long *id)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            get_current = reinterpret_cast<GetCurrent>(f1);
+            get_id = reinterpret_cast<GetId>(f2);
+        }
+        resolved = true;
+    }
+    if (!get_current || !get_id) return false;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+    return get_id(c, id) == CUDA_SUCCESS;
+}
 
 // Block b reduces nodes [b * chunk, min(N, (b + 1) * chunk)) of the
 // pre-collision state: dm_k = sum_i e_ki (n_i - a_i rho0) and dm_k^2 over fluid
@@ -105,8 +143,8 @@ __global__ void k_sums_static_final(const double *partials, int nblocks, double 
     sums[k] = v;
 }
 
-// Device address of the static scratch on the current device, looked up once
-// per device.
+// Device address of the static scratch on the current device, looked up on
+// the first call in a context (once per device while its context lives).
 lb_status static_scratch(double **out)
 {
     int dev = 0;
@@ -117,13 +155,23 @@ lb_status static_scratch(double **out)
         return LB_EUNSUPPORTED;
     }
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_partials_ptr[dev]) {
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(&id);
+    ScratchAddr &c = g_scratch[dev];
+    if (!c.ptr || !have_id || c.ctx_id != id) {
         double *ptr = nullptr;
         e = cudaGetSymbolAddress((void **)&ptr, g_static_partials);
-        if (e != cudaSuccess || !ptr) return lbi::cuda_fail("lb_moment_sums_static (cudaGetSymbolAddress)", e);
-        g_partials_ptr[dev] = ptr;
+        if (e != cudaSuccess) return lbi::cuda_fail("lb_moment_sums_static (cudaGetSymbolAddress)", e);
+        if (!ptr) {
+            lbi::set_error("lb_moment_sums_static: cudaGetSymbolAddress returned a null address");
+            return LB_ECUDA;
+        }
+        // the lookup made the device's primary context current if none was
+        unsigned long long id2 = 0;
+        c.ctx_id = current_context_id(&id2) ? id2 : 0;
+        c.ptr = ptr;
     }
-    *out = g_partials_ptr[dev];
+    *out = c.ptr;
     return LB_OK;
 }
 

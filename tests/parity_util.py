@@ -8,7 +8,14 @@ so an error confined to a few elements (a wrong wall node, one bad row of a
 large box) cannot hide under the field-wide norm.  `check` prints both with
 a tag (run pytest with -s to see them) and asserts each against its bar.
 """
+import os
+
 import numpy as np
+
+
+def tid():
+    """Name of the running test (with its parameters), for the printed tags."""
+    return os.environ.get("PYTEST_CURRENT_TEST", "?").split("::")[-1].split(" ")[0]
 
 
 def errs(got, want):

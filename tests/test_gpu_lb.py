@@ -16,6 +16,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_0803_2826_gb300 import inputs  # noqa: E402
 from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+from parity_util import check  # noqa: E402
 
 
 def rel(a, b):
@@ -30,6 +31,7 @@ def host(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
+NAMES = ["n - a rho0", "rho - rho0", "j", "pi - pi_eq"]
 GAMMAS = dict(gamma_shear=0.2, gamma_bulk=-0.3, gamma_odd=0.4, gamma_even=-0.1)
 
 
@@ -69,9 +71,10 @@ def test_one_step_parity(ora, shape, kT):
                                    body_force=(1e-5, -2e-5, 3e-6), **GAMMAS)
     c, a, e, w, opp = ora.tables()
     aa = a[:, None, None, None]
-    assert rel(got - aa, want - aa) < 2e-6
-    for x, y in zip(_fields(ora, p, got, f64), _fields(ora, p, want, f64)):
-        assert rel(x, y) < 5e-6
+    tag = "one step %s kT=%g" % (shape, kT)
+    check(tag + " n - a rho0", got - aa, want - aa, 2e-6, 5e-6)
+    for nm, x, y in zip(NAMES, _fields(ora, p, got, f64), _fields(ora, p, want, f64)):
+        check(tag + " " + nm, x, y, 5e-6, 2e-5)
 
 
 @pytest.mark.parametrize("kT", [0.0, 1e-4])
@@ -85,7 +88,7 @@ def test_walls_parity(ora, kT):
     c, a, e, w, opp = ora.tables()
     aa = a[:, None, None, None]
     fl = slice(1, shape[2] - 1)
-    assert rel(got[:, fl] - aa, want[:, fl] - aa) < 5e-6
+    check("walls kT=%g n - a rho0" % kT, got[:, fl] - aa, want[:, fl] - aa, 5e-6, 2e-5)
 
 
 @pytest.mark.parametrize("ge", [0.5, -0.5])
@@ -136,7 +139,7 @@ def test_exponential_equilibrium_parity(ora, kT, walls):
     c, a, e, w, opp = ora.tables()
     aa = a[:, None, None, None]
     fl = slice(1, shape[2] - 1) if walls else slice(None)
-    assert rel(got[:, fl] - aa, want[:, fl] - aa) < 5e-6
+    check("exponential equilibrium kT=%g walls=%d" % (kT, walls), got[:, fl] - aa, want[:, fl] - aa, 5e-6, 2e-5)
     # and it is not the quadratic update
     pq, want_q, _, _, _ = _pair(ora, shape, 20, u=u, field=field, **dict(kw, equilibrium=0))
     assert rel(want_q[:, fl] - aa, want[:, fl] - aa) > 20 * rel(got[:, fl] - aa, want[:, fl] - aa)
@@ -165,16 +168,13 @@ def test_shear_wave_1000_steps(ora):
     shape = (32, 32, 32)
     u = inputs.shear_wave(shape, 0.01)
     p, want, got, lat, _ = _pair(ora, shape, 1000, u=u, kT=1e-4, seed=0)
-    names = ["n - a rho0", "rho - rho0", "j", "pi - pi_eq"]
-    errs = [rel(x, y) for x, y in zip(_fields(ora, p, got, None), _fields(ora, p, want, None))]
-    print("1000-step parity (relative L2):", dict(zip(names, ["%.2e" % v for v in errs])))
-    for nm, err in zip(names, errs):
-        assert err < 1e-5, (nm, err)
+    for nm, x, y in zip(NAMES, _fields(ora, p, got, None), _fields(ora, p, want, None)):
+        check("1000 steps 32^3 " + nm, x, y, 1e-5, 1e-5)
     # the GPU's own moment kernel agrees with the oracle's moments too
     rho, j, pi, sums = lat.moments(want_sums=True)
     orho, oj, opi = ora.moments(p, want)
-    assert rel(host(rho) - 1.0, orho - 1.0) < 1e-5
-    assert rel(host(j), oj) < 1e-5
+    check("1000 steps 32^3 lb_moments rho - rho0", host(rho) - 1.0, orho - 1.0, 1e-5, 1e-5)
+    check("1000 steps 32^3 lb_moments j", host(j), oj, 1e-5, 1e-5)
 
 
 @pytest.mark.parametrize("dtype,tol", [(L.LB_F16, 3e-3), (L.LB_BF16, 2.5e-2)])
@@ -184,7 +184,7 @@ def test_reduced_precision_storage(ora, dtype, tol):
     p, want, got, lat, _ = _pair(ora, shape, 20, u=u, kT=1e-4, seed=3, dtype=dtype)
     c, a, e, w, opp = ora.tables()
     aa = a[:, None, None, None]
-    assert rel(got - aa, want - aa) < tol
+    check("20 steps storage %d" % dtype, got - aa, want - aa, tol, 4 * tol)
 
 
 def test_noise_words_bitwise(ora):

@@ -14,8 +14,6 @@ times the errors measured on a GB300:
     momentum it accumulates; the impulses to the fluid, which see the forces
     only through (C2 - dt) F^c, stay smaller.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -24,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_0803_2826_gb300 import inputs  # noqa: E402
 from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
-from parity_util import check, check_pos  # noqa: E402
+from parity_util import check, check_pos, tid  # noqa: E402
 
 # Bars (relative L2, worst element relative to the field's largest entry);
 # see the module docstring.
@@ -33,10 +31,6 @@ FACC = (1.2e-6, 3e-6)
 NEXT = (6e-7, 1.2e-6)
 CHAIN_MOM = (3e-5, 4e-5)    # FENE/WCA chains
 CHAIN_FACC = (1e-5, 1.2e-5)
-
-
-def tid():
-    return os.environ.get("PYTEST_CURRENT_TEST", "?").split("::")[-1].split(" ")[0]
 
 
 def _check_run(r, shape, pos_tol, next_bar=NEXT, mom=MOM, facc=FACC):

@@ -14,6 +14,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_0803_2826_gb300 import inputs  # noqa: E402
 from paper_0803_2826_gb300 import lbfluct as L  # noqa: E402
+from parity_util import check, tid  # noqa: E402
 
 
 def rel(a, b):
@@ -67,9 +68,9 @@ def test_moving_spheres_parity(ora, kT, shape):
     fl = want[1] < 0
     c, a, e, w, opp = ora.tables()
     aa = a[:, None]
-    assert rel(got[0][:, fl] - aa, want[0][:, fl] - aa) < 2e-6
+    check(tid() + " populations", got[0][:, fl] - aa, want[0][:, fl] - aa, 2e-6, 1e-5)
     assert np.abs(got[2] - want[2]).max() < 1e-6
-    assert rel(got[3], want[3]) < 1e-5
+    check(tid() + " velocities", got[3], want[3], 1e-5, 2e-5)
 
 
 @pytest.mark.parametrize("kT", [0.0, 1e-4])
@@ -91,10 +92,10 @@ def test_rotating_spheres_parity(ora, kT):
     fl = want[1] < 0
     c, a, e, w, opp = ora.tables()
     aa = a[:, None]
-    assert rel(got[0][:, fl] - aa, want[0][:, fl] - aa) < 2e-6
+    check("rotating spheres kT=%g populations" % kT, got[0][:, fl] - aa, want[0][:, fl] - aa, 2e-6, 1e-5)
     assert np.abs(got[2] - want[2]).max() < 1e-6
-    assert rel(got[3], want[3]) < 1e-5
-    assert rel(got[6], want[4]) < 1e-5
+    check("rotating spheres kT=%g velocities" % kT, got[3], want[3], 1e-5, 2e-5)
+    check("rotating spheres kT=%g angular velocities" % kT, got[6], want[4], 1e-5, 2e-5)
     assert np.abs(want[4] - Om).max() > 1e-4
 
 

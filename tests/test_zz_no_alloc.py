@@ -26,9 +26,12 @@ def _sums_both(lat):
     return ref.cpu().numpy(), out.cpu().numpy()
 
 
-@pytest.mark.parametrize("shape,walls", [((40, 33, 27), False), ((16, 12, 10), True)])
-def test_static_sums_match_lb_moments(shape, walls):
-    lat = L.Lattice(shape, kT=1e-4, seed=3, walls=walls)
+# (70, 50, 40) has 140000 nodes: three 65536-node chunks, the last one
+# partial, so the multi-block partials and the cross-block final sum run.
+@pytest.mark.parametrize("dtype", [L.LB_F32, L.LB_F16, L.LB_BF16])
+@pytest.mark.parametrize("shape,walls", [((40, 33, 27), False), ((16, 12, 10), True), ((70, 50, 40), True)])
+def test_static_sums_match_lb_moments(shape, walls, dtype):
+    lat = L.Lattice(shape, kT=1e-4, seed=3, walls=walls, dtype=dtype)
     lat.init_equilibrium(None, torch.as_tensor(inputs.shear_wave(shape, 0.01)).cuda())
     lat.step(3)
     ref1, got1 = _sums_both(lat)
