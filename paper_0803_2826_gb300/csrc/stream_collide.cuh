@@ -15,6 +15,7 @@
 #pragma once
 
 #include "d3q19.cuh"
+#include "f32x2.cuh"
 #include "lbf_internal.h"
 
 namespace lbi {
@@ -415,7 +416,8 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restri
 // their populations from the same rows of each plane, so one address per
 // plane serves both (the second is an immediate offset); planes with c_x = 0
 // and all stores move the pair as one 8-byte (FP32) or 4-byte (FP16 / BF16)
-// access.  Collision and noise are those of collide_node, node by node.
+// access.  Collision and noise are those of collide_node, computed for the
+// two nodes at once in packed FP32 (f32x2.cuh).
 template <int DT>
 struct Pair;
 template <>
@@ -483,27 +485,29 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
     const uint32_t P = (uint32_t)a.pitch;
     const uint32_t self = (uint32_t)((z * ny + y) * nx + x0);
 
-    float n0[19], n1[19];
+    lbp::F2 n[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
         const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
         bool bounce = false;
         if (WALLS && lbd::cz(i) != 0) bounce = (sz == 0) || (sz == nz - 1);
+        float v0, v1;
         if (bounce) {
-            PR::load(src + (uint32_t)lbd::opposite(i) * P + self, a.inv_scale, n0[i], n1[i]);
+            PR::load(src + (uint32_t)lbd::opposite(i) * P + self, a.inv_scale, v0, v1);
         } else {
             const uint32_t row = (uint32_t)i * P + (uint32_t)((sz * ny + sy) * nx);
             if (lbd::cx(i) == 0) {
-                PR::load(src + row + x0, a.inv_scale, n0[i], n1[i]);
+                PR::load(src + row + x0, a.inv_scale, v0, v1);
             } else if (lbd::cx(i) == 1) {
-                n0[i] = S::load(src + row + xm, a.inv_scale);
-                n1[i] = S::load(src + row + x0, a.inv_scale);
+                v0 = S::load(src + row + xm, a.inv_scale);
+                v1 = S::load(src + row + x0, a.inv_scale);
             } else {
-                n0[i] = S::load(src + row + x0 + 1, a.inv_scale);
-                n1[i] = S::load(src + row + xp, a.inv_scale);
+                v0 = S::load(src + row + x0 + 1, a.inv_scale);
+                v1 = S::load(src + row + xp, a.inv_scale);
             }
         }
+        n[i] = lbp::f2(v0, v1);
     }
 
     float f0[3] = {a.fx, a.fy, a.fz}, f1[3] = {a.fx, a.fy, a.fz};
@@ -525,21 +529,25 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
             }
         }
     }
-    float out0[19], out1[19];
-    if (SUMS) {  // both nodes' moments first, summed before the collisions
+    // both nodes' moments, collision, noise and back transform in packed
+    // FP32 (f32x2.cuh), node x0 in the low halves
+    lbp::F2 m[19], out[19];
+    lbp::forward2(n, m);
+    if (SUMS) {  // both nodes' moments summed before the collisions
         float m0[19], m1[19];
-        lbd::forward(n0, m0);
-        lbd::forward(n1, m1);
+#pragma unroll
+        for (int k = 0; k < 19; ++k) lbp::split(m[k], m0[k], m1[k]);
         warp_moment_sums(m0, m1, valid, part);
         if (!valid) return;
-        collide_moments<NOISE>(m0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
-        collide_moments<NOISE>(m1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
-    } else {
-        collide_node<NOISE>(n0, f0[0], f0[1], f0[2], a, a.rk, self, a.replica, out0);
-        collide_node<NOISE>(n1, f1[0], f1[1], f1[2], a, a.rk, self + 1, a.replica, out1);
     }
+    lbp::collide_moments2<NOISE>(m, lbp::f2(f0[0], f1[0]), lbp::f2(f0[1], f1[1]), lbp::f2(f0[2], f1[2]), a, a.rk,
+                                 self, a.replica, out);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) PR::store(dst + (uint32_t)i * P + self, out0[i], out1[i], a.scale);
+    for (int i = 0; i < 19; ++i) {
+        float o0, o1;
+        lbp::split(out[i], o0, o1);
+        PR::store(dst + (uint32_t)i * P + self, o0, o1, a.scale);
+    }
 }
 
 template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS>
