@@ -393,15 +393,31 @@ lb_status lb_adjoint_step(lb_handle *h, const void *state, const float *lambda_i
 lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[3], const int hi[3],
                                   float *lambda_out, float *grad_force, double *loss);
 
-/* The whole reverse pass of "advance nsteps, then L of the sub-box": runs the
- * forward steps from the current state (which advances by nsteps, as lb_step
- * would), storing a checkpoint every `checkpoint_every` steps, then walks the
- * segments backwards, recomputing each segment's states from its checkpoint
- * and applying lb_adjoint_step.  Writes dL/d(force field) into grad_force
- * (device FP32 [3][N]; the field is the one the handle was created with) and
- * L into *loss (device double).  Checkpoint and segment buffers are allocated
- * for the call and freed before it returns (it synchronises the stream).
- * Requires kT = 0.  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
+/* Forward half of the reverse pass of "advance nsteps, then L of the
+ * sub-box" (L as in lb_adjoint_seed_kinetic): runs nsteps forward steps
+ * from the current state (which advances, as lb_step would), keeping a
+ * checkpoint every `checkpoint_every` steps, and at the final state forms L
+ * (*loss, device double) and its seed dL/dstate.  The checkpoints, segment
+ * buffers and adjoint buffers live in a device arena the handle owns: the
+ * first call (or one needing more room) allocates it, later calls reuse it
+ * without allocating, lb_destroy frees it.  Asynchronous on the handle's
+ * stream.  Requires kT = 0.  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM,
+ * LB_ECUDA. */
+lb_status lb_adjoint_forward(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
+                             double *loss);
+
+/* Reverse half: walks the segments of the last lb_adjoint_forward backwards,
+ * recomputing each segment's states from its checkpoint and applying
+ * lb_adjoint_step (Sec. 3.4 and 3.7 transposed), and writes dL/d(force field)
+ * into grad_force (device FP32 [3][N]; the field the handle was created
+ * with).  Does not touch the handle's state, so the lattice may have moved
+ * on.  Once per forward (another lb_adjoint_forward or
+ * lb_adjoint_kinetic_coupled in between makes it LB_EINVAL).  Asynchronous,
+ * no allocation.  Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ECUDA. */
+lb_status lb_adjoint_backward(lb_handle *h, float *grad_force);
+
+/* lb_adjoint_forward followed by lb_adjoint_backward: L into *loss and
+ * dL/d(force field) into grad_force.  Errors: as those two. */
 lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
                              float *grad_force, double *loss);
 
@@ -439,8 +455,8 @@ lb_status lb_adjoint_couple(lb_handle *h, const void *state, const lb_particles 
  * lb_adjoint_step_impulse and lb_adjoint_couple.  Writes dL/d(force field)
  * (device FP32 [3][N]), dL/d(initial positions) and dL/d(initial momenta)
  * (device FP32 [n][3]) and L (*loss, device double).  Free particles at
- * kT = 0 only.  Temporaries are allocated for the call and freed before it
- * returns (it synchronises the stream).
+ * kT = 0 only.  Temporaries come from the handle's reverse-mode arena (see
+ * lb_adjoint_forward): allocated on the first call, reused after.
  * Errors: LB_EINVAL, LB_EUNSUPPORTED, LB_ENOMEM, LB_ECUDA. */
 lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp, int nsteps,
                                      int checkpoint_every, const int lo[3], const int hi[3], float *grad_force,
@@ -501,6 +517,39 @@ lb_status lb_batch_get_config(const lb_batch *b, lb_batch_config *c);
 lb_status lb_batch_set_barrier_limit(lb_batch *b, uint32_t spins);
 lb_status lb_batch_get_step(const lb_batch *b, uint32_t *step);
 lb_status lb_batch_get_launch_count(const lb_batch *b, uint64_t *count);
+
+/* Transverse velocity modes of every replica, recorded by the batched run
+ * (Sec. 3.6: in equilibrium each Fourier component of u has variance
+ * kT / (rho0 V); Sec. 3.4, Eq. (shearviscosity): a transverse mode decays by
+ * the shear eigenvalue of the linearised step per step).  From the next
+ * lb_batch_step on, step t (counted from this call, t < capacity) adds to
+ * device modes[r][t][0..11] (FP64, layout [n][capacity][12], caller-owned,
+ * cleared here on the batch's stream) the sums over replica r's nodes of
+ *   u_x e^{-i k_z z}, u_y e^{-i k_z z}, u_y e^{-i k_x x}, u_z e^{-i k_x x},
+ *   u_z e^{-i k_y y}, u_x e^{-i k_y y}     (real part, then imaginary part),
+ * k_b = 2 pi / L_b, u = (sum n c + f/2) / rho of the state that step
+ * collides (its moments as lb_batch_moments defines them, taken inside the
+ * step's own update; FP32 per tile, FP64 accumulation).  Steps past
+ * capacity are not recorded.  modes = NULL stops recording.  Switching
+ * recording on or off may change the grid (the configuration is re-applied
+ * and a captured graph dropped), so call this after lb_batch_autotune; a
+ * new buffer or capacity drops a captured graph; calling again with the same
+ * buffer and capacity restarts the records at the next step and keeps the
+ * graph (the start step lives in device memory).  The library allocates the
+ * phase tables on the first call.
+ * Errors: LB_EINVAL (capacity < 1, misaligned), LB_ENOMEM, LB_ECUDA. */
+lb_status lb_batch_record_modes(lb_batch *b, double *modes, int capacity);
+
+/* Per-replica autocorrelation of recorded modes (device modes as above with
+ * the same capacity) into device acf[n][max_lag + 1] (FP64):
+ *   acf[r][tau] = mean over t0 in [t_begin, t_end - tau) and the six modes of
+ *                 Re u^(t0 + tau) conj(u^(t0)),   u^ = record / V_r,
+ * the velocity autocorrelation whose equal-time value is kT / (rho0 V) and
+ * whose decay is the shear eigenvalue per step.  Asynchronous on the batch's
+ * stream.  Errors: LB_EINVAL (need 0 <= t_begin < t_end <= capacity and
+ * 0 <= max_lag < t_end - t_begin), LB_ECUDA. */
+lb_status lb_batch_mode_acf(lb_batch *b, const double *modes, int capacity, int t_begin, int t_end, int max_lag,
+                            double *acf);
 
 /* Per-replica state access and moments (replica = -1 in init: all replicas,
  * with rho / u then NULL); layouts as for one box of that replica's size. */

@@ -34,6 +34,9 @@ Function -> passage it follows:
   kinetic_energy_and_grad()  forward + reverse pass of a whole run
   exp_equilibrium()  Sec. 3.6 Eq. (equildist_lagrange), the maximum-entropy equilibrium
                   (make_params(equilibrium=1) uses it in the collision)
+  transverse_modes(), mode_autocorrelation()  Sec. 3.6 fluctuation spectrum and
+                  Sec. 3.4 Eq. (shearviscosity): Fourier amplitudes of the transverse
+                  velocity at the smallest wave vectors and their time autocorrelation
 """
 from __future__ import annotations
 
@@ -604,3 +607,46 @@ def kinetic_energy_and_grad(p: Params, pops0, force, nsteps, lo, hi, checkpoint_
         for t in range(t1 - 1, t0 - 1, -1):
             lam, g = adjoint_step(p, states[t - t0], lam, force, g)
     return L, g
+
+
+# The six transverse velocity modes at the smallest wave vector of each axis:
+# (velocity component, axis of the wave vector) in the order the batched
+# records use.
+TRANSVERSE_MODES = ((0, 2), (1, 2), (1, 0), (2, 0), (2, 1), (0, 1))
+
+
+def transverse_modes(p: Params, pops, force=None):
+    """Fourier amplitudes u^_m = (1/V) sum_r u_a(r) exp(-2 pi i r_b / L_b) of
+    the velocity u = j / rho (Sec. 3.7 j, of the pre-collision state as
+    moments() defines it) for the six transverse pairs (a, b) of
+    TRANSVERSE_MODES; the modes whose equal-time variance Sec. 3.6 fixes
+    (kT / (rho0 V)) and whose decay per step is the shear eigenvalue of
+    Sec. 3.4 (Eq. shearviscosity).  Returns complex [6]."""
+    rho, j, _ = moments(p, pops, force)
+    u = j / rho
+    V = float(p.nx * p.ny * p.nz)
+    L = (p.nx, p.ny, p.nz)
+    out = np.zeros(6, dtype=np.complex128)
+    for m, (a, b) in enumerate(TRANSVERSE_MODES):
+        r = np.arange(L[b], dtype=np.float64)
+        ph = np.exp(-2j * np.pi * r / L[b])
+        shape = [1, 1, 1]
+        shape[2 - b] = L[b]  # arrays are (nz, ny, nx)
+        out[m] = np.sum(u[a] * ph.reshape(shape)) / V
+    return out
+
+
+def mode_autocorrelation(series, t_begin, t_end, max_lag):
+    """C(tau) = < Re u^_m(t0 + tau) conj(u^_m(t0)) > over t0 in
+    [t_begin, t_end - tau) and the modes m, for tau = 0 .. max_lag, of a
+    series [T][6] of transverse_modes (the definition, looped)."""
+    s = np.asarray(series)
+    out = np.zeros(max_lag + 1)
+    for tau in range(max_lag + 1):
+        acc, cnt = 0.0, 0
+        for t0 in range(t_begin, t_end - tau):
+            for m in range(s.shape[1]):
+                acc += (s[t0 + tau, m] * np.conj(s[t0, m])).real
+                cnt += 1
+        out[tau] = acc / cnt if cnt else 0.0
+    return out

@@ -7,7 +7,14 @@
 // cut into tiles (runs of consecutive node indices inside one replica); one
 // launch of k_batch runs `nsteps` steps: in each step the resident blocks take
 // tiles in a strided order, then meet at a grid barrier before the buffers
-// swap.  The launch is cooperative (all blocks resident), the barrier spins a
+// swap.  Optionally (lb_batch_record_modes) every step also records, per
+// replica, the six transverse velocity modes u_a(k_b) at the smallest wave
+// vector of each axis (Sec. 3.6 fluctuation spectrum; their decay per step is
+// the shear eigenvalue of Sec. 3.4, Eq. shearviscosity): each warp sums
+// u_a e^{-i k_b r_b} over its nodes of a tile and adds the twelve real parts
+// to the replica's record with FP64 atomics; k_mode_acf forms the per-replica
+// autocorrelation from the records afterwards.
+// The launch is cooperative (all blocks resident), the barrier spins a
 // bounded number of times and on expiry sets LB_DERR_BARRIER and makes every
 // block return.  Loads across barriers bypass L1 (ld.global.cg) because a
 // buffer read two steps ago may be cached there.  The step counter and the
@@ -64,6 +71,7 @@ struct BatchDesc {
     uint64_t off;      // element offset of plane 0 of this replica
     uint32_t pitch;    // elements per plane
     uint32_t replica;  // Philox counter word 3
+    uint32_t phase;    // offset of this replica's phase table (mode records)
     Div dx, dxy;
     lbd::RoundKeys rk;
 };
@@ -74,8 +82,9 @@ struct BatchTile {
 };
 
 struct BatchState {
-    uint32_t step;  // Philox step word of the next step
-    uint32_t cur;   // buffer holding the current state
+    uint32_t step;       // Philox step word of the next step
+    uint32_t cur;        // buffer holding the current state
+    uint32_t rec_step0;  // step recorded at index 0 of the mode records
 };
 
 struct BatchArgs {
@@ -90,7 +99,15 @@ struct BatchArgs {
     unsigned int *bar;  // [0] arrivals, [1] generation, [2] abort
     unsigned int *err;
     unsigned int spin_limit;
+    // transverse-mode records (OBS kernels): modes[rep][t][12], t = step - state->rec_step0 < rec_cap;
+    // phase[desc.phase + ...] = (cos, -sin)(2 pi r / L) for r along x, then y, then z
+    double *modes;
+    const float2 *phase;
+    uint32_t rec_cap;
 };
+
+constexpr int kModeVals = 12;  // six complex transverse modes
+constexpr int kBatchPairMaxRegs = 128;  // keeps 16 warps per SM resident
 
 // Bounded grid barrier (grid_barrier.cuh).  Returns false if the run must
 // stop (a barrier timed out here or elsewhere).
@@ -99,9 +116,10 @@ __device__ __forceinline__ bool batch_barrier(const BatchArgs &a)
     return lbi::grid_barrier(a.bar, a.err, a.spin_limit);
 }
 
-template <int DT, bool NOISE>
+template <int DT, bool NOISE, bool OBS>
 __device__ __forceinline__ void batch_node(const BatchDesc &d, uint32_t s, const typename lbd::Store<DT>::T *src,
-                                           typename lbd::Store<DT>::T *dst, const StepArgs &ph, uint32_t step)
+                                           typename lbd::Store<DT>::T *dst, const StepArgs &ph, uint32_t step,
+                                           const float2 *phase, float acc[kModeVals])
 {
     using S = lbd::Store<DT>;
     const uint32_t row = divide(s, d.dx);
@@ -125,27 +143,199 @@ __device__ __forceinline__ void batch_node(const BatchDesc &d, uint32_t s, const
     }
     StepArgs a = ph;
     a.step = step;
-    float out[19];
-    collide_node<NOISE>(n, ph.fx, ph.fy, ph.fz, a, d.rk, s, d.replica, out);
+    float m[19], out[19];
+    lbd::forward(n, m);
+    if (OBS) {  // u = (sum n c + f/2) / rho of the streamed state (Sec. 3.7)
+        const float ir = 1.0f / (ph.rho0 + m[0]);
+        const float ux = (m[1] + 0.5f * ph.fx) * ir, uy = (m[2] + 0.5f * ph.fy) * ir, uz = (m[3] + 0.5f * ph.fz) * ir;
+        const float2 ex = __ldg(phase + d.phase + x);
+        const float2 ey = __ldg(phase + d.phase + d.nx + y);
+        const float2 ez = __ldg(phase + d.phase + d.nx + d.ny + z);
+        acc[0] = fmaf(ux, ez.x, acc[0]);
+        acc[1] = fmaf(ux, ez.y, acc[1]);
+        acc[2] = fmaf(uy, ez.x, acc[2]);
+        acc[3] = fmaf(uy, ez.y, acc[3]);
+        acc[4] = fmaf(uy, ex.x, acc[4]);
+        acc[5] = fmaf(uy, ex.y, acc[5]);
+        acc[6] = fmaf(uz, ex.x, acc[6]);
+        acc[7] = fmaf(uz, ex.y, acc[7]);
+        acc[8] = fmaf(uz, ey.x, acc[8]);
+        acc[9] = fmaf(uz, ey.y, acc[9]);
+        acc[10] = fmaf(ux, ey.x, acc[10]);
+        acc[11] = fmaf(ux, ey.y, acc[11]);
+    }
+    collide_moments<NOISE>(m, ph.fx, ph.fy, ph.fz, a, d.rk, s, d.replica, out);
     typename S::T *o = dst + d.off;
 #pragma unroll
     for (int i = 0; i < 19; ++i) o[(size_t)i * P + s] = S::pack(out[i], ph.scale);
 }
 
-template <int DT, bool NOISE>
-__global__ void k_batch(BatchArgs a)
+// Nodes s and s + 1 (s even, nx even: the same row) of replica d: the pair
+// update of k_stream_collide2 -- one row address per plane for both nodes,
+// 8-byte (FP32) / 4-byte (FP16, BF16) accesses where the pair moves
+// together, and the collision of both nodes in packed FP32 (f32x2.cuh).
+template <int DT>
+__device__ __forceinline__ void ld_pair(const typename lbd::Store<DT>::T *p, float inv, float &a, float &b);
+template <>
+__device__ __forceinline__ void ld_pair<0>(const float *p, float, float &a, float &b)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
+    a = v.x;
+    b = v.y;
+}
+template <>
+__device__ __forceinline__ void ld_pair<1>(const __half *p, float inv, float &a, float &b)
+{
+    const __half2 v = __ldcg(reinterpret_cast<const __half2 *>(p));
+    a = __low2float(v) * inv;
+    b = __high2float(v) * inv;
+}
+template <>
+__device__ __forceinline__ void ld_pair<2>(const __nv_bfloat16 *p, float inv, float &a, float &b)
+{
+    const __nv_bfloat162 v = __ldcg(reinterpret_cast<const __nv_bfloat162 *>(p));
+    a = __low2float(v) * inv;
+    b = __high2float(v) * inv;
+}
+
+template <int DT, bool NOISE, bool OBS>
+__device__ __forceinline__ void batch_pair(const BatchDesc &d, uint32_t s, const typename lbd::Store<DT>::T *src,
+                                           typename lbd::Store<DT>::T *dst, const StepArgs &ph, uint32_t step,
+                                           const float2 *phase, lbp::F2 acc[kModeVals])
+{
+    using S = lbd::Store<DT>;
+    const uint32_t row = divide(s, d.dx);
+    const int x0 = (int)(s - row * (uint32_t)d.nx);
+    const uint32_t zz = divide(s, d.dxy);
+    const int y = (int)(row - zz * (uint32_t)d.ny);
+    const int z = (int)zz;
+    const int xm = (x0 == 0) ? d.nx - 1 : x0 - 1;   // source of node x0 for c_x = +1
+    const int xp = (x0 + 2 == d.nx) ? 0 : x0 + 2;   // source of node x0 + 1 for c_x = -1
+    const int ym = (y == 0) ? d.ny - 1 : y - 1, yp = (y == d.ny - 1) ? 0 : y + 1;
+    const int zm = (z == 0) ? d.nz - 1 : z - 1, zp = (z == d.nz - 1) ? 0 : z + 1;
+    const uint32_t P = d.pitch;
+    const typename S::T *base = src + d.off;
+    lbp::F2 n[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
+        const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
+        const uint32_t r = (uint32_t)i * P + (uint32_t)((sz * d.ny + sy) * d.nx);
+        float v0, v1;
+        if (lbd::cx(i) == 0) {
+            ld_pair<DT>(base + r + x0, ph.inv_scale, v0, v1);
+        } else if (lbd::cx(i) == 1) {
+            v0 = S::cvt(__ldcg(base + r + xm), ph.inv_scale);
+            v1 = S::cvt(__ldcg(base + r + x0), ph.inv_scale);
+        } else {
+            v0 = S::cvt(__ldcg(base + r + x0 + 1), ph.inv_scale);
+            v1 = S::cvt(__ldcg(base + r + xp), ph.inv_scale);
+        }
+        n[i] = lbp::f2(v0, v1);
+    }
+    StepArgs a = ph;
+    a.step = step;
+    lbp::F2 m[19], out[19];
+    lbp::forward2(n, m);
+    const lbp::F2 fx = lbp::f2s(ph.fx), fy = lbp::f2s(ph.fy), fz = lbp::f2s(ph.fz);
+    if (OBS) {  // u = (sum n c + f/2) / rho of the streamed state (Sec. 3.7)
+        const lbp::F2 rho = lbp::f2s(ph.rho0) + m[0];
+        float rl, rh;
+        lbp::split(rho, rl, rh);
+        const lbp::F2 ir = lbp::f2(__frcp_rn(rl), __frcp_rn(rh));
+        const lbp::F2 half = lbp::f2s(0.5f);
+        const lbp::F2 ux = lbp::fma2(half, fx, m[1]) * ir;
+        const lbp::F2 uy = lbp::fma2(half, fy, m[2]) * ir;
+        const lbp::F2 uz = lbp::fma2(half, fz, m[3]) * ir;
+        const float2 ex0 = __ldg(phase + d.phase + x0), ex1 = __ldg(phase + d.phase + x0 + 1);
+        const float2 ey = __ldg(phase + d.phase + d.nx + y);
+        const float2 ez = __ldg(phase + d.phase + d.nx + d.ny + z);
+        const lbp::F2 czr = lbp::f2s(ez.x), czi = lbp::f2s(ez.y), cyr = lbp::f2s(ey.x), cyi = lbp::f2s(ey.y);
+        const lbp::F2 cxr = lbp::f2(ex0.x, ex1.x), cxi = lbp::f2(ex0.y, ex1.y);
+        acc[0] = lbp::fma2(ux, czr, acc[0]);
+        acc[1] = lbp::fma2(ux, czi, acc[1]);
+        acc[2] = lbp::fma2(uy, czr, acc[2]);
+        acc[3] = lbp::fma2(uy, czi, acc[3]);
+        acc[4] = lbp::fma2(uy, cxr, acc[4]);
+        acc[5] = lbp::fma2(uy, cxi, acc[5]);
+        acc[6] = lbp::fma2(uz, cxr, acc[6]);
+        acc[7] = lbp::fma2(uz, cxi, acc[7]);
+        acc[8] = lbp::fma2(uz, cyr, acc[8]);
+        acc[9] = lbp::fma2(uz, cyi, acc[9]);
+        acc[10] = lbp::fma2(ux, cyr, acc[10]);
+        acc[11] = lbp::fma2(ux, cyi, acc[11]);
+    }
+    lbp::collide_moments2<NOISE>(m, fx, fy, fz, a, d.rk, s, d.replica, out);
+    typename S::T *o = dst + d.off;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float o0, o1;
+        lbp::split(out[i], o0, o1);
+        Pair<DT>::store(o + (uint32_t)i * P + s, o0, o1, ph.scale);
+    }
+}
+
+// The warp's mode sums of one tile (acc of every lane) added to the
+// replica's record of this step: a butterfly reduce-scatter (12 -> 6 -> 3,
+// padded to 4 -> 2 -> 1 values per lane, then the last pair of lanes), after
+// which lane l holds the warp sum of value k = 6 b4 + 3 b3 + 2 b2 + b1 (b_i
+// the bits of l; 2 b2 + b1 = 3 is padding), and the twelve even lanes with a
+// value add it to the record (FP64 atomics; no block barrier).
+__device__ __forceinline__ void record_warp(const float acc[kModeVals], double *rec)
+{
+    const int lane = threadIdx.x & 31;
+    float b[6], c[3], d[4], e[2], f[1];
+    butterfly_half<12>(acc, b, 16, lane & 16);
+    butterfly_half<6>(b, c, 8, lane & 8);
+    d[0] = c[0];
+    d[1] = c[1];
+    d[2] = c[2];
+    d[3] = 0.0f;
+    butterfly_half<4>(d, e, 4, lane & 4);
+    butterfly_half<2>(e, f, 2, lane & 2);
+    const float v = f[0] + __shfl_xor_sync(0xffffffffu, f[0], 1);
+    const int pos = 2 * ((lane >> 2) & 1) + ((lane >> 1) & 1);
+    const int k = 6 * ((lane >> 4) & 1) + 3 * ((lane >> 3) & 1) + pos;
+    if (rec && !(lane & 1) && pos < 3) atomicAdd(rec + k, (double)v);
+}
+
+template <int DT, bool NOISE, bool OBS, bool PAIR>
+__device__ __forceinline__ void batch_run(const BatchArgs &a)
 {
     using T = typename lbd::Store<DT>::T;
     uint32_t step = a.state->step;
     uint32_t cur = a.state->cur;
+    const uint32_t rec_step0 = a.state->rec_step0;
     for (int t = 0; t < a.nsteps; ++t) {
         const T *src = static_cast<const T *>(a.pops[cur]);
         T *dst = static_cast<T *>(a.pops[cur ^ 1u]);
+        const uint32_t trec = step - rec_step0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
             const BatchTile tl = a.tiles[tile];
             const BatchDesc &d = a.desc[tl.rep];
-            for (uint32_t k = threadIdx.x; k < tl.count; k += blockDim.x)
-                batch_node<DT, NOISE>(d, tl.begin + k, src, dst, a.phys, step);
+            float acc[kModeVals];
+            if (PAIR) {  // every replica has even nx: tiles hold whole pairs
+                lbp::F2 acc2[kModeVals];
+#pragma unroll
+                for (int q = 0; q < kModeVals; ++q) acc2[q] = lbp::f2s(0.0f);
+                for (uint32_t k = 2 * threadIdx.x; k < tl.count; k += 2 * blockDim.x)
+                    batch_pair<DT, NOISE, OBS>(d, tl.begin + k, src, dst, a.phys, step, a.phase, acc2);
+#pragma unroll
+                for (int q = 0; q < kModeVals; ++q) {
+                    float l, h;
+                    lbp::split(acc2[q], l, h);
+                    acc[q] = l + h;
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kModeVals; ++q) acc[q] = 0.0f;
+                for (uint32_t k = threadIdx.x; k < tl.count; k += blockDim.x)
+                    batch_node<DT, NOISE, OBS>(d, tl.begin + k, src, dst, a.phys, step, a.phase, acc);
+            }
+            if (OBS) {
+                double *rec = trec < a.rec_cap ? a.modes + ((size_t)tl.rep * a.rec_cap + trec) * kModeVals : nullptr;
+                record_warp(acc, rec);
+            }
         }
         if (!batch_barrier(a)) return;
         cur ^= 1u;
@@ -155,6 +345,47 @@ __global__ void k_batch(BatchArgs a)
         a.state->step = step;
         a.state->cur = cur;
     }
+}
+
+template <int DT, bool NOISE, bool OBS>
+__global__ void k_batch(BatchArgs a)
+{
+    batch_run<DT, NOISE, OBS, false>(a);
+}
+
+template <int DT, bool NOISE, bool OBS>
+__global__ void __maxnreg__(kBatchPairMaxRegs) k_batch_pair(BatchArgs a)
+{
+    batch_run<DT, NOISE, OBS, true>(a);
+}
+
+__global__ void k_set_rec_step0(BatchState *st, uint32_t v)
+{
+    st->rec_step0 = v;
+}
+
+// Autocorrelation of the recorded transverse modes of replica blockIdx.x at
+// lag tau = blockIdx.y * blockDim.x + threadIdx.x:
+//   C(tau) = (1 / (6 (t_end - t_begin - tau) V^2)) sum_{t0 = t_begin}^{t_end - tau - 1}
+//            sum_q rec[t0 + tau][q] rec[t0][q],
+// the mean over t0 and the six modes of Re u^(t0 + tau) conj(u^(t0)) with
+// u^ = (record) / V.
+__global__ void k_mode_acf(const double *modes, const BatchDesc *desc, int cap, int t_begin, int t_end,
+                           int max_lag, double *acf)
+{
+    const int rep = blockIdx.x;
+    const int tau = blockIdx.y * blockDim.x + threadIdx.x;
+    if (tau > max_lag) return;
+    const double *s = modes + (size_t)rep * cap * kModeVals;
+    const int cnt = t_end - t_begin - tau;
+    double acc = 0.0;
+    for (int t0 = t_begin; t0 < t_end - tau; ++t0) {
+        const double *x = s + (size_t)t0 * kModeVals, *y = s + (size_t)(t0 + tau) * kModeVals;
+#pragma unroll
+        for (int q = 0; q < kModeVals; ++q) acc = fma(x[q], y[q], acc);
+    }
+    const double V = (double)desc[rep].nodes;
+    acf[(size_t)rep * (max_lag + 1) + tau] = cnt > 0 ? acc / (6.0 * (double)cnt * V * V) : 0.0;
 }
 
 }  // namespace
@@ -189,6 +420,12 @@ struct lb_batch {
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     uint64_t launches = 0;
+    // transverse-mode records (lb_batch_record_modes)
+    double *modes = nullptr;        // caller's [n][rec_cap][12], NULL: not recording
+    int rec_cap = 0;
+    uint32_t rec_step0 = 0;
+    float2 *phase = nullptr;        // library: per-replica (cos, -sin) tables
+    bool pairs = false;             // every replica has even nx: two nodes per thread
 };
 
 using namespace lbi;
@@ -239,20 +476,27 @@ StepArgs batch_phys(const lb_batch *b)
     return make_args(&tmp);
 }
 
-template <int DT, bool NOISE>
-void *kernel_ptr()
+template <int DT, bool NOISE, bool OBS>
+void *kernel_ptr(bool pair)
 {
-    return (void *)k_batch<DT, NOISE>;
+    return pair ? (void *)k_batch_pair<DT, NOISE, OBS> : (void *)k_batch<DT, NOISE, OBS>;
+}
+
+template <bool OBS>
+void *pick_kernel_obs(const lb_batch *b)
+{
+    const bool noise = b->phys.kT > 0.0;
+    const bool pr = b->pairs;
+    switch (b->phys.dtype) {
+    case LB_F32: return noise ? kernel_ptr<0, true, OBS>(pr) : kernel_ptr<0, false, OBS>(pr);
+    case LB_F16: return noise ? kernel_ptr<1, true, OBS>(pr) : kernel_ptr<1, false, OBS>(pr);
+    default: return noise ? kernel_ptr<2, true, OBS>(pr) : kernel_ptr<2, false, OBS>(pr);
+    }
 }
 
 void *pick_kernel(const lb_batch *b)
 {
-    const bool noise = b->phys.kT > 0.0;
-    switch (b->phys.dtype) {
-    case LB_F32: return noise ? kernel_ptr<0, true>() : kernel_ptr<0, false>();
-    case LB_F16: return noise ? kernel_ptr<1, true>() : kernel_ptr<1, false>();
-    default: return noise ? kernel_ptr<2, true>() : kernel_ptr<2, false>();
-    }
+    return b->modes ? pick_kernel_obs<true>(b) : pick_kernel_obs<false>(b);
 }
 
 // Resident blocks for a configuration (cooperative launches need all of them).
@@ -279,6 +523,9 @@ cudaError_t launch_batch(lb_batch *b, int nsteps)
     a.bar = b->bar;
     a.err = b->err;
     a.spin_limit = b->spin_limit;
+    a.modes = b->modes;
+    a.phase = b->phase;
+    a.rec_cap = (uint32_t)b->rec_cap;
     const int grid = std::min(b->cfg.grid, b->ntiles);
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(grid > 0 ? grid : 1);
@@ -397,6 +644,8 @@ lb_status lb_batch_create(const lb_params *per_replica, int n, void *pops_a, voi
     b->pops[1] = pops_b;
     b->stream = (cudaStream_t)stream;
     b->rep_params.assign(per_replica, per_replica + n);
+    b->pairs = true;
+    for (int r = 0; r < n; ++r) b->pairs = b->pairs && (per_replica[r].nx % 2 == 0);
     size_t off = 0;
     for (int r = 0; r < n; ++r) {
         const lb_params &p = per_replica[r];
@@ -408,6 +657,7 @@ lb_status lb_batch_create(const lb_params *per_replica, int n, void *pops_a, voi
         d.pitch = (uint32_t)lb_plane_pitch(&p);
         d.off = off;
         d.replica = p.replica;
+        d.phase = 0;  // set by lb_batch_record_modes
         d.dx = make_div((uint32_t)p.nx);
         d.dxy = make_div((uint32_t)(p.nx * p.ny));
         d.rk = lbd::make_round_keys(p.seed);
@@ -426,7 +676,7 @@ lb_status lb_batch_create(const lb_params *per_replica, int n, void *pops_a, voi
         set_error("lb_batch_create: device allocation failed (%s)", cudaGetErrorString(e));
         return LB_ENOMEM;
     }
-    BatchState s0{0u, 0u};
+    BatchState s0{0u, 0u, 0u};
     e = cudaMemcpy(b->desc, b->desc_h.data(), n * sizeof(BatchDesc), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->state, &s0, sizeof(s0), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->bar, 0, 3 * sizeof(unsigned int));
@@ -456,6 +706,7 @@ lb_status lb_batch_destroy(lb_batch *b)
     cudaFree(b->bar);
     cudaFree(b->err);
     cudaFree(b->partials);
+    cudaFree(b->phase);
     delete b;
     return LB_OK;
 }
@@ -551,7 +802,7 @@ lb_status lb_batch_sync(lb_batch *b, uint32_t *bits)
         // reset the error word, the barrier (abort flag, counters) and the
         // device step / buffer record to the host's for reuse; the populations
         // of a stopped run are undefined and must be set again
-        BatchState s{b->step, (uint32_t)b->cur};
+        BatchState s{b->step, (uint32_t)b->cur, b->rec_step0};
         e = cudaMemcpy(b->state, &s, sizeof(s), cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemset(b->err, 0, sizeof(unsigned int));
         if (e == cudaSuccess) e = cudaMemset(b->bar, 0, 3 * sizeof(unsigned int));
@@ -676,6 +927,85 @@ lb_status lb_batch_moments(lb_batch *b, int replica, float *rho, float *j, float
     cudaError_t e = launch_moments(&h, h.pops[h.cur], rho, j, pi, sums);
     b->launches += sums ? 2 : 1;
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_batch_moments", e);
+}
+
+lb_status lb_batch_record_modes(lb_batch *b, double *modes, int capacity)
+{
+    if (!b || (modes && capacity < 1)) {
+        set_error("lb_batch_record_modes: bad argument");
+        return LB_EINVAL;
+    }
+    if (modes && ((uintptr_t)modes & 7u)) {
+        set_error("lb_batch_record_modes: records must be 8-byte aligned");
+        return LB_EINVAL;
+    }
+    cudaError_t e = cudaSuccess;
+    if (modes && !b->phase) {
+        // (cos, -sin)(2 pi r / L) for r along x, y, z of every replica, in FP64 rounded once
+        std::vector<float2> tab;
+        for (int r = 0; r < b->n; ++r) {
+            BatchDesc &d = b->desc_h[r];
+            d.phase = (uint32_t)tab.size();
+            const int L3[3] = {d.nx, d.ny, d.nz};
+            for (int ax = 0; ax < 3; ++ax)
+                for (int q = 0; q < L3[ax]; ++q) {
+                    const double ph = 2.0 * M_PI * (double)q / (double)L3[ax];
+                    tab.push_back(make_float2((float)std::cos(ph), (float)-std::sin(ph)));
+                }
+        }
+        e = cudaMalloc((void **)&b->phase, tab.size() * sizeof(float2));
+        if (e != cudaSuccess) {
+            b->phase = nullptr;
+            set_error("lb_batch_record_modes: phase table allocation failed");
+            return LB_ENOMEM;
+        }
+        e = cudaMemcpy(b->phase, tab.data(), tab.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(b->desc, b->desc_h.data(), b->n * sizeof(BatchDesc), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail("lb_batch_record_modes (phase tables)", e);
+    }
+    if (modes) {
+        e = cudaMemsetAsync(modes, 0, (size_t)b->n * capacity * kModeVals * sizeof(double), b->stream);
+        if (e == cudaSuccess) {
+            k_set_rec_step0<<<1, 1, 0, b->stream>>>(b->state, b->step);
+            b->launches += 1;
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return cuda_fail("lb_batch_record_modes (clearing the records)", e);
+    }
+    const bool kernel_changes = (modes != nullptr) != (b->modes != nullptr);
+    const bool args_change = modes != b->modes || (modes ? capacity : 0) != b->rec_cap;
+    b->modes = modes;
+    b->rec_cap = modes ? capacity : 0;
+    b->rec_step0 = b->step;
+    if (kernel_changes) {
+        // the recording kernel may differ in occupancy: recompute the grid (this drops the graph)
+        lb_batch_config c = b->cfg;
+        return apply_config(b, &c);
+    }
+    if (args_change && b->graph) {  // the captured launch holds the old record arguments
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_steps = 0;
+    }
+    return LB_OK;
+}
+
+lb_status lb_batch_mode_acf(lb_batch *b, const double *modes, int capacity, int t_begin, int t_end, int max_lag,
+                            double *acf)
+{
+    if (!b || !modes || !acf || capacity < 1 || t_begin < 0 || t_end > capacity || t_begin >= t_end ||
+        max_lag < 0 || max_lag >= t_end - t_begin) {
+        set_error("lb_batch_mode_acf: bad argument (need 0 <= t_begin < t_end <= capacity, 0 <= max_lag < t_end - "
+                  "t_begin)");
+        return LB_EINVAL;
+    }
+    const int threads = 128;
+    const dim3 grid((unsigned)b->n, (unsigned)((max_lag + threads) / threads));
+    k_mode_acf<<<grid, threads, 0, b->stream>>>(modes, b->desc, capacity, t_begin, t_end, max_lag, acf);
+    b->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_batch_mode_acf", e);
 }
 
 lb_status lb_batch_get_launch_count(const lb_batch *b, uint64_t *count)

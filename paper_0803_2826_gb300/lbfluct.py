@@ -39,11 +39,11 @@ EXPORTS = (
     "lb_set_timing", "lb_get_timing", "lb_step_sums", "lb_adjoint_step_impulse", "lb_adjoint_couple",
     "lb_adjoint_kinetic_coupled",
     "lb_get_launch_count", "lb_moment_sums_static", "lb_step_from", "lb_adjoint_step",
-    "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic",
+    "lb_adjoint_seed_kinetic", "lb_adjoint_kinetic", "lb_adjoint_forward", "lb_adjoint_backward",
     "lb_batch_population_bytes", "lb_batch_create", "lb_batch_destroy", "lb_batch_step", "lb_batch_sync",
     "lb_batch_autotune", "lb_batch_set_config", "lb_batch_get_config", "lb_batch_set_barrier_limit",
     "lb_batch_get_step", "lb_batch_get_launch_count", "lb_batch_init_equilibrium", "lb_batch_set_populations",
-    "lb_batch_get_populations", "lb_batch_moments", "lb_version",
+    "lb_batch_get_populations", "lb_batch_moments", "lb_batch_record_modes", "lb_batch_mode_acf", "lb_version",
 )
 
 
@@ -155,6 +155,8 @@ def load(path: str | None = None):
             "lb_adjoint_step": (i, [H, vp, vp, vp, vp]),
             "lb_adjoint_seed_kinetic": (i, [H, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp, vp]),
             "lb_adjoint_kinetic": (i, [H, i, i, C.POINTER(C.c_int), C.POINTER(C.c_int), vp, vp]),
+            "lb_adjoint_forward": (i, [H, i, i, C.POINTER(C.c_int), C.POINTER(C.c_int), vp]),
+            "lb_adjoint_backward": (i, [H, vp]),
             "lb_batch_population_bytes": (C.c_size_t, [P, i]),
             "lb_batch_create": (i, [P, i, vp, vp, vp, C.POINTER(H)]),
             "lb_batch_destroy": (i, [H]),
@@ -170,6 +172,8 @@ def load(path: str | None = None):
             "lb_batch_set_populations": (i, [H, i, vp]),
             "lb_batch_get_populations": (i, [H, i, vp]),
             "lb_batch_moments": (i, [H, i, vp, vp, vp, vp]),
+            "lb_batch_record_modes": (i, [H, vp, i]),
+            "lb_batch_mode_acf": (i, [H, vp, i, i, i, i, vp]),
             "lb_version": (C.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -415,6 +419,14 @@ def lb_adjoint_kinetic(h, nsteps, checkpoint_every, lo, hi, grad_force, loss):
                                      _ptr(grad_force), _ptr(loss)))
 
 
+def lb_adjoint_forward(h, nsteps, checkpoint_every, lo, hi, loss):
+    _check(load().lb_adjoint_forward(h, int(nsteps), int(checkpoint_every), _int3(lo), _int3(hi), _ptr(loss)))
+
+
+def lb_adjoint_backward(h, grad_force):
+    _check(load().lb_adjoint_backward(h, _ptr(grad_force)))
+
+
 def _params_array(plist):
     arr = (lb_params * len(plist))()
     for k, p in enumerate(plist):
@@ -497,6 +509,17 @@ def lb_batch_get_populations(b, replica, n):
 
 def lb_batch_moments(b, replica, rho=None, j=None, pi=None, sums=None):
     _check(load().lb_batch_moments(b, int(replica), _ptr(rho), _ptr(j), _ptr(pi), _ptr(sums)))
+
+
+def lb_batch_record_modes(b, modes, capacity):
+    """modes: device float64 [n][capacity][12] (or None to stop recording)."""
+    _check(load().lb_batch_record_modes(b, _ptr(modes), int(capacity)))
+
+
+def lb_batch_mode_acf(b, modes, capacity, t_begin, t_end, max_lag, acf):
+    """acf: device float64 [n][max_lag + 1]."""
+    _check(load().lb_batch_mode_acf(b, _ptr(modes), int(capacity), int(t_begin), int(t_end), int(max_lag),
+                                    _ptr(acf)))
 
 
 class Batch:

@@ -130,3 +130,91 @@ def test_seed7_replica_workload_subset(ora):
         torch.cuda.synchronize()
         assert abs(sums[0].item()) < 1e-6 * np.prod(shapes[r])
     B.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_mode_records_match_oracle(ora, use_graph):
+    """lb_batch_record_modes: the six transverse velocity modes each step
+    records, per replica, against oracle.transverse_modes of the state that
+    step collides (uneven boxes, gammas, noise, a recording started after two
+    unrecorded steps, steps past the capacity dropped); lb_batch_mode_acf
+    against oracle.mode_autocorrelation of the same records."""
+    shapes = [(8, 8, 8), (12, 10, 8), (6, 5, 7), (16, 16, 16)]
+    n, cap, nsteps = len(shapes), 12, 14
+    stream = torch.cuda.Stream()
+    B = L.Batch(shapes, seeds=[21 + k for k in range(n)], replicas=list(range(n)), kT=1e-4, stream=stream, **GAM)
+    us = [inputs.shear_wave(s, 0.01) + inputs.gaussian_field(s, 3, 1e-3, seed=30 + k) for k, s in enumerate(shapes)]
+    rec = torch.full((n, cap, 12), float("nan"), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        for k in range(n):
+            L.lb_batch_init_equilibrium(B.b, k, None, _dev(us[k]))
+        L.lb_batch_step(B.b, 2, use_graph)
+        L.lb_batch_record_modes(B.b, rec, cap)
+        L.lb_batch_step(B.b, 5, use_graph)
+        L.lb_batch_step(B.b, nsteps - 5, use_graph)
+    L.lb_batch_sync(B.b)
+    got = rec.cpu().numpy()
+    for k, s in enumerate(shapes):
+        p = ora.make_params(s, kT=1e-4, seed=21 + k, replica=k, **GAM)
+        pops = ora.run(p, ora.equilibrium(p, None, us[k]), 2)
+        want = np.zeros((cap, 6), dtype=np.complex128)
+        for t in range(cap):
+            want[t] = ora.transverse_modes(p, pops)
+            pops = ora.step(p, pops, None, 2 + t)
+        V = float(np.prod(s))
+        g = (got[k, :, 0::2] + 1j * got[k, :, 1::2]) / V
+        check("mode records replica %d %s" % (k, s), np.stack([g.real, g.imag]), np.stack([want.real, want.imag]),
+              1e-5, 1e-5)
+    acf = torch.empty((n, 6), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        L.lb_batch_mode_acf(B.b, rec, cap, 1, cap, 5, acf)
+    stream.synchronize()
+    for k, s in enumerate(shapes):
+        V = float(np.prod(s))
+        series = (got[k, :, 0::2] + 1j * got[k, :, 1::2]) / V
+        want = ora.mode_autocorrelation(series, 1, cap, 5)
+        check("mode acf replica %d" % k, acf[k].cpu().numpy(), want, 1e-12, 1e-12)
+    with pytest.raises(L.LBError):
+        L.lb_batch_mode_acf(B.b, rec, cap, 0, cap + 1, 3, acf)
+    B.close()
+
+
+def test_velocity_autocorrelation_512_replicas(ora):
+    """The batched workload as configured: 512 fluctuating replicas (edges
+    from {16, 24, 32, 48, 64} drawn with seed 7, replica r keyed by seed r),
+    kT = 1e-4, 2000 steps from rest in one graph-captured persistent launch
+    that records the transverse modes.  For every edge length, the replicas'
+    mean velocity autocorrelation matches the exact linear theory of the
+    update (tests/lb_linear.py: variance kT / (rho0 V) once thermalised, decay
+    by the shear eigenvalue lambda(L) per step, the transient from rest
+    included) within five standard errors of the replica mean."""
+    import lb_linear as LL
+    edges = inputs.replica_edges(512, 7)
+    shapes = [(e, e, e) for e in edges]
+    n, T, max_lag, kT = 512, 2000, 200, 1e-4
+    stream = torch.cuda.Stream()
+    B = L.Batch(shapes, kT=kT, stream=stream)
+    rec = torch.empty((n, T, 12), dtype=torch.float64, device="cuda")
+    acf = torch.empty((n, max_lag + 1), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        L.lb_batch_init_equilibrium(B.b)
+        L.lb_batch_record_modes(B.b, rec, T)
+        L.lb_batch_step(B.b, T, True)
+        L.lb_batch_mode_acf(B.b, rec, T, 0, T, max_lag, acf)
+    assert L.lb_batch_sync(B.b) == (L.LB_OK, 0)
+    A = acf.cpu().numpy()
+    tables = ora.tables()
+    taus = [0, 1, 10, 50, 100, 200]
+    ed = np.array(edges)
+    for e in sorted(set(edges)):
+        sel = A[ed == e][:, taus]
+        V = float(e) ** 3
+        want = LL.transverse_acf(e, tables, kT, 1.0, V, taus, 0, T)
+        mean = sel.mean(0)
+        se = sel.std(0, ddof=1) / np.sqrt(sel.shape[0])
+        z = (mean - want) / se
+        lam = LL.shear_eigenvalue(e, tables).real
+        print("L=%d (%d replicas) acf / (kT/rho0 V): %s theory %s z %s lambda %.6f" % (
+            e, sel.shape[0], np.round(mean / (kT / V), 4), np.round(want / (kT / V), 4), np.round(z, 2), lam))
+        assert np.all(np.abs(z) < 5), (e, z)
+    B.close()
