@@ -262,13 +262,23 @@ def run_ours(args):
     shape = (args.box,) * 3
     nodes = shape[0] * shape[1] * shape[2]
     npart = N_CHAINS * CHAIN_LEN
+    # the particle state and the moment sums live in one device buffer (so the
+    # end-to-end loop moves each step's input and result in one copy each):
+    # positions FP64 [n][3], momenta FP32 [n][3], then the 38 FP64 sums
+    pos_b, mom_b = npart * 3 * 8, npart * 3 * 4
+    sums_off = (pos_b + mom_b + 255) // 256 * 256
+    io_bytes = sums_off + L.LB_NSUMS * 8
     with torch.cuda.stream(stream):
         lat = L.Lattice(shape, kT=KT, seed=rank, replica=rank, stream=stream)
         lat.init_equilibrium()
         pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, shape, seed=rank)
         mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000 + rank)
-        gpos = torch.as_tensor(pos0).to(dev)
-        gmom = torch.as_tensor(mom0, dtype=torch.float32).to(dev)
+        dio = torch.zeros(io_bytes, dtype=torch.uint8, device=dev)
+        gpos = dio[:pos_b].view(torch.float64).view(npart, 3)
+        gmom = dio[pos_b:pos_b + mom_b].view(torch.float32).view(npart, 3)
+        dsums = dio[sums_off:].view(torch.float64)
+        gpos.copy_(torch.as_tensor(pos0))
+        gmom.copy_(torch.as_tensor(mom0, dtype=torch.float32))
     torch.cuda.synchronize()
     parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
     cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=7 + rank, chain_len=CHAIN_LEN, use_wca=True,
@@ -320,36 +330,44 @@ def run_ours(args):
     st, bits = lat.sync()
     assert bits == 0, "device error word 0x%x" % bits
 
+    # a steadier view of the same loop: max(200, K) steps timed the same way
+    # (the JSON line's value stays the K-step measurement)
+    KS = max(200, K)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with torch.cuda.stream(stream):
+        s0.record(stream)
+        for _ in range(KS):
+            one_step()
+        s1.record(stream)
+    barrier()
+    steady_ms = s0.elapsed_time(s1)
+
     # end to end through the public API with host buffers: per step the
     # particle state goes host -> device from pinned memory, and the particle
     # state plus the moment sums (the 38 sums of lb_moments, accumulated by
-    # the step's stream-collide launch) come back
+    # the step's stream-collide launch) come back -- one copy each way, since
+    # they share one buffer
     KE = min(args.e2e_steps, K)
-    hpos = torch.empty((npart, 3), dtype=torch.float64, pin_memory=True)
-    hmom = torch.empty((npart, 3), dtype=torch.float32, pin_memory=True)
-    hsums = torch.empty(L.LB_NSUMS, dtype=torch.float64, pin_memory=True)
-    dsums = torch.empty(L.LB_NSUMS, dtype=torch.float64, device=dev)
-    hpos.copy_(gpos.cpu())
-    hmom.copy_(gmom.cpu())
+    hio = torch.empty(io_bytes, dtype=torch.uint8, pin_memory=True)
+    hio.copy_(dio.cpu())
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     with torch.cuda.stream(stream):
         e0.record(stream)
         for _ in range(KE):
-            gpos.copy_(hpos, non_blocking=True)
-            gmom.copy_(hmom, non_blocking=True)
+            dio[:pos_b + mom_b].copy_(hio[:pos_b + mom_b], non_blocking=True)
             one_step(dsums)
-            hpos.copy_(gpos, non_blocking=True)
-            hmom.copy_(gmom, non_blocking=True)
-            hsums.copy_(dsums, non_blocking=True)
+            hio.copy_(dio, non_blocking=True)
         e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    h2d = npart * 3 * 8 + npart * 3 * 4
-    d2h = h2d + L.LB_NSUMS * 8
+    h2d = pos_b + mom_b
+    d2h = io_bytes
 
     # max over ranks
-    ms_total, sc_avg, e2e_ms, couple_ms = max_over_ranks([ms_total, sc_avg, e2e_ms, couple_ms], dist, dev)
+    ms_total, sc_avg, e2e_ms, couple_ms, steady_ms = max_over_ranks([ms_total, sc_avg, e2e_ms, couple_ms, steady_ms],
+                                                                   dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -376,7 +394,9 @@ def run_ours(args):
                      "peak_source": peak_src},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": KE},
+                "steps": KE, "copies_per_step": {"h2d": 1, "d2h": 1}},
+        "steady": {"steps": KS, "ms_per_step": steady_ms / KS,
+                   "value": world * nodes * KS / (steady_ms * 1e-3) / 1e6, "unit": "MLUPS"},
         "clocks": clk,
         "wall_s": wall,
     }
@@ -402,15 +422,18 @@ def _forms(peak):
     FP32 form on the same box:
       batched   512 periodic replicas, edges from {16,24,32,48,64} drawn with
                 seed 7, replica r keyed by seed r, kT = 1e-4, FP32: autotuned,
-                then 2000 steps in one graph-replayed persistent launch;
+                then 2000 steps in one graph-replayed persistent launch that
+                records the transverse velocity modes, and their per-replica
+                autocorrelation (see _batched_form);
       adjoint   64^3, kT = 0, force field ~ N(0, 1e-5), kinetic energy of the
                 central 16^3 after 500 steps, checkpoints every 50: forward +
                 reverse ms per step vs 500 plain FP32 steps;
       interpolation  the headline coupled workload with phi_3 and phi_4;
       spheres   256^3 with 512 moving solid spheres (moving bounce-back);
       exp_equilibrium  256^3 steps with the exponential vs the quadratic equilibrium;
-      precision 512^3 between walls, g = 1e-6, kT = 1e-4: ms per LB step with
-                FP16 / BF16 storage vs FP32 storage (no particles)."""
+      precision 512^3 between walls, g = 1e-6, kT = 1e-4, 1e5 free point
+                particles: ms per coupled LB step with FP16 / BF16 storage vs
+                FP32 storage, and the LB step alone."""
     import numpy as np
     import torch
     from paper_0803_2826_gb300 import inputs
@@ -420,33 +443,7 @@ def _forms(peak):
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     # batched replicas
-    edges = inputs.replica_edges(512, 7)
-    B = L.Batch([(e, e, e) for e in edges], kT=KT, stream=stream)
-    with torch.cuda.stream(stream):
-        L.lb_batch_init_equilibrium(B.b)
-    cfg, _ = L.lb_batch_autotune(B.b, 2)
-    with torch.cuda.stream(stream):
-        L.lb_batch_step(B.b, 5, True)
-    torch.cuda.synchronize()
-    nsteps = 2000
-    with torch.cuda.stream(stream):
-        L.lb_batch_step(B.b, nsteps, True)  # records the graph for this length
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    with torch.cuda.stream(stream):
-        a.record(stream)
-        L.lb_batch_step(B.b, nsteps, True)
-        b.record(stream)
-    torch.cuda.synchronize()
-    L.lb_batch_sync(B.b)
-    ms = a.elapsed_time(b)
-    nodes = int(sum(e ** 3 for e in edges))
-    out["batched"] = {"replicas": 512, "nodes": nodes, "steps": nsteps, "launches": 1,
-                      "mlups": nodes * nsteps / (ms * 1e-3) / 1e6,
-                      "hbm_frac": 152 * nodes * nsteps / (ms * 1e-3) / 1e9 / peak,
-                      "config": {"threads": cfg.threads, "tile_nodes": cfg.tile_nodes,
-                                 "blocks_per_sm": cfg.blocks_per_sm, "grid": cfg.grid}}
-    B.close()
+    out["batched"] = _batched_form(stream, peak)
 
     # adjoint vs plain forward
     shape, T, K = (64, 64, 64), 500, 50
@@ -465,16 +462,33 @@ def _forms(peak):
         b.record(stream)
     torch.cuda.synchronize()
     fwd_ms = a.elapsed_time(b) / T
-    t0 = time.perf_counter()
+    # one untimed call sizes the handle's reverse-mode arena; the timed calls
+    # then allocate nothing (CUDA events on the handle's stream)
     with torch.cuda.stream(stream):
         lat.init_equilibrium()
         L.lb_adjoint_kinetic(lat.h, T, K, (24, 24, 24), (40, 40, 40), g, loss)
     torch.cuda.synchronize()
-    adj_ms = (time.perf_counter() - t0) * 1e3 / T
+    a, b, c = ev(), ev(), ev()
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        a.record(stream)
+        L.lb_adjoint_forward(lat.h, T, K, (24, 24, 24), (40, 40, 40), loss)
+        b.record(stream)
+        L.lb_adjoint_backward(lat.h, g)
+        c.record(stream)
+    torch.cuda.synchronize()
+    fwd_ck_ms = a.elapsed_time(b) / T
+    adj_ms = a.elapsed_time(c) / T
+    # algorithmic bytes per node and step: forward 152 + 12 (force field);
+    # reverse 264 (lambda in and out, the state, the force gradient) plus the
+    # recompute of the segment states, 152 + 12
+    alg_ratio = (164 + 264 + 164) / 164
     out["adjoint"] = {"shape": list(shape), "steps": T, "checkpoint_every": K,
-                      "fwd_plus_adj_ms_per_step": adj_ms, "plain_fp32_ms_per_step": fwd_ms,
-                      "ratio": adj_ms / fwd_ms, "loss": loss.item(),
-                      "timing": "wall clock around lb_adjoint_kinetic (includes its checkpoint allocations)"}
+                      "fwd_plus_adj_ms_per_step": adj_ms, "fwd_with_checkpoints_ms_per_step": fwd_ck_ms,
+                      "plain_fp32_ms_per_step": fwd_ms, "ratio": adj_ms / fwd_ms,
+                      "algorithmic_bytes_ratio": alg_ratio, "loss": loss.item(),
+                      "timing": "CUDA events around lb_adjoint_forward + lb_adjoint_backward on the handle's "
+                                "stream; the checkpoint arena was allocated by an earlier call"}
     lat.close()
 
     # wider interpolation stencils on the headline workload
@@ -504,31 +518,135 @@ def _forms(peak):
         torch.cuda.empty_cache()
     out["exp_equilibrium"] = exp_eq
 
-    # reduced-precision storage
+    # reduced-precision storage: the configured workload (512^3 between walls,
+    # Poiseuille force, 1e5 free point particles with Gamma = 20 in MD units,
+    # 10 sub-steps per LB step), and the LB step alone beside it
     shape = (512, 512, 512)
+    npart = 100000
+    pos = inputs.uniform_particles(npart, shape, seed=1, zrange=(1.0, 510.0))
+    mom = inputs.maxwell_momenta(npart, MASS, KT, seed=2)
     prec = {}
     for name, code, esz in (("f32", L.LB_F32, 4), ("f16", L.LB_F16, 2), ("bf16", L.LB_BF16, 2)):
         lat = L.Lattice(shape, dtype=code, kT=KT, seed=3, walls=True, body_force=(1e-6, 0, 0), stream=stream)
+        gpos = torch.as_tensor(pos).cuda()
+        gmom = torch.as_tensor(mom, dtype=torch.float32).cuda()
+        parts = L.particles(npart, gpos, gmom, mass0=MASS, gamma0=GAMMA)
+        cpp = L.couple_params(n_substeps=NSUB, dt=DT, seed=5, overlap=True)
+        nt = [0]
+
+        def coupled(n):
+            for _ in range(n):
+                cpp.md_step0 = NSUB * nt[0]
+                L.lb_couple_particles(lat.h, parts, cpp)
+                lat.step(1)
+                nt[0] += 1
+
         with torch.cuda.stream(stream):
             lat.init_equilibrium()
+            coupled(3)
             lat.step(3)
         torch.cuda.synchronize()
-        a, b = ev(), ev()
+        a, b, c = ev(), ev(), ev()
         with torch.cuda.stream(stream):
             a.record(stream)
-            lat.step(20)
+            coupled(20)
             b.record(stream)
+            lat.step(20)
+            c.record(stream)
         torch.cuda.synchronize()
+        assert lat.sync() == (L.LB_OK, 0)
         ms = a.elapsed_time(b) / 20
+        ms_lb = b.elapsed_time(c) / 20
         nfl = 512 * 512 * 510
         prec[name] = {"ms_per_step": ms, "mlups": nfl / (ms * 1e-3) / 1e6,
-                      "hbm_frac": 2 * 19 * esz * nfl / (ms * 1e-3) / 1e9 / peak}
+                      "hbm_frac": 2 * 19 * esz * nfl / (ms * 1e-3) / 1e9 / peak,
+                      "lb_only_ms_per_step": ms_lb,
+                      "lb_only_hbm_frac": 2 * 19 * esz * nfl / (ms_lb * 1e-3) / 1e9 / peak}
         lat.close()
+        del gpos, gmom
         torch.cuda.empty_cache()
     for name in ("f16", "bf16"):
         prec[name]["speedup_vs_f32"] = prec["f32"]["ms_per_step"] / prec[name]["ms_per_step"]
-    out["precision"] = {"shape": list(shape), "walls": True, "kT": KT, **prec}
+        prec[name]["lb_only_speedup_vs_f32"] = prec["f32"]["lb_only_ms_per_step"] / prec[name]["lb_only_ms_per_step"]
+    out["precision"] = {"shape": list(shape), "walls": True, "kT": KT, "particles": npart,
+                        "workload": "Poiseuille g = 1e-6 between walls at z = 0, 511, 1e5 free particles "
+                                    "(Gamma = 20 MD units), 10 sub-steps per LB step, overlapped coupling",
+                        **prec}
     return out
+
+
+def _batched_form(stream, peak, nsteps=2000, max_lag=200, t_begin=1000):
+    """512 replicas, autotuned, 2000 steps per graph-replayed persistent
+    launch: first without the mode records, then from rest with them
+    (lb_batch_record_modes) and their per-replica velocity autocorrelation
+    (lb_batch_mode_acf over steps t_begin .. nsteps), summarised per edge
+    length as the replicas' mean C(0) / (kT / (rho0 V)) and the mean decay per
+    step (C(tau) / C(0))^(1/tau) at tau = 1 and 20 (the shear eigenvalue; the
+    hydrodynamic value exp(-nu k^2), nu = 1/6, beside it)."""
+    import math
+
+    import numpy as np
+    import torch
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    edges = inputs.replica_edges(512, 7)
+    n = len(edges)
+    nodes = int(sum(e ** 3 for e in edges))
+    B = L.Batch([(e, e, e) for e in edges], kT=KT, stream=stream)
+    with torch.cuda.stream(stream):
+        L.lb_batch_init_equilibrium(B.b)
+    cfg, _ = L.lb_batch_autotune(B.b, 2)
+
+    def timed():
+        a, b = ev(), ev()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            L.lb_batch_step(B.b, nsteps, True)
+            b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    with torch.cuda.stream(stream):
+        L.lb_batch_step(B.b, nsteps, True)  # records the graph for this length
+    torch.cuda.synchronize()
+    ms_plain = timed()
+    rec = torch.empty((n, nsteps, 12), dtype=torch.float64, device="cuda")
+    acf = torch.empty((n, max_lag + 1), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        L.lb_batch_record_modes(B.b, rec, nsteps)
+        L.lb_batch_step(B.b, nsteps, True)  # graph of the recording kernel
+        L.lb_batch_init_equilibrium(B.b)    # rest again; the records restart at the next step
+        L.lb_batch_record_modes(B.b, rec, nsteps)
+    torch.cuda.synchronize()
+    ms_rec = timed()
+    with torch.cuda.stream(stream):
+        L.lb_batch_mode_acf(B.b, rec, nsteps, t_begin, nsteps, max_lag, acf)
+    L.lb_batch_sync(B.b)
+    A = acf.cpu().numpy()
+    ed = np.array(edges)
+    per_edge = {}
+    for e in sorted(set(edges)):
+        sel = A[ed == e]
+        V = float(e) ** 3
+        c0 = sel[:, 0].mean()
+        per_edge[str(e)] = {
+            "replicas": int(sel.shape[0]),
+            "c0_over_kT_rho0V": c0 / (KT / V),
+            "c0_stderr": sel[:, 0].std(ddof=1) / math.sqrt(sel.shape[0]) / (KT / V),
+            "decay_per_step_tau1": sel[:, 1].mean() / c0,
+            "decay_per_step_tau20": (sel[:, 20].mean() / c0) ** (1.0 / 20),
+            "exp_minus_nu_k2": math.exp(-(1.0 / 6.0) * (2 * math.pi / e) ** 2),
+        }
+    B.close()
+    mk = lambda ms: {"ms": ms, "mlups": nodes * nsteps / (ms * 1e-3) / 1e6,  # noqa: E731
+                     "hbm_frac": 152 * nodes * nsteps / (ms * 1e-3) / 1e9 / peak}
+    return {"replicas": n, "nodes": nodes, "steps": nsteps, "launches": 1,
+            **mk(ms_rec), "plain": mk(ms_plain), "timing": "with the mode records (the configured workload); "
+            "'plain' without them",
+            "autocorrelation": {"steps": [t_begin, nsteps], "start": "rest", "per_edge": per_edge},
+            "config": {"threads": cfg.threads, "tile_nodes": cfg.tile_nodes,
+                       "blocks_per_sm": cfg.blocks_per_sm, "grid": cfg.grid}}
 
 
 def _interpolation_forms(stream, steps=100):

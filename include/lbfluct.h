@@ -69,6 +69,9 @@ typedef enum { LB_F32 = 0, LB_F16 = 1, LB_BF16 = 2 } lb_dtype;
                                         finite (its stencil was clamped)         */
 #define LB_DERR_SPHERE        0x20u  /* spheres: a node claimed by two spheres, or
                                         a sphere moved more than one node a step */
+#define LB_DERR_BOUNDS        0x40u  /* a library built with LB_DEBUG_BOUNDS found an
+                                        element index outside its array (the access
+                                        was skipped)                               */
 
 #define LB_NSUMS 38  /* lb_moments sums: [0..18] sum_r dm_k, [19..37] sum_r dm_k^2 */
 

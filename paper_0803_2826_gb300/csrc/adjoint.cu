@@ -434,6 +434,37 @@ bool box_ok(const lb_handle *h, const int lo[3], const int hi[3])
     return true;
 }
 
+// Carve `count` blocks of `bytes` each (256-byte aligned) from the handle's
+// arena, growing it first if needed (the only allocation of the reverse-mode
+// drivers; a grown arena replaces the old one, whose contents are dropped).
+struct Carver {
+    size_t need = 0;
+    std::vector<std::pair<void **, size_t>> req;
+    void add(void **p, size_t bytes)
+    {
+        req.push_back({p, need});
+        need += (bytes + 255) & ~(size_t)255;
+    }
+    cudaError_t place(lb_handle *h)
+    {
+        if (h->arena_bytes < need) {
+            cudaError_t e = cudaStreamSynchronize(h->stream);  // the old arena may still be in use
+            if (e != cudaSuccess) return e;
+            cudaFree(h->arena);
+            h->arena = nullptr;
+            h->arena_bytes = 0;
+            e = cudaMalloc((void **)&h->arena, need);
+            if (e != cudaSuccess) {
+                h->arena = nullptr;
+                return e;
+            }
+            h->arena_bytes = need;
+        }
+        for (auto &r : req) *r.first = h->arena + r.second;
+        return cudaSuccess;
+    }
+};
+
 }  // namespace
 }  // namespace lbi
 
@@ -487,75 +518,125 @@ lb_status lb_adjoint_seed_kinetic(lb_handle *h, const void *state, const int lo[
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_seed_kinetic", e);
 }
 
-lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
-                             float *grad_force, double *loss)
+// Arena layout of the uncoupled reverse pass: nseg checkpoints, K - 1
+// segment states, two adjoint buffers.
+struct KineticBuffers {
+    std::vector<void *> ckpt, seg;
+    float *lam[2] = {nullptr, nullptr};
+    float *gseed = nullptr;  // dL/df of the loss itself (j = sum n c + f/2), [3][N]
+};
+
+static cudaError_t kinetic_buffers(lb_handle *h, int nsteps, int K, KineticBuffers &b)
 {
-    if (!check_adjoint_handle(h, "lb_adjoint_kinetic")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
-    if (nsteps < 1 || checkpoint_every < 1 || !lo || !hi || !grad_force || !loss || !box_ok(h, lo, hi)) {
-        set_error("lb_adjoint_kinetic: need nsteps >= 1, checkpoint_every >= 1, a valid sub-box and outputs");
+    const int nseg = (nsteps + K - 1) / K;
+    const size_t pop_bytes = 19 * h->pitch * h->elem;
+    const size_t lam_bytes = 19 * h->pitch * sizeof(float);
+    b.ckpt.assign(nseg, nullptr);
+    b.seg.assign(K, nullptr);
+    Carver c;
+    for (int s = 0; s < nseg; ++s) c.add(&b.ckpt[s], pop_bytes);
+    for (int k = 1; k < K; ++k) c.add(&b.seg[k], pop_bytes);
+    for (int q = 0; q < 2; ++q) c.add((void **)&b.lam[q], lam_bytes);
+    c.add((void **)&b.gseed, 3 * h->n_nodes * sizeof(float));
+    return c.place(h);
+}
+
+lb_status lb_adjoint_forward(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
+                             double *loss)
+{
+    const NvtxRange range("lb_adjoint_forward");
+    if (!check_adjoint_handle(h, "lb_adjoint_forward")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
+    if (nsteps < 1 || checkpoint_every < 1 || !lo || !hi || !loss || !box_ok(h, lo, hi)) {
+        set_error("lb_adjoint_forward: need nsteps >= 1, checkpoint_every >= 1, a valid sub-box and a loss");
         return LB_EINVAL;
     }
     join_overlap(h);
     if (h->facc_dirty) {
-        set_error("lb_adjoint_kinetic: pending particle impulses are not differentiated");
+        set_error("lb_adjoint_forward: pending particle impulses are not differentiated");
         return LB_EUNSUPPORTED;
     }
     const int K = std::min(checkpoint_every, nsteps);
-    const int nseg = (nsteps + K - 1) / K;
-    const size_t pop_bytes = 19 * h->pitch * h->elem;
-    const size_t lam_bytes = 19 * h->pitch * sizeof(float);
-    std::vector<void *> ckpt(nseg, nullptr), seg(K, nullptr);
-    float *lam[2] = {nullptr, nullptr};
-    cudaError_t e = cudaSuccess;
-    auto cleanup = [&]() {
-        for (void *p : ckpt) cudaFree(p);
-        for (int k = 1; k < K; ++k) cudaFree(seg[k]);
-        cudaFree(lam[0]);
-        cudaFree(lam[1]);
-    };
-    for (int s = 0; s < nseg && e == cudaSuccess; ++s) e = cudaMalloc(&ckpt[s], pop_bytes);
-    for (int k = 1; k < K && e == cudaSuccess; ++k) e = cudaMalloc(&seg[k], pop_bytes);
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc((void **)&lam[b], lam_bytes);
+    KineticBuffers b;
+    cudaError_t e = kinetic_buffers(h, nsteps, K, b);
     if (e != cudaSuccess) {
-        cleanup();
-        set_error("lb_adjoint_kinetic: checkpoint allocation failed (%s)", cudaGetErrorString(e));
+        set_error("lb_adjoint_forward: checkpoint allocation failed (%s)", cudaGetErrorString(e));
         return LB_ENOMEM;
     }
+    h->adj_ready = 0;
+    const size_t pop_bytes = 19 * h->pitch * h->elem;
     const uint32_t step0 = h->step;
-    // forward pass with checkpoints every K steps
-    e = cudaMemsetAsync(lam[0], 0, lam_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(lam[1], 0, lam_bytes, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad_force, 0, 3 * h->n_nodes * sizeof(float), h->stream);
     for (int t = 0; t < nsteps && e == cudaSuccess; ++t) {
-        if (t % K == 0) e = cudaMemcpyAsync(ckpt[t / K], h->pops[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        if (t % K == 0) e = cudaMemcpyAsync(b.ckpt[t / K], h->pops[h->cur], pop_bytes, cudaMemcpyDeviceToDevice, h->stream);
         if (e == cudaSuccess && lb_step(h, 1) != LB_OK) e = cudaErrorLaunchFailure;
     }
-    // seed at the final state, then the segments in reverse
-    int cur = 0;
-    if (e == cudaSuccess) {
-        e = cudaMemsetAsync(loss, 0, sizeof(double), h->stream);
-        if (e == cudaSuccess)
-            e = launch_seed(h, h->pops[h->cur], lam[cur], grad_force, loss, make_int3(lo[0], lo[1], lo[2]),
-                            make_int3(hi[0], hi[1], hi[2]));
-        h->launches += 1;
+    // the loss and its seed lambda_T = dL/dstate at the final state (first
+    // adjoint buffer) with its own dL/df (gseed), for lb_adjoint_backward
+    if (e == cudaSuccess) e = cudaMemsetAsync(loss, 0, sizeof(double), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.gseed, 0, 3 * h->n_nodes * sizeof(float), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.lam[0], 0, 19 * h->pitch * sizeof(float), h->stream);
+    if (e == cudaSuccess)
+        e = launch_seed(h, h->pops[h->cur], b.lam[0], b.gseed, loss, make_int3(lo[0], lo[1], lo[2]),
+                        make_int3(hi[0], hi[1], hi[2]));
+    h->launches += 1;
+    if (e != cudaSuccess) return cuda_fail("lb_adjoint_forward", e);
+    h->adj_ready = 1;
+    h->adj_nsteps = nsteps;
+    h->adj_K = K;
+    h->adj_step0 = step0;
+    return LB_OK;
+}
+
+lb_status lb_adjoint_backward(lb_handle *h, float *grad_force)
+{
+    const NvtxRange range("lb_adjoint_backward");
+    if (!check_adjoint_handle(h, "lb_adjoint_backward")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
+    if (!grad_force) {
+        set_error("lb_adjoint_backward: grad_force is NULL");
+        return LB_EINVAL;
     }
+    join_overlap(h);
+    if (!h->adj_ready) {
+        set_error("lb_adjoint_backward: no lb_adjoint_forward run to reverse");
+        return LB_EINVAL;
+    }
+    const int nsteps = h->adj_nsteps, K = h->adj_K;
+    const int nseg = (nsteps + K - 1) / K;
+    KineticBuffers b;
+    cudaError_t e = kinetic_buffers(h, nsteps, K, b);  // the forward's layout: no allocation
+    if (e != cudaSuccess) return cuda_fail("lb_adjoint_backward", e);
+    const size_t lam_bytes = 19 * h->pitch * sizeof(float);
+    e = cudaMemsetAsync(b.lam[1], 0, lam_bytes, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(grad_force, b.gseed, 3 * h->n_nodes * sizeof(float), cudaMemcpyDeviceToDevice,
+                            h->stream);
+    int cur = 0;
     for (int s = nseg - 1; s >= 0 && e == cudaSuccess; --s) {
         const int t0 = s * K, t1 = std::min(nsteps, t0 + K);
-        seg[0] = ckpt[s];
+        b.seg[0] = b.ckpt[s];
         for (int t = t0; t < t1 - 1 && e == cudaSuccess; ++t) {
-            e = step_from(h, seg[t - t0], seg[t - t0 + 1], step0 + (uint32_t)t);
+            e = step_from(h, b.seg[t - t0], b.seg[t - t0 + 1], h->adj_step0 + (uint32_t)t);
             h->launches += 1;
         }
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; --t) {
-            e = launch_adjoint(h, seg[t - t0], lam[cur], lam[1 - cur], grad_force);
+            e = launch_adjoint(h, b.seg[t - t0], b.lam[cur], b.lam[1 - cur], grad_force);
             h->launches += 1;
             cur = 1 - cur;
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // temporaries are freed below
-    seg[0] = nullptr;
-    cleanup();
-    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_kinetic", e);
+    h->adj_ready = 0;  // the adjoint buffers were consumed
+    return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_backward", e);
+}
+
+lb_status lb_adjoint_kinetic(lb_handle *h, int nsteps, int checkpoint_every, const int lo[3], const int hi[3],
+                             float *grad_force, double *loss)
+{
+    if (!grad_force) {
+        set_error("lb_adjoint_kinetic: grad_force is NULL");
+        return LB_EINVAL;
+    }
+    lb_status st = lb_adjoint_forward(h, nsteps, checkpoint_every, lo, hi, loss);
+    if (st != LB_OK) return st;
+    return lb_adjoint_backward(h, grad_force);
 }
 
 
@@ -603,6 +684,7 @@ lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, co
                                      int checkpoint_every, const int lo[3], const int hi[3], float *grad_force,
                                      float *grad_pos, float *grad_mom, double *loss)
 {
+    const NvtxRange range("lb_adjoint_kinetic_coupled");
     if (!check_adjoint_handle(h, "lb_adjoint_kinetic_coupled")) return h ? LB_EUNSUPPORTED : LB_EINVAL;
     if (!parts || !cp || nsteps < 1 || checkpoint_every < 1 || !lo || !hi || !grad_force || !loss ||
         !box_ok(h, lo, hi) || (parts->n > 0 && (!grad_pos || !grad_mom))) {
@@ -632,33 +714,26 @@ lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, co
     float *lam[2] = {nullptr, nullptr};
     float *gstep = nullptr;
     cudaError_t e = cudaSuccess;
-    auto cleanup = [&]() {
-        for (void *p : ckpt) cudaFree(p);
-        for (int k = 1; k < K; ++k) cudaFree(seg[k]);
-        for (double *p : cpos) cudaFree(p);
-        for (float *p : cmom) cudaFree(p);
-        for (double *p : spos) cudaFree(p);
-        for (float *p : smom) cudaFree(p);
-        for (float *p : sfacc) cudaFree(p);
-        cudaFree(lam[0]);
-        cudaFree(lam[1]);
-        cudaFree(gstep);
-    };
-    for (int s = 0; s < nseg && e == cudaSuccess; ++s) {
-        e = cudaMalloc(&ckpt[s], pop_bytes);
-        if (e == cudaSuccess && n) e = cudaMalloc((void **)&cpos[s], pos_bytes);
-        if (e == cudaSuccess && n) e = cudaMalloc((void **)&cmom[s], mom_bytes);
+    {
+        // all temporaries from the handle's arena (allocated once, reused)
+        Carver c;
+        for (int s = 0; s < nseg; ++s) {
+            c.add(&ckpt[s], pop_bytes);
+            if (n) c.add((void **)&cpos[s], pos_bytes);
+            if (n) c.add((void **)&cmom[s], mom_bytes);
+        }
+        for (int k = 0; k <= K; ++k) {
+            if (k > 0 && k < K) c.add(&seg[k], pop_bytes);
+            if (n) c.add((void **)&spos[k], pos_bytes);
+            if (n) c.add((void **)&smom[k], mom_bytes);
+            if (k < K) c.add((void **)&sfacc[k], facc_bytes);
+        }
+        for (int b = 0; b < 2; ++b) c.add((void **)&lam[b], lam_bytes);
+        c.add((void **)&gstep, grad_bytes);
+        e = c.place(h);
     }
-    for (int k = 0; k <= K && e == cudaSuccess; ++k) {
-        if (k > 0 && k < K) e = cudaMalloc(&seg[k], pop_bytes);
-        if (e == cudaSuccess && n) e = cudaMalloc((void **)&spos[k], pos_bytes);
-        if (e == cudaSuccess && n) e = cudaMalloc((void **)&smom[k], mom_bytes);
-        if (e == cudaSuccess && k < K) e = cudaMalloc((void **)&sfacc[k], facc_bytes);
-    }
-    for (int b = 0; b < 2 && e == cudaSuccess; ++b) e = cudaMalloc((void **)&lam[b], lam_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&gstep, grad_bytes);
+    h->adj_ready = 0;  // the arena now holds this call's buffers
     if (e != cudaSuccess) {
-        cleanup();
         set_error("lb_adjoint_kinetic_coupled: checkpoint allocation failed (%s)", cudaGetErrorString(e));
         return LB_ENOMEM;
     }
@@ -675,7 +750,6 @@ lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, co
         lb_status st = (e == cudaSuccess) ? couple_particles(h, parts, &c1) : LB_ECUDA;
         if (st == LB_OK) st = lb_step(h, 1);
         if (st != LB_OK) {
-            cleanup();
             return st;
         }
     }
@@ -742,9 +816,6 @@ lb_status lb_adjoint_kinetic_coupled(lb_handle *h, const lb_particles *parts, co
             cur = 1 - cur;
         }
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // temporaries are freed below
-    seg[0] = nullptr;
-    cleanup();
     return e == cudaSuccess ? LB_OK : cuda_fail("lb_adjoint_kinetic_coupled", e);
 }
 

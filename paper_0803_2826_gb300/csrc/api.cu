@@ -93,6 +93,7 @@ StepArgs make_args(const lb_handle *h)
     a.replica = p.replica;
     a.step = h->step;
     a.rk = lbd::make_round_keys(p.seed);
+    a.err = h->d_err;
     return a;
 }
 
@@ -398,6 +399,7 @@ lb_status lb_destroy(lb_handle *h)
     destroy_spheres(h);
     if (h->claim) cudaFree(h->claim);
     if (h->lam_u) cudaFree(h->lam_u);
+    if (h->arena) cudaFree(h->arena);
     if (h->sc_partials) cudaFree(h->sc_partials);
     if (h->ev_main) cudaEventDestroy(h->ev_main);
     if (h->ev_couple) cudaEventDestroy(h->ev_couple);
@@ -516,6 +518,7 @@ lb_status lb_get_populations(const lb_handle *h, double *n)
 
 lb_status lb_step(lb_handle *h, int nsteps)
 {
+    const lbi::NvtxRange range("lb_step");
     if (!h) {
         set_error("lb_step: handle is NULL");
         return LB_EINVAL;
@@ -533,6 +536,7 @@ lb_status lb_step(lb_handle *h, int nsteps)
 
 lb_status lb_step_sums(lb_handle *h, int nsteps, double *sums)
 {
+    const lbi::NvtxRange range("lb_step_sums");
     if (!h || !sums || nsteps < 1) {
         set_error("lb_step_sums: need a handle, a sums buffer and nsteps >= 1");
         return LB_EINVAL;
@@ -581,6 +585,7 @@ lb_status lb_moments(lb_handle *h, float *rho, float *j, float *pi, double *sums
 
 lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp)
 {
+    const lbi::NvtxRange range("lb_couple_particles");
     if (!h || !parts || !cp) {
         set_error("lb_couple_particles: NULL argument");
         return LB_EINVAL;

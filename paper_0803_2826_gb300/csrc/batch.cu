@@ -139,7 +139,8 @@ __device__ __forceinline__ void batch_node(const BatchDesc &d, uint32_t s, const
         const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
         const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
         const uint32_t off = (uint32_t)((sz * d.ny + sy) * d.nx + sx);
-        n[i] = S::cvt(__ldcg(base + (size_t)i * P + off), ph.inv_scale);
+        n[i] = in_bounds((size_t)i * P + off, 19 * P, ph.err) ? S::cvt(__ldcg(base + (size_t)i * P + off), ph.inv_scale)
+                                                             : 0.0f;
     }
     StepArgs a = ph;
     a.step = step;
@@ -167,7 +168,8 @@ __device__ __forceinline__ void batch_node(const BatchDesc &d, uint32_t s, const
     collide_moments<NOISE>(m, ph.fx, ph.fy, ph.fz, a, d.rk, s, d.replica, out);
     typename S::T *o = dst + d.off;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) o[(size_t)i * P + s] = S::pack(out[i], ph.scale);
+    for (int i = 0; i < 19; ++i)
+        if (in_bounds((size_t)i * P + s, 19 * P, ph.err)) o[(size_t)i * P + s] = S::pack(out[i], ph.scale);
 }
 
 // Nodes s and s + 1 (s even, nx even: the same row) of replica d: the pair
@@ -221,17 +223,22 @@ __device__ __forceinline__ void batch_pair(const BatchDesc &d, uint32_t s, const
         const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
         const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
         const uint32_t r = (uint32_t)i * P + (uint32_t)((sz * d.ny + sy) * d.nx);
-        float v0, v1;
+        const size_t lim = 19 * (size_t)P;
+        float v0 = 0.0f, v1 = 0.0f;  // stored values; FP16 / BF16 unscaled below by one packed multiply
         if (lbd::cx(i) == 0) {
-            ld_pair<DT>(base + r + x0, ph.inv_scale, v0, v1);
+            if (in_bounds(r + x0 + 1, lim, ph.err)) ld_pair<DT>(base + r + x0, 1.0f, v0, v1);
         } else if (lbd::cx(i) == 1) {
-            v0 = S::cvt(__ldcg(base + r + xm), ph.inv_scale);
-            v1 = S::cvt(__ldcg(base + r + x0), ph.inv_scale);
+            if (in_bounds(r + xm, lim, ph.err) && in_bounds(r + x0, lim, ph.err)) {
+                v0 = S::cvt(__ldcg(base + r + xm), 1.0f);
+                v1 = S::cvt(__ldcg(base + r + x0), 1.0f);
+            }
         } else {
-            v0 = S::cvt(__ldcg(base + r + x0 + 1), ph.inv_scale);
-            v1 = S::cvt(__ldcg(base + r + xp), ph.inv_scale);
+            if (in_bounds(r + x0 + 1, lim, ph.err) && in_bounds(r + xp, lim, ph.err)) {
+                v0 = S::cvt(__ldcg(base + r + x0 + 1), 1.0f);
+                v1 = S::cvt(__ldcg(base + r + xp), 1.0f);
+            }
         }
-        n[i] = lbp::f2(v0, v1);
+        n[i] = DT == 0 ? lbp::f2(v0, v1) : lbp::f2(v0, v1) * lbp::f2s(ph.inv_scale);
     }
     StepArgs a = ph;
     a.step = step;
@@ -270,8 +277,8 @@ __device__ __forceinline__ void batch_pair(const BatchDesc &d, uint32_t s, const
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         float o0, o1;
-        lbp::split(out[i], o0, o1);
-        Pair<DT>::store(o + (uint32_t)i * P + s, o0, o1, ph.scale);
+        lbp::split(DT == 0 ? out[i] : out[i] * lbp::f2s(ph.scale), o0, o1);
+        if (in_bounds((uint32_t)i * P + s + 1, 19 * (size_t)P, ph.err)) Pair<DT>::store(o + (uint32_t)i * P + s, o0, o1, 1.0f);
     }
 }
 
@@ -512,6 +519,7 @@ cudaError_t launch_batch(lb_batch *b, int nsteps)
 {
     BatchArgs a;
     a.phys = batch_phys(b);
+    a.phys.err = b->err;
     a.desc = b->desc;
     a.tiles = b->tiles;
     a.ntiles = b->ntiles;
@@ -747,6 +755,7 @@ lb_status lb_batch_set_barrier_limit(lb_batch *b, uint32_t spins)
 
 lb_status lb_batch_step(lb_batch *b, int nsteps, int use_graph)
 {
+    const NvtxRange range("lb_batch_step");
     if (!b || nsteps < 0) {
         set_error("lb_batch_step: bad argument");
         return LB_EINVAL;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstddef>
 #include <cstdint>
@@ -15,6 +16,15 @@
 namespace lbi {
 
 struct Particles;  // defined in particles.cu
+
+// NVTX range around a host call (visible to profilers that attach an NVTX
+// tool; a no-op otherwise, the header-only NVTX loads no library by itself).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace lbi
 
@@ -68,6 +78,15 @@ struct lb_handle {
     int sph_cap;
     int sph_n;            // spheres of the current solid map (-1: none placed)
     double sph_a;
+    // reverse mode: one device arena for the checkpoints, segment states and
+    // adjoint buffers of lb_adjoint_forward / _backward / _kinetic_coupled,
+    // grown on demand and kept until lb_destroy
+    char *arena;
+    size_t arena_bytes;
+    // the run lb_adjoint_forward checkpointed (for lb_adjoint_backward)
+    int adj_ready;        // 1 from a forward until its backward (or another reverse-mode driver)
+    int adj_nsteps, adj_K;
+    uint32_t adj_step0;
 };
 
 namespace lbi {

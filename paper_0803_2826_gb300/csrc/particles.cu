@@ -760,9 +760,11 @@ __global__ void __launch_bounds__(kPartThreads)
             const float w = stencil_node_k<KW>(st, qq, g, x, y, z);
             const size_t P = g.pitch;
             const size_t s = ((size_t)z * g.ny + y) * g.nx + x;
-            atomicAdd(facc + s, -J[0] * w);
-            atomicAdd(facc + P + s, -J[1] * w);
-            atomicAdd(facc + 2 * P + s, -J[2] * w);
+            if (in_bounds(s, g.nn, g.err)) {
+                atomicAdd(facc + s, -J[0] * w);
+                atomicAdd(facc + P + s, -J[1] * w);
+                atomicAdd(facc + 2 * P + s, -J[2] * w);
+            }
         }
     }
     if (q != 0) return;
@@ -1161,9 +1163,11 @@ __device__ __forceinline__ void flush_impulses(const int cell[3], float acc[8][3
         int x, y, z;
         (void)stencil_node(cq, q, g, x, y, z);
         const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
-        atomicAdd(facc + node, acc[q][0]);
-        atomicAdd(facc + g.pitch + node, acc[q][1]);
-        atomicAdd(facc + 2 * g.pitch + node, acc[q][2]);
+        if (in_bounds(node, g.nn, g.err)) {
+            atomicAdd(facc + node, acc[q][0]);
+            atomicAdd(facc + g.pitch + node, acc[q][1]);
+            atomicAdd(facc + 2 * g.pitch + node, acc[q][2]);
+        }
         acc[q][0] = acc[q][1] = acc[q][2] = 0.0f;
     }
 }

@@ -731,6 +731,7 @@ lb_status lb_spheres_place(lb_handle *h, const lb_spheres *s)
 
 lb_status lb_step_spheres(lb_handle *h, const lb_spheres *s)
 {
+    const lbi::NvtxRange range("lb_step_spheres");
     if (!h || !check_spheres(h, s, "lb_step_spheres")) return LB_EINVAL;
     lb_status st = spheres_supported(h, "lb_step_spheres");
     if (st != LB_OK) return st;

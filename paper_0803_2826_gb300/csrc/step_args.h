@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include "d3q19.cuh"
+#include "lbfluct.h"
 
 namespace lbi {
 
@@ -29,6 +30,22 @@ struct StepArgs {
     uint32_t replica;
     uint32_t step;
     lbd::RoundKeys rk;     // Philox round keys of (key0, key1)
+    unsigned int *err;     // device error word (index checks of LB_DEBUG_BOUNDS builds)
 };
+
+// Index checks of a library built with -DLB_DEBUG_BOUNDS: the element index i
+// of an access to an array of n elements is tested first; outside, the error
+// word gets LB_DERR_BOUNDS and the caller skips the access.  In ordinary
+// builds the test is the constant true and costs nothing.
+#ifdef LB_DEBUG_BOUNDS
+__device__ __forceinline__ bool in_bounds(size_t i, size_t n, unsigned int *err)
+{
+    if (i < n) return true;
+    if (err) atomicOr(err, LB_DERR_BOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(size_t, size_t, unsigned int *) { return true; }
+#endif
 
 }  // namespace lbi

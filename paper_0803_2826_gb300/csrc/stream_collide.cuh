@@ -202,12 +202,9 @@ __device__ __forceinline__ void update_node(const typename lbd::Store<DT>::T *__
         const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
         bool bounce = false;
         if (WALLS && lbd::cz(i) != 0) bounce = (sz == 0) || (sz == nz - 1);
-        if (bounce) {
-            n[i] = S::load(src + (size_t)lbd::opposite(i) * P + self, a.inv_scale);
-        } else {
-            const uint32_t off = (uint32_t)((sz * ny + sy) * nx + sx);
-            n[i] = S::load(src + (size_t)i * P + off, a.inv_scale);
-        }
+        const size_t k = bounce ? (size_t)lbd::opposite(i) * P + self
+                                : (size_t)i * P + (uint32_t)((sz * ny + sy) * nx + sx);
+        n[i] = in_bounds(k, 19 * P, a.err) ? S::load(src + k, a.inv_scale) : 0.0f;
     }
 
     // ---- force and collision -----------------------------------------------
@@ -235,7 +232,8 @@ __device__ __forceinline__ void update_node(const typename lbd::Store<DT>::T *__
     if (!valid) return;
     collide_moments<NOISE>(m, fx, fy, fz, a, a.rk, self, a.replica, out);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
+    for (int i = 0; i < 19; ++i)
+        if (in_bounds((size_t)i * P + self, 19 * P, a.err)) dst[(size_t)i * P + self] = S::pack(out[i], a.scale);
 }
 
 __device__ __forceinline__ size_t block_linear()
@@ -484,6 +482,7 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
     }
     const uint32_t P = (uint32_t)a.pitch;
     const uint32_t self = (uint32_t)((z * ny + y) * nx + x0);
+    const size_t lim = 19 * (size_t)P;  // elements of a population buffer (index checks)
 
     lbp::F2 n[19];
 #pragma unroll
@@ -492,22 +491,29 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
         const int sz = lbd::cz(i) == 1 ? zm : (lbd::cz(i) == -1 ? zp : z);
         bool bounce = false;
         if (WALLS && lbd::cz(i) != 0) bounce = (sz == 0) || (sz == nz - 1);
-        float v0, v1;
+        // stored values as loaded (FP16 / BF16: still scaled; the pair is
+        // unscaled below by one packed multiply)
+        float v0 = 0.0f, v1 = 0.0f;
         if (bounce) {
-            PR::load(src + (uint32_t)lbd::opposite(i) * P + self, a.inv_scale, v0, v1);
+            const uint32_t k = (uint32_t)lbd::opposite(i) * P + self;
+            if (in_bounds(k + 1, lim, a.err)) PR::load(src + k, 1.0f, v0, v1);
         } else {
             const uint32_t row = (uint32_t)i * P + (uint32_t)((sz * ny + sy) * nx);
             if (lbd::cx(i) == 0) {
-                PR::load(src + row + x0, a.inv_scale, v0, v1);
+                if (in_bounds(row + x0 + 1, lim, a.err)) PR::load(src + row + x0, 1.0f, v0, v1);
             } else if (lbd::cx(i) == 1) {
-                v0 = S::load(src + row + xm, a.inv_scale);
-                v1 = S::load(src + row + x0, a.inv_scale);
+                if (in_bounds(row + xm, lim, a.err) && in_bounds(row + x0, lim, a.err)) {
+                    v0 = S::load(src + row + xm, 1.0f);
+                    v1 = S::load(src + row + x0, 1.0f);
+                }
             } else {
-                v0 = S::load(src + row + x0 + 1, a.inv_scale);
-                v1 = S::load(src + row + xp, a.inv_scale);
+                if (in_bounds(row + x0 + 1, lim, a.err) && in_bounds(row + xp, lim, a.err)) {
+                    v0 = S::load(src + row + x0 + 1, 1.0f);
+                    v1 = S::load(src + row + xp, 1.0f);
+                }
             }
         }
-        n[i] = lbp::f2(v0, v1);
+        n[i] = DT == 0 ? lbp::f2(v0, v1) : lbp::f2(v0, v1) * lbp::f2s(a.inv_scale);
     }
 
     float f0[3] = {a.fx, a.fy, a.fz}, f1[3] = {a.fx, a.fy, a.fz};
@@ -545,8 +551,8 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         float o0, o1;
-        lbp::split(out[i], o0, o1);
-        PR::store(dst + (uint32_t)i * P + self, o0, o1, a.scale);
+        lbp::split(DT == 0 ? out[i] : out[i] * lbp::f2s(a.scale), o0, o1);
+        if (in_bounds((uint32_t)i * P + self + 1, lim, a.err)) PR::store(dst + (uint32_t)i * P + self, o0, o1, 1.0f);
     }
 }
 

@@ -17,6 +17,7 @@ import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "liblbfluct.so")
+BOUNDS_LIB_PATH = os.path.join(PKG, "liblbfluct_bounds.so")
 
 LB_OK, LB_EINVAL, LB_ENOMEM, LB_ECUDA, LB_ENONFINITE, LB_ETIMEOUT, LB_EUNSUPPORTED, LB_EDEVICE = range(8)
 LB_F32, LB_F16, LB_BF16 = 0, 1, 2
@@ -24,6 +25,7 @@ LB_NSUMS = 38
 LB_DERR_FENE_BROKEN, LB_DERR_NLIST_FULL, LB_DERR_NONFINITE, LB_DERR_BARRIER = 1, 2, 4, 8
 LB_DERR_PARTICLE_RANGE = 16
 LB_DERR_SPHERE = 32
+LB_DERR_BOUNDS = 64
 LB_COUPLE_PER_SUBSTEP, LB_COUPLE_OVERLAP, LB_COUPLE_PHI3, LB_COUPLE_PHI4 = 1, 2, 4, 8
 
 STATUS_NAMES = {0: "LB_OK", 1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENONFINITE",
@@ -101,19 +103,22 @@ _lib = None
 
 
 def load(path: str | None = None):
-    """Load liblbfluct.so (building it first if it is missing); raise if impossible."""
+    """Load liblbfluct.so (building it first if it is missing); raise if
+    impossible.  With LB_DEBUG_BOUNDS=1 in the environment the index-checking
+    build liblbfluct_bounds.so is loaded instead (built on first use)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
-        if not os.path.exists(p):
+        bounds = os.environ.get("LB_DEBUG_BOUNDS", "") not in ("", "0")
+        p = path or (BOUNDS_LIB_PATH if bounds else LIB_PATH)
+        if not os.path.exists(p) or (bounds and path is None):
             from . import build as _build
-            _build.build()
+            _build.build(debug_bounds=bounds)
         try:
             lib = C.CDLL(p)
         except OSError as e:  # no silent fallback
-            raise RuntimeError("liblbfluct.so could not be loaded (%s); the CUDA library is required" % e)
+            raise RuntimeError("%s could not be loaded (%s); the CUDA library is required" % (os.path.basename(p), e))
         vp, i, u32, u64 = C.c_void_p, C.c_int, C.c_uint32, C.c_uint64
         P = C.POINTER(lb_params)
         H = C.c_void_p

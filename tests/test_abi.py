@@ -118,3 +118,13 @@ def test_struct_layouts_match_header(lib, tmp_path):
         want.append(C.sizeof(st))
         want += [getattr(st, f[0]).offset for f in st._fields_]
     assert got == want
+
+
+def test_index_checking_variant_compiles(tmp_path):
+    """The LB_DEBUG_BOUNDS variant (index checks before every population pull
+    and store) compiles for sm_103a: the fused stream-collide unit."""
+    from paper_0803_2826_gb300 import build as B
+    src = os.path.join(B.CSRC, "sc_f32.cu")
+    cmd = [B.nvcc(), *B.ARCH, *B.NVCC_FLAGS, "-DLB_DEBUG_BOUNDS", "-c", src, "-o", str(tmp_path / "sc.o")]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

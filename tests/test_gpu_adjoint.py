@@ -96,6 +96,46 @@ def test_reverse_pass_parity_and_autograd(ora):
     lat.sync()
 
 
+def test_adjoint_forward_backward_split():
+    """lb_adjoint_forward + lb_adjoint_backward give lb_adjoint_kinetic's loss
+    and gradient, also when the lattice moves on in between; the backward
+    runs once per forward; after the first call the reverse-mode arena is
+    reused (no further device allocation)."""
+    shape, T, K = (12, 10, 8), 12, 5
+    lo, hi = (2, 2, 2), (9, 8, 6)
+    ft = dev(inputs.gaussian_field(shape, 3, 1e-5, seed=3).astype(np.float32))
+    lat = L.Lattice(shape, force=ft)
+    g = torch.empty_like(ft)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    def one(split):
+        lat.init_equilibrium()
+        lat.step_index = 0
+        g.fill_(float("nan"))
+        if split:
+            L.lb_adjoint_forward(lat.h, T, K, lo, hi, loss)
+            lat.step(3)
+            L.lb_adjoint_backward(lat.h, g)
+        else:
+            L.lb_adjoint_kinetic(lat.h, T, K, lo, hi, g, loss)
+        torch.cuda.synchronize()
+        return loss.item(), g.cpu().numpy().astype(np.float64)
+
+    la, ga = one(False)
+    free0 = torch.cuda.mem_get_info()[0]
+    lb, gb = one(True)
+    lc, gc = one(True)
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.isfinite(ga).all() and np.abs(ga).max() > 0
+    for l_, g_ in ((lb, gb), (lc, gc)):
+        assert abs(l_ / la - 1) < 1e-12
+        assert np.allclose(g_, ga, rtol=1e-6, atol=1e-9 * np.abs(ga).max())
+    with pytest.raises(L.LBError) as ei:  # consumed by the last backward
+        L.lb_adjoint_backward(lat.h, g)
+    assert ei.value.status == L.LB_EINVAL
+    assert lat.sync() == (L.LB_OK, 0)
+
+
 def test_adjoint_requires_deterministic_run():
     lat = L.Lattice((8, 8, 8), kT=1e-4, force=torch.zeros((3, 8, 8, 8), device="cuda"))
     g = torch.zeros((3, 8, 8, 8), device="cuda")
@@ -125,8 +165,11 @@ def test_config_64cubed_500_steps(ora):
         lat.init_equilibrium()
         lat.step_index = 0
         ft.copy_(field)
-        g = torch.empty_like(ft)
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        if not want_grad:  # the forward half alone (checkpoints and L)
+            L.lb_adjoint_forward(lat.h, T, K, lo, hi, loss)
+            return loss.item(), None
+        g = torch.empty_like(ft)
         L.lb_adjoint_kinetic(lat.h, T, K, lo, hi, g, loss)
         return loss.item(), g.cpu().numpy().astype(np.float64)
 
