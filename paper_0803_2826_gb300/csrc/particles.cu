@@ -14,6 +14,10 @@
 //               during the update)                         Eq. (ftotal)
 //   drift       second half drift of this sub-step and first half drift of the next
 //
+// Free particles (no FENE / WCA) take k_couple_free instead: one launch for
+// all sub-steps of a call (each particle's sub-steps depend on no other
+// particle), with the stencil's node velocities and impulse sums in registers.
+//
 // Positions are double in the caller's buffer, but inside a coupling call a
 // position is an integer cell plus an FP32 offset in [0, 1) (a "shadow"
 // float4, the cell packed in 10-bit fields), so the kernels do no FP64
@@ -21,6 +25,7 @@
 // at a small fraction of its FP32 rate).  Shadows ping-pong between two
 // buffers so every thread reads the positions of the same sub-step.
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "d3q19.cuh"
@@ -380,6 +385,22 @@ __device__ __forceinline__ float stencil_node_k(const Stencil<KW> &s, int q, con
     if (g.z0 > 0) z = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
     else z = wrap_node(z, g.nz);
     return wx * wy * wz;
+}
+
+template <int KW>
+constexpr int free_lanes() { return KW == 2 ? 1 : 8; }
+
+// Coordinates of node q of the stencil with first nodes o (stencil_node_k
+// without the weight).
+template <int KW>
+__device__ __forceinline__ void stencil_coords(const int o[3], int q, const StepArgs &g, int &x, int &y, int &z)
+{
+    const int dx = q % KW, dy = (q / KW) % KW, dz = q / (KW * KW);
+    x = wrap_node(o[0] + dx, g.nx);
+    y = wrap_node(o[1] + dy, g.ny);
+    z = o[2] + dz;
+    if (g.z0 > 0) z = z < 0 ? 0 : (z >= g.nz ? g.nz - 1 : z);
+    else z = wrap_node(z, g.nz);
 }
 
 // ---------------------------------------------------------------------------
@@ -1388,6 +1409,474 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent variant for the wide stencils (phi_3, phi_4: 27 / 64 nodes) of
+// k_couple_persistent: the same sub-step loop, forces, list rebuilds and
+// barriers, one thread per particle, but the fluid velocity at the stencil
+// nodes and the impulse sums there live in the block's shared memory (the
+// 27 / 64 nodes do not fit in registers): column t of sm[c][q][t], c = u_x,
+// u_y, u_z, J_x, J_y, J_z, q the stencil node.  When a particle's stencil
+// origin moves, its thread adds the impulse sums to the accumulator and the
+// warp gathers the new stencil's velocities (four particles per round, the
+// nodes spread over the lanes).  One block of kPThreads per SM (the cache
+// takes 81 KB / 192 KB).
+// ---------------------------------------------------------------------------
+template <int KW>
+constexpr size_t wide_smem_bytes() { return (size_t)6 * KW * KW * KW * kPThreads * sizeof(float); }
+
+template <int KW>
+__device__ __forceinline__ float &wide_cache(float *sm, int c, int q, int t)
+{
+    return sm[((size_t)c * (KW * KW * KW) + q) * kPThreads + t];
+}
+
+// Gather the fluid velocity of all stencil nodes of origin org into the
+// cache column of every lane with `need`; the whole warp calls.
+template <int DT, int KW>
+__device__ __forceinline__ void warp_gather_wide(bool need, const int org[3], const typename lbd::Store<DT>::T *src,
+                                                 const float *ffield, const StepArgs &g, float *sm)
+{
+    constexpr int kN = KW * KW * KW, kR = 4;                // owners per round
+    constexpr int kSlots = (kR * kN + 31) / 32;             // nodes per lane per round
+    const int lane = threadIdx.x & 31, wbase = threadIdx.x & ~31;
+    unsigned m = __ballot_sync(kFullMask, need);
+    while (m) {
+        int own[kR];
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            own[k] = -1;
+            if (m) {
+                own[k] = __ffs(m) - 1;
+                m &= m - 1;
+            }
+        }
+        int o[kR][3];
+#pragma unroll
+        for (int k = 0; k < kR; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) o[k][d] = __shfl_sync(kFullMask, org[d], own[k] < 0 ? 0 : own[k]);
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int item = lane + 32 * sl;
+            if (item < kR * kN) {
+                const int k = item / kN, q = item % kN;
+                int ok = own[0];
+                int oo[3] = {o[0][0], o[0][1], o[0][2]};
+#pragma unroll
+                for (int kk = 1; kk < kR; ++kk)
+                    if (k == kk) {
+                        ok = own[kk];
+                        oo[0] = o[kk][0];
+                        oo[1] = o[kk][1];
+                        oo[2] = o[kk][2];
+                    }
+                if (ok >= 0) {
+                    int x, y, z;
+                    stencil_coords<KW>(oo, q, g, x, y, z);
+                    float u[3];
+                    node_velocity<DT>(src, ffield, x, y, z, g, u);
+                    wide_cache<KW>(sm, 0, q, wbase + ok) = u[0];
+                    wide_cache<KW>(sm, 1, q, wbase + ok) = u[1];
+                    wide_cache<KW>(sm, 2, q, wbase + ok) = u[2];
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// Add this thread's impulse sums at origin org to the accumulator and zero them.
+template <int KW>
+__device__ __forceinline__ void flush_wide(const int org[3], float *sm, float *facc, const StepArgs &g)
+{
+    constexpr int kN = KW * KW * KW;
+    const int t = threadIdx.x;
+#pragma unroll 4
+    for (int q = 0; q < kN; ++q) {
+        int x, y, z;
+        stencil_coords<KW>(org, q, g, x, y, z);
+        const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+        float &jx = wide_cache<KW>(sm, 3, q, t), &jy = wide_cache<KW>(sm, 4, q, t), &jz = wide_cache<KW>(sm, 5, q, t);
+        if (in_bounds(node, g.nn, g.err)) {
+            atomicAdd(facc + node, jx);
+            atomicAdd(facc + g.pitch + node, jy);
+            atomicAdd(facc + 2 * g.pitch + node, jz);
+        }
+        jx = jy = jz = 0.0f;
+    }
+}
+
+template <int DT, int KW>
+__global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArgs a)
+{
+    using T = typename lbd::Store<DT>::T;
+    constexpr int kN = KW * KW * KW;
+    extern __shared__ float wsm[];
+    const CoupleArgs &c = a.c;
+    const StepArgs &g = c.g;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = p < c.n;
+    const T *src = static_cast<const T *>(a.src);
+    if (c.use_wca && blockIdx.x == 0 && threadIdx.x == 0) a.flags[0] = 0u;  // the pre-launch build has run
+
+    // phase 0: first half drift, neighbours (the previous call's impulses were
+    // cleared before the launch)
+    CPos me{}, refp{};
+    float pm[3] = {0.f, 0.f, 0.f};
+    float m = 1.f, G = 1.f, C1 = c.C1, C2 = c.C2, C3 = c.C3;
+    const int self = active ? p : 0;
+    int nnb = 0;
+    int nb[kNbReg];
+#pragma unroll
+    for (int k = 0; k < kNbReg; ++k) nb[k] = self;
+    bool bond_lo = false, bond_hi = false;
+    if (active) {
+        if (c.use_wca) unbin_particle(p, a.head, a.bucket_of);
+        m = a.mass ? a.mass[p] : c.mass0;
+        G = a.gamma ? a.gamma[p] : c.gamma0;
+        if (!c.uniform_coef) {
+            const float x1 = G * c.dt / m;
+            C1 = expf(-x1);
+            C2 = (m / G) * (-expm1f(-x1));
+            C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+        }
+        double r[3] = {a.pos[3 * p], a.pos[3 * p + 1], a.pos[3 * p + 2]};
+        pm[0] = a.mom[3 * p];
+        pm[1] = a.mom[3 * p + 1];
+        pm[2] = a.mom[3 * p + 2];
+        const double hd = 0.5 * (double)c.dt / (double)m;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] += hd * (double)pm[k];
+        confine_d(r, pm, g, KW);
+        if (!split(r, g, me)) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+        a.sh[0][p] = pack(me);
+        if (c.use_wca) {
+            nnb = a.ncount[p];
+            const int *lst = a.nlist + (size_t)p * kMaxNb;
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < nnb) nb[k] = lst[k];
+            refp = unpack(a.ref[p]);
+        }
+        if (c.chain_len > 1) {
+            const int k = p % c.chain_len;
+            bond_lo = k > 0;
+            bond_hi = k < c.chain_len - 1 && p + 1 < c.n;
+        }
+    }
+    const int jlo = bond_lo ? p - 1 : self, jhi = bond_hi ? p + 1 : self;
+    int kmax = __reduce_max_sync(kFullMask, min(nnb, kNbReg));
+    for (int q = 0; q < kN; ++q)
+        wide_cache<KW>(wsm, 3, q, threadIdx.x) = wide_cache<KW>(wsm, 4, q, threadIdx.x) =
+            wide_cache<KW>(wsm, 5, q, threadIdx.x) = 0.0f;
+    int org[3];
+    {
+        Stencil<KW> st;
+        make_stencil<KW>(me, st);
+        org[0] = st.o[0];
+        org[1] = st.o[1];
+        org[2] = st.o[2];
+    }
+    warp_gather_wide<DT, KW>(active, org, src, a.ffield, g, wsm);
+    if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+
+    bool binned = false;
+    const float h = 0.5f * c.dt / m;
+    for (int s = 0; s < a.nsub; ++s) {
+        const float4 *shin = a.sh[s & 1];
+        float4 *shout = a.sh[(s + 1) & 1];
+        float4 v[kNbReg];
+#pragma unroll
+        for (int k = 0; k < kNbReg; ++k)
+            if (k < kmax) v[k] = __ldcg(shin + nb[k]);
+        const float4 vlo = __ldcg(shin + jlo), vhi = __ldcg(shin + jhi);
+        const unsigned int req = c.use_wca ? __ldcg(a.flags + 1 + (s & 1)) : 0u;
+        float th[3] = {0.f, 0.f, 0.f};
+        if (g.kT > 0.0f) particle_theta((uint32_t)p, c.md_step + (uint32_t)s, c, th);
+        Stencil<KW> st;
+        make_stencil<KW>(me, st);
+
+        if (c.use_wca && req == a.epoch0 + (uint32_t)s) {
+            // a particle moved more than half the skin: re-bin all, rebuild every list
+            if (binned) {
+                if (active) unbin_particle(p, a.head, a.bucket_of);
+                if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+            }
+            if (active) bin_particle(p, me, c, a.head, a.next, a.bucket_of);
+            if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+            binned = true;
+            if (active) {
+                int *mine = a.nlist + (size_t)p * kMaxNb;
+                nnb = build_own_list(p, me, shin, a.head, a.next, c, mine, a.err);
+#pragma unroll
+                for (int k = 0; k < kNbReg; ++k) nb[k] = k < nnb ? mine[k] : self;
+                a.ncount[p] = nnb;
+                a.ref[p] = pack(me);
+                refp = me;
+            }
+            kmax = __reduce_max_sync(kFullMask, min(nnb, kNbReg));
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < kmax) v[k] = __ldcg(shin + nb[k]);
+        }
+
+        float F[3] = {c.fext[0], c.fext[1], c.fext[2]};
+        if (c.use_wca) {
+#pragma unroll
+            for (int k = 0; k < kNbReg; ++k)
+                if (k < kmax) wca_add(me, unpack(v[k]), c, F, k < nnb);
+            for (int k = kNbReg; k < nnb; ++k) wca_add(me, unpack(__ldcg(shin + a.nlist[(size_t)p * kMaxNb + k])), c, F);
+        }
+        if (c.chain_len > 1) {
+            if (bond_lo && !fene_add(me, unpack(vlo), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
+            if (bond_hi && !fene_add(me, unpack(vhi), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
+        }
+
+        // particles whose stencil origin moved hand in their impulse sums and
+        // the warp gathers their new stencils
+        const bool moved = active && (st.o[0] != org[0] || st.o[1] != org[1] || st.o[2] != org[2]);
+        if (__any_sync(kFullMask, moved)) {
+            if (moved) {
+                flush_wide<KW>(org, wsm, a.facc, g);
+                org[0] = st.o[0];
+                org[1] = st.o[1];
+                org[2] = st.o[2];
+            }
+            warp_gather_wide<DT, KW>(moved, org, src, a.ffield, g, wsm);
+        }
+
+        if (active) {
+            float up[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < kN; ++q) {
+                const float w = st.w[0][q % KW] * st.w[1][(q / KW) % KW] * st.w[2][q / (KW * KW)];
+                up[0] = fmaf(w, wide_cache<KW>(wsm, 0, q, threadIdx.x), up[0]);
+                up[1] = fmaf(w, wide_cache<KW>(wsm, 1, q, threadIdx.x), up[1]);
+                up[2] = fmaf(w, wide_cache<KW>(wsm, 2, q, threadIdx.x), up[2]);
+            }
+            float pn[3], J[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pn[k] = C1 * pm[k] + C2 * (F[k] + G * up[k]) + C3 * th[k];
+                J[k] = pn[k] - pm[k] - c.dt * F[k];
+            }
+#pragma unroll
+            for (int q = 0; q < kN; ++q) {
+                const float w = st.w[0][q % KW] * st.w[1][(q / KW) % KW] * st.w[2][q / (KW * KW)];
+                float &jx = wide_cache<KW>(wsm, 3, q, threadIdx.x);
+                float &jy = wide_cache<KW>(wsm, 4, q, threadIdx.x);
+                float &jz = wide_cache<KW>(wsm, 5, q, threadIdx.x);
+                jx = fmaf(-J[0], w, jx);
+                jy = fmaf(-J[1], w, jy);
+                jz = fmaf(-J[2], w, jz);
+            }
+            a.records[(size_t)s * c.n + p] = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+
+            const bool last = (s == a.nsub - 1);
+            bool ok = drift(me, pn, h, g, KW);
+            if (last) {
+                a.pos[3 * p] = join1(me.c[0], me.f[0]);
+                a.pos[3 * p + 1] = join1(me.c[1], me.f[1]);
+                a.pos[3 * p + 2] = join1(me.c[2], me.f[2]);
+                a.mom[3 * p] = pn[0];
+                a.mom[3 * p + 1] = pn[1];
+                a.mom[3 * p + 2] = pn[2];
+            } else {
+                ok = drift(me, pn, h, g, KW) && ok;
+            }
+            if (!ok) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+            pm[0] = pn[0];
+            pm[1] = pn[1];
+            pm[2] = pn[2];
+            shout[p] = pack(me);
+            if (c.use_wca) {
+                float d[3];
+                separation(me, refp, g, d);
+                const float d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (!last && d2 > c.half_skin2) atomicMax(&a.flags[1 + ((s + 1) & 1)], a.epoch0 + (uint32_t)s + 1u);
+                if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
+            }
+        }
+        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+    }
+    if (active) {
+        flush_wide<KW>(org, wsm, a.facc, g);
+        if (binned) unbin_particle(p, a.head, a.bucket_of);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Free particles (no pair or bond forces): with the fluid frozen during a
+// call, a particle's sub-steps depend on no other particle, so one launch
+// runs all sub-steps of every particle with no grid barrier and no limit on
+// the particle count.  A group of LANES threads serves a particle (one for
+// phi_2, eight for phi_3 / phi_4); lane q keeps the fluid velocity of the
+// stencil nodes q, q + LANES, ... of the particle's current stencil origin in
+// registers, gathers them again only when the origin moves, and sums the
+// impulses it spreads there over the sub-steps spent at that origin, adding
+// them to the accumulator when the origin moves or the call ends.  Per
+// sub-step: interpolation (Eqs. ufluid_discrete, Delta), the exact OU update
+// (Eq. langevin_momentum_update), the impulse -J Delta with
+// J = p' - p - dt F^c (Eq. ftotal; F^c the constant external force), the two
+// half drifts.  Every lane of a group computes the same position and
+// momentum; lane 0 writes them.
+// ---------------------------------------------------------------------------
+struct FreeArgs {
+    CoupleArgs c;
+    int nsub;
+    const void *src;
+    const float *ffield;
+    double *pos;
+    float *mom;
+    const float *mass, *gamma;
+    float *facc;
+    int *records;  // [nsub][n] cell of each sub-step (the overlapped re-update's list)
+    unsigned int *err;
+};
+
+template <int DT, int KW>
+__global__ void __launch_bounds__(kPartThreads) k_couple_free(FreeArgs a)
+{
+    using T = typename lbd::Store<DT>::T;
+    constexpr int LANES = free_lanes<KW>();
+    constexpr int kNodes = KW * KW * KW, kPer = (kNodes + LANES - 1) / LANES;
+    const CoupleArgs &c = a.c;
+    const StepArgs &g = c.g;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = tid / LANES, q = tid % LANES;
+    if (p >= c.n) return;  // whole groups leave together (LANES divides the block)
+    const unsigned gmask = LANES == 1 ? 0xFFFFFFFFu : (0xFFu << (threadIdx.x & 24));
+    const T *src = static_cast<const T *>(a.src);
+
+    const float m = a.mass ? a.mass[p] : c.mass0;
+    const float G = a.gamma ? a.gamma[p] : c.gamma0;
+    float C1 = c.C1, C2 = c.C2, C3 = c.C3;
+    if (!c.uniform_coef) {
+        const float x1 = G * c.dt / m;
+        C1 = expf(-x1);
+        C2 = (m / G) * (-expm1f(-x1));
+        C3 = sqrtf(m * g.kT * (-expm1f(-2.0f * x1)));
+    }
+    // first half drift in FP64 from the caller's position, then cell + offset
+    float pm[3] = {a.mom[3 * p], a.mom[3 * p + 1], a.mom[3 * p + 2]};
+    CPos me;
+    {
+        double r[3] = {a.pos[3 * p], a.pos[3 * p + 1], a.pos[3 * p + 2]};
+        const double hd = 0.5 * (double)c.dt / (double)m;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) r[k] += hd * (double)pm[k];
+        confine_d(r, pm, g, KW);
+        if (!split(r, g, me) && q == 0) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+    }
+
+    float uc[kPer][3], acc[kPer][3];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) uc[i][0] = uc[i][1] = uc[i][2] = acc[i][0] = acc[i][1] = acc[i][2] = 0.0f;
+    int org[3] = {INT_MIN, INT_MIN, INT_MIN};  // stencil origin of uc / acc (none yet)
+    bool ok = true;
+    const float h = 0.5f * c.dt / m;
+    for (int s = 0; s < a.nsub; ++s) {
+        Stencil<KW> st;
+        make_stencil<KW>(me, st);
+        if (st.o[0] != org[0] || st.o[1] != org[1] || st.o[2] != org[2]) {
+            if (org[0] != INT_MIN) {  // hand in the impulses summed at the old origin
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const int qq = q + LANES * i;
+                    if (kNodes % LANES == 0 || qq < kNodes) {
+                        int x, y, z;
+                        stencil_coords<KW>(org, qq, g, x, y, z);
+                        const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+                        if (in_bounds(node, g.nn, g.err)) {
+                            atomicAdd(a.facc + node, acc[i][0]);
+                            atomicAdd(a.facc + g.pitch + node, acc[i][1]);
+                            atomicAdd(a.facc + 2 * g.pitch + node, acc[i][2]);
+                        }
+                        acc[i][0] = acc[i][1] = acc[i][2] = 0.0f;
+                    }
+                }
+            }
+            org[0] = st.o[0];
+            org[1] = st.o[1];
+            org[2] = st.o[2];
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                const int qq = q + LANES * i;
+                if (kNodes % LANES == 0 || qq < kNodes) {
+                    int x, y, z;
+                    stencil_coords<KW>(org, qq, g, x, y, z);
+                    node_velocity<DT>(src, a.ffield, x, y, z, g, uc[i]);
+                }
+            }
+        }
+        float w[kPer];
+        float up[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int qq = q + LANES * i;
+            w[i] = 0.0f;
+            if (kNodes % LANES == 0 || qq < kNodes) {
+                int x, y, z;
+                w[i] = stencil_node_k<KW>(st, qq, g, x, y, z);
+                up[0] = fmaf(w[i], uc[i][0], up[0]);
+                up[1] = fmaf(w[i], uc[i][1], up[1]);
+                up[2] = fmaf(w[i], uc[i][2], up[2]);
+            }
+        }
+        if (LANES > 1) {
+#pragma unroll
+            for (int o = 1; o < LANES; o <<= 1)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) up[k] += __shfl_xor_sync(gmask, up[k], o);
+        }
+        float th[3] = {0.f, 0.f, 0.f};
+        if (g.kT > 0.0f) particle_theta((uint32_t)p, c.md_step + (uint32_t)s, c, th);
+        float pn[3], J[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            pn[k] = C1 * pm[k] + C2 * (c.fext[k] + G * up[k]) + C3 * th[k];
+            J[k] = pn[k] - pm[k] - c.dt * c.fext[k];
+        }
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            acc[i][0] = fmaf(-J[0], w[i], acc[i][0]);
+            acc[i][1] = fmaf(-J[1], w[i], acc[i][1]);
+            acc[i][2] = fmaf(-J[2], w[i], acc[i][2]);
+        }
+        if (q == 0 && a.records) a.records[(size_t)s * c.n + p] = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+        // second half drift of this sub-step, then the first of the next one
+        ok = drift(me, pn, h, g, KW) && ok;
+        if (s + 1 < a.nsub) ok = drift(me, pn, h, g, KW) && ok;
+        pm[0] = pn[0];
+        pm[1] = pn[1];
+        pm[2] = pn[2];
+    }
+    if (org[0] != INT_MIN) {
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int qq = q + LANES * i;
+            if (kNodes % LANES == 0 || qq < kNodes) {
+                int x, y, z;
+                stencil_coords<KW>(org, qq, g, x, y, z);
+                const size_t node = ((size_t)z * g.ny + y) * g.nx + x;
+                if (in_bounds(node, g.nn, g.err)) {
+                    atomicAdd(a.facc + node, acc[i][0]);
+                    atomicAdd(a.facc + g.pitch + node, acc[i][1]);
+                    atomicAdd(a.facc + 2 * g.pitch + node, acc[i][2]);
+                }
+            }
+        }
+    }
+    if (q != 0) return;
+    if (!ok) atomicOr(a.err, LB_DERR_PARTICLE_RANGE);
+    a.pos[3 * p] = join1(me.c[0], me.f[0]);
+    a.pos[3 * p + 1] = join1(me.c[1], me.f[1]);
+    a.pos[3 * p + 2] = join1(me.c[2], me.f[2]);
+    a.mom[3 * p] = pm[0];
+    a.mom[3 * p + 1] = pm[1];
+    a.mom[3 * p + 2] = pm[2];
+}
+
 // Kernel arguments of a coupling call (everything but the cell list).
 // Interpolation stencil width selected by lb_couple_params.flags.
 int stencil_width(int flags)
@@ -1464,11 +1953,120 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
     const T *src = static_cast<const T *>(h->pops[h->cur]);
     const bool need_nlist = cp->use_wca != 0;
 
+    // free particles: one launch runs every sub-step, no grid barrier, any count
+    if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && !need_nlist && c.chain_len <= 1) {
+        if (h->facc_stale) {
+            cudaError_t e = clear_particle_forces(h);
+            if (e != cudaSuccess) return e;
+            h->facc_stale = 0;
+        }
+        FreeArgs fa;
+        fa.c = c;
+        fa.nsub = cp->n_substeps;
+        fa.src = src;
+        fa.ffield = h->force;
+        fa.pos = pp->pos;
+        fa.mom = pp->mom;
+        fa.mass = pp->mass;
+        fa.gamma = pp->gamma;
+        fa.facc = h->facc;
+        fa.records = P->records + P->rec_off + P->n_records;
+        fa.err = h->d_err;
+        const int lanes = c.kw == 2 ? free_lanes<2>() : free_lanes<3>();
+        const unsigned int fblocks = (unsigned int)(((size_t)n * lanes + kPartThreads - 1) / kPartThreads);
+        if (c.kw == 3) k_couple_free<DT, 3><<<fblocks, kPartThreads, 0, h->stream>>>(fa);
+        else if (c.kw == 4) k_couple_free<DT, 4><<<fblocks, kPartThreads, 0, h->stream>>>(fa);
+        else k_couple_free<DT, 2><<<fblocks, kPartThreads, 0, h->stream>>>(fa);
+        h->launches += 1;
+        note_records(P, n, (size_t)n * (size_t)cp->n_substeps);
+        if (c.kw > 2) P->rec_span = 4;
+        P->sub_counter += (uint32_t)cp->n_substeps;
+        P->last_nsub = cp->n_substeps;
+        return cudaGetLastError();
+    }
+
     // persistent path when every particle group can be resident at once
     const int gblocks = (int)(((size_t)n * kChunks + kPartThreads - 1) / kPartThreads);  // 8 lanes a particle
     const int pblocks = (n + kPThreads - 1) / kPThreads;                                   // one thread a particle
     int per_sm = 0;
-    // (phi_3 and phi_4 stencils run on the per-sub-step kernels only)
+    if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && c.kw > 2) {
+        // phi_3 / phi_4: the persistent kernel with the stencil caches in shared memory
+        const size_t smem = c.kw == 3 ? wide_smem_bytes<3>() : wide_smem_bytes<4>();
+        const void *kfn = c.kw == 3 ? (const void *)k_couple_persistent_wide<DT, 3>
+                                    : (const void *)k_couple_persistent_wide<DT, 4>;
+        cudaError_t e = cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, kPThreads, smem);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();  // no wide persistent kernel here: the per-sub-step path below
+            per_sm = 0;
+        }
+        if (per_sm > 0 && pblocks <= per_sm * device_sm_count()) {
+            if (need_nlist && P->nlist_n != n) {
+                const unsigned int init[kFlagWords] = {0u, 0u, 1u, 0u, 0u};  // [2]: build before the launch
+                e = cudaMemcpyAsync(P->flags, init, sizeof(init), cudaMemcpyHostToDevice, h->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+                if (e != cudaSuccess) return e;
+                P->nlist_n = n;
+            }
+            if (h->facc_stale) {
+                e = clear_particle_forces(h);
+                if (e != cudaSuccess) return e;
+                h->facc_stale = 0;
+            }
+            if (need_nlist) {
+                k_shadow_from_pos<<<blocks, kPartThreads, 0, h->stream>>>(pp->pos, P->shadow[1], P->head, P->next,
+                                                                           P->bucket_of, P->flags + 2, h->d_err, c);
+                k_build_nlist<<<gblocks, kPartThreads, 0, h->stream>>>(P->shadow[1], P->head, P->next, P->nlist,
+                                                                       P->ncount, P->ref, P->flags, h->d_err, c, 2u);
+                h->launches += 2;
+            }
+            PersistArgs a;
+            a.c = c;
+            a.nsub = cp->n_substeps;
+            a.src = src;
+            a.ffield = h->force;
+            a.pos = pp->pos;
+            a.mom = pp->mom;
+            a.mass = pp->mass;
+            a.gamma = pp->gamma;
+            a.sh[0] = P->shadow[0];
+            a.sh[1] = P->shadow[1];
+            a.nlist = P->nlist;
+            a.ncount = P->ncount;
+            a.ref = P->ref;
+            a.head = P->head;
+            a.next = P->next;
+            a.bucket_of = P->bucket_of;
+            a.facc = h->facc;
+            a.records = P->records + P->rec_off + P->n_records;
+            a.stale = nullptr;
+            a.nstale_sub = 0;
+            a.flags = P->flags + 2;
+            a.epoch0 = P->sub_counter + 1u;
+            a.bar = P->bar;
+            a.err = h->d_err;
+            a.spin_limit = 1u << 22;
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3(pblocks);
+            lc.blockDim = dim3(kPThreads);
+            lc.dynamicSmemBytes = smem;
+            lc.stream = h->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            lc.attrs = attr;
+            lc.numAttrs = 1;
+            void *args[] = {&a};
+            e = cudaLaunchKernelExC(&lc, kfn, args);
+            if (e != cudaSuccess) return e;
+            h->launches += 1;
+            note_records(P, n, (size_t)n * (size_t)cp->n_substeps);
+            P->rec_span = 4;
+            P->sub_counter += (uint32_t)cp->n_substeps;
+            P->last_nsub = cp->n_substeps;
+            return cudaGetLastError();
+        }
+    }
     if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && c.kw == 2 &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>, kPThreads, 0) == cudaSuccess &&
         pblocks <= per_sm * device_sm_count()) {

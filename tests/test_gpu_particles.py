@@ -291,13 +291,15 @@ def test_coupled_momentum_conservation_gpu(ora):
     assert lat.sync() == (L.LB_OK, 0)
 
 
-def test_many_particles_multi_kernel_path(ora):
-    """200000 free particles do not fit resident as 8-lane groups, so the
-    coupling runs the per-sub-step kernels instead of the persistent one."""
+@pytest.mark.parametrize("per_substep", [False, True])
+def test_many_free_particles(ora, per_substep):
+    """200000 free particles (several per node): the one-launch free-particle
+    kernel (no grid barrier, so no residency limit), and the per-sub-step
+    kernels (LB_COUPLE_PER_SUBSTEP)."""
     shape = (32, 32, 32)
     pos = inputs.uniform_particles(200000, shape, seed=21)
     mom = inputs.maxwell_momenta(200000, 1.0, 1e-4, seed=22)
-    r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3)
+    r = _run(ora, shape, pos, mom, kT=1e-4, nsub=3, per_substep=per_substep)
     _check_run(r, shape, 1e-6, next_bar=None)
 
 
@@ -482,3 +484,35 @@ def test_step_sums_with_overlapped_coupling():
         w, g = want.cpu().numpy(), got.cpu().numpy()
         assert np.abs(g - w).max() < 1e-6 * np.abs(w).max()
     assert lat.sync() == (L.LB_OK, 0)
+
+
+@pytest.mark.parametrize("kernel,walls", [(2, False), (4, False), (3, True)])
+def test_free_particles_overlap_matches_serial(kernel, walls):
+    """Free particles on the one-launch kernel with LB_COUPLE_OVERLAP: the
+    re-update of the nodes its stencil records list gives the serial result
+    (up to the order of the impulse atomics), over four coupled steps with
+    particles fast enough to change cells."""
+    shape = (20, 18, 16)
+    out = []
+    for overlap in (False, True):
+        zr = (kernel / 2, shape[2] - 1 - kernel / 2) if walls else None
+        pos = inputs.uniform_particles(3000, shape, seed=71, zrange=zr) if walls else \
+            inputs.uniform_particles(3000, shape, seed=71)
+        mom = inputs.maxwell_momenta(3000, 1.0, 2e-3, seed=72).astype(np.float32)
+        lat = L.Lattice(shape, kT=1e-4, seed=6, walls=walls, body_force=(1e-5, 0.0, 0.0))
+        u = inputs.shear_wave(shape, 0.01)
+        if walls:
+            u[:, 0] = 0
+            u[:, -1] = 0
+        lat.init_equilibrium(None, dev(u))
+        gpos, gmom = dev(pos), dev(mom, torch.float32)
+        parts = L.particles(3000, gpos, gmom, mass0=1.0, gamma0=2.0)
+        for t in range(4):
+            cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, overlap=overlap, kernel=kernel)
+            L.lb_couple_particles(lat.h, parts, cp)
+            lat.step(1)
+        assert lat.sync() == (L.LB_OK, 0)
+        out.append((lat.get_populations().cpu().numpy(), gpos.cpu().numpy(), gmom.cpu().numpy()))
+    assert np.abs(out[0][0] - out[1][0]).max() < 1e-7
+    assert _pos_err(out[0][1], out[1][1], shape) < 1e-6
+    assert np.abs(out[0][2] - out[1][2]).max() < 1e-6
