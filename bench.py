@@ -71,6 +71,9 @@ def _args():
     ap.add_argument("--dtype", default="f32")
     ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
                     help="time only the moving-sphere form for STEPS steps (profiling runs)")
+    ap.add_argument("--free-particles", type=int, default=0, metavar="N",
+                    help="time coupled steps of N free particles (Gamma = 2, phi_2) in --shape between walls "
+                         "(--serial: serial order; profiling runs)")
     return ap.parse_args()
 
 
@@ -110,6 +113,54 @@ def run_kernel_only(args):
                               "ms_median": med, "ms_min": ms[0], "mlups": nodes / (med * 1e-3) / 1e6,
                               "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": src}))
             lat.close()
+    return 0
+
+
+def run_free_particles(args):
+    """Coupled steps of N free point particles (uniform between the walls,
+    Gamma = 2 per LB time, 10 sub-steps, phi_2) in a --shape box with walls,
+    FP32, kT = 1e-4, g = 1e-6: the particle load of the reduced-precision
+    workload on a box of the caller's choosing.  One JSON line with the ms per
+    coupled step (overlapped order unless --serial)."""
+    import torch
+    from paper_0803_2826_gb300 import build as B
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    B.build()
+    torch.cuda.set_device(0)
+    shape = tuple(int(v) for v in args.shape.split(","))
+    n = args.free_particles
+    stream = torch.cuda.Stream()
+    pos = inputs.uniform_particles(n, shape, seed=1, zrange=(1.0, shape[2] - 2.0))
+    mom = inputs.maxwell_momenta(n, MASS, KT, seed=2)
+    lat = L.Lattice(shape, kT=KT, seed=3, walls=True, body_force=(1e-6, 0, 0), stream=stream)
+    gpos = torch.as_tensor(pos).cuda()
+    gmom = torch.as_tensor(mom, dtype=torch.float32).cuda()
+    parts = L.particles(n, gpos, gmom, mass0=MASS, gamma0=GAMMA)
+    t = [0]
+
+    def coupled(k):
+        for _ in range(k):
+            cp = L.couple_params(n_substeps=NSUB, dt=DT, seed=5, md_step0=NSUB * t[0], overlap=not args.serial)
+            L.lb_couple_particles(lat.h, parts, cp)
+            lat.step(1)
+            t[0] += 1
+
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        coupled(args.warmup)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        coupled(args.steps)
+        b.record(stream)
+    torch.cuda.synchronize()
+    st, bits = lat.sync()
+    print(json.dumps({"form": "free_particles", "shape": shape, "particles": n, "order": "serial" if args.serial
+                      else "overlapped", "steps": args.steps, "ms_per_step": a.elapsed_time(b) / max(args.steps, 1),
+                      "error_bits": bits}))
+    lat.close()
     return 0
 
 
@@ -784,6 +835,8 @@ def _profiled_traffic(mode):
 
 def main():
     args = _args()
+    if args.free_particles:
+        return run_free_particles(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.kernel_only:
