@@ -107,7 +107,11 @@ struct BatchArgs {
 };
 
 constexpr int kModeVals = 12;  // six complex transverse modes
-constexpr int kBatchPairMaxRegs = 128;  // keeps 16 warps per SM resident
+// register caps of the paired kernels (no spills at these; a cap of 102,
+// which would let five 128-thread blocks share an SM, measured slower: the
+// autotuner keeps 512-thread blocks)
+constexpr int kBatchPairMaxRegs = 128;
+constexpr int kBatchPairObsMaxRegs = 128;
 
 // Bounded grid barrier (grid_barrier.cuh).  Returns false if the run must
 // stop (a barrier timed out here or elsewhere).
@@ -360,10 +364,16 @@ __global__ void k_batch(BatchArgs a)
     batch_run<DT, NOISE, OBS, false>(a);
 }
 
-template <int DT, bool NOISE, bool OBS>
+template <int DT, bool NOISE>
 __global__ void __maxnreg__(kBatchPairMaxRegs) k_batch_pair(BatchArgs a)
 {
-    batch_run<DT, NOISE, OBS, true>(a);
+    batch_run<DT, NOISE, false, true>(a);
+}
+
+template <int DT, bool NOISE>
+__global__ void __maxnreg__(kBatchPairObsMaxRegs) k_batch_pair_obs(BatchArgs a)
+{
+    batch_run<DT, NOISE, true, true>(a);
 }
 
 __global__ void k_set_rec_step0(BatchState *st, uint32_t v)
@@ -486,7 +496,8 @@ StepArgs batch_phys(const lb_batch *b)
 template <int DT, bool NOISE, bool OBS>
 void *kernel_ptr(bool pair)
 {
-    return pair ? (void *)k_batch_pair<DT, NOISE, OBS> : (void *)k_batch<DT, NOISE, OBS>;
+    if (!pair) return (void *)k_batch<DT, NOISE, OBS>;
+    return OBS ? (void *)k_batch_pair_obs<DT, NOISE> : (void *)k_batch_pair<DT, NOISE>;
 }
 
 template <bool OBS>
