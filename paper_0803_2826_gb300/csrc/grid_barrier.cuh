@@ -18,15 +18,29 @@
 
 namespace lbi {
 
-__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *err, unsigned int spin_limit)
+// The barrier in two halves, for work that touches nothing another block
+// reads before the barrier ends (it can then run while the other blocks
+// arrive): grid_arrive publishes this block's writes and adds its arrival,
+// grid_wait polls as above.  *ticket (block-shared) carries the arrival
+// word's value from one half to the other.
+__device__ __forceinline__ void grid_arrive(unsigned int *bar, unsigned int *ticket)
 {
-    __shared__ int stop;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
         const bool first = (blockIdx.x | blockIdx.y | blockIdx.z) == 0;
         __threadfence();  // this block's writes before its arrival
-        const unsigned int old = atomicAdd(&bar[0], first ? 0x80000000u - (nb - 1u) : 1u);
+        *ticket = atomicAdd(&bar[0], first ? 0x80000000u - (nb - 1u) : 1u);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(unsigned int *bar, unsigned int *err, unsigned int spin_limit,
+                                          const unsigned int *ticket)
+{
+    __shared__ int stop;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int old = *ticket;
         volatile unsigned int *vbar = bar;
         unsigned int spins = 0;
         int s = 0;
@@ -48,6 +62,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *er
     }
     __syncthreads();
     return !stop;
+}
+
+__device__ __forceinline__ bool grid_barrier(unsigned int *bar, unsigned int *err, unsigned int spin_limit)
+{
+    __shared__ unsigned int ticket;
+    grid_arrive(bar, &ticket);
+    return grid_wait(bar, err, spin_limit, &ticket);
 }
 
 }  // namespace lbi

@@ -1197,6 +1197,7 @@ template <int DT>
 __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
 {
     using T = typename lbd::Store<DT>::T;
+    __shared__ unsigned int ticket;  // arrival word of the split barrier
     const CoupleArgs &c = a.c;
     const StepArgs &g = c.g;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1340,19 +1341,8 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
             if (bond_hi && !fene_add(me, unpack(vhi), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
         }
 
-        // fluid velocity: particles that changed cell hand in their impulse
-        // sums and the warp gathers their new cells
-        const bool moved = active && (me.c[0] != ccell[0] || me.c[1] != ccell[1] || me.c[2] != ccell[2]);
-        if (__any_sync(kFullMask, moved)) {
-            if (moved) {
-                flush_impulses(ccell, acc, a.facc, g);
-                ccell[0] = me.c[0];
-                ccell[1] = me.c[1];
-                ccell[2] = me.c[2];
-            }
-            warp_gather<DT>(moved, ccell, src, a.ffield, g, uc);
-        }
-
+        // (uc already holds the fluid velocity of cell me.c: gathered before
+        // the first sub-step or, after a cell change, inside the previous barrier)
         if (active) {
             float up[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -1401,7 +1391,24 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
                 if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
             }
         }
-        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+        // the barrier in two halves: between them, particles that change cell
+        // for the next sub-step hand in their impulse sums and the warp gathers
+        // their new cells (this reads only the frozen fluid and writes only
+        // registers and the accumulator, which no block reads during the call)
+        grid_arrive(a.bar, &ticket);
+        if (s + 1 < a.nsub) {
+            const bool moved = active && (me.c[0] != ccell[0] || me.c[1] != ccell[1] || me.c[2] != ccell[2]);
+            if (__any_sync(kFullMask, moved)) {
+                if (moved) {
+                    flush_impulses(ccell, acc, a.facc, g);
+                    ccell[0] = me.c[0];
+                    ccell[1] = me.c[1];
+                    ccell[2] = me.c[2];
+                }
+                warp_gather<DT>(moved, ccell, src, a.ffield, g, uc);
+            }
+        }
+        if (!grid_wait(a.bar, a.err, a.spin_limit, &ticket)) return;
     }
     if (active) {
         flush_impulses(ccell, acc, a.facc, g);
@@ -1512,6 +1519,7 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
     using T = typename lbd::Store<DT>::T;
     constexpr int kN = KW * KW * KW;
     extern __shared__ float wsm[];
+    __shared__ unsigned int ticket;  // arrival word of the split barrier
     const CoupleArgs &c = a.c;
     const StepArgs &g = c.g;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1632,19 +1640,8 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
             if (bond_hi && !fene_add(me, unpack(vhi), c, F)) atomicOr(a.err, LB_DERR_FENE_BROKEN);
         }
 
-        // particles whose stencil origin moved hand in their impulse sums and
-        // the warp gathers their new stencils
-        const bool moved = active && (st.o[0] != org[0] || st.o[1] != org[1] || st.o[2] != org[2]);
-        if (__any_sync(kFullMask, moved)) {
-            if (moved) {
-                flush_wide<KW>(org, wsm, a.facc, g);
-                org[0] = st.o[0];
-                org[1] = st.o[1];
-                org[2] = st.o[2];
-            }
-            warp_gather_wide<DT, KW>(moved, org, src, a.ffield, g, wsm);
-        }
-
+        // (the stencil cache already holds origin st.o: gathered before the
+        // first sub-step or, for a moved origin, inside the previous barrier)
         if (active) {
             float up[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -1697,7 +1694,27 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
                 if (last && d2 > 0.25f * c.half_skin2) a.flags[0] = 1u;  // build before the next call
             }
         }
-        if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
+        // the barrier in two halves: between them, particles whose stencil
+        // origin moves for the next sub-step hand in their impulse sums and the
+        // warp gathers their new stencils (this reads only the frozen fluid and
+        // writes only the block's cache and the accumulator, which no block
+        // reads during the call)
+        grid_arrive(a.bar, &ticket);
+        if (s + 1 < a.nsub) {
+            Stencil<KW> stn;
+            make_stencil<KW>(me, stn);
+            const bool moved = active && (stn.o[0] != org[0] || stn.o[1] != org[1] || stn.o[2] != org[2]);
+            if (__any_sync(kFullMask, moved)) {
+                if (moved) {
+                    flush_wide<KW>(org, wsm, a.facc, g);
+                    org[0] = stn.o[0];
+                    org[1] = stn.o[1];
+                    org[2] = stn.o[2];
+                }
+                warp_gather_wide<DT, KW>(moved, org, src, a.ffield, g, wsm);
+            }
+        }
+        if (!grid_wait(a.bar, a.err, a.spin_limit, &ticket)) return;
     }
     if (active) {
         flush_wide<KW>(org, wsm, a.facc, g);
