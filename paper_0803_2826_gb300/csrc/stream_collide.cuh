@@ -458,12 +458,15 @@ struct Pair<2> {
     }
 };
 
-template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS = false>
-__device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__restrict__ src,
-                                            typename lbd::Store<DT>::T *__restrict__ dst,
-                                            const float *__restrict__ ffield, const float *__restrict__ facc,
-                                            const StepArgs &a, int x0, int y, int z, bool valid = true,
-                                            float (*part)[38] = nullptr)
+// Pull streaming of nodes x0, x0 + 1 of row (y, z) (link bounce-back at solid
+// z-planes) into packed pairs n (node x0 in the low halves, FP16 / BF16
+// unscaled), and their force densities f0, f1 (body force + caller's field +
+// library accumulator).
+template <int DT, bool FIELD, bool WALLS>
+__device__ __forceinline__ void load_pair(const typename lbd::Store<DT>::T *__restrict__ src,
+                                          const float *__restrict__ ffield, const float *__restrict__ facc,
+                                          const StepArgs &a, int x0, int y, int z, lbp::F2 n[19], float f0[3],
+                                          float f1[3])
 {
     using S = lbd::Store<DT>;
     using PR = Pair<DT>;
@@ -483,8 +486,6 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
     const uint32_t P = (uint32_t)a.pitch;
     const uint32_t self = (uint32_t)((z * ny + y) * nx + x0);
     const size_t lim = 19 * (size_t)P;  // elements of a population buffer (index checks)
-
-    lbp::F2 n[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const int sy = lbd::cy(i) == 1 ? ym : (lbd::cy(i) == -1 ? yp : y);
@@ -516,7 +517,9 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
         n[i] = DT == 0 ? lbp::f2(v0, v1) : lbp::f2(v0, v1) * lbp::f2s(a.inv_scale);
     }
 
-    float f0[3] = {a.fx, a.fy, a.fz}, f1[3] = {a.fx, a.fy, a.fz};
+    f0[0] = f1[0] = a.fx;
+    f0[1] = f1[1] = a.fy;
+    f0[2] = f1[2] = a.fz;
     if (FIELD) {
         if (ffield) {  // caller's field, component stride N
 #pragma unroll
@@ -535,6 +538,35 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
             }
         }
     }
+}
+
+// Store of the packed post-collision pair (FP16 / BF16: scaled by one packed
+// multiply, then rounded to nearest even).
+template <int DT>
+__device__ __forceinline__ void store_pair(typename lbd::Store<DT>::T *__restrict__ dst, const StepArgs &a,
+                                           uint32_t self, const lbp::F2 out[19])
+{
+    const uint32_t P = (uint32_t)a.pitch;
+    const size_t lim = 19 * (size_t)P;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float o0, o1;
+        lbp::split(DT == 0 ? out[i] : out[i] * lbp::f2s(a.scale), o0, o1);
+        if (in_bounds((uint32_t)i * P + self + 1, lim, a.err)) Pair<DT>::store(dst + (uint32_t)i * P + self, o0, o1, 1.0f);
+    }
+}
+
+template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS = false>
+__device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__restrict__ src,
+                                            typename lbd::Store<DT>::T *__restrict__ dst,
+                                            const float *__restrict__ ffield, const float *__restrict__ facc,
+                                            const StepArgs &a, int x0, int y, int z, bool valid = true,
+                                            float (*part)[38] = nullptr)
+{
+    const uint32_t self = (uint32_t)((z * a.ny + y) * a.nx + x0);
+    lbp::F2 n[19];
+    float f0[3], f1[3];
+    load_pair<DT, FIELD, WALLS>(src, ffield, facc, a, x0, y, z, n, f0, f1);
     // both nodes' moments, collision, noise and back transform in packed
     // FP32 (f32x2.cuh), node x0 in the low halves
     lbp::F2 m[19], out[19];
@@ -548,12 +580,7 @@ __device__ __forceinline__ void update_pair(const typename lbd::Store<DT>::T *__
     }
     lbp::collide_moments2<NOISE>(m, lbp::f2(f0[0], f1[0]), lbp::f2(f0[1], f1[1]), lbp::f2(f0[2], f1[2]), a, a.rk,
                                  self, a.replica, out);
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        float o0, o1;
-        lbp::split(DT == 0 ? out[i] : out[i] * lbp::f2s(a.scale), o0, o1);
-        if (in_bounds((uint32_t)i * P + self + 1, lim, a.err)) PR::store(dst + (uint32_t)i * P + self, o0, o1, 1.0f);
-    }
+    store_pair<DT>(dst, a, self, out);
 }
 
 template <int DT, bool NOISE, bool FIELD, bool WALLS, bool SUMS>

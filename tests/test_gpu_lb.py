@@ -126,12 +126,13 @@ def test_two_rate_poiseuille_gpu(ora, ge):
         assert np.abs(ux - want).max() < 2e-5 * ua.max(), (gam_o, np.abs(ux - want).max() / ua.max())
 
 
+@pytest.mark.parametrize("shape", [(9, 8, 10), (10, 8, 9)])
 @pytest.mark.parametrize("kT,walls", [(0.0, False), (1e-4, False), (1e-4, True)])
-def test_exponential_equilibrium_parity(ora, kT, walls):
+def test_exponential_equilibrium_parity(ora, kT, walls, shape):
     """lb_params.equilibrium = 1 (Sec. 3.6, Eq. equildist_lagrange): 20
     steps with a force field against the oracle, velocities up to 0.1 (the
-    exponential and quadratic forms differ there by ~1e-4 of a population)."""
-    shape = (9, 8, 10)
+    exponential and quadratic forms differ there by ~1e-4 of a population);
+    odd nx runs one node per thread, even nx two in packed FP32."""
     u = inputs.gaussian_field(shape, 3, 0.04, seed=11)
     if walls:
         u[:, 0] = 0
@@ -142,7 +143,8 @@ def test_exponential_equilibrium_parity(ora, kT, walls):
     c, a, e, w, opp = ora.tables()
     aa = a[:, None, None, None]
     fl = slice(1, shape[2] - 1) if walls else slice(None)
-    check("exponential equilibrium kT=%g walls=%d" % (kT, walls), got[:, fl] - aa, want[:, fl] - aa, 5e-6, 2e-5)
+    check("exponential equilibrium %s kT=%g walls=%d" % (shape, kT, walls), got[:, fl] - aa, want[:, fl] - aa, 5e-6,
+          2e-5)
     # and it is not the quadratic update
     pq, want_q, _, _, _ = _pair(ora, shape, 20, u=u, field=field, **dict(kw, equilibrium=0))
     assert rel(want_q[:, fl] - aa, want[:, fl] - aa) > 20 * rel(got[:, fl] - aa, want[:, fl] - aa)
