@@ -57,7 +57,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched / adjoint / reduced-precision measurements")
-    ap.add_argument("--e2e-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=200,
+                    help="steps of the end-to-end loop with host copies")
     ap.add_argument("--serial", action="store_true",
                     help="run the coupling before the LB update instead of overlapping the two")
     ap.add_argument("--box", type=int, default=SHAPE[0],
@@ -69,6 +70,8 @@ def _args():
     ap.add_argument("--shape", default="256,256,256")
     ap.add_argument("--kT", default="0,1e-4")
     ap.add_argument("--dtype", default="f32")
+    ap.add_argument("--batched-form", type=int, default=0, metavar="STEPS",
+                    help="run only the batched-replica form with this many steps (profiling)")
     ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
                     help="time only the moving-sphere form for STEPS steps (profiling runs)")
     ap.add_argument("--free-particles", type=int, default=0, metavar="N",
@@ -313,21 +316,23 @@ def run_ours(args):
     shape = (args.box,) * 3
     nodes = shape[0] * shape[1] * shape[2]
     npart = N_CHAINS * CHAIN_LEN
-    # the particle state and the moment sums live in one device buffer (so the
-    # end-to-end loop moves each step's input and result in one copy each):
-    # positions FP64 [n][3], momenta FP32 [n][3], then the 38 FP64 sums
-    pos_b, mom_b = npart * 3 * 8, npart * 3 * 4
+    # the particle state and two slots of moment sums live in one device
+    # buffer: positions FP64 [n][3], momenta FP32 [n][3], then the two slots
+    # of 38 FP64 sums (the end-to-end loop alternates them between steps)
+    pos_b, mom_b, sums_b = npart * 3 * 8, npart * 3 * 4, L.LB_NSUMS * 8
+    pos_off = 0
     sums_off = (pos_b + mom_b + 255) // 256 * 256
-    io_bytes = sums_off + L.LB_NSUMS * 8
+    sstride = (sums_b + 255) // 256 * 256
+    io_bytes = sums_off + 2 * sstride
     with torch.cuda.stream(stream):
         lat = L.Lattice(shape, kT=KT, seed=rank, replica=rank, stream=stream)
         lat.init_equilibrium()
         pos0 = inputs.random_walk_chains(N_CHAINS, CHAIN_LEN, shape, seed=rank)
         mom0 = inputs.maxwell_momenta(npart, MASS, KT, seed=1000 + rank)
         dio = torch.zeros(io_bytes, dtype=torch.uint8, device=dev)
-        gpos = dio[:pos_b].view(torch.float64).view(npart, 3)
-        gmom = dio[pos_b:pos_b + mom_b].view(torch.float32).view(npart, 3)
-        dsums = dio[sums_off:].view(torch.float64)
+        gpos = dio[pos_off:pos_off + pos_b].view(torch.float64).view(npart, 3)
+        gmom = dio[pos_off + pos_b:pos_off + pos_b + mom_b].view(torch.float32).view(npart, 3)
+        dsums = tuple(dio[sums_off + sstride * q:sums_off + sstride * q + sums_b].view(torch.float64) for q in (0, 1))
         gpos.copy_(torch.as_tensor(pos0))
         gmom.copy_(torch.as_tensor(mom0, dtype=torch.float32))
     torch.cuda.synchronize()
@@ -336,9 +341,12 @@ def run_ours(args):
                          eps=EPS, sigma=SIGMA, k_fene=K_FENE, r0=R0, overlap=not args.serial, kernel=args.phi)
     t_step = [0]
 
-    def one_step(sums=None):
+    def one_step(sums=None, ready=None, cdone=None):
         cp.md_step0 = (NSUB * t_step[0]) & 0xffffffff
-        L.lb_couple_particles(lat.h, parts, cp)
+        if ready is None:
+            L.lb_couple_particles(lat.h, parts, cp)
+        else:  # the particle state comes and goes on a copy stream
+            L.lb_couple_particles_async(lat.h, parts, cp, ready, cdone)
         if sums is None:
             L.lb_step(lat.h, 1)
         else:  # the step also returns the moment sums of the state it started from
@@ -386,39 +394,80 @@ def run_ours(args):
     KS = max(200, K)
     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    sissue0 = time.perf_counter()
     with torch.cuda.stream(stream):
         s0.record(stream)
         for _ in range(KS):
             one_step()
         s1.record(stream)
+    steady_issue_ms = (time.perf_counter() - sissue0) * 1e3
     barrier()
     steady_ms = s0.elapsed_time(s1)
 
     # end to end through the public API with host buffers: per step the
-    # particle state goes host -> device from pinned memory, and the particle
-    # state plus the moment sums (the 38 sums of lb_moments, accumulated by
-    # the step's stream-collide launch) come back -- one copy each way, since
-    # they share one buffer
-    KE = min(args.e2e_steps, K)
-    hio = torch.empty(io_bytes, dtype=torch.uint8, pin_memory=True)
-    hio.copy_(dio.cpu())
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(KE):
-            dio[:pos_b + mom_b].copy_(hio[:pos_b + mom_b], non_blocking=True)
-            one_step(dsums)
-            hio.copy_(dio, non_blocking=True)
-        e1.record(stream)
-    barrier()
-    e2e_ms = e0.elapsed_time(e1)
+    # particle state goes host -> device from pinned memory and the step's
+    # result comes back: the particle state (and, in the second loop, also
+    # the moment sums, the 38 sums of lb_moments that lb_step_sums accumulates
+    # in the step's stream-collide launch).  The copies run on copy streams,
+    # pipelined with the compute: the particle state of step k comes back as
+    # soon as the coupling of step k has finished (while that step's
+    # stream-collide launch still runs) and goes up again as step k+1's input
+    # (the host returns the state it received), which only the coupling of
+    # step k+1 waits for; the sums of step k come back beside step k+1
+    KE = args.e2e_steps
+    dpart = dio[pos_off:pos_off + pos_b + mom_b]
+    hio = torch.empty(pos_b + mom_b, dtype=torch.uint8, pin_memory=True)
+    hio.copy_(dpart.cpu())
+    hsums_all = torch.empty((2, L.LB_NSUMS), dtype=torch.float64, pin_memory=True)
+    hsums = (hsums_all[0], hsums_all[1])
+    cpy, rd = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ready, cdone, done = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    rdone = (torch.cuda.Event(), torch.cuda.Event())
+
+    def e2e_loop(with_sums):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        issue0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            cpy.wait_stream(stream)
+            rd.wait_stream(stream)
+            for k in range(KE):
+                with torch.cuda.stream(cpy):
+                    if k:
+                        cpy.wait_event(cdone)
+                        hio.copy_(dpart, non_blocking=True)   # step k-1's particle state
+                    dpart.copy_(hio, non_blocking=True)       # step k's input
+                    ready.record(cpy)
+                if not with_sums:
+                    one_step(None, ready, cdone)
+                    continue
+                if k >= 2:  # the slot's previous sums have reached the host
+                    stream.wait_event(rdone[k % 2])
+                one_step(dsums[k % 2], ready, cdone)
+                done.record(stream)
+                with torch.cuda.stream(rd):
+                    rd.wait_event(done)
+                    hsums[k % 2].copy_(dsums[k % 2], non_blocking=True)
+                    rdone[k % 2].record(rd)
+            with torch.cuda.stream(cpy):
+                cpy.wait_event(cdone)
+                hio.copy_(dpart, non_blocking=True)
+            stream.wait_stream(cpy)
+            stream.wait_stream(rd)
+            e1.record(stream)
+        issue = (time.perf_counter() - issue0) * 1e3 / KE  # host time to issue a step
+        barrier()
+        return e0.elapsed_time(e1), issue
+
+    e2e_ms, issue_ms = e2e_loop(False)
+    e2e_sums_ms, issue_sums_ms = e2e_loop(True)
     h2d = pos_b + mom_b
-    d2h = io_bytes
+    d2h = pos_b + mom_b
 
     # max over ranks
-    ms_total, sc_avg, e2e_ms, couple_ms, steady_ms = max_over_ranks([ms_total, sc_avg, e2e_ms, couple_ms, steady_ms],
-                                                                   dist, dev)
+    ms_total, sc_avg, e2e_ms, e2e_sums_ms, couple_ms, steady_ms = max_over_ranks(
+        [ms_total, sc_avg, e2e_ms, e2e_sums_ms, couple_ms, steady_ms], dist, dev)
     if rank != 0:
         dist.destroy_process_group()
         return 0
@@ -445,9 +494,15 @@ def run_ours(args):
                      "peak_source": peak_src},
         "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": KE, "copies_per_step": {"h2d": 1, "d2h": 1}},
+                "steps": KE, "copies_per_step": {"h2d": 1, "d2h": 1}, "result": "particle state",
+                "host_issue_ms_per_step": issue_ms,
+                "with_moment_sums": {"value": world * nodes * KE / (e2e_sums_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                                     "d2h_bytes_per_step": d2h + sums_b, "copies_per_step": {"h2d": 1, "d2h": 2},
+                                     "host_issue_ms_per_step": issue_sums_ms,
+                                     "result": "particle state + the 38 moment sums (lb_step_sums)"}},
         "steady": {"steps": KS, "ms_per_step": steady_ms / KS,
-                   "value": world * nodes * KS / (steady_ms * 1e-3) / 1e6, "unit": "MLUPS"},
+                   "value": world * nodes * KS / (steady_ms * 1e-3) / 1e6, "unit": "MLUPS",
+                   "host_issue_ms_per_step": steady_issue_ms / KS},
         "clocks": clk,
         "wall_s": wall,
     }
@@ -619,9 +674,29 @@ def _forms(peak):
         lat.close()
         del gpos, gmom
         torch.cuda.empty_cache()
+        # the same LB step without the noise (kT = 0): what the storage format
+        # gives where the arithmetic does not bind
+        lat = L.Lattice(shape, dtype=code, kT=0.0, seed=3, walls=True, body_force=(1e-6, 0, 0), stream=stream)
+        with torch.cuda.stream(stream):
+            lat.init_equilibrium()
+            lat.step(3)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            a.record(stream)
+            lat.step(20)
+            b.record(stream)
+        torch.cuda.synchronize()
+        assert lat.sync() == (L.LB_OK, 0)
+        ms0 = a.elapsed_time(b) / 20
+        prec[name]["lb_only_kT0_ms_per_step"] = ms0
+        prec[name]["lb_only_kT0_hbm_frac"] = 2 * 19 * esz * nfl / (ms0 * 1e-3) / 1e9 / peak
+        lat.close()
+        torch.cuda.empty_cache()
     for name in ("f16", "bf16"):
         prec[name]["speedup_vs_f32"] = prec["f32"]["ms_per_step"] / prec[name]["ms_per_step"]
         prec[name]["lb_only_speedup_vs_f32"] = prec["f32"]["lb_only_ms_per_step"] / prec[name]["lb_only_ms_per_step"]
+        prec[name]["lb_only_kT0_speedup_vs_f32"] = (prec["f32"]["lb_only_kT0_ms_per_step"]
+                                                    / prec[name]["lb_only_kT0_ms_per_step"])
     out["precision"] = {"shape": list(shape), "walls": True, "kT": KT, "particles": npart,
                         "workload": "Poiseuille g = 1e-6 between walls at z = 0, 511, 1e5 free particles "
                                     "(Gamma = 20 MD units), 10 sub-steps per LB step, serial coupling",
@@ -841,6 +916,12 @@ def main():
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.batched_form:
+        import torch
+        n = max(args.batched_form, 44)
+        print(json.dumps(_batched_form(torch.cuda.Stream(), _peak_hbm()[0], nsteps=n, t_begin=n // 2,
+                                       max_lag=min(200, n // 2 - 1))))
+        return 0
     if args.sphere_form:
         import torch
         print(json.dumps(_sphere_form(torch.cuda.Stream(), _peak_hbm()[0], steps=args.sphere_form)))

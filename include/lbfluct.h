@@ -254,7 +254,7 @@ typedef struct {
  * call returns with the coupling queued after all work on the handle's
  * stream; the next lb_step, or any other call on the handle, orders the
  * handle's stream after the coupling.  Until then the caller must not read
- * pos / mom itself.  A call made while impulses of an earlier call still
+ * pos / mom itself (lb_couple_particles_async gives an event for that).  A call made while impulses of an earlier call still
  * wait for a step runs in the serial order (the flag is ignored). */
 #define LB_COUPLE_OVERLAP 0x2
 
@@ -265,9 +265,10 @@ typedef struct {
  * and 3/8 wherever the particle is), so the friction a particle feels does
  * not depend on its position within a cell.  With walls a particle is kept
  * K/2 lattice units from the solid planes (K = 3 or 4, the stencil width;
- * 1 for phi_2), so nz must be at least K + 1.  These calls take the
- * per-sub-step kernels (the cooperative kernel covers phi_2 only); at most
- * one of the two bits may be set; the reverse-mode entry points reject
+ * 1 for phi_2), so nz must be at least K + 1.  Free particles take the
+ * one-launch kernel, pair forces a cooperative kernel with the stencil nodes
+ * cached in shared memory (per-sub-step kernels when it does not fit); at
+ * most one of the two bits may be set; the reverse-mode entry points reject
  * them. */
 #define LB_COUPLE_PHI3 0x4
 #define LB_COUPLE_PHI4 0x8
@@ -288,6 +289,22 @@ typedef struct {
  * The caller's pos and mom are updated in place.  Errors: LB_EINVAL,
  * LB_ENOMEM, LB_ECUDA; broken bonds and neighbour overflow set device bits. */
 lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
+
+/* lb_couple_particles for callers that move the particle state with other
+ * work, e.g. copies on a copy stream; either event may be NULL.
+ * ready_event: a cudaEvent_t recorded after the work that wrote the
+ * particle inputs (pos, mom, optional per-particle arrays).  With
+ * LB_COUPLE_OVERLAP only the coupling, on the library stream, waits for it,
+ * so the stream-collide launch of the next lb_step does not wait for the
+ * copy; without it the handle's stream waits.
+ * done_event: recorded where pos and mom hold this call's result (on the
+ * library stream with LB_COUPLE_OVERLAP, else on the handle's stream; at
+ * once for n = 0); a caller's stream that waits for it may read them before
+ * the next lb_step, while the impulses still wait for that step.
+ * The caller keeps the events alive until the work has used them.  Nothing is
+ * recorded when the call fails.  Errors: those of lb_couple_particles. */
+lb_status lb_couple_particles_async(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp,
+                                    void *ready_event, void *done_event);
 
 /* Interpolated fluid velocity u_p (device FP32 [n][3]) at device positions
  * pos[n][3] (Eq. (ufluid_discrete) with the linear stencil). */

@@ -593,6 +593,17 @@ lb_status lb_couple_particles(lb_handle *h, const lb_particles *parts, const lb_
     return couple_particles(h, parts, cp);
 }
 
+lb_status lb_couple_particles_async(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp,
+                                    void *ready_event, void *done_event)
+{
+    const lbi::NvtxRange range("lb_couple_particles");
+    if (!h || !parts || !cp) {
+        set_error("lb_couple_particles_async: NULL argument");
+        return LB_EINVAL;
+    }
+    return couple_particles(h, parts, cp, ready_event, done_event);
+}
+
 lb_status lb_interpolate(lb_handle *h, int n, const double *pos, float *u_out)
 {
     return lb_interpolate_phi(h, 2, n, pos, u_out);

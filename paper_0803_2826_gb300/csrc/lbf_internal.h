@@ -107,7 +107,8 @@ cudaError_t launch_get_populations(const lb_handle *h, const void *src, double *
 cudaError_t launch_moments(const lb_handle *h, const void *src, float *rho, float *j, float *pi,
                            double *sums);
 // particles.cu
-lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp);
+lb_status couple_particles(lb_handle *h, const lb_particles *parts, const lb_couple_params *cp,
+                          void *ready = nullptr, void *done = nullptr);
 lb_status interpolate(lb_handle *h, int kernel, int n, const double *pos, float *u_out);
 cudaError_t clear_particle_forces(lb_handle *h);
 void join_overlap(const lb_handle *h);  // order h->stream after a pending overlapped coupling

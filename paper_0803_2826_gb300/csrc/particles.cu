@@ -2371,7 +2371,7 @@ __global__ void __launch_bounds__(kPartThreads)
 
 }  // namespace
 
-lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp)
+lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple_params *cp, void *ready, void *done)
 {
     const int known = LB_COUPLE_PER_SUBSTEP | LB_COUPLE_OVERLAP | LB_COUPLE_PHI3 | LB_COUPLE_PHI4;
     if (pp->n < 0 || pp->reserved != 0 || (cp->flags & ~known) != 0 ||
@@ -2383,7 +2383,10 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         set_error("lb_couple_particles: the channel is too narrow for the interpolation stencil");
         return LB_EINVAL;
     }
-    if (pp->n == 0) return LB_OK;
+    if (pp->n == 0) {
+        const cudaError_t e = done ? cudaEventRecord((cudaEvent_t)done, h->stream) : cudaSuccess;
+        return e == cudaSuccess ? LB_OK : cuda_fail("lb_couple_particles", e);
+    }
     if (!pp->pos || !pp->mom) {
         set_error("lb_couple_particles: pos and mom are required");
         return LB_EINVAL;
@@ -2440,8 +2443,13 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         }
         if (e == cudaSuccess) e = cudaEventRecord(h->ev_main, main_stream);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->aux, h->ev_main, 0);
+        // the caller's inputs: only the coupling waits for them
+        if (e == cudaSuccess && ready) e = cudaStreamWaitEvent(h->aux, (cudaEvent_t)ready, 0);
         if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
         h->stream = h->aux;
+    } else if (ready) {
+        const cudaError_t e = cudaStreamWaitEvent(main_stream, (cudaEvent_t)ready, 0);
+        if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
     }
     struct Restore {  // the main stream comes back on every return
         lb_handle *h;
@@ -2461,6 +2469,8 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
     }
     timer_mark(h, 1, 1, h->stream);
     if (e == cudaSuccess && overlap) e = cudaEventRecord(h->ev_couple, h->aux);
+    // the caller's event: pos and mom hold this call's result
+    if (e == cudaSuccess && done) e = cudaEventRecord((cudaEvent_t)done, overlap ? h->aux : main_stream);
     if (e != cudaSuccess) return cuda_fail("lb_couple_particles", e);
     h->facc_dirty = 1;
     if (overlap) {

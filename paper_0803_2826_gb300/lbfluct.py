@@ -36,7 +36,7 @@ EXPORTS = (
     "lb_plane_pitch", "lb_population_bytes", "lb_create", "lb_destroy", "lb_last_error",
     "lb_sync", "lb_get_step", "lb_set_step", "lb_state_buffers", "lb_init_equilibrium",
     "lb_set_populations", "lb_get_populations", "lb_step", "lb_moments",
-    "lb_couple_particles", "lb_interpolate", "lb_interpolate_phi", "lb_get_particle_forces",
+    "lb_couple_particles", "lb_couple_particles_async", "lb_interpolate", "lb_interpolate_phi", "lb_get_particle_forces",
     "lb_spheres_place", "lb_step_spheres", "lb_get_solid_map", "lb_noise_words", "lb_box_muller",
     "lb_set_timing", "lb_get_timing", "lb_step_sums", "lb_adjoint_step_impulse", "lb_adjoint_couple",
     "lb_adjoint_kinetic_coupled",
@@ -138,6 +138,7 @@ def load(path: str | None = None):
             "lb_step": (i, [H, i]),
             "lb_moments": (i, [H, vp, vp, vp, vp]),
             "lb_couple_particles": (i, [H, C.POINTER(lb_particles), C.POINTER(lb_couple_params)]),
+            "lb_couple_particles_async": (i, [H, C.POINTER(lb_particles), C.POINTER(lb_couple_params), vp, vp]),
             "lb_interpolate": (i, [H, i, vp, vp]),
             "lb_interpolate_phi": (i, [H, i, i, vp, vp]),
             "lb_get_particle_forces": (i, [H, vp]),
@@ -308,6 +309,21 @@ def lb_moments(h, rho=None, j=None, pi=None, sums=None):
 
 def lb_couple_particles(h, parts: lb_particles, cp: lb_couple_params):
     _check(load().lb_couple_particles(h, C.byref(parts), C.byref(cp)))
+
+
+def lb_couple_particles_async(h, parts: lb_particles, cp: lb_couple_params, ready_event=None, done_event=None):
+    """ready_event: a recorded torch.cuda.Event (or a raw cudaEvent_t) after
+    the work that wrote the particle inputs; done_event: a torch.cuda.Event
+    (or raw cudaEvent_t) that the call records once pos / mom hold its
+    result.  Either may be None."""
+    def raw(ev):
+        if ev is None or isinstance(ev, int):
+            return ev
+        if ev.cuda_event == 0:  # torch creates its events lazily
+            import torch
+            ev.record(torch.cuda.current_stream())
+        return ev.cuda_event
+    _check(load().lb_couple_particles_async(h, C.byref(parts), C.byref(cp), raw(ready_event), raw(done_event)))
 
 
 def lb_interpolate(h, n, pos, u_out):

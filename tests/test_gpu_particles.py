@@ -516,3 +516,46 @@ def test_free_particles_overlap_matches_serial(kernel, walls):
     assert np.abs(out[0][0] - out[1][0]).max() < 1e-7
     assert _pos_err(out[0][1], out[1][1], shape) < 1e-6
     assert np.abs(out[0][2] - out[1][2]).max() < 1e-6
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_couple_async_events_match(overlap):
+    """lb_couple_particles_async: each call's particle state read back on a
+    copy stream as soon as the call's done event fires and uploaded again as
+    the next call's input (the host returns the state it read), the next
+    coupling ordered after the upload by its ready event; the results are the
+    same bits as lb_couple_particles with the state left on the device."""
+    shape = (24, 24, 24)
+    pos = inputs.random_walk_chains(6, 32, shape, seed=51)
+    n = pos.shape[0]
+    mom = inputs.maxwell_momenta(n, 1.0, 2e-3, seed=52).astype(np.float32)
+    out = []
+    for use_async in (False, True):
+        lat = L.Lattice(shape, kT=1e-4, seed=6)
+        lat.init_equilibrium(None, dev(inputs.shear_wave(shape, 0.01)))
+        gpos, gmom = dev(pos), dev(mom, torch.float32)
+        hpos = torch.empty(gpos.shape, dtype=gpos.dtype, pin_memory=True)
+        hmom = torch.empty(gmom.shape, dtype=gmom.dtype, pin_memory=True)
+        parts = L.particles(n, gpos, gmom, mass0=1.0, gamma0=2.0)
+        copy, ready, cdone = torch.cuda.Stream(), torch.cuda.Event(), torch.cuda.Event()
+        torch.cuda.synchronize()
+        for t in range(6):
+            cp = L.couple_params(n_substeps=10, dt=0.1, seed=3, md_step0=10 * t, chain_len=32, use_wca=True,
+                                 eps=0.01, sigma=1.0, k_fene=0.3, r0=1.5, overlap=overlap)
+            if use_async:
+                with torch.cuda.stream(copy):
+                    if t:
+                        copy.wait_event(cdone)
+                    hpos.copy_(gpos, non_blocking=True)
+                    hmom.copy_(gmom, non_blocking=True)
+                    gpos.copy_(hpos, non_blocking=True)
+                    gmom.copy_(hmom, non_blocking=True)
+                    ready.record(copy)
+                L.lb_couple_particles_async(lat.h, parts, cp, ready, cdone)
+            else:
+                L.lb_couple_particles(lat.h, parts, cp)
+            lat.step(1)
+        assert lat.sync() == (L.LB_OK, 0)
+        out.append((gpos.cpu().numpy(), gmom.cpu().numpy(), lat.get_populations().cpu().numpy()))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
