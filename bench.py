@@ -70,6 +70,11 @@ def _args():
     ap.add_argument("--shape", default="256,256,256")
     ap.add_argument("--kT", default="0,1e-4")
     ap.add_argument("--dtype", default="f32")
+    ap.add_argument("--equilibrium", type=int, default=0, choices=[0, 1],
+                    help="with --kernel-only: 1 times the exponential equilibrium's collision")
+    ap.add_argument("--batch-profile", default="", metavar="R,S,THREADS,TILE,BPS",
+                    help="profiling: R replicas of the batched form's edge mix, one launch of S steps "
+                         "with the given configuration (no autotuning, no graph), then exit")
     ap.add_argument("--batched-form", type=int, default=0, metavar="STEPS",
                     help="run only the batched-replica form with this many steps (profiling)")
     ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
@@ -97,7 +102,7 @@ def run_kernel_only(args):
         code, esz = dts[dname]
         for kT in (float(v) for v in args.kT.split(",")):
             with torch.cuda.stream(stream):
-                lat = L.Lattice(shape, kT=kT, seed=1, dtype=code, stream=stream)
+                lat = L.Lattice(shape, kT=kT, seed=1, dtype=code, stream=stream, equilibrium=args.equilibrium)
                 lat.init_equilibrium()
                 lat.step(args.warmup)
             torch.cuda.synchronize()
@@ -112,7 +117,8 @@ def run_kernel_only(args):
             ms = sorted(a.elapsed_time(b) for a, b in evs)
             med = ms[len(ms) // 2]
             gbs = 2 * 19 * esz * nodes / (med * 1e-3) / 1e9
-            print(json.dumps({"kernel": "k_stream_collide", "dtype": dname, "kT": kT, "shape": shape,
+            print(json.dumps({"kernel": "k_stream_collide_exp" if args.equilibrium else "k_stream_collide",
+                              "dtype": dname, "kT": kT, "shape": shape,
                               "ms_median": med, "ms_min": ms[0], "mlups": nodes / (med * 1e-3) / 1e6,
                               "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": src}))
             lat.close()
@@ -784,6 +790,37 @@ def _batched_form(stream, peak, nsteps=2000, max_lag=200, t_begin=1000):
                              "blocks_per_sm": cfg_plain.blocks_per_sm, "grid": cfg_plain.grid}}
 
 
+def run_batch_profile(args):
+    """One persistent launch of the batched kernel on a smaller replica set,
+    in a fixed configuration, timed with CUDA events (the kernel for ncu)."""
+    import torch
+    from paper_0803_2826_gb300 import build as B
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    B.build()
+    r, steps, threads, tile, bps = (int(v) for v in args.batch_profile.split(","))
+    edges = inputs.replica_edges(r, 7)
+    nodes = int(sum(e ** 3 for e in edges))
+    stream = torch.cuda.Stream()
+    Bt = L.Batch([(e, e, e) for e in edges], kT=KT, stream=stream)
+    L.lb_batch_set_config(Bt.b, threads, tile, bps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        L.lb_batch_init_equilibrium(Bt.b)
+        a.record(stream)
+        L.lb_batch_step(Bt.b, steps, False)
+        b.record(stream)
+    torch.cuda.synchronize()
+    L.lb_batch_sync(Bt.b)
+    ms = a.elapsed_time(b)
+    peak = _peak_hbm()[0]
+    print(json.dumps({"kernel": "k_batch_pair", "replicas": r, "nodes": nodes, "steps": steps,
+                      "config": [threads, tile, bps], "ms": ms,
+                      "hbm_frac": 152 * nodes * steps / (ms * 1e-3) / 1e9 / peak}))
+    Bt.close()
+    return 0
+
+
 def _interpolation_forms(stream, steps=100):
     """The coupled 256^3 workload of the headline line with the three- and
     four-point interpolation functions (27 / 64 stencil nodes per monomer,
@@ -916,6 +953,8 @@ def main():
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.batch_profile:
+        return run_batch_profile(args)
     if args.batched_form:
         import torch
         n = max(args.batched_form, 44)
