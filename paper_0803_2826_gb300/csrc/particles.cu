@@ -1513,6 +1513,103 @@ __device__ __forceinline__ void flush_wide(const int org[3], float *sm, float *f
     }
 }
 
+// Start of a call: the fluid velocity at every particle's stencil nodes,
+// each distinct node gathered once by the whole block.  The particles of a
+// block are usually consecutive monomers, whose stencils overlap (for the
+// random-walk chains of the workload 128 monomers touch ~1000 distinct nodes
+// with phi_3 and ~1600 with phi_4, against 3456 and 8192 stencil entries);
+// the impulse columns, still empty, hold a hash table of the distinct nodes
+// (open addressing, linear probing, inserted with atomicCAS): node index + 1
+// as key, its velocity, and the list of slots in insertion order, from which
+// all threads gather with several nodes' loads in flight.  Each particle then
+// copies its nodes' velocities into its own columns, so the sub-steps read
+// the same values, in the same layout, as with a gather per particle.  A node
+// that finds no slot within kTableProbes probes is gathered by its particle
+// directly.  All threads of the block call; on return the table is dead.
+template <int KW>
+constexpr int wide_table_cap()
+{
+    return (int)((size_t)3 * KW * KW * KW * kPThreads * sizeof(float) / 18);  // key 4 + velocity 12 + list 2 bytes
+}
+constexpr int kTableProbes = 32;
+
+template <int DT, int KW>
+__device__ __forceinline__ void block_gather_wide(bool active, const int org[3],
+                                                  const typename lbd::Store<DT>::T *src, const float *ffield,
+                                                  const StepArgs &g, float *sm, int *count)
+{
+    constexpr int kN = KW * KW * KW;
+    constexpr uint32_t cap = (uint32_t)wide_table_cap<KW>();
+    unsigned char *tb = reinterpret_cast<unsigned char *>(&wide_cache<KW>(sm, 3, 0, 0));
+    unsigned int *key = reinterpret_cast<unsigned int *>(tb);
+    float *tu = reinterpret_cast<float *>(tb + (size_t)cap * 4);
+    unsigned short *list = reinterpret_cast<unsigned short *>(tb + (size_t)cap * 16);
+    const int t = threadIdx.x;
+    for (uint32_t i = t; i < cap; i += kPThreads) key[i] = 0u;
+    if (t == 0) *count = 0;
+    __syncthreads();
+    if (active) {
+#pragma unroll 1
+        for (int q = 0; q < kN; ++q) {
+            int x, y, z;
+            stencil_coords<KW>(org, q, g, x, y, z);
+            const uint32_t k = (uint32_t)(((size_t)z * g.ny + y) * g.nx + x) + 1u;
+            uint32_t h = __umulhi(k * 2654435761u, cap);  // Fibonacci hashing onto [0, cap)
+            int slot = -1;
+            for (int probe = 0; probe < kTableProbes; ++probe) {
+                const uint32_t old = atomicCAS(&key[h], 0u, k);
+                if (old == 0u) {
+                    list[atomicAdd(count, 1)] = (unsigned short)h;
+                    slot = (int)h;
+                    break;
+                }
+                if (old == k) {
+                    slot = (int)h;
+                    break;
+                }
+                h = (h + 1u == cap) ? 0u : h + 1u;
+            }
+            wide_cache<KW>(sm, 0, q, t) = __int_as_float(slot);  // the slot until the copy below
+        }
+    }
+    __syncthreads();
+    const int n = *count;
+    const uint32_t nxy = (uint32_t)g.nx * (uint32_t)g.ny;
+#pragma unroll 2
+    for (int i = t; i < n; i += kPThreads) {
+        const uint32_t h = list[i];
+        const uint32_t node = key[h] - 1u;
+        const uint32_t z = node / nxy, r = node - z * nxy;
+        const uint32_t y = r / (uint32_t)g.nx, x = r - y * (uint32_t)g.nx;
+        float u[3];
+        node_velocity<DT>(src, ffield, (int)x, (int)y, (int)z, g, u);
+        tu[h] = u[0];
+        tu[cap + h] = u[1];
+        tu[2 * cap + h] = u[2];
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll 1
+        for (int q = 0; q < kN; ++q) {
+            const int slot = __float_as_int(wide_cache<KW>(sm, 0, q, t));
+            float u[3];
+            if (slot >= 0) {
+                u[0] = tu[slot];
+                u[1] = tu[cap + slot];
+                u[2] = tu[2 * cap + slot];
+            } else {  // no room in the table
+                int x, y, z;
+                stencil_coords<KW>(org, q, g, x, y, z);
+                node_velocity<DT>(src, ffield, x, y, z, g, u);
+            }
+            wide_cache<KW>(sm, 0, q, t) = u[0];
+            wide_cache<KW>(sm, 1, q, t) = u[1];
+            wide_cache<KW>(sm, 2, q, t) = u[2];
+        }
+    }
+    __syncthreads();
+}
+
 template <int DT, int KW>
 __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArgs a)
 {
@@ -1520,6 +1617,7 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
     constexpr int kN = KW * KW * KW;
     extern __shared__ float wsm[];
     __shared__ unsigned int ticket;  // arrival word of the split barrier
+    __shared__ int tcount;           // entries of the start-of-call node table
     const CoupleArgs &c = a.c;
     const StepArgs &g = c.g;
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1574,9 +1672,6 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
     }
     const int jlo = bond_lo ? p - 1 : self, jhi = bond_hi ? p + 1 : self;
     int kmax = __reduce_max_sync(kFullMask, min(nnb, kNbReg));
-    for (int q = 0; q < kN; ++q)
-        wide_cache<KW>(wsm, 3, q, threadIdx.x) = wide_cache<KW>(wsm, 4, q, threadIdx.x) =
-            wide_cache<KW>(wsm, 5, q, threadIdx.x) = 0.0f;
     int org[3];
     {
         Stencil<KW> st;
@@ -1585,7 +1680,10 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
         org[1] = st.o[1];
         org[2] = st.o[2];
     }
-    warp_gather_wide<DT, KW>(active, org, src, a.ffield, g, wsm);
+    block_gather_wide<DT, KW>(active, org, src, a.ffield, g, wsm, &tcount);
+    for (int q = 0; q < kN; ++q)
+        wide_cache<KW>(wsm, 3, q, threadIdx.x) = wide_cache<KW>(wsm, 4, q, threadIdx.x) =
+            wide_cache<KW>(wsm, 5, q, threadIdx.x) = 0.0f;
     if (!grid_barrier(a.bar, a.err, a.spin_limit)) return;
 
     bool binned = false;

@@ -224,13 +224,72 @@ def test_phi_kernel_walls_parity(ora, kernel):
 
 
 @pytest.mark.parametrize("kernel", [3, 4])
-def test_phi_kernel_chains_parity(ora, kernel):
-    """FENE + WCA chains with the wide stencils (per-sub-step kernels)."""
+@pytest.mark.parametrize("per_substep", [False, True])
+def test_phi_kernel_chains_parity(ora, kernel, per_substep):
+    """FENE + WCA chains with the wide stencils: the persistent kernel (its
+    start-of-call gather through the block's node table) and the
+    per-sub-step kernels."""
     shape = (16, 16, 16)
     pos = inputs.random_walk_chains(2, 24, shape, seed=7)
     mom = inputs.maxwell_momenta(48, 1.0, 1e-4, seed=8)
-    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), kernel=kernel)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(2, 24), kernel=kernel, per_substep=per_substep)
     _check_run(r, shape, 1e-6, next_bar=None, mom=CHAIN_MOM, facc=CHAIN_FACC)
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_phi_node_cache_moving_chains(ora, kernel):
+    """Chains of 64 monomers launched fast: stencil origins move every few
+    sub-steps (new stencils gathered inside the grid barrier), three blocks
+    sharing the start-of-call node tables."""
+    shape = (24, 20, 22)
+    pos = inputs.random_walk_chains(6, 64, shape, min_dist=1.0, seed=17)
+    mom = inputs.maxwell_momenta(pos.shape[0], 1.0, 2e-2, seed=18)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(6, 64), kernel=kernel)
+    _check_run(r, shape, 1.2e-6, next_bar=None, mom=CHAIN_MOM, facc=CHAIN_FACC)
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_phi_node_cache_dimers_walls(ora, kernel):
+    """Fast dimers (chains of two) between walls on the persistent wide
+    kernel: centres on a grid of spacing 2 inside the band K/2 + 1 from the
+    solid planes, bonds of 0.97 in random directions, 14 blocks."""
+    shape = (24, 20, 22)
+    b = kernel // 2 + 1
+    g = np.stack(np.meshgrid(np.arange(1.0, 24.0, 2.0), np.arange(1.0, 20.0, 2.0),
+                             np.arange(b + 1.0, shape[2] - b - 1.0, 2.0), indexing="ij"), -1).reshape(-1, 3)
+    e = np.random.default_rng(27).normal(size=g.shape)
+    e /= np.linalg.norm(e, axis=1)[:, None]
+    pos = np.stack([g - 0.485 * e, g + 0.485 * e], axis=1).reshape(-1, 3) % np.array(shape, dtype=np.float64)
+    n = pos.shape[0]
+    mom = inputs.maxwell_momenta(n, 1.0, 2e-2, seed=28)
+    r = _run(ora, shape, pos, mom, kT=1e-4, walls=True, chains=(n // 2, 2), kernel=kernel, body_force=(1e-5, 0, 0))
+    _check_run(r, shape, 1.2e-6, next_bar=None, mom=CHAIN_MOM, facc=CHAIN_FACC)
+    assert r["gpos"][:, 2].min() >= kernel / 2 and r["gpos"][:, 2].max() <= shape[2] - 1 - kernel / 2
+
+
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_phi_node_cache_full(ora, kernel):
+    """WCA particles scattered through a 64^3 box: the 128 particles of a
+    block share no stencil nodes, more than the block's start-of-call node
+    table holds (2304 / 5461 slots), so the nodes that find no slot are
+    gathered by their particles directly; the results still match the
+    oracle."""
+    shape = (64, 64, 64)
+    rng = np.random.default_rng(29)
+    pts = []
+    while len(pts) < 512:  # at least 2.5 apart (periodic)
+        c = rng.uniform(0.0, 64.0, 3)
+        if all(np.linalg.norm((c - d + 32.0) % 64.0 - 32.0) >= 2.5 for d in pts):
+            pts.append(c)
+    pos = np.array(pts)
+    # distinct stencil nodes of the first block's 128 particles: more than the table holds
+    o = np.floor(pos[:128] + (0.5 if kernel == 3 else 0.0)).astype(int) - 1
+    d = np.stack(np.meshgrid(*[np.arange(kernel)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    nodes = {tuple(x) for x in ((o[:, None, :] + d[None]) % 64).reshape(-1, 3)}
+    assert len(nodes) > (2304 if kernel == 3 else 5461)
+    mom = inputs.maxwell_momenta(pos.shape[0], 1.0, 1e-4, seed=28)
+    r = _run(ora, shape, pos, mom, kT=1e-4, chains=(512, 1), kernel=kernel, nsub=4, lb_after=False)
+    _check_run(r, shape, 1e-6, next_bar=None)
 
 
 def test_phi3_many_particles_parity(ora):
