@@ -336,9 +336,10 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes(const typename lbd:
 // impulse, the stored moments change by dM_1..3 = 3 (f_n - f_b) and, for
 // k = 4..9, dM_k = ((1 - gamma_k) (m^eq_k(u_n) - m^eq_k(u_b)) + F_k(u_n, f_n)
 // - F_k(u_b, f_b)) / w_k; n* += backward(dM).  No pull and no noise; the
-// claim makes sure each node is corrected once.
+// claim makes sure each node is corrected once.  Eight blocks per SM (64 registers, no
+// spills): the launch for the workload's ~1.3e5 threads fits in one wave.
 template <bool WALLS>
-__global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restrict__ dst, const float *__restrict__ ffield,
+__global__ void __launch_bounds__(kBX, 8) k_patch_impulse_nodes_f32(float *__restrict__ dst, const float *__restrict__ ffield,
                                                                  float *__restrict__ facc, const int *records, int n,
                                                                  int nsub, int span, unsigned int *claim,
                                                                  unsigned int tag, const StepArgs a)
@@ -358,12 +359,17 @@ __global__ void __launch_bounds__(kBX) k_patch_impulse_nodes_f32(float *__restri
             int x, y, z;
             if (!patch_node<WALLS>(bx, by, bz, e, span, a, x, y, z)) continue;  // solid node
             const size_t node = ((size_t)z * a.ny + y) * a.nx + x;
-            if (atomicMax(claim + node, tag) == tag) continue;  // another thread has it
+            // the claim, the impulse and the stored values are requested
+            // together (one memory round trip instead of three); the values
+            // are used only by the thread that wins the claim, and nothing
+            // else writes this node during the kernel
+            const unsigned int had = atomicMax(claim + node, tag);
             const float df[3] = {facc[node], facc[P + node], facc[2 * P + node]};
-            if (df[0] == 0.0f && df[1] == 0.0f && df[2] == 0.0f) continue;
             float ns[19], m[19];
 #pragma unroll
             for (int i = 0; i < 19; ++i) ns[i] = dst[(size_t)i * P + node];
+            if (had == tag) continue;  // another thread has it
+            if (df[0] == 0.0f && df[1] == 0.0f && df[2] == 0.0f) continue;
             lbd::forward(ns, m);
             float fb[3] = {a.fx, a.fy, a.fz};
             if (ffield) {
