@@ -266,10 +266,10 @@ typedef struct {
  * not depend on its position within a cell.  With walls a particle is kept
  * K/2 lattice units from the solid planes (K = 3 or 4, the stencil width;
  * 1 for phi_2), so nz must be at least K + 1.  Free particles take the
- * one-launch kernel, pair forces a cooperative kernel with the stencil nodes
- * cached in shared memory (per-sub-step kernels when it does not fit); at
- * most one of the two bits may be set; the reverse-mode entry points reject
- * them. */
+ * one-launch kernel, pair forces a cooperative kernel with each particle's
+ * stencil velocities and impulse sums cached in shared memory (per-sub-step
+ * kernels when its grid cannot be resident); at most one of the two bits may
+ * be set; the reverse-mode entry points reject them. */
 #define LB_COUPLE_PHI3 0x4
 #define LB_COUPLE_PHI4 0x8
 
