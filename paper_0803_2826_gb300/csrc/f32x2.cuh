@@ -219,13 +219,41 @@ __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t b0, uint32_t a
     g1 = nr * f2(s0, s1);
 }
 
+// Where collide_moments2 takes its Philox round keys: ParamKeys reads the
+// precomputed keys of one seed (kernel parameters: constant-bank operands);
+// RunningKeys forms round r's keys as key + r W from the two key words (two
+// adds a round, but only two registers: for kernels whose key is data, e.g.
+// one per replica, and which would otherwise hold all twenty).  pair() runs
+// the two nodes' counter blocks.
+struct ParamKeys {
+    const lbd::RoundKeys &rk;
+    __device__ __forceinline__ void pair(const lbd::U4 &c0, const lbd::U4 &c1, lbd::U4 &r0, lbd::U4 &r1) const
+    {
+        r0 = lbd::philox10(c0, rk);
+        r1 = lbd::philox10(c1, rk);
+    }
+};
+struct RunningKeys {
+    uint32_t k0, k1;
+    __device__ __forceinline__ void pair(const lbd::U4 &c0, const lbd::U4 &c1, lbd::U4 &r0, lbd::U4 &r1) const
+    {
+        r0 = c0;
+        r1 = c1;
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+            const uint32_t q0 = k0 + (uint32_t)r * lbd::kPhiloxW0, q1 = k1 + (uint32_t)r * lbd::kPhiloxW1;
+            lbd::philox_round(r0, q0, q1);
+            lbd::philox_round(r1, q0, q1);
+        }
+    }
+};
+
 // Collision of nodes node0, node0 + 1 (Sec. 3.4, 3.5, 3.7) from their
 // moments m and force densities (fx, fy, fz) to the post-collision
 // deviations out: lbi::collide_moments of each node, paired.
-template <bool NOISE>
-__device__ __forceinline__ void collide_moments2(const F2 m[19], F2 fx, F2 fy, F2 fz, const lbi::StepArgs &a,
-                                                 const lbd::RoundKeys &rk, uint32_t node0, uint32_t replica,
-                                                 F2 out[19])
+template <bool NOISE, class Keys>
+__device__ __forceinline__ void collide_moments2k(const F2 m[19], F2 fx, F2 fy, F2 fz, const lbi::StepArgs &a,
+                                                  const Keys &keys, uint32_t node0, uint32_t replica, F2 out[19])
 {
     const F2 half = f2s(0.5f), three = f2s(3.0f);
     const F2 rho = f2s(a.rho0) + m[0];
@@ -280,8 +308,9 @@ __device__ __forceinline__ void collide_moments2(const F2 m[19], F2 fx, F2 fy, F
         const F2 var = a.noise_rho0 ? f2s(a.mu * a.rho0) : rho * a.mu;
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const lbd::U4 r0 = lbd::philox10(lbd::U4{node0, a.step, (uint32_t)b, replica}, rk);
-            const lbd::U4 r1 = lbd::philox10(lbd::U4{node0 + 1u, a.step, (uint32_t)b, replica}, rk);
+            lbd::U4 r0, r1;
+            keys.pair(lbd::U4{node0, a.step, (uint32_t)b, replica}, lbd::U4{node0 + 1u, a.step, (uint32_t)b, replica},
+                      r0, r1);
             F2 g[4];
             box_muller2(r0.x, r0.y, r1.x, r1.y, g[0], g[1], var);
             box_muller2(r0.z, r0.w, r1.z, r1.w, g[2], g[3], var);
@@ -294,6 +323,14 @@ __device__ __forceinline__ void collide_moments2(const F2 m[19], F2 fx, F2 fy, F
     }
 
     backward2(M, out);
+}
+
+template <bool NOISE>
+__device__ __forceinline__ void collide_moments2(const F2 m[19], F2 fx, F2 fy, F2 fz, const lbi::StepArgs &a,
+                                                 const lbd::RoundKeys &rk, uint32_t node0, uint32_t replica,
+                                                 F2 out[19])
+{
+    collide_moments2k<NOISE>(m, fx, fy, fz, a, ParamKeys{rk}, node0, replica, out);
 }
 
 }  // namespace lbp
