@@ -315,7 +315,9 @@ def lb_couple_particles_async(h, parts: lb_particles, cp: lb_couple_params, read
     """ready_event: a recorded torch.cuda.Event (or a raw cudaEvent_t) after
     the work that wrote the particle inputs; done_event: a torch.cuda.Event
     (or raw cudaEvent_t) that the call records once pos / mom hold its
-    result.  Either may be None."""
+    result.  Either may be None.  torch creates an event's CUDA handle at its
+    first record: an event never recorded is first recorded on the current
+    stream (for ready_event: the inputs are taken as ready there)."""
     def raw(ev):
         if ev is None or isinstance(ev, int):
             return ev

@@ -305,3 +305,26 @@ def test_step_sums_equal_moment_sums(shape, walls, dtype):
     assert np.abs(g - w).max() < 1e-6 * scale, (g, w)
     assert np.array_equal(a.get_populations().cpu().numpy(), b.get_populations().cpu().numpy())
     assert a.sync() == (L.LB_OK, 0) and b.sync() == (L.LB_OK, 0)
+
+
+def test_nonfinite_sums_reported():
+    """A non-finite population (a NaN planted at one node) makes the moment
+    sums non-finite: lb_moments and lb_step_sums set the device error word,
+    lb_sync reports LB_ENONFINITE and clears it; no fault, no abort."""
+    shape = (8, 6, 5)
+    lat = L.Lattice(shape, kT=0.0, seed=1)
+    lat.init_equilibrium()
+    n = lat.get_populations()
+    n[3, 2, 1, 4] = float("nan")
+    lat.set_populations(n)
+    _, _, _, sums = lat.moments(want_sums=True)
+    with pytest.raises(L.LBError) as ei:
+        lat.sync()
+    assert ei.value.status == L.LB_ENONFINITE
+    assert not np.isfinite(sums.cpu().numpy()).all()
+    assert lat.sync() == (L.LB_OK, 0)
+    got = torch.empty(L.LB_NSUMS, dtype=torch.float64, device="cuda")
+    L.lb_step_sums(lat.h, 1, got)
+    st, bits = L.lb_sync(lat.h, raise_on_error=False)
+    assert st == L.LB_ENONFINITE and bits & L.LB_DERR_NONFINITE
+    assert lat.sync() == (L.LB_OK, 0)
