@@ -403,6 +403,32 @@ __device__ __forceinline__ void stencil_coords(const int o[3], int q, const Step
     else z = wrap_node(z, g.nz);
 }
 
+// The record of a particle's sub-step, which the overlapped step's
+// re-update and the clearing of applied impulses expand to a block of
+// record_span^3 nodes: for phi_2 and phi_4 the linear index of the
+// particle's cell (the block is the cell's corners, resp. one node further
+// on each side: the stencil), for phi_3 the wrapped stencil origin (the
+// block is the 27-node stencil itself, not the 64 nodes around the cell).
+template <int KW>
+constexpr int record_span() { return KW == 3 ? 3 : (KW == 4 ? 4 : 2); }
+
+template <int KW>
+__device__ __forceinline__ int stencil_record(const CPos &me, const StepArgs &g)
+{
+    if constexpr (KW == 3) {
+        int o[3];
+        const int L[3] = {g.nx, g.ny, g.nz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = me.c[k] - 1 + (me.f[k] >= 0.5f ? 1 : 0);  // the origin of axis_weights<3>
+            if (o[k] < 0) o[k] += L[k];
+        }
+        return (o[2] * g.ny + o[1]) * g.nx + o[0];
+    } else {
+        return (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
@@ -789,7 +815,7 @@ __global__ void __launch_bounds__(kPartThreads)
         }
     }
     if (q != 0) return;
-    if (records) records[p] = (int)(((size_t)me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0]);
+    if (records) records[p] = stencil_record<KW>(me, g);
 
     // second half drift of this sub-step, then the first of the next one
     const float h = 0.5f * c.dt / m;
@@ -1765,7 +1791,7 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent_wide(PersistArg
                 jy = fmaf(-J[1], w, jy);
                 jz = fmaf(-J[2], w, jz);
             }
-            a.records[(size_t)s * c.n + p] = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+            a.records[(size_t)s * c.n + p] = stencil_record<KW>(me, g);
 
             const bool last = (s == a.nsub - 1);
             bool ok = drift(me, pn, h, g, KW);
@@ -1958,7 +1984,7 @@ __global__ void __launch_bounds__(kPartThreads) k_couple_free(FreeArgs a)
             acc[i][1] = fmaf(-J[1], w[i], acc[i][1]);
             acc[i][2] = fmaf(-J[2], w[i], acc[i][2]);
         }
-        if (q == 0 && a.records) a.records[(size_t)s * c.n + p] = (me.c[2] * g.ny + me.c[1]) * g.nx + me.c[0];
+        if (q == 0 && a.records) a.records[(size_t)s * c.n + p] = stencil_record<KW>(me, g);
         // second half drift of this sub-step, then the first of the next one
         ok = drift(me, pn, h, g, KW) && ok;
         if (s + 1 < a.nsub) ok = drift(me, pn, h, g, KW) && ok;
@@ -2094,7 +2120,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         else k_couple_free<DT, 2><<<fblocks, kPartThreads, 0, h->stream>>>(fa);
         h->launches += 1;
         note_records(P, n, (size_t)n * (size_t)cp->n_substeps);
-        if (c.kw > 2) P->rec_span = 4;
+        P->rec_span = std::max(P->rec_span, c.kw == 3 ? 3 : (c.kw == 4 ? 4 : 2));
         P->sub_counter += (uint32_t)cp->n_substeps;
         P->last_nsub = cp->n_substeps;
         return cudaGetLastError();
@@ -2176,7 +2202,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
             if (e != cudaSuccess) return e;
             h->launches += 1;
             note_records(P, n, (size_t)n * (size_t)cp->n_substeps);
-            P->rec_span = 4;
+            P->rec_span = std::max(P->rec_span, c.kw == 3 ? 3 : 4);
             P->sub_counter += (uint32_t)cp->n_substeps;
             P->last_nsub = cp->n_substeps;
             return cudaGetLastError();
@@ -2315,7 +2341,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         else LBI_SUBSTEP(2);
 #undef LBI_SUBSTEP
         note_records(P, n, (size_t)n);
-        if (c.kw > 2) P->rec_span = 4;
+        P->rec_span = std::max(P->rec_span, c.kw == 3 ? 3 : (c.kw == 4 ? 4 : 2));
         P->sub_counter += 1;
         h->launches += 1;
     }
@@ -2577,7 +2603,7 @@ lb_status couple_particles(lb_handle *h, const lb_particles *pp, const lb_couple
         h->patch_n = pp->n;
         h->patch_nsub = cp->n_substeps;
         h->patch_rec = P->records + P->rec_off + P->n_records - (size_t)pp->n * (size_t)cp->n_substeps;
-        h->patch_span = stencil_width(cp->flags) > 2 ? 4 : 2;
+        h->patch_span = stencil_width(cp->flags);  // the record span: 2, 3 (origin records) or 4
     }
     return LB_OK;
 }
@@ -2594,12 +2620,16 @@ cudaError_t clear_particle_forces(lb_handle *h)
             const unsigned int blocks = (unsigned int)(((size_t)P->rec_n * 8 + 255) / 256);
             if (P->rec_span == 4)
                 k_clear_records_by_particle<4><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->rec_n, nsub, g);
+            else if (P->rec_span == 3)
+                k_clear_records_by_particle<3><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->rec_n, nsub, g);
             else
                 k_clear_records_by_particle<2><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->rec_n, nsub, g);
         } else {
             int blocks = (int)std::min<size_t>((P->n_records + 255) / 256, (size_t)8 * device_sm_count());
             if (P->rec_span == 4)
                 k_clear_records<4><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->n_records, g);
+            else if (P->rec_span == 3)
+                k_clear_records<3><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->n_records, g);
             else
                 k_clear_records<2><<<blocks, 256, 0, h->stream>>>(h->facc, rec, P->n_records, g);
         }

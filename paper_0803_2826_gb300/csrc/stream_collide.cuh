@@ -271,10 +271,16 @@ template <bool WALLS>
 __device__ __forceinline__ bool patch_node(int bx, int by, int bz, int k, int span, const StepArgs &a, int &x,
                                            int &y, int &z)
 {
-    const int sh = span == 4 ? 2 : 1, lo = span == 4 ? -1 : 0, m = span - 1;
-    x = bx + lo + (k & m);
-    y = by + lo + ((k >> sh) & m);
-    z = bz + lo + (k >> (2 * sh));
+    if (span == 3) {  // a phi_3 stencil origin: the 27 nodes of the stencil
+        x = bx + k % 3;
+        y = by + (k / 3) % 3;
+        z = bz + k / 9;
+    } else {  // a cell: its corners (span 2) or one node further on each side (span 4)
+        const int sh = span == 4 ? 2 : 1, lo = span == 4 ? -1 : 0, m = span - 1;
+        x = bx + lo + (k & m);
+        y = by + lo + ((k >> sh) & m);
+        z = bz + lo + (k >> (2 * sh));
+    }
     x = x < 0 ? x + a.nx : (x >= a.nx ? x - a.nx : x);
     y = y < 0 ? y + a.ny : (y >= a.ny ? y - a.ny : y);
     if ((unsigned)x >= (unsigned)a.nx) x = ((x % a.nx) + a.nx) % a.nx;  // boxes narrower than the stencil
@@ -288,8 +294,9 @@ __device__ __forceinline__ bool patch_node(int bx, int by, int bz, int k, int sp
 
 // Re-update of the nodes that received particle impulses, after an update of
 // all nodes that left the impulses out (the coupling ran meanwhile): the
-// span^3 nodes around each cell particle p visited, records[s][p] (linear
-// cell index at sub-step s), are updated again from the same pre-step state
+// span^3 nodes of each record of particle p, records[s][p] (the linear index
+// of its cell at sub-step s, or of its phi_3 stencil origin: span 3), are
+// updated again from the same pre-step state
 // with the impulses added.  The update of a node depends only on that state, the
 // forces at the node and the counter-based noise, so the result is the one a
 // single update with the impulses would give.  Thread (p, q) walks p's
