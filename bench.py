@@ -72,9 +72,10 @@ def _args():
     ap.add_argument("--dtype", default="f32")
     ap.add_argument("--equilibrium", type=int, default=0, choices=[0, 1],
                     help="with --kernel-only: 1 times the exponential equilibrium's collision")
-    ap.add_argument("--batch-profile", default="", metavar="R,S,THREADS,TILE,BPS",
+    ap.add_argument("--batch-profile", default="", metavar="R,S,THREADS,TILE,BPS[,REC]",
                     help="profiling: R replicas of the batched form's edge mix, one launch of S steps "
-                         "with the given configuration (no autotuning, no graph), then exit")
+                         "with the given configuration (no autotuning, no graph; REC = 1 records the "
+                         "transverse modes), then exit")
     ap.add_argument("--batched-form", type=int, default=0, metavar="STEPS",
                     help="run only the batched-replica form with this many steps (profiling)")
     ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
@@ -798,15 +799,20 @@ def run_batch_profile(args):
     from paper_0803_2826_gb300 import inputs
     from paper_0803_2826_gb300 import lbfluct as L
     B.build()
-    r, steps, threads, tile, bps = (int(v) for v in args.batch_profile.split(","))
+    vals = [int(v) for v in args.batch_profile.split(",")]
+    r, steps, threads, tile, bps = vals[:5]
+    records = len(vals) > 5 and vals[5] != 0
     edges = inputs.replica_edges(r, 7)
     nodes = int(sum(e ** 3 for e in edges))
     stream = torch.cuda.Stream()
     Bt = L.Batch([(e, e, e) for e in edges], kT=KT, stream=stream)
     L.lb_batch_set_config(Bt.b, threads, tile, bps)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rec = torch.empty((len(edges), steps, 12), dtype=torch.float64, device="cuda") if records else None
     with torch.cuda.stream(stream):
         L.lb_batch_init_equilibrium(Bt.b)
+        if records:
+            L.lb_batch_record_modes(Bt.b, rec, steps)
         a.record(stream)
         L.lb_batch_step(Bt.b, steps, False)
         b.record(stream)
@@ -814,7 +820,8 @@ def run_batch_profile(args):
     L.lb_batch_sync(Bt.b)
     ms = a.elapsed_time(b)
     peak = _peak_hbm()[0]
-    print(json.dumps({"kernel": "k_batch_pair", "replicas": r, "nodes": nodes, "steps": steps,
+    print(json.dumps({"kernel": "k_batch_pair_obs" if records else "k_batch_pair", "replicas": r, "nodes": nodes,
+                      "steps": steps,
                       "config": [threads, tile, bps], "ms": ms,
                       "hbm_frac": 152 * nodes * steps / (ms * 1e-3) / 1e9 / peak}))
     Bt.close()
