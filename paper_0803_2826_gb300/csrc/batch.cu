@@ -211,7 +211,7 @@ __device__ __forceinline__ void ld_pair<2>(const __nv_bfloat16 *p, float inv, fl
 template <int DT, bool NOISE, bool OBS>
 __device__ __forceinline__ void batch_pair(const BatchDesc &d, uint32_t s, const typename lbd::Store<DT>::T *src,
                                            typename lbd::Store<DT>::T *dst, const StepArgs &ph, uint32_t step,
-                                           const float2 *phase, lbp::F2 acc[kModeVals])
+                                           const float2 *phase, float acc[kModeVals])
 {
     using S = lbd::Store<DT>;
     const uint32_t row = divide(s, d.dx);
@@ -265,20 +265,25 @@ __device__ __forceinline__ void batch_pair(const BatchDesc &d, uint32_t s, const
         const float2 ex0 = __ldg(phase + d.phase + x0), ex1 = __ldg(phase + d.phase + x0 + 1);
         const float2 ey = __ldg(phase + d.phase + d.nx + y);
         const float2 ez = __ldg(phase + d.phase + d.nx + d.ny + z);
-        const lbp::F2 czr = lbp::f2s(ez.x), czi = lbp::f2s(ez.y), cyr = lbp::f2s(ey.x), cyi = lbp::f2s(ey.y);
-        const lbp::F2 cxr = lbp::f2(ex0.x, ex1.x), cxi = lbp::f2(ex0.y, ex1.y);
-        acc[0] = lbp::fma2(ux, czr, acc[0]);
-        acc[1] = lbp::fma2(ux, czi, acc[1]);
-        acc[2] = lbp::fma2(uy, czr, acc[2]);
-        acc[3] = lbp::fma2(uy, czi, acc[3]);
-        acc[4] = lbp::fma2(uy, cxr, acc[4]);
-        acc[5] = lbp::fma2(uy, cxi, acc[5]);
-        acc[6] = lbp::fma2(uz, cxr, acc[6]);
-        acc[7] = lbp::fma2(uz, cxi, acc[7]);
-        acc[8] = lbp::fma2(uz, cyr, acc[8]);
-        acc[9] = lbp::fma2(uz, cyi, acc[9]);
-        acc[10] = lbp::fma2(ux, cyr, acc[10]);
-        acc[11] = lbp::fma2(ux, cyi, acc[11]);
+        // scalar sums (twelve registers, not twenty-four): the y and z phases
+        // are the same for both nodes of the pair, the x phases are not
+        float uxl, uxh, uyl, uyh, uzl, uzh;
+        lbp::split(ux, uxl, uxh);
+        lbp::split(uy, uyl, uyh);
+        lbp::split(uz, uzl, uzh);
+        const float sx = uxl + uxh, sy = uyl + uyh, sz = uzl + uzh;
+        acc[0] = fmaf(sx, ez.x, acc[0]);
+        acc[1] = fmaf(sx, ez.y, acc[1]);
+        acc[2] = fmaf(sy, ez.x, acc[2]);
+        acc[3] = fmaf(sy, ez.y, acc[3]);
+        acc[4] = fmaf(uyh, ex1.x, fmaf(uyl, ex0.x, acc[4]));
+        acc[5] = fmaf(uyh, ex1.y, fmaf(uyl, ex0.y, acc[5]));
+        acc[6] = fmaf(uzh, ex1.x, fmaf(uzl, ex0.x, acc[6]));
+        acc[7] = fmaf(uzh, ex1.y, fmaf(uzl, ex0.y, acc[7]));
+        acc[8] = fmaf(sz, ey.x, acc[8]);
+        acc[9] = fmaf(sz, ey.y, acc[9]);
+        acc[10] = fmaf(sx, ey.x, acc[10]);
+        acc[11] = fmaf(sx, ey.y, acc[11]);
     }
     lbp::collide_moments2k<NOISE>(m, fx, fy, fz, a, lbp::RunningKeys{d.key0, d.key1}, s, d.replica, out);
     typename S::T *o = dst + d.off;
@@ -330,17 +335,10 @@ __device__ __forceinline__ void batch_run(const BatchArgs &a)
             const BatchDesc &d = a.desc[tl.rep];
             float acc[kModeVals];
             if (PAIR) {  // every replica has even nx: tiles hold whole pairs
-                lbp::F2 acc2[kModeVals];
 #pragma unroll
-                for (int q = 0; q < kModeVals; ++q) acc2[q] = lbp::f2s(0.0f);
+                for (int q = 0; q < kModeVals; ++q) acc[q] = 0.0f;
                 for (uint32_t k = 2 * threadIdx.x; k < tl.count; k += 2 * blockDim.x)
-                    batch_pair<DT, NOISE, OBS>(d, tl.begin + k, src, dst, a.phys, step, a.phase, acc2);
-#pragma unroll
-                for (int q = 0; q < kModeVals; ++q) {
-                    float l, h;
-                    lbp::split(acc2[q], l, h);
-                    acc[q] = l + h;
-                }
+                    batch_pair<DT, NOISE, OBS>(d, tl.begin + k, src, dst, a.phys, step, a.phase, acc);
             } else {
 #pragma unroll
                 for (int q = 0; q < kModeVals; ++q) acc[q] = 0.0f;
