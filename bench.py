@@ -76,6 +76,8 @@ def _args():
                     help="profiling: R replicas of the batched form's edge mix, one launch of S steps "
                          "with the given configuration (no autotuning, no graph; REC = 1 records the "
                          "transverse modes), then exit")
+    ap.add_argument("--adjoint-form", action="store_true",
+                    help="run only the adjoint form (profiling)")
     ap.add_argument("--batched-form", type=int, default=0, metavar="STEPS",
                     help="run only the batched-replica form with this many steps (profiling)")
     ap.add_argument("--sphere-form", type=int, default=0, metavar="STEPS",
@@ -559,50 +561,7 @@ def _forms(peak):
     out["batched"] = _batched_form(stream, peak)
 
     # adjoint vs plain forward
-    shape, T, K = (64, 64, 64), 500, 50
-    f = torch.as_tensor(inputs.gaussian_field(shape, 3, 1e-5, seed=0).astype(np.float32)).cuda()
-    lat = L.Lattice(shape, force=f, stream=stream)
-    g = torch.empty_like(f)
-    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with torch.cuda.stream(stream):
-        lat.init_equilibrium()
-        lat.step(20)
-    torch.cuda.synchronize()
-    a, b = ev(), ev()
-    with torch.cuda.stream(stream):
-        a.record(stream)
-        lat.step(T)
-        b.record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = a.elapsed_time(b) / T
-    # one untimed call sizes the handle's reverse-mode arena; the timed calls
-    # then allocate nothing (CUDA events on the handle's stream)
-    with torch.cuda.stream(stream):
-        lat.init_equilibrium()
-        L.lb_adjoint_kinetic(lat.h, T, K, (24, 24, 24), (40, 40, 40), g, loss)
-    torch.cuda.synchronize()
-    a, b, c = ev(), ev(), ev()
-    with torch.cuda.stream(stream):
-        lat.init_equilibrium()
-        a.record(stream)
-        L.lb_adjoint_forward(lat.h, T, K, (24, 24, 24), (40, 40, 40), loss)
-        b.record(stream)
-        L.lb_adjoint_backward(lat.h, g)
-        c.record(stream)
-    torch.cuda.synchronize()
-    fwd_ck_ms = a.elapsed_time(b) / T
-    adj_ms = a.elapsed_time(c) / T
-    # algorithmic bytes per node and step: forward 152 + 12 (force field);
-    # reverse 264 (lambda in and out, the state, the force gradient) plus the
-    # recompute of the segment states, 152 + 12
-    alg_ratio = (164 + 264 + 164) / 164
-    out["adjoint"] = {"shape": list(shape), "steps": T, "checkpoint_every": K,
-                      "fwd_plus_adj_ms_per_step": adj_ms, "fwd_with_checkpoints_ms_per_step": fwd_ck_ms,
-                      "plain_fp32_ms_per_step": fwd_ms, "ratio": adj_ms / fwd_ms,
-                      "algorithmic_bytes_ratio": alg_ratio, "loss": loss.item(),
-                      "timing": "CUDA events around lb_adjoint_forward + lb_adjoint_backward on the handle's "
-                                "stream; the checkpoint arena was allocated by an earlier call"}
-    lat.close()
+    out["adjoint"] = _adjoint_form(stream)
 
     # wider interpolation stencils on the headline workload
     out["interpolation"] = _interpolation_forms(stream)
@@ -709,6 +668,61 @@ def _forms(peak):
                                     "(Gamma = 20 MD units), 10 sub-steps per LB step, serial coupling",
                         **prec}
     return out
+
+
+def _adjoint_form(stream):
+    """64^3, kT = 0, force field ~ N(0, 1e-5), kinetic energy of the central
+    16^3 after 500 steps, checkpoints every 50: forward + reverse ms per step
+    against 500 plain FP32 steps (CUDA events)."""
+    import numpy as np
+    import torch
+    from paper_0803_2826_gb300 import inputs
+    from paper_0803_2826_gb300 import lbfluct as L
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    shape, T, K = (64, 64, 64), 500, 50
+    f = torch.as_tensor(inputs.gaussian_field(shape, 3, 1e-5, seed=0).astype(np.float32)).cuda()
+    lat = L.Lattice(shape, force=f, stream=stream)
+    g = torch.empty_like(f)
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        lat.step(20)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    with torch.cuda.stream(stream):
+        a.record(stream)
+        lat.step(T)
+        b.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / T
+    # one untimed call sizes the handle's reverse-mode arena; the timed calls
+    # then allocate nothing (CUDA events on the handle's stream)
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        L.lb_adjoint_kinetic(lat.h, T, K, (24, 24, 24), (40, 40, 40), g, loss)
+    torch.cuda.synchronize()
+    a, b, c = ev(), ev(), ev()
+    with torch.cuda.stream(stream):
+        lat.init_equilibrium()
+        a.record(stream)
+        L.lb_adjoint_forward(lat.h, T, K, (24, 24, 24), (40, 40, 40), loss)
+        b.record(stream)
+        L.lb_adjoint_backward(lat.h, g)
+        c.record(stream)
+    torch.cuda.synchronize()
+    fwd_ck_ms = a.elapsed_time(b) / T
+    adj_ms = a.elapsed_time(c) / T
+    # algorithmic bytes per node and step: forward 152 + 12 (force field);
+    # reverse 264 (lambda in and out, the state, the force gradient) plus the
+    # recompute of the segment states, 152 + 12
+    alg_ratio = (164 + 264 + 164) / 164
+    lat.close()
+    return {"shape": list(shape), "steps": T, "checkpoint_every": K,
+                      "fwd_plus_adj_ms_per_step": adj_ms, "fwd_with_checkpoints_ms_per_step": fwd_ck_ms,
+                      "plain_fp32_ms_per_step": fwd_ms, "ratio": adj_ms / fwd_ms,
+                      "algorithmic_bytes_ratio": alg_ratio, "loss": loss.item(),
+                      "timing": "CUDA events around lb_adjoint_forward + lb_adjoint_backward on the handle's "
+                                "stream; the checkpoint arena was allocated by an earlier call"}
 
 
 def _batched_form(stream, peak, nsteps=2000, max_lag=200, t_begin=1000):
@@ -962,6 +976,12 @@ def main():
         return run_kernel_only(args)
     if args.batch_profile:
         return run_batch_profile(args)
+    if args.adjoint_form:
+        import torch
+        from paper_0803_2826_gb300 import build as B
+        B.build()
+        print(json.dumps(_adjoint_form(torch.cuda.Stream())))
+        return 0
     if args.batched_form:
         import torch
         n = max(args.batched_form, 44)
