@@ -1220,7 +1220,7 @@ __device__ __forceinline__ void flush_impulses(const int cell[3], float acc[8][3
 }
 
 template <int DT>
-__global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
+__device__ __forceinline__ void couple_persistent_run(const PersistArgs &a)
 {
     using T = typename lbd::Store<DT>::T;
     __shared__ unsigned int ticket;  // arrival word of the split barrier
@@ -1441,6 +1441,28 @@ __global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
         if (binned) unbin_particle(p, a.head, a.bucket_of);
     }
 }
+
+// The phi_2 persistent coupling, and the same code capped at 112 registers
+// for large boxes: its blocks then leave room for five instead of four
+// stream-collide blocks on the SMs they share while the two run side by side.
+// The cap spills (the coupling takes ~0.37 instead of ~0.23 ms at 256^3,
+// still shorter than the stream-collide launch beside it, 0.44 ms) and took
+// the 256^3 step from 0.470 to 0.464 ms; in small boxes, where the coupling
+// is the longer of the two, the uncapped kernel is faster.
+template <int DT>
+__global__ void __launch_bounds__(kPThreads) k_couple_persistent(PersistArgs a)
+{
+    couple_persistent_run<DT>(a);
+}
+
+template <int DT>
+__global__ void __maxnreg__(112) k_couple_persistent_lean(PersistArgs a)
+{
+    couple_persistent_run<DT>(a);
+}
+
+// Boxes from this many nodes take k_couple_persistent_lean.
+constexpr size_t kLeanCouplingNodes = (size_t)1 << 24;
 
 // ---------------------------------------------------------------------------
 // Persistent variant for the wide stencils (phi_3, phi_4: 27 / 64 nodes) of
@@ -2209,7 +2231,7 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         }
     }
     if (!(cp->flags & LB_COUPLE_PER_SUBSTEP) && c.kw == 2 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_couple_persistent<DT>, kPThreads, 0) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)(h->n_nodes >= kLeanCouplingNodes ? k_couple_persistent_lean<DT> : k_couple_persistent<DT>), kPThreads, 0) == cudaSuccess &&
         pblocks <= per_sm * device_sm_count()) {
         cudaError_t e = cudaSuccess;
         if (need_nlist && P->nlist_n != n) {
@@ -2273,7 +2295,9 @@ cudaError_t run_substeps(lb_handle *h, const lb_particles *pp, const lb_couple_p
         lc.attrs = attr;
         lc.numAttrs = 1;
         void *args[] = {&a};
-        e = cudaLaunchKernelExC(&lc, (const void *)k_couple_persistent<DT>, args);
+        const void *kfn = h->n_nodes >= kLeanCouplingNodes ? (const void *)k_couple_persistent_lean<DT>
+                                                           : (const void *)k_couple_persistent<DT>;
+        e = cudaLaunchKernelExC(&lc, kfn, args);
         if (e != cudaSuccess) return e;
         h->launches += 1;
         if (fold_clear) {
